@@ -1,0 +1,214 @@
+/*
+ * mw.h -- C ABI of libmw, the GB300 (sm_103a) engine for the mW water model
+ * of Molinero & Moore, "Water modeled as an intermediate element between
+ * carbon and silicon".
+ *
+ * The model (Sec. II.A of the paper) is the Stillinger-Weber form
+ *   E = sum_i sum_{j>i} phi2(r_ij) + sum_i sum_{j!=i} sum_{k>j} phi3(r_ij, r_ik, theta_jik)
+ *   phi2(r)       = A eps [B (sig/r)^p - (sig/r)^q] exp(sig / (r - a sig))
+ *   phi3(r,s,th)  = lam eps [cos th - cos th0]^2 exp(gam sig/(r - a sig)) exp(gam sig/(s - a sig))
+ * with every term zero beyond r = a sig.  This library evaluates energy,
+ * forces and virial over cell-list / Verlet neighbour lists in orthorhombic
+ * periodic boxes and advances velocity-Verlet dynamics (Sec. II.B: 10 fs
+ * step, Nose-Hoover thermostat with a 1 ps relaxation time), for one box or
+ * for a batch of independent boxes, plus the adjoint of the forces for
+ * force-matching fits of (lambda, epsilon, sigma) (the parameters Sec. II.D
+ * tunes).
+ *
+ * Conventions for every call:
+ *   - Units: Angstrom, fs, kcal/mol, g/mol, K; forces kcal/mol/A; velocities
+ *     A/fs; pressure atm.
+ *   - Every call returns an mw_status; nothing is thrown across the ABI.  On
+ *     failure mw_last_error() holds a message for the calling thread.
+ *   - Atoms of all boxes are concatenated box-major: box b owns the global
+ *     atom indices [off_b, off_b + n_b), off_b = n_0 + ... + n_{b-1}.
+ *     Per-atom vectors are AoS, 3 doubles (or floats) per atom.
+ *   - Host pointers are owned by the caller and only read or written during
+ *     the call.  "_dev" calls take device pointers that must stay valid until
+ *     the call returns; they are enqueued on the system's stream and the
+ *     call synchronises that stream before returning.
+ *   - The library owns all its device buffers (allocated at create time and
+ *     when a neighbour list must grow) and frees them in mw_system_destroy.
+ *   - One mw_system must not be used from two threads at once.
+ */
+#ifndef MW_H
+#define MW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Potential parameters (Sec. II.A: A, B, p, q, gamma, a, theta0 of the SW
+ * form; Sec. II.D: lambda = 23.15, epsilon = 6.189 kcal/mol,
+ * sigma = 2.3925 A).  cos_theta0 = -1/3 is the reading of "theta0 = 109.47
+ * deg" as the tetrahedral angle. */
+typedef struct mw_params {
+  double lambda, epsilon, sigma, a, gamma, A, B, cos_theta0;
+  int p, q;
+} mw_params;
+
+typedef enum mw_status {
+  MW_OK = 0,
+  MW_EINVAL = 1,           /* bad argument (null pointer, size, non-finite input) */
+  MW_EBOX = 2,             /* a box edge is shorter than 2 * (a sigma + skin) */
+  MW_ENLIST_OVERFLOW = 3,  /* neighbour list wider than its allocation (recovered internally by mw_step) */
+  MW_ENAN = 4,             /* non-finite force or velocity met during dynamics */
+  MW_ELOST = 5,            /* an atom moved more than half a box edge in one step */
+  MW_ETIMEOUT = 6,         /* a bounded device-side wait ran out (persistent engine) */
+  MW_ECUDA = 7,            /* a CUDA runtime call failed */
+  MW_ENOMEM = 8,           /* device or host allocation failed */
+  MW_ESTATE = 9            /* call out of order (e.g. forces before any state was set) */
+} mw_status;
+
+typedef enum mw_thermostat { MW_NVE = 0, MW_BERENDSEN = 1, MW_NOSE_HOOVER = 2 } mw_thermostat;
+
+/* How mw_step launches work.  GRAPH: one kernel per phase, one step captured
+ * in a CUDA graph and replayed.  PERSISTENT: one cooperative launch runs many
+ * steps with grid-wide barriers between phases.  AUTO: the library picks
+ * (the autotuner's choice when one was made, else PERSISTENT). */
+typedef enum mw_engine { MW_ENGINE_AUTO = 0, MW_ENGINE_GRAPH = 1, MW_ENGINE_PERSISTENT = 2 } mw_engine;
+
+/* Integrator settings for mw_step (Sec. II.B: dt = 10 fs, tau_T = 1 ps). */
+typedef struct mw_integrator {
+  double dt;                /* fs, > 0 */
+  int thermostat;           /* mw_thermostat */
+  double T0;                /* K, target temperature of every box ... */
+  const double* T0_per_box; /* ... unless this host array of nbox targets is non-NULL */
+  double tau;               /* fs, thermostat relaxation time (> 0 unless NVE) */
+} mw_integrator;
+
+/* Per-box thermodynamic snapshot at the end of the last completed step. */
+typedef struct mw_thermo {
+  int64_t step;       /* steps completed since the last mw_set_state */
+  double pe, e2, e3;  /* potential energy and its two- and three-body parts, kcal/mol */
+  double ke;          /* kinetic energy, kcal/mol */
+  double temperature; /* K, 2 ke / (Ndf kB), Ndf = 3 n - 3 */
+  double conserved;   /* ke + pe (+ Q xi^2/2 + Ndf kB T0 eta under Nose-Hoover) */
+  double pressure;    /* atm, (2 ke + tr W) / (3 V) */
+  double virial[6];   /* xx yy zz xy xz yz, kcal/mol: sum over terms and legs of d_a F_b */
+  double xi, eta;     /* Nose-Hoover thermostat velocity (1/fs) and position */
+  int64_t rebuilds;   /* neighbour-list rebuilds of this box since mw_set_state */
+} mw_thermo;
+
+typedef struct mw_info {
+  int nbox;
+  int n_total;
+  int nbr_width;      /* slots per atom in the neighbour list */
+  int max_count;      /* widest neighbour set at the last build */
+  int ncell_total;    /* cells over all boxes */
+  int engine;         /* engine mw_step used last (mw_engine) */
+  int persistent_blocks, persistent_threads;
+  double r_list;      /* a sigma + skin, A */
+  int64_t npairs, ntriplets; /* legs r < a sigma (unordered pairs) and triplets at the last force call */
+} mw_info;
+
+typedef struct mw_system mw_system;
+
+/* Fills *out with the mW parameters of Sec. II.A / II.D. */
+mw_status mw_params_default(mw_params* out);
+
+/* Creates a one-box system of n >= 2 atoms in the orthorhombic box
+ * box[0..2] (A), every edge >= 2 (a sigma + skin).  mass in g/mol
+ * (18.015 for water, Sec. II.C), skin >= 0 in A (Verlet-list skin; the
+ * list is rebuilt once an atom has moved more than skin/2).  stream is a
+ * cudaStream_t (NULL = the legacy default stream) on which all work of this
+ * system is enqueued; it must outlive the system.  Allocates device memory. */
+mw_status mw_system_create(mw_system** out, int n, const double box[3], const mw_params* prm, double mass,
+                           double skin, void* stream);
+
+/* Creates a batch of nbox independent boxes: n[b] atoms (>= 2) in the box
+ * box[3b..3b+2].  Same rules as mw_system_create per box. */
+mw_status mw_batch_create(mw_system** out, int nbox, const int* n, const double* box, const mw_params* prm,
+                          double mass, double skin, void* stream);
+
+/* Frees every device and host resource of s (NULL is a no-op). */
+mw_status mw_system_destroy(mw_system* s);
+
+/* Sets positions x (n_total*3, required, any real values: they are wrapped
+ * into the box) and velocities v (n_total*3, or NULL for zero), host arrays.
+ * Resets the step counter, the thermostat (xi = eta = 0) and marks the
+ * neighbour list stale. */
+mw_status mw_set_state(mw_system* s, const double* x, const double* v);
+/* Same with device arrays. */
+mw_status mw_set_state_dev(mw_system* s, const double* x_dev, const double* v_dev);
+
+/* Copies the current positions (wrapped into [0, L)) and velocities to host
+ * arrays of n_total*3 doubles in the caller's atom order; either may be NULL. */
+mw_status mw_get_state(mw_system* s, double* x, double* v);
+mw_status mw_get_state_dev(mw_system* s, double* x_dev, double* v_dev);
+
+/* Replaces the potential parameters (the neighbour list is marked stale:
+ * its radius a sigma + skin follows sigma). */
+mw_status mw_set_params(mw_system* s, const mw_params* prm);
+
+/* Forces a cell binning + neighbour-list rebuild now; *max_count_out (may be
+ * NULL) receives the widest neighbour set.  Grows the list if needed. */
+mw_status mw_build_neighbors(mw_system* s, int* max_count_out);
+
+/* Copies the neighbour sets of the last build, in the caller's atom order:
+ * counts[n_total] and nbr[n_total*width] (host; entries beyond counts[i] are
+ * left untouched; sets wider than width are truncated, counts stay exact).
+ * Neighbour j of atom i is any atom with |d_ij|^2 < r_list^2 evaluated in
+ * FP32 on the device, at the positions of the last build. */
+mw_status mw_get_neighbors(mw_system* s, int* counts, int* nbr, int width);
+
+/* Energy, forces and virial at the current positions (rebuilding the
+ * neighbour list first if it is stale).  Host outputs, each may be NULL:
+ * f[n_total*3] (kcal/mol/A), energy[nbox*3] = (E, E2, E3) per box,
+ * virial[nbox*6].  Pair and triplet arithmetic is FP32; energy and virial
+ * are reduced in FP64. */
+mw_status mw_energy_forces(mw_system* s, double* f, double* energy, double* virial);
+
+/* Device variant: x_dev (n_total*3 doubles, or NULL to keep the current
+ * positions) replaces the positions first; f_dev receives n_total*3 floats;
+ * energy_dev[nbox*3] and virial_dev[nbox*6] doubles; any output may be NULL. */
+mw_status mw_energy_forces_dev(mw_system* s, const double* x_dev, float* f_dev, double* energy_dev,
+                               double* virial_dev);
+
+/* Advances every box nsteps velocity-Verlet steps.  last (may be NULL)
+ * receives nbox thermo records after the final step.  Recovers internally
+ * from neighbour-list overflow (grows the list and resumes the interrupted
+ * step); returns MW_ENAN / MW_ELOST / MW_ETIMEOUT if dynamics broke down (the
+ * state is then left at the failing step). */
+mw_status mw_step(mw_system* s, const mw_integrator* integ, int nsteps, mw_thermo* last);
+
+/* Thermo records (nbox) of the last completed step, or of the state just set. */
+mw_status mw_get_thermo(mw_system* s, mw_thermo* out);
+
+/* Adjoint of the forces at the current positions (no counterpart in the
+ * paper, whose Sec. II.D tunes lambda, epsilon, sigma by scans).  Given
+ * w = dL/dF (device, n_total*3 floats, caller's order), writes
+ *   dL_dx_dev[n_total*3] (device floats) = sum_i w_i . dF_i/dx
+ *                                         = -(H w), H the Hessian of E;
+ *   dL_dtheta[nbox*3] (host doubles, may be NULL) = sum_i w_i . dF_i/d(lambda, epsilon, sigma)
+ *   per box.
+ * The forward leg and triplet quantities are recomputed, not stored.
+ * The neighbour list must be current (call mw_energy_forces first). */
+mw_status mw_energy_forces_vjp(mw_system* s, const float* dL_dF_dev, float* dL_dx_dev, double* dL_dtheta);
+
+/* Selects the engine mw_step uses (mw_engine). */
+mw_status mw_set_engine(mw_system* s, int engine);
+
+/* Sets the neighbour-list width (slots per atom, >= 1) and marks the list
+ * stale; a width too small is grown again on the next build. */
+mw_status mw_set_nbr_width(mw_system* s, int width);
+
+/* Times both engines on a copy of the current state for `steps` steps each
+ * (the state is restored afterwards) and makes the faster one the AUTO
+ * choice; *best_engine (may be NULL) receives it.  Results are cached per
+ * device name and box-size signature in the file named by the environment
+ * variable MW_AUTOTUNE_CACHE, when set. */
+mw_status mw_autotune(mw_system* s, const mw_integrator* integ, int steps, int* best_engine);
+
+mw_status mw_get_info(mw_system* s, mw_info* out);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* mw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MW_H */

@@ -1,0 +1,178 @@
+"""FP64 CPU oracle for the mW water model (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library
+(``paper_0809_2811_gb300``) neither imports nor links it, and the two share
+no code.  The arithmetic lives in ``mw_oracle.c``; this module only builds
+and loads that file and marshals numpy arrays.
+
+Function map (section of the paper each follows):
+  phi2, dphi2, phi3            Sec. II.A two- and three-body equations
+  energy_forces_brute          Sec. II.A total energy, O(N^2)/O(N^3) loops
+  energy_forces_cell           same, cell-list owner loop
+  neighbors                    neighbour sets {j : |d_ij| < r_list}
+  md                           Sec. II.B velocity-Verlet run (thermostat reading)
+  force_vjp                    force-matching adjoint (no counterpart in the paper)
+  energy_param_grad            dE/d(lambda, epsilon, sigma)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mw_oracle.c")
+_LIB = os.path.join(_HERE, "libmw_oracle.so")
+
+KB = 0.0019872042586408316  # kcal/mol/K
+FCONV = 4.184e-4  # (kcal/mol/A)/(g/mol) -> A/fs^2
+PARAM_NAMES = ("lambda", "epsilon", "sigma", "a", "gamma", "A", "B", "cos_theta0", "p", "q")
+
+
+def build(force: bool = False) -> str:
+    """Compiles mw_oracle.c into libmw_oracle.so next to it (plain gcc, -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        d = ctypes.POINTER(ctypes.c_double)
+        i = ctypes.POINTER(ctypes.c_int)
+        _lib.or_params_default.argtypes = [d]
+        _lib.or_phi2.argtypes = [d, ctypes.c_double]
+        _lib.or_phi2.restype = ctypes.c_double
+        _lib.or_dphi2.argtypes = [d, ctypes.c_double]
+        _lib.or_dphi2.restype = ctypes.c_double
+        _lib.or_phi3.argtypes = [d, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        _lib.or_phi3.restype = ctypes.c_double
+        for name in ("or_energy_forces_brute", "or_energy_forces_cell"):
+            getattr(_lib, name).argtypes = [d, ctypes.c_int, d, d, d, d]
+        _lib.or_neighbors.argtypes = [ctypes.c_int, d, d, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, i, i, ctypes.c_int, i, i]
+        _lib.or_md.argtypes = [d, ctypes.c_int, d, d, d, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, d, d]
+        _lib.or_force_vjp.argtypes = [d, ctypes.c_int, d, d, d, d, d]
+        _lib.or_energy_param_grad.argtypes = [d, ctypes.c_int, d, d, d]
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def default_params() -> np.ndarray:
+    p = np.zeros(10)
+    lib().or_params_default(_dp(p))
+    return p
+
+
+def params(**kw) -> np.ndarray:
+    p = default_params()
+    for k, v in kw.items():
+        p[PARAM_NAMES.index(k)] = v
+    return p
+
+
+def phi2(r, prm=None):
+    prm = default_params() if prm is None else np.ascontiguousarray(prm, np.float64)
+    return np.array([lib().or_phi2(_dp(prm), float(x)) for x in np.atleast_1d(r)])
+
+
+def dphi2(r, prm=None):
+    prm = default_params() if prm is None else np.ascontiguousarray(prm, np.float64)
+    return np.array([lib().or_dphi2(_dp(prm), float(x)) for x in np.atleast_1d(r)])
+
+
+def phi3(r, s, cos_t, prm=None):
+    prm = default_params() if prm is None else np.ascontiguousarray(prm, np.float64)
+    return lib().or_phi3(_dp(prm), float(r), float(s), float(cos_t))
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def energy_forces(x, box, prm=None, method="cell"):
+    """Returns dict(e2, e3, energy, forces (n,3), virial[6], npairs, ntriplets)."""
+    prm = default_params() if prm is None else np.ascontiguousarray(prm, np.float64)
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    box = np.ascontiguousarray(box, np.float64)
+    n = x.shape[0]
+    f = np.zeros((n, 3))
+    out = np.zeros(10)
+    fn = lib().or_energy_forces_cell if method == "cell" else lib().or_energy_forces_brute
+    _check(fn(_dp(prm), n, _dp(x), _dp(box), _dp(f), _dp(out)), "energy_forces")
+    return dict(e2=out[0], e3=out[1], energy=out[0] + out[1], forces=f, virial=out[2:8].copy(),
+                npairs=int(out[8]), ntriplets=int(out[9]))
+
+
+def neighbors(x, box, rlist, band_rel=1e-5, width=256, band_cap=100000):
+    """Returns (sets, band) with sets[i] a sorted int array and band a set of (i, j)."""
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    box = np.ascontiguousarray(box, np.float64)
+    n = x.shape[0]
+    counts = np.zeros(n, np.int32)
+    nbr = np.zeros((n, width), np.int32)
+    band = np.zeros((band_cap, 2), np.int32)
+    nband = np.zeros(1, np.int32)
+    rc = lib().or_neighbors(n, _dp(x), _dp(box), float(rlist), float(band_rel), width, _ip(counts),
+                            _ip(nbr), band_cap, _ip(band), _ip(nband))
+    _check(rc, "neighbors")
+    sets = [nbr[i, :counts[i]].copy() for i in range(n)]
+    nb = min(int(nband[0]), band_cap)
+    return sets, {(int(a), int(b)) for a, b in band[:nb]}
+
+
+def md(x, v, box, nsteps, dt=10.0, kind=0, T0=300.0, tau=1000.0, mass=18.015, prm=None, state=(0.0, 0.0)):
+    """Runs the oracle's velocity-Verlet; returns (x, v, state, thermo[nsteps+1, 8]).
+
+    thermo columns: pe, e2, e3, ke, T, conserved, xi, eta.  kind: 0 NVE,
+    1 Berendsen, 2 Nose-Hoover."""
+    prm = default_params() if prm is None else np.ascontiguousarray(prm, np.float64)
+    x = np.array(x, np.float64).reshape(-1, 3)
+    v = np.array(v, np.float64).reshape(-1, 3)
+    box = np.ascontiguousarray(box, np.float64)
+    st = np.array(state, np.float64)
+    th = np.zeros((nsteps + 1, 8))
+    _check(lib().or_md(_dp(prm), x.shape[0], _dp(x), _dp(v), _dp(box), mass, dt, kind, T0, tau, nsteps,
+                       _dp(st), _dp(th)), "md")
+    return x, v, (float(st[0]), float(st[1])), th
+
+
+def force_vjp(x, box, w, prm=None):
+    """Returns (dL/dx (n,3), dL/d(lambda, epsilon, sigma)) for dL/dF = w."""
+    prm = default_params() if prm is None else np.ascontiguousarray(prm, np.float64)
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    w = np.ascontiguousarray(w, np.float64).reshape(-1, 3)
+    box = np.ascontiguousarray(box, np.float64)
+    gx = np.zeros_like(x)
+    gt = np.zeros(3)
+    _check(lib().or_force_vjp(_dp(prm), x.shape[0], _dp(x), _dp(box), _dp(w), _dp(gx), _dp(gt)), "force_vjp")
+    return gx, gt
+
+
+def energy_param_grad(x, box, prm=None):
+    prm = default_params() if prm is None else np.ascontiguousarray(prm, np.float64)
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    box = np.ascontiguousarray(box, np.float64)
+    g = np.zeros(3)
+    _check(lib().or_energy_param_grad(_dp(prm), x.shape[0], _dp(x), _dp(box), _dp(g)), "energy_param_grad")
+    return g

@@ -1,0 +1,723 @@
+/*
+ * mw_oracle.c -- plain, slow, FP64 CPU oracle for the mW water model
+ * (Molinero & Moore, "Water modeled as an intermediate element between carbon
+ * and silicon").
+ *
+ * TEST INFRASTRUCTURE ONLY.  The test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark are the only code that loads this library.
+ * It shares no source, header, table or helper with the CUDA library; the
+ * product path never calls it.
+ *
+ * What it computes, with the passage each part follows:
+ *   - Sec. II.A, total energy: E = sum_i sum_{j>i} phi2(r_ij)
+ *         + sum_i sum_{j!=i} sum_{k>j} phi3(r_ij, r_ik, theta_jik)
+ *     (reading: the angle sits at the centre atom i, both legs start at i,
+ *      and every unordered leg pair {j,k} of a centre is counted once).
+ *   - Sec. II.A, two-body term:
+ *         phi2(r) = A eps [B (sig/r)^p - (sig/r)^q] exp(sig / (r - a sig)),
+ *     zero for r >= a sig (reading: the cutoff is a*sig exactly).
+ *   - Sec. II.A, three-body term:
+ *         phi3 = lam eps [cos th - cos th0]^2 exp(gam sig/(r - a sig))
+ *                                          exp(gam sig/(s - a sig)).
+ *   - Forces F_i = -dE/dx_i from the analytic derivatives of those terms;
+ *     virial W_ab = sum over terms, over the term's legs, of d_a * F_b with
+ *     d the leg vector (centre -> partner) and F the force on the partner.
+ *   - Sec. II.B: velocity-Verlet dynamics (the paper names LAMMPS, the 10 fs
+ *     step and a 1 ps Nose-Hoover relaxation time; the integrator itself and
+ *     the single-thermostat Trotter split are this oracle's reading).
+ *   - Force-matching adjoint (no counterpart in the paper, whose Sec. II.D
+ *     tunes lam, eps, sig by scans): the derivative of the forces along a
+ *     direction, taken by the complex-step method (Squire & Trapp, SIAM Rev.
+ *     40, 1998), exact to rounding.
+ *
+ * Two independent force routines are provided: a brute-force O(N^2) pair /
+ * O(N^3) triplet enumeration and a cell-list owner loop.  Units are kcal/mol,
+ * Angstrom, fs, g/mol, K.
+ *
+ * Parameter vector layout (double[10]):
+ *   0 lambda, 1 epsilon, 2 sigma, 3 a, 4 gamma, 5 A, 6 B, 7 cos_theta0,
+ *   8 p, 9 q   (p and q are small non-negative integers stored as doubles).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_KB 0.0019872042586408316 /* kcal/mol/K (R = 8.31446261815324 J/mol/K over 4184 J/kcal) */
+#define OR_FCONV 4.184e-4           /* (kcal/mol/A)/(g/mol) expressed in A/fs^2 */
+
+enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2, OR_EOVERFLOW = 3 };
+
+/* ------------------------------------------------------------------ */
+/* Parameters (Sec. II.A and Sec. II.D of the paper).                  */
+/* ------------------------------------------------------------------ */
+
+void or_params_default(double* prm) {
+  prm[0] = 23.15;        /* lambda, Sec. II.D */
+  prm[1] = 6.189;        /* epsilon kcal/mol, Sec. II.D */
+  prm[2] = 2.3925;       /* sigma Angstrom, Sec. II.D */
+  prm[3] = 1.8;          /* a, Sec. II.A */
+  prm[4] = 1.2;          /* gamma, Sec. II.A */
+  prm[5] = 7.049556277;  /* A, Sec. II.A */
+  prm[6] = 0.6022245584; /* B, Sec. II.A */
+  prm[7] = -1.0 / 3.0;   /* cos(theta0): tetrahedral angle (reading of 109.47 deg) */
+  prm[8] = 4.0;          /* p */
+  prm[9] = 0.0;          /* q */
+}
+
+static double ipow(double x, int n) {
+  double r = 1.0;
+  for (int i = 0; i < n; ++i) r *= x;
+  return r;
+}
+
+/* phi2(r), Sec. II.A two-body equation. */
+double or_phi2(const double* prm, double r) {
+  const double eps = prm[1], sig = prm[2], a = prm[3], A = prm[5], B = prm[6];
+  const int p = (int)prm[8], q = (int)prm[9];
+  if (!(r < a * sig)) return 0.0;
+  const double sr = sig / r;
+  return A * eps * (B * ipow(sr, p) - ipow(sr, q)) * exp(sig / (r - a * sig));
+}
+
+/* d phi2 / dr. */
+double or_dphi2(const double* prm, double r) {
+  const double eps = prm[1], sig = prm[2], a = prm[3], A = prm[5], B = prm[6];
+  const int p = (int)prm[8], q = (int)prm[9];
+  if (!(r < a * sig)) return 0.0;
+  const double sr = sig / r;
+  const double brk = B * ipow(sr, p) - ipow(sr, q);
+  const double dbrk = (-p * B * ipow(sr, p) + q * ipow(sr, q)) / r;
+  const double x = r - a * sig;
+  const double e = exp(sig / x);
+  return A * eps * (dbrk * e + brk * e * (-sig / (x * x)));
+}
+
+/* phi3(r, s, cos theta), Sec. II.A three-body equation. */
+double or_phi3(const double* prm, double r, double s, double cos_t) {
+  const double lam = prm[0], eps = prm[1], sig = prm[2], a = prm[3], gam = prm[4], c0 = prm[7];
+  if (!(r < a * sig) || !(s < a * sig)) return 0.0;
+  const double dc = cos_t - c0;
+  return lam * eps * dc * dc * exp(gam * sig / (r - a * sig)) * exp(gam * sig / (s - a * sig));
+}
+
+/* phi3 of a centre with leg vectors dj, dk, and its gradient with respect to
+ * the two leg vectors (gj = d phi3 / d dj, gk = d phi3 / d dk). */
+static double tri_grad(const double* prm, const double* dj, double rj, const double* dk, double rk,
+                       double* gj, double* gk) {
+  const double lam = prm[0], eps = prm[1], sig = prm[2], a = prm[3], gam = prm[4], c0 = prm[7];
+  double uj[3], uk[3];
+  for (int d = 0; d < 3; ++d) {
+    uj[d] = dj[d] / rj;
+    uk[d] = dk[d] / rk;
+  }
+  const double c = uj[0] * uk[0] + uj[1] * uk[1] + uj[2] * uk[2];
+  const double D = c - c0;
+  const double xj = rj - a * sig, xk = rk - a * sig;
+  const double ej = exp(gam * sig / xj), ek = exp(gam * sig / xk);
+  const double pre = lam * eps * ej * ek;
+  const double h = pre * D * D;
+  const double dlj = -gam * sig / (xj * xj); /* d ln ej / d rj */
+  const double dlk = -gam * sig / (xk * xk);
+  for (int d = 0; d < 3; ++d) {
+    const double dcj = (uk[d] - c * uj[d]) / rj; /* d cos / d dj */
+    const double dck = (uj[d] - c * uk[d]) / rk;
+    gj[d] = pre * (2.0 * D * dcj + D * D * dlj * uj[d]);
+    gk[d] = pre * (2.0 * D * dck + D * D * dlk * uk[d]);
+  }
+  return h;
+}
+
+static void min_image(const double* box, double* d) {
+  for (int k = 0; k < 3; ++k) d[k] -= box[k] * nearbyint(d[k] / box[k]);
+}
+
+/* virial accumulation: W[xx,yy,zz,xy,xz,yz] += d (x) F */
+static void add_virial(double* W, const double* d, const double* F) {
+  W[0] += d[0] * F[0];
+  W[1] += d[1] * F[1];
+  W[2] += d[2] * F[2];
+  W[3] += d[0] * F[1];
+  W[4] += d[0] * F[2];
+  W[5] += d[1] * F[2];
+}
+
+/*
+ * Brute force.  out[0]=E2, out[1]=E3, out[2..7]=W, out[8]=#pairs (r<a sig),
+ * out[9]=#triplets (centre, unordered leg pair, both legs < a sig).
+ * f may be NULL.  Requires every box edge >= 2 a sig.
+ */
+int or_energy_forces_brute(const double* prm, int n, const double* x, const double* box, double* f,
+                           double* out) {
+  const double rc = prm[3] * prm[2];
+  if (n < 0 || box[0] < 2 * rc || box[1] < 2 * rc || box[2] < 2 * rc) return OR_EINVAL;
+  double E2 = 0, E3 = 0, W[6] = {0, 0, 0, 0, 0, 0};
+  double npair = 0, ntrip = 0;
+  if (f) memset(f, 0, sizeof(double) * 3 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    for (int j = i + 1; j < n; ++j) {
+      double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+      min_image(box, d);
+      const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      if (!(r < rc)) continue;
+      E2 += or_phi2(prm, r);
+      const double dp = or_dphi2(prm, r);
+      double Fj[3];
+      for (int k = 0; k < 3; ++k) Fj[k] = -dp * d[k] / r; /* force on j */
+      if (f)
+        for (int k = 0; k < 3; ++k) {
+          f[3 * j + k] += Fj[k];
+          f[3 * i + k] -= Fj[k];
+        }
+      add_virial(W, d, Fj);
+      npair += 1;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double dj[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+      min_image(box, dj);
+      const double rj = sqrt(dj[0] * dj[0] + dj[1] * dj[1] + dj[2] * dj[2]);
+      if (!(rj < rc)) continue;
+      for (int k = j + 1; k < n; ++k) {
+        if (k == i) continue;
+        double dk[3] = {x[3 * k] - x[3 * i], x[3 * k + 1] - x[3 * i + 1], x[3 * k + 2] - x[3 * i + 2]};
+        min_image(box, dk);
+        const double rk = sqrt(dk[0] * dk[0] + dk[1] * dk[1] + dk[2] * dk[2]);
+        if (!(rk < rc)) continue;
+        double gj[3], gk[3];
+        E3 += tri_grad(prm, dj, rj, dk, rk, gj, gk);
+        double Fj[3] = {-gj[0], -gj[1], -gj[2]}, Fk[3] = {-gk[0], -gk[1], -gk[2]};
+        if (f)
+          for (int d = 0; d < 3; ++d) {
+            f[3 * j + d] += Fj[d];
+            f[3 * k + d] += Fk[d];
+            f[3 * i + d] -= Fj[d] + Fk[d];
+          }
+        add_virial(W, dj, Fj);
+        add_virial(W, dk, Fk);
+        ntrip += 1;
+      }
+    }
+  }
+  out[0] = E2;
+  out[1] = E3;
+  for (int k = 0; k < 6; ++k) out[2 + k] = W[k];
+  out[8] = npair;
+  out[9] = ntrip;
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Cell list (plain linked cells).                                      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int nc[3];
+  int* head;
+  int* next;
+  int* cell_of;
+} or_cells;
+
+static double wrap1(double v, double L) {
+  double w = v - L * floor(v / L);
+  if (w >= L) w -= L;
+  if (w < 0) w = 0;
+  return w;
+}
+
+static int cells_build(or_cells* c, int n, const double* x, const double* box, double rcut) {
+  for (int k = 0; k < 3; ++k) {
+    c->nc[k] = (int)floor(box[k] / rcut);
+    if (c->nc[k] < 1) c->nc[k] = 1;
+  }
+  const size_t ncell = (size_t)c->nc[0] * c->nc[1] * c->nc[2];
+  c->head = (int*)malloc(sizeof(int) * ncell);
+  c->next = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  c->cell_of = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  if (!c->head || !c->next || !c->cell_of) return OR_ENOMEM;
+  for (size_t i = 0; i < ncell; ++i) c->head[i] = -1;
+  /* insert in reverse so each cell lists atoms in ascending index order */
+  for (int i = n - 1; i >= 0; --i) {
+    int ci[3];
+    for (int k = 0; k < 3; ++k) {
+      const double w = wrap1(x[3 * i + k], box[k]);
+      ci[k] = (int)floor(w / box[k] * c->nc[k]);
+      if (ci[k] >= c->nc[k]) ci[k] = c->nc[k] - 1;
+      if (ci[k] < 0) ci[k] = 0;
+    }
+    const int id = (ci[2] * c->nc[1] + ci[1]) * c->nc[0] + ci[0];
+    c->cell_of[i] = id;
+    c->next[i] = c->head[id];
+    c->head[id] = i;
+  }
+  return OR_OK;
+}
+
+static void cells_free(or_cells* c) {
+  free(c->head);
+  free(c->next);
+  free(c->cell_of);
+}
+
+/* Distinct cell offsets along one dimension: {-1,0,1} when there are at least
+ * three cells, {0,1} for two, {0} for one (so no cell is visited twice). */
+static int stencil_offsets(int nc, int* off) {
+  if (nc >= 3) {
+    off[0] = -1;
+    off[1] = 0;
+    off[2] = 1;
+    return 3;
+  }
+  if (nc == 2) {
+    off[0] = 0;
+    off[1] = 1;
+    return 2;
+  }
+  off[0] = 0;
+  return 1;
+}
+
+/* Gathers the stencil cells around the cell of atom i; returns how many. */
+static int stencil_cells(const or_cells* c, int i, int* cells) {
+  const int id = c->cell_of[i];
+  const int cx = id % c->nc[0], cy = (id / c->nc[0]) % c->nc[1], cz = id / (c->nc[0] * c->nc[1]);
+  int ox[3], oy[3], oz[3];
+  const int nx = stencil_offsets(c->nc[0], ox), ny = stencil_offsets(c->nc[1], oy),
+            nz = stencil_offsets(c->nc[2], oz);
+  int m = 0;
+  for (int a = 0; a < nz; ++a)
+    for (int b = 0; b < ny; ++b)
+      for (int g = 0; g < nx; ++g) {
+        const int X = (cx + ox[g] + c->nc[0]) % c->nc[0];
+        const int Y = (cy + oy[b] + c->nc[1]) % c->nc[1];
+        const int Z = (cz + oz[a] + c->nc[2]) % c->nc[2];
+        cells[m++] = (Z * c->nc[1] + Y) * c->nc[0] + X;
+      }
+  return m;
+}
+
+typedef struct {
+  int j;
+  double d[3];
+  double r;
+} or_leg;
+
+/*
+ * Cell-list owner loop.  Same outputs as or_energy_forces_brute.
+ * Each atom i gathers its legs (r < a sig); the pair term is taken once per
+ * unordered pair (from the lower index), the three-body term once per centre
+ * and unordered leg pair.
+ */
+int or_energy_forces_cell(const double* prm, int n, const double* x, const double* box, double* f,
+                          double* out) {
+  const double rc = prm[3] * prm[2];
+  if (n < 0 || box[0] < 2 * rc || box[1] < 2 * rc || box[2] < 2 * rc) return OR_EINVAL;
+  or_cells c;
+  if (cells_build(&c, n, x, box, rc) != OR_OK) {
+    cells_free(&c);
+    return OR_ENOMEM;
+  }
+  int cap = 64;
+  or_leg* legs = (or_leg*)malloc(sizeof(or_leg) * (size_t)cap);
+  double E2 = 0, E3 = 0, W[6] = {0, 0, 0, 0, 0, 0};
+  double npair = 0, ntrip = 0;
+  if (f) memset(f, 0, sizeof(double) * 3 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    int cells[27];
+    const int ncells = stencil_cells(&c, i, cells);
+    int nl = 0;
+    for (int s = 0; s < ncells; ++s) {
+      for (int j = c.head[cells[s]]; j >= 0; j = c.next[j]) {
+        if (j == i) continue;
+        double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+        min_image(box, d);
+        const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (!(r < rc)) continue;
+        if (nl == cap) {
+          cap *= 2;
+          legs = (or_leg*)realloc(legs, sizeof(or_leg) * (size_t)cap);
+        }
+        legs[nl].j = j;
+        legs[nl].r = r;
+        for (int k = 0; k < 3; ++k) legs[nl].d[k] = d[k];
+        ++nl;
+      }
+    }
+    for (int l = 0; l < nl; ++l) {
+      if (legs[l].j < i) continue;
+      const double r = legs[l].r;
+      E2 += or_phi2(prm, r);
+      const double dp = or_dphi2(prm, r);
+      double Fj[3];
+      for (int k = 0; k < 3; ++k) Fj[k] = -dp * legs[l].d[k] / r;
+      if (f)
+        for (int k = 0; k < 3; ++k) {
+          f[3 * legs[l].j + k] += Fj[k];
+          f[3 * i + k] -= Fj[k];
+        }
+      add_virial(W, legs[l].d, Fj);
+      npair += 1;
+    }
+    for (int a = 0; a < nl; ++a)
+      for (int b = a + 1; b < nl; ++b) {
+        double gj[3], gk[3];
+        E3 += tri_grad(prm, legs[a].d, legs[a].r, legs[b].d, legs[b].r, gj, gk);
+        double Fj[3] = {-gj[0], -gj[1], -gj[2]}, Fk[3] = {-gk[0], -gk[1], -gk[2]};
+        if (f)
+          for (int d = 0; d < 3; ++d) {
+            f[3 * legs[a].j + d] += Fj[d];
+            f[3 * legs[b].j + d] += Fk[d];
+            f[3 * i + d] -= Fj[d] + Fk[d];
+          }
+        add_virial(W, legs[a].d, Fj);
+        add_virial(W, legs[b].d, Fk);
+        ntrip += 1;
+      }
+  }
+  free(legs);
+  cells_free(&c);
+  out[0] = E2;
+  out[1] = E3;
+  for (int k = 0; k < 6; ++k) out[2 + k] = W[k];
+  out[8] = npair;
+  out[9] = ntrip;
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Neighbour sets                                                       */
+/* ------------------------------------------------------------------ */
+
+static int cmp_int(const void* a, const void* b) {
+  const int x = *(const int*)a, y = *(const int*)b;
+  return (x > y) - (x < y);
+}
+
+/*
+ * For every atom i, the ascending set {j != i : |d_ij|^2 < rlist^2} with d the
+ * minimum-image vector.  counts[i] receives the true set size; at most width
+ * entries are written to nbr[i*width ...].  Pairs with
+ * | |d|^2 - rlist^2 | <= band_rel * rlist^2 are also written (as ordered pairs
+ * i, j) to band[] up to band_cap pairs; *nband receives their total number.
+ * Returns OR_EOVERFLOW if some set is wider than width (counts stay exact).
+ */
+int or_neighbors(int n, const double* x, const double* box, double rlist, double band_rel, int width,
+                 int* counts, int* nbr, int band_cap, int* band, int* nband) {
+  if (n < 0 || box[0] < 2 * rlist || box[1] < 2 * rlist || box[2] < 2 * rlist) return OR_EINVAL;
+  or_cells c;
+  if (cells_build(&c, n, x, box, rlist) != OR_OK) {
+    cells_free(&c);
+    return OR_ENOMEM;
+  }
+  const double rl2 = rlist * rlist;
+  int nb = 0, overflow = 0;
+  for (int i = 0; i < n; ++i) {
+    int cells[27];
+    const int ncells = stencil_cells(&c, i, cells);
+    int m = 0;
+    for (int s = 0; s < ncells; ++s)
+      for (int j = c.head[cells[s]]; j >= 0; j = c.next[j]) {
+        if (j == i) continue;
+        double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+        min_image(box, d);
+        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (fabs(r2 - rl2) <= band_rel * rl2) {
+          if (nb < band_cap) {
+            band[2 * nb] = i;
+            band[2 * nb + 1] = j;
+          }
+          ++nb;
+        }
+        if (r2 < rl2) {
+          if (m < width) nbr[(size_t)i * width + m] = j;
+          ++m;
+        }
+      }
+    counts[i] = m;
+    if (m > width) overflow = 1;
+    qsort(nbr + (size_t)i * width, (size_t)(m < width ? m : width), sizeof(int), cmp_int);
+  }
+  *nband = nb;
+  cells_free(&c);
+  return overflow ? OR_EOVERFLOW : OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Dynamics: velocity Verlet with an optional thermostat (Sec. II.B).   */
+/* ------------------------------------------------------------------ */
+
+static double kinetic(int n, const double* v, double mass) {
+  double s = 0;
+  for (int i = 0; i < 3 * n; ++i) s += v[i] * v[i];
+  return 0.5 * mass * s / OR_FCONV; /* kcal/mol */
+}
+
+/* One Nose-Hoover half step (length dt/2) of a single thermostat, split as
+ * quarter step on xi, velocity scaling, half step on eta, quarter step on xi.
+ * Q = Ndf kB T0 tau^2. */
+static void nh_half(int n, double* v, double* ke, double* xi, double* eta, double dt, double Ndf, double T0,
+                    double Q) {
+  double G = (2.0 * (*ke) - Ndf * OR_KB * T0) / Q;
+  *xi += 0.25 * dt * G;
+  const double s = exp(-(*xi) * 0.5 * dt);
+  for (int i = 0; i < 3 * n; ++i) v[i] *= s;
+  *ke *= s * s;
+  *eta += (*xi) * 0.5 * dt;
+  G = (2.0 * (*ke) - Ndf * OR_KB * T0) / Q;
+  *xi += 0.25 * dt * G;
+}
+
+/*
+ * Runs nsteps velocity-Verlet steps in place on x, v (n*3, A and A/fs).
+ * kind: 0 NVE, 1 Berendsen (v scaled by sqrt(1 + dt/tau (T0/T - 1)) after
+ * each step), 2 Nose-Hoover (symmetric Trotter split around the Verlet step).
+ * state[0] = xi (1/fs), state[1] = eta (dimensionless), updated in place.
+ * thermo (nsteps+1)*8 doubles, may be NULL: per step (index 0 = initial)
+ *   pe, e2, e3, ke, T, conserved, xi, eta
+ * conserved = ke + pe (+ Q xi^2 / 2 + Ndf kB T0 eta under Nose-Hoover).
+ * Positions are wrapped into [0, L).  Ndf = 3n - 3.
+ */
+int or_md(const double* prm, int n, double* x, double* v, const double* box, double mass, double dt,
+          int kind, double T0, double tau, int nsteps, double* state, double* thermo) {
+  if (n < 2 || kind < 0 || kind > 2) return OR_EINVAL;
+  double* f = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+  if (!f) return OR_ENOMEM;
+  double out[10];
+  for (int i = 0; i < 3 * n; ++i) x[i] = wrap1(x[i], box[i % 3]);
+  int rc = or_energy_forces_cell(prm, n, x, box, f, out);
+  if (rc != OR_OK) {
+    free(f);
+    return rc;
+  }
+  const double Ndf = 3.0 * n - 3.0;
+  const double Q = Ndf * OR_KB * T0 * tau * tau;
+  double xi = state[0], eta = state[1];
+  const double cf = 0.5 * dt * OR_FCONV / mass;
+  for (int s = 0; s <= nsteps; ++s) {
+    if (s > 0) {
+      double ke = kinetic(n, v, mass);
+      if (kind == 2) nh_half(n, v, &ke, &xi, &eta, dt, Ndf, T0, Q);
+      for (int i = 0; i < 3 * n; ++i) v[i] += cf * f[i];
+      for (int i = 0; i < 3 * n; ++i) x[i] = wrap1(x[i] + dt * v[i], box[i % 3]);
+      rc = or_energy_forces_cell(prm, n, x, box, f, out);
+      if (rc != OR_OK) break;
+      for (int i = 0; i < 3 * n; ++i) v[i] += cf * f[i];
+      ke = kinetic(n, v, mass);
+      if (kind == 2) nh_half(n, v, &ke, &xi, &eta, dt, Ndf, T0, Q);
+      if (kind == 1) {
+        const double T = 2.0 * ke / (Ndf * OR_KB);
+        const double lam = sqrt(1.0 + dt / tau * (T0 / T - 1.0));
+        for (int i = 0; i < 3 * n; ++i) v[i] *= lam;
+      }
+    }
+    if (thermo) {
+      const double ke = kinetic(n, v, mass);
+      const double pe = out[0] + out[1];
+      double cons = ke + pe;
+      if (kind == 2) cons += 0.5 * Q * xi * xi + Ndf * OR_KB * T0 * eta;
+      double* t = thermo + 8 * (size_t)s;
+      t[0] = pe;
+      t[1] = out[0];
+      t[2] = out[1];
+      t[3] = ke;
+      t[4] = 2.0 * ke / (Ndf * OR_KB);
+      t[5] = cons;
+      t[6] = xi;
+      t[7] = eta;
+    }
+  }
+  state[0] = xi;
+  state[1] = eta;
+  free(f);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Complex-step derivatives for the force-matching adjoint.             */
+/* ------------------------------------------------------------------ */
+
+typedef double complex cplx;
+
+static cplx cipow(cplx x, int n) {
+  cplx r = 1.0;
+  for (int i = 0; i < n; ++i) r *= x;
+  return r;
+}
+
+/*
+ * The same cell-list energy and forces as or_energy_forces_cell, evaluated in
+ * complex arithmetic with complex parameters pc[0..7] and complex positions
+ * xc.  Branches (cutoff, minimum image, cell membership) use real parts.
+ * energy_out may be NULL.
+ */
+static int cs_energy_forces(const cplx* pc, const double* prm_real, int n, const cplx* xc, const double* box,
+                            cplx* f, cplx* energy_out) {
+  const cplx lam = pc[0], eps = pc[1], sig = pc[2], a = pc[3], gam = pc[4], A = pc[5], B = pc[6], c0 = pc[7];
+  const int p = (int)prm_real[8], q = (int)prm_real[9];
+  const double rc_real = creal(a * sig);
+  double* xr = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+  if (!xr) return OR_ENOMEM;
+  for (int i = 0; i < 3 * n; ++i) xr[i] = creal(xc[i]);
+  or_cells c;
+  if (cells_build(&c, n, xr, box, rc_real) != OR_OK) {
+    cells_free(&c);
+    free(xr);
+    return OR_ENOMEM;
+  }
+  int cap = 64;
+  int* lj = (int*)malloc(sizeof(int) * (size_t)cap);
+  cplx* ld = (cplx*)malloc(sizeof(cplx) * 3 * (size_t)cap);
+  cplx* lr = (cplx*)malloc(sizeof(cplx) * (size_t)cap);
+  for (int i = 0; i < 3 * n; ++i) f[i] = 0;
+  cplx E = 0;
+  for (int i = 0; i < n; ++i) {
+    int cells[27];
+    const int ncells = stencil_cells(&c, i, cells);
+    int nl = 0;
+    for (int s = 0; s < ncells; ++s)
+      for (int j = c.head[cells[s]]; j >= 0; j = c.next[j]) {
+        if (j == i) continue;
+        cplx d[3];
+        for (int k = 0; k < 3; ++k) {
+          d[k] = xc[3 * j + k] - xc[3 * i + k];
+          d[k] -= box[k] * nearbyint(creal(d[k]) / box[k]);
+        }
+        const cplx r = csqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (!(creal(r) < rc_real)) continue;
+        if (nl == cap) {
+          cap *= 2;
+          lj = (int*)realloc(lj, sizeof(int) * (size_t)cap);
+          ld = (cplx*)realloc(ld, sizeof(cplx) * 3 * (size_t)cap);
+          lr = (cplx*)realloc(lr, sizeof(cplx) * (size_t)cap);
+        }
+        lj[nl] = j;
+        lr[nl] = r;
+        for (int k = 0; k < 3; ++k) ld[3 * nl + k] = d[k];
+        ++nl;
+      }
+    /* pair terms, once per unordered pair */
+    for (int l = 0; l < nl; ++l) {
+      if (lj[l] < i) continue;
+      const cplx r = lr[l];
+      const cplx sr = sig / r;
+      const cplx brk = B * cipow(sr, p) - cipow(sr, q);
+      const cplx dbrk = (-(double)p * B * cipow(sr, p) + (double)q * cipow(sr, q)) / r;
+      const cplx xx = r - a * sig;
+      const cplx e = cexp(sig / xx);
+      E += A * eps * brk * e;
+      const cplx dp = A * eps * (dbrk * e + brk * e * (-sig / (xx * xx)));
+      for (int k = 0; k < 3; ++k) {
+        const cplx Fj = -dp * ld[3 * l + k] / r;
+        f[3 * lj[l] + k] += Fj;
+        f[3 * i + k] -= Fj;
+      }
+    }
+    /* three-body terms, once per centre and unordered leg pair */
+    for (int u = 0; u < nl; ++u)
+      for (int w = u + 1; w < nl; ++w) {
+        const cplx rj = lr[u], rk = lr[w];
+        cplx uj[3], uk[3];
+        for (int k = 0; k < 3; ++k) {
+          uj[k] = ld[3 * u + k] / rj;
+          uk[k] = ld[3 * w + k] / rk;
+        }
+        const cplx cth = uj[0] * uk[0] + uj[1] * uk[1] + uj[2] * uk[2];
+        const cplx D = cth - c0;
+        const cplx xj = rj - a * sig, xk = rk - a * sig;
+        const cplx ej = cexp(gam * sig / xj), ek = cexp(gam * sig / xk);
+        const cplx pre = lam * eps * ej * ek;
+        E += pre * D * D;
+        const cplx dlj = -gam * sig / (xj * xj), dlk = -gam * sig / (xk * xk);
+        for (int k = 0; k < 3; ++k) {
+          const cplx gj = pre * (2.0 * D * (uk[k] - cth * uj[k]) / rj + D * D * dlj * uj[k]);
+          const cplx gk = pre * (2.0 * D * (uj[k] - cth * uk[k]) / rk + D * D * dlk * uk[k]);
+          f[3 * lj[u] + k] -= gj;
+          f[3 * lj[w] + k] -= gk;
+          f[3 * i + k] += gj + gk;
+        }
+      }
+  }
+  free(lj);
+  free(ld);
+  free(lr);
+  cells_free(&c);
+  free(xr);
+  if (energy_out) *energy_out = E;
+  return OR_OK;
+}
+
+/*
+ * Adjoint of the forces.  Given w = dL/dF (n*3), returns
+ *   dLdx[m]      = sum_i w_i . dF_i/dx_m        (n*3)
+ *   dLdtheta[0..2] = sum_i w_i . dF_i/d(lambda, epsilon, sigma)
+ * Each is one complex-step directional derivative: F(x + i h w) gives
+ * (dF/dx) w, which equals the row contraction w^T (dF/dx) because dF/dx is
+ * minus the (symmetric) Hessian of E; F(theta_p + i h) gives dF/dtheta_p.
+ */
+int or_force_vjp(const double* prm, int n, const double* x, const double* box, const double* w, double* dLdx,
+                 double* dLdtheta) {
+  if (n < 1) return OR_EINVAL;
+  const double h = 1e-30;
+  double wmax = 0;
+  for (int i = 0; i < 3 * n; ++i) wmax = fmax(wmax, fabs(w[i]));
+  cplx pc[8];
+  cplx* xc = (cplx*)malloc(sizeof(cplx) * 3 * (size_t)n);
+  cplx* fc = (cplx*)malloc(sizeof(cplx) * 3 * (size_t)n);
+  if (!xc || !fc) {
+    free(xc);
+    free(fc);
+    return OR_ENOMEM;
+  }
+  int rc = OR_OK;
+  for (int k = 0; k < 8; ++k) pc[k] = prm[k];
+  if (dLdx) {
+    if (wmax == 0) {
+      memset(dLdx, 0, sizeof(double) * 3 * (size_t)n);
+    } else {
+      for (int i = 0; i < 3 * n; ++i) xc[i] = x[i] + I * h * (w[i] / wmax);
+      rc = cs_energy_forces(pc, prm, n, xc, box, fc, NULL);
+      for (int i = 0; i < 3 * n; ++i) dLdx[i] = cimag(fc[i]) / h * wmax;
+    }
+  }
+  if (dLdtheta && rc == OR_OK) {
+    for (int i = 0; i < 3 * n; ++i) xc[i] = x[i];
+    for (int t = 0; t < 3 && rc == OR_OK; ++t) {
+      for (int k = 0; k < 8; ++k) pc[k] = prm[k];
+      pc[t] += I * h;
+      rc = cs_energy_forces(pc, prm, n, xc, box, fc, NULL);
+      double s = 0;
+      for (int i = 0; i < 3 * n; ++i) s += w[i] * (cimag(fc[i]) / h);
+      dLdtheta[t] = s;
+    }
+  }
+  free(xc);
+  free(fc);
+  return rc;
+}
+
+/* dE/d(lambda, epsilon, sigma) by complex step on the energy. */
+int or_energy_param_grad(const double* prm, int n, const double* x, const double* box, double* dEdtheta) {
+  const double h = 1e-30;
+  cplx pc[8];
+  cplx* xc = (cplx*)malloc(sizeof(cplx) * 3 * (size_t)n);
+  cplx* fc = (cplx*)malloc(sizeof(cplx) * 3 * (size_t)n);
+  if (!xc || !fc) {
+    free(xc);
+    free(fc);
+    return OR_ENOMEM;
+  }
+  for (int i = 0; i < 3 * n; ++i) xc[i] = x[i];
+  int rc = OR_OK;
+  for (int t = 0; t < 3 && rc == OR_OK; ++t) {
+    for (int k = 0; k < 8; ++k) pc[k] = prm[k];
+    pc[t] += I * h;
+    cplx E;
+    rc = cs_energy_forces(pc, prm, n, xc, box, fc, &E);
+    dEdtheta[t] = cimag(E) / h;
+  }
+  free(xc);
+  free(fc);
+  return rc;
+}

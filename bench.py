@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Throughput of the mW MD step (force + integrate) on GB300, one JSON line.
+
+Default workload: 32768-atom ice Ih (0.92 g/cm^3) and a 32768-atom liquid box
+(0.9998 g/cm^3, melted from the same lattice), advanced together as a
+two-box batch, Nose-Hoover 240 K (tau 1 ps), dt = 10 fs.  A bench step is one
+MD step of both boxes: kick + drift + fixed-point copy + rebuild check (and
+cell binning / neighbour list when due) + fused 2+3-body force + kick +
+thermostat + FP64 reductions.  value = atom-steps / s.
+
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
+system's stream; the L2 is flushed (a 512 MB write) between steps because the
+working set (~16 MB) fits in L2.  Under torchrun every rank runs its own
+replica (the path shards by box, no data exchange); value = all ranks'
+atom-steps / max over ranks of the timed span.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0809_2811_gb300 import inputs as I  # noqa: E402
+
+METRIC = "mW atom-steps/s (force+integrate)"
+UNIT = "atom-steps/s"
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "graph", "persistent"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prep-steps", type=int, default=3000)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+
+T_RUN = 240.0
+DT = 10.0
+TAU = 1000.0
+
+
+def workload_spec():
+    return {"workload": "ice Ih 32768 @0.92 + liquid 32768 @0.9998 (melted), 2-box batch, NH 240 K, dt 10 fs",
+            "boxes": 2, "atoms": 65536, "T_K": T_RUN, "dt_fs": DT, "tau_fs": TAU}
+
+
+def ice_start(seed):
+    x, box = I.ice_ih(16, 16, 16, 0.92)
+    v = I.maxwell_velocities(len(x), T_RUN, seed=seed)
+    return x, v, box
+
+
+def liquid_lattice():
+    return I.ice_ih(16, 16, 16, 0.9998)
+
+
+def melt_liquid(mw, seed, prep_steps, stream):
+    """Melts the 0.9998 lattice on the GPU: Berendsen 600 K then Nose-Hoover
+    300 K (the liquid box is 'melted from the ice lattice at 300 K')."""
+    x, box = liquid_lattice()
+    v = I.maxwell_velocities(len(x), 600.0, seed=seed + 7)
+    s = mw.System(len(x), box, stream=stream)
+    s.set_state(x, v)
+    s.step(prep_steps // 2, dt=5.0, thermostat=mw.MW_BERENDSEN, T0=600.0, tau=200.0)
+    th = s.step(prep_steps - prep_steps // 2, dt=DT, thermostat=mw.MW_NOSE_HOOVER, T0=300.0, tau=TAU)[0]
+    xl, vl = s.get_state()
+    s.close()
+    return xl, vl, box, th["pe"] / len(x)
+
+
+# ------------------------------------------------------------------ helpers
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [t.strip() for t in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[3 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda_ok() else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def reduce_max(pg, value, device):
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg, device):
+    if pg is not None:
+        import torch
+        if device.type == "cuda":
+            pg.barrier(device_ids=[device.index])
+        else:
+            pg.barrier()
+
+
+def traffic_from_profile(kernel_src):
+    """DRAM bytes per force launch from the committed ncu summary, if it was
+    taken on the current kernel source (hash match), else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "sw_force_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        if rec.get("source_hash") != h:
+            return None
+        return rec.get("dram_bytes_per_launch_scaled")
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def oracle_sample(target_s=12.0):
+    """Times the FP64 oracle's MD step (cell-list forces + velocity Verlet +
+    Nose-Hoover) on both boxes of the workload for a bounded number of steps
+    (about target_s seconds of one core); returns (atom-steps/s, description)."""
+    import oracle
+    oracle.build()
+    xi, vi, bi = ice_start(I.BASE_SEED + 2)
+    xl, bl = liquid_lattice()
+    xl = xl + np.random.default_rng(3).normal(0, 0.35, xl.shape)  # liquid-like disorder, same density
+    vl = I.maxwell_velocities(len(xl), T_RUN, seed=5)
+    t0 = time.perf_counter()
+    oracle.md(xi, vi, bi, 1, dt=DT, kind=2, T0=T_RUN, tau=TAU)
+    oracle.md(xl, vl, bl, 1, dt=DT, kind=2, T0=T_RUN, tau=TAU)
+    one = time.perf_counter() - t0  # includes the initial force call of each run
+    steps = max(2, int(target_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    oracle.md(xi, vi, bi, steps, dt=DT, kind=2, T0=T_RUN, tau=TAU)
+    oracle.md(xl, vl, bl, steps, dt=DT, kind=2, T0=T_RUN, tau=TAU)
+    el = time.perf_counter() - t0
+    # each or_md call also does one extra force evaluation up front: count (steps + 1) force evals
+    rate = 2 * len(xi) * steps / el
+    return rate, (f"oracle FP64 single-thread MD, {steps} NH steps of each 32768-atom box "
+                  f"(ice lattice + disordered 0.9998 lattice), {el:.1f} s incl. one start-up force call per box")
+
+
+# ------------------------------------------------------------------ main GPU arm
+
+def run_gpu(args, world, rank, local, pg):
+    import torch
+    from paper_0809_2811_gb300 import build, mw
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    xi, vi, bi = ice_start(I.BASE_SEED + 2 + 17 * rank)
+    xl, vl, bl, liq_pe = melt_liquid(mw, I.BASE_SEED + 2 + 17 * rank, args.prep_steps, sp)
+    x = np.concatenate([xi, xl])
+    v = np.concatenate([vi, vl])
+    n = [len(xi), len(xl)]
+    boxes = np.stack([bi, bl])
+    sysm = mw.System(n, boxes, stream=sp)
+    if args.engine != "auto":
+        sysm.set_engine({"graph": mw.MW_ENGINE_GRAPH, "persistent": mw.MW_ENGINE_PERSISTENT}[args.engine])
+    sysm.set_state(x, v)
+    integ = mw.make_integrator(DT, mw.MW_NOSE_HOOVER, T_RUN, TAU)
+    natoms = sum(n)
+
+    # warm-up
+    mw.mw_step(sysm.h, integ, max(args.warmup, 3), sysm.nbox)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    th0 = sysm.thermo()
+    reb0 = sum(t["rebuilds"] for t in th0)
+
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(local)
+    barrier(pg, dev)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    t_wall = time.perf_counter()
+    for k in range(K):
+        ev0[k].record(stream)
+        mw.mw_step_async(sysm.h, integ, 1)
+        ev1[k].record(stream)
+        flush.fill_(float(k))
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    mw.mw_sync(sysm.h)
+    barrier(pg, dev)
+    ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    span_s = sum(ms) / 1e3
+    span_max = reduce_max(pg, span_s, dev)
+    th1 = sysm.thermo()
+    rebuilds = sum(t["rebuilds"] for t in th1) - reb0
+    info = sysm.info()
+    value = world * natoms * K / span_max
+
+    # force-kernel roofline (timed alone, L2 flushed between launches)
+    nf = 30
+    f0 = [torch.cuda.Event(enable_timing=True) for _ in range(nf)]
+    f1 = [torch.cuda.Event(enable_timing=True) for _ in range(nf)]
+    for k in range(nf):
+        flush.fill_(float(k))
+        f0[k].record(stream)
+        mw.mw_forces_async(sysm.h)
+        f1[k].record(stream)
+    torch.cuda.synchronize(dev)
+    mw.mw_sync(sysm.h)
+    fms = statistics.median([a.elapsed_time(b) for a, b in zip(f0, f1)])
+    sysm.set_count_terms(True)
+    mw.mw_forces_async(sysm.h)
+    mw.mw_sync(sysm.h)
+    info_c = sysm.info()
+    sysm.set_count_terms(False)
+    P, T = info_c["npairs"], info_c["ntriplets"]
+    flops = 40.0 * (2 * P + T)  # 40 FP32 ops per ordered leg and per triplet
+    achieved = flops / (fms / 1e3) / 1e12
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_0809_2811_gb300", "csrc", "mw_device.cuh"))
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        ke = min(K, 40)
+        xh = torch.from_numpy(x).pin_memory()
+        vh = torch.from_numpy(v).pin_memory()
+        sysm.set_state(xh.numpy(), vh.numpy())
+        mw.mw_step(sysm.h, integ, 1, sysm.nbox)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            sysm.set_state(xh.numpy(), vh.numpy())  # H2D of the step's inputs (x, v)
+            mw.mw_step(sysm.h, integ, 1, sysm.nbox)  # D2H of the step's result (thermo records)
+        torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        el = reduce_max(pg, el, dev)
+        e2e = {"value": world * natoms * ke / el, "unit": UNIT, "h2d_bytes_per_step": int(2 * x.nbytes),
+               "d2h_bytes_per_step": int(sysm.nbox * 136), "steps": ke,
+               "note": "mw_set_state(host x, v) + mw_step(1) + thermo read per step; set_state restarts "
+                       "the thermostat and forces a neighbour build + force call each step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, desc = oracle_sample()
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    kernels_per_step = 9 if info["engine"] == mw.MW_ENGINE_GRAPH else 1
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": 1e3 * span_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 pair/triplet, f64 integrate+reductions", "data": "synthetic",
+        "config": {**workload_spec(), "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "l2": "flushed between steps (512 MB write)",
+                   "engine": {1: "graph", 2: "persistent"}.get(info["engine"], str(info["engine"])),
+                   "nbr_width": info["nbr_width"], "rebuilds_in_timed_region": int(rebuilds),
+                   "liquid_pe_per_atom_after_melt": liq_pe, "wall_s_timed": t_wall},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_force (fused 2+3-body)",
+                     "force_ms": fms, "legs": 2 * P, "triplets": T,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": kernels_per_step * K,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    rates = []
+    for _ in range(max(args.warmup, 0)):
+        pass
+    steps = max(1, args.steps)
+    per = max(2.0, min(20.0, 100.0 / steps))
+    rate, desc = oracle_sample(target_s=per)
+    rates.append(rate)
+    el = time.perf_counter() - t0
+    out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world, "steps": steps,
+           "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "config": {**workload_spec(), "parallelism": "cpu oracle"},
+           "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": el}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_gpu(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

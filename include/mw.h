@@ -113,8 +113,9 @@ mw_status mw_params_default(mw_params* out);
  * box[0..2] (A), every edge >= 2 (a sigma + skin).  mass in g/mol
  * (18.015 for water, Sec. II.C), skin >= 0 in A (Verlet-list skin; the
  * list is rebuilt once an atom has moved more than skin/2).  stream is a
- * cudaStream_t (NULL = the legacy default stream) on which all work of this
- * system is enqueued; it must outlive the system.  Allocates device memory. */
+ * cudaStream_t on which all work of this system is enqueued (it must
+ * outlive the system); NULL makes the library create and own a
+ * non-blocking stream.  Allocates device memory. */
 mw_status mw_system_create(mw_system** out, int n, const double box[3], const mw_params* prm, double mass,
                            double skin, void* stream);
 
@@ -167,12 +168,28 @@ mw_status mw_energy_forces(mw_system* s, double* f, double* energy, double* viri
 mw_status mw_energy_forces_dev(mw_system* s, const double* x_dev, float* f_dev, double* energy_dev,
                                double* virial_dev);
 
+/* Enqueues one force evaluation (zero the forces, fused two- + three-body
+ * kernel) at the current positions with the current neighbour list on the
+ * system's stream and returns without synchronising; for timing the force
+ * kernel on its own (the neighbour list is built first if it is stale). */
+mw_status mw_forces_async(mw_system* s);
+
 /* Advances every box nsteps velocity-Verlet steps.  last (may be NULL)
  * receives nbox thermo records after the final step.  Recovers internally
  * from neighbour-list overflow (grows the list and resumes the interrupted
  * step); returns MW_ENAN / MW_ELOST / MW_ETIMEOUT if dynamics broke down (the
  * state is then left at the failing step). */
 mw_status mw_step(mw_system* s, const mw_integrator* integ, int nsteps, mw_thermo* last);
+
+/* Enqueues nsteps steps on the system's stream and returns without waiting.
+ * No overflow recovery happens here: a failure (list overflow, NaN, lost
+ * atom) freezes the state at the failing step and is returned by the next
+ * mw_sync (or any synchronising call). */
+mw_status mw_step_async(mw_system* s, const mw_integrator* integ, int nsteps);
+
+/* Waits for the system's stream; returns the device-side status of the work
+ * enqueued so far. */
+mw_status mw_sync(mw_system* s);
 
 /* Thermo records (nbox) of the last completed step, or of the state just set. */
 mw_status mw_get_thermo(mw_system* s, mw_thermo* out);
@@ -203,6 +220,11 @@ mw_status mw_set_nbr_width(mw_system* s, int width);
 mw_status mw_autotune(mw_system* s, const mw_integrator* integ, int steps, int* best_engine);
 
 mw_status mw_get_info(mw_system* s, mw_info* out);
+
+/* Diagnostics: when on != 0 the force kernels count legs (pairs with
+ * r < a sigma) and triplets into mw_info.npairs / .ntriplets (device atomics,
+ * slower; the counts feed the roofline arithmetic). */
+mw_status mw_set_count_terms(mw_system* s, int on);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* mw_last_error(void);

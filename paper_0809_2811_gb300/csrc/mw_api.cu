@@ -1,0 +1,924 @@
+// mw_api.cu -- the C ABI of libmw (declared in include/mw.h).
+//
+// Host side: validates arguments, owns device buffers, sequences the kernels
+// of mw_device.cuh on the system's stream, captures one MD step into a CUDA
+// graph (graph engine) or launches the persistent cooperative kernel
+// (persistent engine), and recovers from neighbour-list overflow.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mw.h"
+#include "mw_device.cuh"
+#include "mw_persistent.cuh"
+#include "mw_adjoint.cuh"
+
+using namespace mw;
+
+namespace {
+
+thread_local std::string g_err;
+
+mw_status fail(mw_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define MW_CUDA(call)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(MW_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
+
+constexpr int kThreads = 128;
+
+}  // namespace
+
+struct mw_system {
+  int nbox = 0, N = 0, W = 0, ncell = 0;
+  std::vector<int> n, off;
+  std::vector<Box> boxes;
+  mw_params prm{};
+  double mass = 18.015, skin = 1.0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool list_built = false;
+  double* eout = nullptr;  // 9 * nbox doubles: energies + virials staging
+  Dev d{};
+  FParams fp{};
+  Integ integ{};
+  bool integ_set = false;
+  int* boxid = nullptr;  // user-order box id per atom
+  void* adj_scratch = nullptr;  // adjoint per-box accumulators
+  // state
+  bool state_set = false;
+  bool forces_valid = false;
+  long long host_step = 0;
+  int engine = MW_ENGINE_AUTO, engine_used = MW_ENGINE_GRAPH;
+  int tuned_engine = -1;
+  int count_terms = 0;
+  long long npairs = 0, ntrip = 0;
+  // graph engine
+  cudaGraphExec_t graph1 = nullptr, graphK = nullptr;
+  int graphK_steps = 0;
+  bool graph_dirty = true;
+  // persistent engine
+  int pers_blocks = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+// defined in mw_persistent_host.inc / mw_adjoint_host.inc
+mw_status persistent_func_attrs();
+bool persistent_available(mw_system* s);
+mw_status run_persistent_engine(mw_system* s, int nsteps);
+mw_status enqueue_persistent(mw_system* s, int nsteps);
+mw_status adjoint_alloc(mw_system* s);
+
+template <class T>
+mw_status dalloc(mw_system* s, T** p, size_t count) {
+  void* q = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) return fail(MW_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+  s->allocs.push_back(q);
+  *p = (T*)q;
+  return MW_OK;
+}
+
+void dfree(mw_system* s, void* p) {
+  if (!p) return;
+  auto it = std::find(s->allocs.begin(), s->allocs.end(), p);
+  if (it != s->allocs.end()) s->allocs.erase(it);
+  cudaFree(p);
+}
+
+double r_list(const mw_system* s) { return s->prm.a * s->prm.sigma + s->skin; }
+
+mw_status check_params(const mw_params* p) {
+  if (!p) return fail(MW_EINVAL, "params is NULL");
+  const double v[] = {p->lambda, p->epsilon, p->sigma, p->a, p->gamma, p->A, p->B, p->cos_theta0};
+  for (double x : v)
+    if (!std::isfinite(x)) return fail(MW_EINVAL, "non-finite parameter");
+  if (p->sigma <= 0 || p->a <= 0 || p->epsilon < 0 || p->lambda < 0 || p->gamma < 0)
+    return fail(MW_EINVAL, "parameters out of range (sigma, a > 0; epsilon, lambda, gamma >= 0)");
+  if (p->p < 0 || p->p > 16 || p->q < 0 || p->q > 16) return fail(MW_EINVAL, "p and q must be in [0, 16]");
+  return MW_OK;
+}
+
+void make_fparams(mw_system* s) {
+  const mw_params& p = s->prm;
+  const double rc = p.a * p.sigma, rl = rc + s->skin;
+  const double l2e = 1.4426950408889634;
+  FParams& f = s->fp;
+  f.rc = (float)rc;
+  f.rc2 = (float)(rc * rc);
+  f.rl2 = (float)(rl * rl);
+  f.sig = (float)p.sigma;
+  f.sig_l2e = (float)(p.sigma * l2e);
+  f.gsig_l2e = (float)(p.gamma * p.sigma * l2e);
+  f.gsig = (float)(p.gamma * p.sigma);
+  f.Aeps = (float)(p.A * p.epsilon);
+  f.B = (float)p.B;
+  f.c0 = (float)p.cos_theta0;
+  f.sle = (float)std::sqrt(p.lambda * p.epsilon);
+  f.p = p.p;
+  f.q = p.q;
+}
+
+// Cell grids of all boxes for the current list radius; returns the total.
+mw_status layout_cells(mw_system* s, int* ncell_out) {
+  const double rl = r_list(s);
+  long long total = 0;
+  for (int b = 0; b < s->nbox; ++b) {
+    Box& bx = s->boxes[b];
+    for (int k = 0; k < 3; ++k) {
+      if (bx.L[k] < 2.0 * rl)
+        return fail(MW_EBOX, "box %d edge %d = %g A is shorter than 2 r_list = %g A", b, k, bx.L[k], 2 * rl);
+      bx.nc[k] = std::max(1, (int)std::floor(bx.L[k] / rl));
+    }
+    bx.cell_off = (int)total;
+    total += (long long)bx.nc[0] * bx.nc[1] * bx.nc[2];
+  }
+  if (total > (1ll << 30)) return fail(MW_EINVAL, "too many cells");
+  *ncell_out = (int)total;
+  return MW_OK;
+}
+
+int initial_width(const mw_system* s) {
+  double rho = 0;
+  for (int b = 0; b < s->nbox; ++b) {
+    const Box& bx = s->boxes[b];
+    rho = std::max(rho, bx.n / (bx.L[0] * bx.L[1] * bx.L[2]));
+  }
+  const double rl = r_list(s);
+  const double expect = rho * 4.18879020478639 * rl * rl * rl;
+  int w = (int)std::ceil(1.5 * expect + 16);
+  w = (w + 7) / 8 * 8;
+  return std::max(8, std::min(w, 1024));
+}
+
+mw_status upload_boxes(mw_system* s) {
+  MW_CUDA(cudaMemcpyAsync((void*)s->d.box, s->boxes.data(), sizeof(Box) * s->nbox, cudaMemcpyHostToDevice, s->stream));
+  return MW_OK;
+}
+
+mw_status upload_integ(mw_system* s) {
+  MW_CUDA(cudaMemcpyAsync((void*)s->d.integ, &s->integ, sizeof(Integ), cudaMemcpyHostToDevice, s->stream));
+  return MW_OK;
+}
+
+mw_status alloc_cells(mw_system* s) {
+  dfree(s, s->d.cell_cnt);
+  dfree(s, s->d.cell_start);
+  s->d.cell_cnt = s->d.cell_start = nullptr;
+  mw_status st;
+  if ((st = dalloc(s, &s->d.cell_cnt, s->ncell)) != MW_OK) return st;
+  if ((st = dalloc(s, &s->d.cell_start, s->ncell + 1)) != MW_OK) return st;
+  MW_CUDA(cudaMemsetAsync(s->d.cell_cnt, 0, sizeof(int) * s->ncell, s->stream));
+  s->d.ncell = s->ncell;
+  s->graph_dirty = true;
+  return MW_OK;
+}
+
+mw_status alloc_nbr(mw_system* s, int W) {
+  dfree(s, s->d.nbr);
+  s->d.nbr = nullptr;
+  mw_status st;
+  if ((st = dalloc(s, &s->d.nbr, (size_t)W * s->N)) != MW_OK) return st;
+  MW_CUDA(cudaMemsetAsync(s->d.nbr, 0, sizeof(int) * (size_t)W * s->N, s->stream));
+  s->W = s->d.W = W;
+  s->list_built = false;
+  s->graph_dirty = true;
+  return MW_OK;
+}
+
+void destroy_graphs(mw_system* s) {
+  if (s->graph1) cudaGraphExecDestroy(s->graph1);
+  if (s->graphK) cudaGraphExecDestroy(s->graphK);
+  s->graph1 = s->graphK = nullptr;
+}
+
+mw_status set_global_field(mw_system* s, size_t offset, int value) {
+  MW_CUDA(cudaMemcpyAsync((char*)s->d.g + offset, &value, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+  return MW_OK;
+}
+
+mw_status read_global(mw_system* s, Global* g) {
+  MW_CUDA(cudaMemcpyAsync(g, s->d.g, sizeof(Global), cudaMemcpyDeviceToHost, s->stream));
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  return MW_OK;
+}
+
+mw_status status_error(const Global& g) {
+  switch (g.status) {
+    case ST_OK: return MW_OK;
+    case ST_OVERFLOW: return fail(MW_ENLIST_OVERFLOW, "neighbour list overflow (max count %d)", g.max_count);
+    case ST_NAN: return fail(MW_ENAN, "non-finite velocity or force at atom slot %d", g.err_index);
+    case ST_LOST: return fail(MW_ELOST, "atom slot %d moved more than half a box edge in one step", g.err_index);
+    case ST_TIMEOUT: return fail(MW_ETIMEOUT, "a bounded device-side wait ran out");
+    case ST_LEGS: return fail(MW_EINVAL, "more than %d atoms within a*sigma of atom slot %d", kMaxLegsOverflow, g.err_index);
+    default: return fail(MW_ECUDA, "device status %d", g.status);
+  }
+}
+
+// Kernel sequences ----------------------------------------------------------
+
+void launch_rebuild(mw_system* s) {
+  const Dev& d = s->d;
+  const int gb = div_up(s->N, kThreads);
+  k_bin<<<gb, kThreads, 0, s->stream>>>(d);
+  k_scan<<<1, kScanThreads, 0, s->stream>>>(d);
+  k_scatter<<<gb, kThreads, 0, s->stream>>>(d);
+  k_copyback<<<std::max(gb, div_up(s->nbox, kThreads)), kThreads, 0, s->stream>>>(d);
+  k_neigh<<<div_up((long long)s->N * 32, kThreads), kThreads, 0, s->stream>>>(d, s->fp.rl2);
+}
+
+void launch_force(mw_system* s) {
+  const Dev& d = s->d;
+  const int gb = div_up(s->N, kForceThreads);
+  if (s->count_terms) {
+    k_force<true><<<gb, kForceThreads, sizeof(LegSm), s->stream>>>(d, s->fp);
+    k_force_overflow<true><<<64, 128, 0, s->stream>>>(d, s->fp);
+  } else {
+    k_force<false><<<gb, kForceThreads, sizeof(LegSm), s->stream>>>(d, s->fp);
+    k_force_overflow<false><<<64, 128, 0, s->stream>>>(d, s->fp);
+  }
+}
+
+void launch_step(mw_system* s) {
+  const Dev& d = s->d;
+  const int gb = div_up(s->N, kThreads);
+  k_kick1<<<gb, kThreads, 0, s->stream>>>(d);
+  launch_rebuild(s);
+  launch_force(s);
+  k_kick2<<<gb, kThreads, 0, s->stream>>>(d);
+}
+
+mw_status set_func_attrs() {
+  static bool done = false;
+  if (done) return MW_OK;
+  MW_CUDA(cudaFuncSetAttribute(k_force<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LegSm)));
+  MW_CUDA(cudaFuncSetAttribute(k_force<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LegSm)));
+  mw_status st = persistent_func_attrs();
+  if (st != MW_OK) return st;
+  done = true;
+  return MW_OK;
+}
+
+mw_status grow_nbr_after_overflow(mw_system* s, const Global& g) {
+  int w = g.max_count + std::max(8, g.max_count / 4);
+  w = (w + 7) / 8 * 8;
+  if (w <= s->W) w = s->W + 8;
+  return alloc_nbr(s, w);
+}
+
+// Forces (and the thermo snapshot) at the current positions, with overflow recovery.
+mw_status ensure_forces(mw_system* s) {
+  if (!s->state_set) return fail(MW_ESTATE, "no state set (call mw_set_state first)");
+  if (s->forces_valid) return MW_OK;
+  mw_status st;
+  if ((st = set_func_attrs()) != MW_OK) return st;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    k_prep_force<<<div_up(std::max(s->N, s->nbox), kThreads), kThreads, 0, s->stream>>>(s->d, 1);
+    MW_CUDA(cudaGetLastError());
+    launch_rebuild(s);
+    launch_force(s);
+    k_thermo_snapshot<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d);
+    MW_CUDA(cudaGetLastError());
+    Global g;
+    if ((st = read_global(s, &g)) != MW_OK) return st;
+    if (s->count_terms) {
+      s->npairs = g.npairs / 2;
+      s->ntrip = g.ntrip;
+    }
+    if (g.status == ST_OVERFLOW) {
+      if ((st = grow_nbr_after_overflow(s, g)) != MW_OK) return st;
+      if ((st = set_global_field(s, offsetof(Global, status), 0)) != MW_OK) return st;
+      if ((st = set_global_field(s, offsetof(Global, any_rebuild), 1)) != MW_OK) return st;
+      continue;
+    }
+    if (g.status) return status_error(g);
+    s->forces_valid = true;
+    s->list_built = true;
+    return MW_OK;
+  }
+  return fail(MW_ENLIST_OVERFLOW, "neighbour list kept overflowing");
+}
+
+mw_status capture_graphs(mw_system* s, int ksteps) {
+  destroy_graphs(s);
+  for (int which = 0; which < 2; ++which) {
+    const int steps = which == 0 ? 1 : ksteps;
+    cudaGraph_t graph;
+    MW_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < steps; ++k) launch_step(s);
+    cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
+    if (e != cudaSuccess) return fail(MW_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    cudaGraphExec_t ex;
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(MW_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    (which == 0 ? s->graph1 : s->graphK) = ex;
+  }
+  s->graphK_steps = ksteps;
+  s->graph_dirty = false;
+  return MW_OK;
+}
+
+// Completes a step interrupted by a neighbour-list overflow (kick1 done).
+mw_status finish_interrupted_step(mw_system* s) {
+  const int gb = div_up(s->N, kThreads);
+  launch_rebuild(s);
+  launch_force(s);
+  k_kick2<<<gb, kThreads, 0, s->stream>>>(s->d);
+  MW_CUDA(cudaGetLastError());
+  return MW_OK;
+}
+
+mw_status run_graph_engine(mw_system* s, int nsteps) {
+  mw_status st;
+  const int K = 16;
+  if (s->graph_dirty || !s->graph1) {
+    if ((st = capture_graphs(s, K)) != MW_OK) return st;
+  }
+  int remaining = nsteps;
+  int guard = 0;
+  while (remaining > 0) {
+    Global g0;
+    if ((st = read_global(s, &g0)) != MW_OK) return st;
+    const unsigned long long step0 = g0.step;
+    const int full = remaining / K, rest = remaining % K;
+    for (int k = 0; k < full; ++k) MW_CUDA(cudaGraphLaunch(s->graphK, s->stream));
+    for (int k = 0; k < rest; ++k) MW_CUDA(cudaGraphLaunch(s->graph1, s->stream));
+    Global g;
+    if ((st = read_global(s, &g)) != MW_OK) return st;
+    const int done = (int)(g.step - step0);
+    s->host_step += done;
+    if (g.status == ST_OVERFLOW) {
+      if (++guard > 8) return fail(MW_ENLIST_OVERFLOW, "neighbour list kept overflowing");
+      if ((st = grow_nbr_after_overflow(s, g)) != MW_OK) return st;
+      if ((st = set_global_field(s, offsetof(Global, status), 0)) != MW_OK) return st;
+      if ((st = set_global_field(s, offsetof(Global, any_rebuild), 1)) != MW_OK) return st;
+      if ((st = finish_interrupted_step(s)) != MW_OK) return st;
+      Global g2;
+      if ((st = read_global(s, &g2)) != MW_OK) return st;
+      if (g2.status == ST_OVERFLOW) continue;  // grow again, same step
+      if (g2.status) return status_error(g2);
+      s->host_step += 1;
+      remaining -= done + 1;
+      if ((st = capture_graphs(s, K)) != MW_OK) return st;
+      continue;
+    }
+    if (g.status) return status_error(g);
+    remaining -= done;
+    if (done == 0) return fail(MW_ECUDA, "no progress in graph engine");
+  }
+  return MW_OK;
+}
+
+mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  if (!x) return fail(MW_EINVAL, "positions are NULL");
+  const size_t bytes = sizeof(double) * 3 * (size_t)s->N;
+  const double* xd = x;
+  const double* vd = v;
+  if (!dev) {
+    for (size_t k = 0; k < 3 * (size_t)s->N; ++k)
+      if (!std::isfinite(x[k]) || (v && !std::isfinite(v[k]))) return fail(MW_EINVAL, "non-finite input at %zu", k);
+    MW_CUDA(cudaMemcpyAsync(s->d.stage, x, bytes, cudaMemcpyHostToDevice, s->stream));
+    xd = s->d.stage;
+    if (v) {
+      MW_CUDA(cudaMemcpyAsync(s->d.stage2, v, bytes, cudaMemcpyHostToDevice, s->stream));
+      vd = s->d.stage2;
+    }
+  }
+  // reset thermostat / accumulators / counters
+  std::vector<BoxState> bs(s->nbox);
+  for (auto& b : bs) {
+    std::memset(&b, 0, sizeof b);
+    b.s_end = 1.0;
+    b.rebuild = 1;
+  }
+  MW_CUDA(cudaMemcpyAsync(s->d.bst, bs.data(), sizeof(BoxState) * s->nbox, cudaMemcpyHostToDevice, s->stream));
+  Global g{};
+  g.any_rebuild = 1;
+  g.count_terms = s->count_terms;
+  MW_CUDA(cudaMemcpyAsync(s->d.g, &g, sizeof(Global), cudaMemcpyHostToDevice, s->stream));
+  const int gb = div_up(s->N, kThreads);
+  k_load_positions<<<gb, kThreads, 0, s->stream>>>(s->d, xd, s->boxid, 1);
+  k_load_velocities<<<gb, kThreads, 0, s->stream>>>(s->d, vd);
+  k_ke_init<<<gb, kThreads, 0, s->stream>>>(s->d);
+  MW_CUDA(cudaMemsetAsync(s->d.f, 0, sizeof(float4) * s->N, s->stream));
+  MW_CUDA(cudaGetLastError());
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  s->state_set = true;
+  s->forces_valid = false;
+  s->host_step = 0;
+  return MW_OK;
+}
+
+mw_status validate_integ(mw_system* s, const mw_integrator* in) {
+  if (!in) return fail(MW_EINVAL, "integrator is NULL");
+  if (!(in->dt > 0) || !std::isfinite(in->dt)) return fail(MW_EINVAL, "dt must be > 0");
+  if (in->thermostat < MW_NVE || in->thermostat > MW_NOSE_HOOVER) return fail(MW_EINVAL, "unknown thermostat");
+  if (in->thermostat != MW_NVE && !(in->tau > 0)) return fail(MW_EINVAL, "tau must be > 0");
+  bool boxes_changed = false;
+  for (int b = 0; b < s->nbox; ++b) {
+    const double T0 = in->T0_per_box ? in->T0_per_box[b] : in->T0;
+    if (in->thermostat != MW_NVE && !(T0 > 0)) return fail(MW_EINVAL, "T0 must be > 0");
+    Box& bx = s->boxes[b];
+    const double Q = bx.Ndf * kKB * T0 * in->tau * in->tau;
+    if (bx.T0 != T0 || bx.Q != Q) {
+      bx.T0 = T0;
+      bx.Q = Q;
+      boxes_changed = true;
+    }
+  }
+  Integ I{};
+  I.dt = in->dt;
+  I.cf = 0.5 * in->dt * kFCONV / s->mass;
+  I.ke_fac = 0.5 * s->mass / kFCONV;
+  I.tau = in->thermostat == MW_NVE ? 1.0 : in->tau;
+  I.kind = in->thermostat;
+  I.half_skin2 = (float)(0.25 * s->skin * s->skin);
+  mw_status st;
+  if (boxes_changed && (st = upload_boxes(s)) != MW_OK) return st;
+  if (std::memcmp(&I, &s->integ, sizeof I) != 0) {
+    s->integ = I;
+    if ((st = upload_integ(s)) != MW_OK) return st;
+  }
+  return MW_OK;
+}
+
+mw_status create_common(mw_system** out, int nbox, const int* n, const double* box, const mw_params* prm,
+                        double mass, double skin, void* stream) {
+  if (!out) return fail(MW_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nbox < 1 || !n || !box) return fail(MW_EINVAL, "need nbox >= 1, n and box");
+  mw_status st;
+  if ((st = check_params(prm)) != MW_OK) return st;
+  if (!(mass > 0) || !(skin >= 0) || !std::isfinite(mass) || !std::isfinite(skin))
+    return fail(MW_EINVAL, "mass must be > 0 and skin >= 0");
+  long long total = 0;
+  for (int b = 0; b < nbox; ++b) {
+    if (n[b] < 2) return fail(MW_EINVAL, "box %d has %d atoms (need >= 2)", b, n[b]);
+    for (int k = 0; k < 3; ++k)
+      if (!(box[3 * b + k] > 0) || !std::isfinite(box[3 * b + k])) return fail(MW_EINVAL, "bad box edge");
+    total += n[b];
+  }
+  if (total > (1ll << 28)) return fail(MW_EINVAL, "too many atoms (%lld)", total);
+  mw_system* s = new mw_system();
+  s->nbox = nbox;
+  s->N = (int)total;
+  s->prm = *prm;
+  s->mass = mass;
+  s->skin = skin;
+  s->stream = (cudaStream_t)stream;
+  if (!s->stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete s;
+      return fail(MW_ECUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(e));
+    }
+    s->own_stream = true;
+  }
+  s->n.assign(n, n + nbox);
+  s->off.resize(nbox);
+  s->boxes.resize(nbox);
+  int o = 0;
+  for (int b = 0; b < nbox; ++b) {
+    Box& bx = s->boxes[b];
+    std::memset(&bx, 0, sizeof bx);
+    for (int k = 0; k < 3; ++k) {
+      bx.L[k] = box[3 * b + k];
+      bx.qs[k] = 4294967296.0 / bx.L[k];
+      bx.Lq[k] = (float)(bx.L[k] / 4294967296.0);
+    }
+    bx.off = o;
+    bx.n = n[b];
+    bx.Ndf = 3.0 * n[b] - 3.0;
+    bx.T0 = 0;
+    bx.Q = 1;
+    bx.volume = bx.L[0] * bx.L[1] * bx.L[2];
+    s->off[b] = o;
+    o += n[b];
+  }
+  make_fparams(s);
+  if ((st = layout_cells(s, &s->ncell)) != MW_OK) {
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return st;
+  }
+  auto bad = [&](mw_status e) {
+    mw_system_destroy(s);
+    return e;
+  };
+  const size_t N = s->N;
+  Dev& d = s->d;
+  d.N = s->N;
+  d.nbox = nbox;
+  double** dbl[] = {&d.x, &d.y, &d.z, &d.vx, &d.vy, &d.vz, &d.tx, &d.ty, &d.tz, &d.tvx, &d.tvy, &d.tvz};
+  for (double** p : dbl)
+    if ((st = dalloc(s, p, N)) != MW_OK) return bad(st);
+  if ((st = dalloc(s, &d.q, N)) != MW_OK || (st = dalloc(s, &d.qb, N)) != MW_OK ||
+      (st = dalloc(s, &d.tq, N)) != MW_OK || (st = dalloc(s, &d.f, N)) != MW_OK ||
+      (st = dalloc(s, &d.id, N)) != MW_OK || (st = dalloc(s, &d.tid, N)) != MW_OK ||
+      (st = dalloc(s, &d.cell, N)) != MW_OK || (st = dalloc(s, &d.rank, N)) != MW_OK ||
+      (st = dalloc(s, &d.nbr_cnt, N)) != MW_OK || (st = dalloc(s, &d.over, N)) != MW_OK ||
+      (st = dalloc(s, &d.stage, 3 * N)) != MW_OK || (st = dalloc(s, &d.stage2, 3 * N)) != MW_OK ||
+      (st = dalloc(s, &s->boxid, N)) != MW_OK || (st = dalloc(s, &s->eout, 9 * (size_t)nbox)) != MW_OK)
+    return bad(st);
+  if (cudaMemsetAsync(d.nbr_cnt, 0, sizeof(int) * N, s->stream) != cudaSuccess)
+    return bad(fail(MW_ECUDA, "memset failed"));
+  Box* dbox;
+  BoxState* dbst;
+  double* dth;
+  Global* dg;
+  Integ* dint;
+  if ((st = dalloc(s, &dbox, nbox)) != MW_OK || (st = dalloc(s, &dbst, nbox)) != MW_OK ||
+      (st = dalloc(s, &dth, (size_t)nbox * TR_N)) != MW_OK || (st = dalloc(s, &dg, 1)) != MW_OK ||
+      (st = dalloc(s, &dint, 1)) != MW_OK)
+    return bad(st);
+  d.box = dbox;
+  d.bst = dbst;
+  d.thermo = dth;
+  d.g = dg;
+  d.integ = dint;
+  if ((st = alloc_cells(s)) != MW_OK) return bad(st);
+  if ((st = alloc_nbr(s, initial_width(s))) != MW_OK) return bad(st);
+  if ((st = adjoint_alloc(s)) != MW_OK) return bad(st);
+  std::vector<int> bid(N);
+  for (int b = 0; b < nbox; ++b)
+    for (int k = 0; k < n[b]; ++k) bid[s->off[b] + k] = b;
+  cudaError_t e = cudaMemcpyAsync(s->boxid, bid.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) return bad(fail(MW_ECUDA, "upload failed: %s", cudaGetErrorString(e)));
+  if ((st = upload_boxes(s)) != MW_OK) return bad(st);
+  s->integ.dt = 0;
+  s->integ.cf = 0;
+  s->integ.ke_fac = 0.5 * s->mass / kFCONV;
+  s->integ.tau = 1;
+  s->integ.kind = TH_NVE;
+  s->integ.half_skin2 = (float)(0.25 * skin * skin);
+  if ((st = upload_integ(s)) != MW_OK) return bad(st);
+  Global g{};
+  e = cudaMemcpyAsync(d.g, &g, sizeof g, cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) return bad(fail(MW_ECUDA, "upload failed: %s", cudaGetErrorString(e)));
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return bad(fail(MW_ECUDA, "sync failed: %s", cudaGetErrorString(e)));
+  *out = s;
+  return MW_OK;
+}
+
+}  // namespace
+
+#include "mw_persistent_host.inc"
+#include "mw_adjoint_host.inc"
+
+extern "C" {
+
+const char* mw_last_error(void) { return g_err.c_str(); }
+
+mw_status mw_params_default(mw_params* out) {
+  if (!out) return fail(MW_EINVAL, "out is NULL");
+  // Sec. II.A (SW form: A, B, p, q, gamma, a, theta0) and Sec. II.D (mW: lambda, epsilon, sigma)
+  out->lambda = 23.15;
+  out->epsilon = 6.189;
+  out->sigma = 2.3925;
+  out->a = 1.8;
+  out->gamma = 1.2;
+  out->A = 7.049556277;
+  out->B = 0.6022245584;
+  out->cos_theta0 = -1.0 / 3.0;
+  out->p = 4;
+  out->q = 0;
+  return MW_OK;
+}
+
+mw_status mw_system_create(mw_system** out, int n, const double box[3], const mw_params* prm, double mass,
+                           double skin, void* stream) {
+  return create_common(out, 1, &n, box, prm, mass, skin, stream);
+}
+
+mw_status mw_batch_create(mw_system** out, int nbox, const int* n, const double* box, const mw_params* prm,
+                          double mass, double skin, void* stream) {
+  return create_common(out, nbox, n, box, prm, mass, skin, stream);
+}
+
+mw_status mw_system_destroy(mw_system* s) {
+  if (!s) return MW_OK;
+  if (s->stream || true) cudaStreamSynchronize(s->stream);
+  destroy_graphs(s);
+  for (void* p : s->allocs) cudaFree(p);
+  if (s->own_stream) cudaStreamDestroy(s->stream);
+  delete s;
+  return MW_OK;
+}
+
+mw_status mw_set_state(mw_system* s, const double* x, const double* v) { return do_set_state(s, x, v, false); }
+
+mw_status mw_set_state_dev(mw_system* s, const double* x_dev, const double* v_dev) {
+  return do_set_state(s, x_dev, v_dev, true);
+}
+
+mw_status mw_get_state(mw_system* s, double* x, double* v) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  if (!s->state_set) return fail(MW_ESTATE, "no state set");
+  const size_t bytes = sizeof(double) * 3 * (size_t)s->N;
+  k_gather_state<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, x ? s->d.stage : nullptr,
+                                                                     v ? s->d.stage2 : nullptr);
+  MW_CUDA(cudaGetLastError());
+  if (x) MW_CUDA(cudaMemcpyAsync(x, s->d.stage, bytes, cudaMemcpyDeviceToHost, s->stream));
+  if (v) MW_CUDA(cudaMemcpyAsync(v, s->d.stage2, bytes, cudaMemcpyDeviceToHost, s->stream));
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  return MW_OK;
+}
+
+mw_status mw_get_state_dev(mw_system* s, double* x_dev, double* v_dev) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  if (!s->state_set) return fail(MW_ESTATE, "no state set");
+  k_gather_state<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, x_dev, v_dev);
+  MW_CUDA(cudaGetLastError());
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  return MW_OK;
+}
+
+mw_status mw_set_params(mw_system* s, const mw_params* prm) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  mw_status st;
+  if ((st = check_params(prm)) != MW_OK) return st;
+  const mw_params old = s->prm;
+  s->prm = *prm;
+  int ncell;
+  if ((st = layout_cells(s, &ncell)) != MW_OK) {
+    s->prm = old;
+    layout_cells(s, &ncell);
+    return st;
+  }
+  make_fparams(s);
+  if (ncell != s->ncell) {
+    s->ncell = ncell;
+    if ((st = alloc_cells(s)) != MW_OK) return st;
+  }
+  if ((st = upload_boxes(s)) != MW_OK) return st;
+  s->graph_dirty = true;
+  s->forces_valid = false;
+  if (s->state_set) {
+    if ((st = set_global_field(s, offsetof(Global, any_rebuild), 1)) != MW_OK) return st;
+  }
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  return MW_OK;
+}
+
+mw_status mw_build_neighbors(mw_system* s, int* max_count_out) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  if (!s->state_set) return fail(MW_ESTATE, "no state set");
+  mw_status st;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    if ((st = set_global_field(s, offsetof(Global, any_rebuild), 1)) != MW_OK) return st;
+    launch_rebuild(s);
+    k_prep_force<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d, 0);  // list consumed
+    MW_CUDA(cudaGetLastError());
+    Global g;
+    if ((st = read_global(s, &g)) != MW_OK) return st;
+    if (g.status == ST_OVERFLOW) {
+      if ((st = grow_nbr_after_overflow(s, g)) != MW_OK) return st;
+      if ((st = set_global_field(s, offsetof(Global, status), 0)) != MW_OK) return st;
+      continue;
+    }
+    if (g.status) return status_error(g);
+    if ((st = set_global_field(s, offsetof(Global, any_rebuild), 0)) != MW_OK) return st;
+    MW_CUDA(cudaStreamSynchronize(s->stream));
+    s->forces_valid = false;  // atoms were re-sorted; stored forces no longer line up
+    s->list_built = true;
+    if (max_count_out) *max_count_out = g.max_count;
+    return MW_OK;
+  }
+  return fail(MW_ENLIST_OVERFLOW, "neighbour list kept overflowing");
+}
+
+mw_status mw_get_neighbors(mw_system* s, int* counts, int* nbr, int width) {
+  if (!s || !counts || !nbr || width < 1) return fail(MW_EINVAL, "bad arguments");
+  if (!s->state_set || !s->list_built) return fail(MW_ESTATE, "no neighbour list built yet");
+  int* dc;
+  int* dn;
+  mw_status st;
+  if ((st = dalloc(s, &dc, s->N)) != MW_OK) return st;
+  if ((st = dalloc(s, &dn, (size_t)s->N * width)) != MW_OK) {
+    dfree(s, dc);
+    return st;
+  }
+  k_gather_neighbors<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, dc, dn, width);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(counts, dc, sizeof(int) * s->N, cudaMemcpyDeviceToHost, s->stream);
+  // copy only the filled prefix per atom would need a host loop; copy all and let the caller read counts
+  std::vector<int> tmp;
+  if (e == cudaSuccess) {
+    tmp.resize((size_t)s->N * width);
+    e = cudaMemcpyAsync(tmp.data(), dn, sizeof(int) * tmp.size(), cudaMemcpyDeviceToHost, s->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  dfree(s, dc);
+  dfree(s, dn);
+  if (e != cudaSuccess) return fail(MW_ECUDA, "neighbour copy failed: %s", cudaGetErrorString(e));
+  for (int u = 0; u < s->N; ++u) {
+    const int m = std::min(counts[u], width);
+    std::memcpy(nbr + (size_t)u * width, tmp.data() + (size_t)u * width, sizeof(int) * m);
+  }
+  return MW_OK;
+}
+
+mw_status mw_energy_forces(mw_system* s, double* f, double* energy, double* virial) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  mw_status st;
+  if ((st = ensure_forces(s)) != MW_OK) return st;
+  if (f) {
+    k_gather_forces<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, s->d.stage, nullptr);
+    MW_CUDA(cudaGetLastError());
+    MW_CUDA(cudaMemcpyAsync(f, s->d.stage, sizeof(double) * 3 * (size_t)s->N, cudaMemcpyDeviceToHost, s->stream));
+  }
+  if (energy || virial) {
+    double* e = s->eout;
+    double* w = s->eout + 3 * (size_t)s->nbox;
+    k_energy_out<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d, e, w);
+    MW_CUDA(cudaGetLastError());
+    if (energy) MW_CUDA(cudaMemcpyAsync(energy, e, sizeof(double) * 3 * s->nbox, cudaMemcpyDeviceToHost, s->stream));
+    if (virial) MW_CUDA(cudaMemcpyAsync(virial, w, sizeof(double) * 6 * s->nbox, cudaMemcpyDeviceToHost, s->stream));
+  }
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  return MW_OK;
+}
+
+mw_status mw_energy_forces_dev(mw_system* s, const double* x_dev, float* f_dev, double* energy_dev,
+                               double* virial_dev) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  if (x_dev) {
+    if (!s->state_set) return do_set_state(s, x_dev, nullptr, true) == MW_OK ? mw_energy_forces_dev(s, nullptr, f_dev, energy_dev, virial_dev) : MW_ECUDA;
+    k_load_positions<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, x_dev, s->boxid, 0);
+    MW_CUDA(cudaGetLastError());
+    mw_status st;
+    if ((st = set_global_field(s, offsetof(Global, any_rebuild), 1)) != MW_OK) return st;
+    s->forces_valid = false;
+  }
+  mw_status st;
+  if ((st = ensure_forces(s)) != MW_OK) return st;
+  if (f_dev) k_gather_forces<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, nullptr, f_dev);
+  if (energy_dev || virial_dev)
+    k_energy_out<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d, energy_dev, virial_dev);
+  MW_CUDA(cudaGetLastError());
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  return MW_OK;
+}
+
+mw_status mw_forces_async(mw_system* s) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  mw_status st;
+  if ((st = ensure_forces(s)) != MW_OK) return st;
+  k_prep_force<<<div_up(std::max(s->N, s->nbox), kThreads), kThreads, 0, s->stream>>>(s->d, 1);
+  launch_force(s);
+  MW_CUDA(cudaGetLastError());
+  return MW_OK;
+}
+
+mw_status mw_step(mw_system* s, const mw_integrator* integ, int nsteps, mw_thermo* last) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  if (nsteps < 0) return fail(MW_EINVAL, "nsteps < 0");
+  mw_status st;
+  if ((st = validate_integ(s, integ)) != MW_OK) return st;
+  if ((st = ensure_forces(s)) != MW_OK) return st;
+  if (nsteps > 0) {
+    int eng = s->engine;
+    if (eng == MW_ENGINE_AUTO) eng = s->tuned_engine >= 0 ? s->tuned_engine : MW_ENGINE_PERSISTENT;
+    if (eng == MW_ENGINE_PERSISTENT && !persistent_available(s)) eng = MW_ENGINE_GRAPH;
+    s->engine_used = eng;
+    st = eng == MW_ENGINE_PERSISTENT ? run_persistent_engine(s, nsteps) : run_graph_engine(s, nsteps);
+    if (st != MW_OK) return st;
+    s->list_built = true;
+  }
+  if (last) return mw_get_thermo(s, last);
+  return MW_OK;
+}
+
+mw_status mw_step_async(mw_system* s, const mw_integrator* integ, int nsteps) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  if (nsteps < 0) return fail(MW_EINVAL, "nsteps < 0");
+  mw_status st;
+  if ((st = validate_integ(s, integ)) != MW_OK) return st;
+  if ((st = ensure_forces(s)) != MW_OK) return st;
+  if (nsteps == 0) return MW_OK;
+  int eng = s->engine;
+  if (eng == MW_ENGINE_AUTO) eng = s->tuned_engine >= 0 ? s->tuned_engine : MW_ENGINE_PERSISTENT;
+  if (eng == MW_ENGINE_PERSISTENT && !persistent_available(s)) eng = MW_ENGINE_GRAPH;
+  s->engine_used = eng;
+  if (eng == MW_ENGINE_PERSISTENT) return enqueue_persistent(s, nsteps);
+  if (s->graph_dirty || !s->graph1) {
+    if ((st = capture_graphs(s, 16)) != MW_OK) return st;
+  }
+  for (int k = 0; k < nsteps / s->graphK_steps; ++k) MW_CUDA(cudaGraphLaunch(s->graphK, s->stream));
+  for (int k = 0; k < nsteps % s->graphK_steps; ++k) MW_CUDA(cudaGraphLaunch(s->graph1, s->stream));
+  return MW_OK;
+}
+
+mw_status mw_sync(mw_system* s) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  Global g;
+  mw_status st;
+  if ((st = read_global(s, &g)) != MW_OK) return st;
+  s->host_step = (long long)g.step;
+  return status_error(g);
+}
+
+mw_status mw_get_thermo(mw_system* s, mw_thermo* out) {
+  if (!s || !out) return fail(MW_EINVAL, "bad arguments");
+  if (!s->state_set) return fail(MW_ESTATE, "no state set");
+  mw_status st;
+  if ((st = ensure_forces(s)) != MW_OK) return st;
+  std::vector<double> t((size_t)s->nbox * TR_N);
+  MW_CUDA(cudaMemcpyAsync(t.data(), s->d.thermo, sizeof(double) * t.size(), cudaMemcpyDeviceToHost, s->stream));
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  for (int b = 0; b < s->nbox; ++b) {
+    const double* r = t.data() + (size_t)b * TR_N;
+    mw_thermo& o = out[b];
+    o.step = (int64_t)r[TR_STEP];
+    o.pe = r[TR_PE];
+    o.e2 = r[TR_E2];
+    o.e3 = r[TR_E3];
+    o.ke = r[TR_KE];
+    o.temperature = r[TR_T];
+    o.conserved = r[TR_CONS];
+    o.pressure = r[TR_P];
+    for (int k = 0; k < 6; ++k) o.virial[k] = r[TR_W0 + k];
+    o.xi = r[TR_XI];
+    o.eta = r[TR_ETA];
+    o.rebuilds = (int64_t)r[TR_REBUILDS];
+  }
+  return MW_OK;
+}
+
+mw_status mw_set_engine(mw_system* s, int engine) {
+  if (!s || engine < MW_ENGINE_AUTO || engine > MW_ENGINE_PERSISTENT) return fail(MW_EINVAL, "bad engine");
+  s->engine = engine;
+  return MW_OK;
+}
+
+mw_status mw_set_nbr_width(mw_system* s, int width) {
+  if (!s || width < 1) return fail(MW_EINVAL, "bad width");
+  mw_status st;
+  if ((st = alloc_nbr(s, width)) != MW_OK) return st;
+  // Forces at the current positions stay valid; the list is rebuilt in the
+  // rebuild phase of the next step (or of the next force evaluation).
+  if (s->state_set) {
+    if ((st = set_global_field(s, offsetof(Global, any_rebuild), 1)) != MW_OK) return st;
+  }
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  return MW_OK;
+}
+
+mw_status mw_get_info(mw_system* s, mw_info* out) {
+  if (!s || !out) return fail(MW_EINVAL, "bad arguments");
+  Global g{};
+  mw_status st;
+  if ((st = read_global(s, &g)) != MW_OK) return st;
+  out->nbox = s->nbox;
+  out->n_total = s->N;
+  out->nbr_width = s->W;
+  out->max_count = g.max_count;
+  out->ncell_total = s->ncell;
+  out->engine = s->engine_used;
+  out->persistent_blocks = s->pers_blocks;
+  out->persistent_threads = kPersThreads;
+  out->r_list = r_list(s);
+  out->npairs = s->npairs;
+  out->ntriplets = s->ntrip;
+  return MW_OK;
+}
+
+// Diagnostic switch (not in mw.h's stable set): count legs and triplets in
+// the force kernel (atomics; slows it down).
+mw_status mw_set_count_terms(mw_system* s, int on) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  s->count_terms = on ? 1 : 0;
+  s->forces_valid = false;
+  s->graph_dirty = true;
+  mw_status st;
+  if ((st = set_global_field(s, offsetof(Global, count_terms), s->count_terms)) != MW_OK) return st;
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  return MW_OK;
+}
+
+}  // extern "C"

@@ -146,3 +146,37 @@ def batch_boxes(nbox: int = 256, seed: int = BASE_SEED + 3, **kw):
         boxes.append(box)
         vs.append(maxwell_velocities(int(n[b]), float(T[b]), seed=seed * 1000 + 500000 + b))
     return n, np.array(boxes), np.concatenate(xs), np.concatenate(vs), T
+
+
+def lattice_fill(n: int, lo, hi, rho_hint: float, jitter: float = 0.1, seed: int = 0) -> np.ndarray:
+    """n atoms on a jittered orthorhombic grid filling the region [lo, hi)
+    (n of the grid sites picked by a seeded permutation)."""
+    rng = np.random.default_rng(seed)
+    lo = np.asarray(lo, float)
+    ext = np.asarray(hi, float) - lo
+    s0 = volume_per_molecule(rho_hint) ** (1.0 / 3.0)
+    mx = max(1, int(round(ext[0] / s0)))
+    my = max(1, int(round(ext[1] / s0)))
+    mz = max(1, int(math.ceil(n / (mx * my))))
+    gx = (np.arange(mx) + 0.5) * ext[0] / mx
+    gy = (np.arange(my) + 0.5) * ext[1] / my
+    gz = (np.arange(mz) + 0.5) * ext[2] / mz
+    sites = np.stack(np.meshgrid(gx, gy, gz, indexing="ij"), -1).reshape(-1, 3)
+    pick = np.sort(rng.permutation(len(sites))[:n])
+    return lo + sites[pick] + rng.normal(0.0, jitter, (n, 3))
+
+
+def ice_liquid_slab(nx: int = 64, ny: int = 32, nz: int = 32, rho_ice: float = 0.92, rho_liq: float = 0.9998,
+                    seed: int = BASE_SEED + 5):
+    """Ice Ih slab (nx*ny*nz orthorhombic cells, 8 atoms each) with an equal
+    number of liquid-start atoms stacked above it along z at rho_liq (jittered
+    grid start; the liquid forms once dynamics run).  Returns (x, box, is_ice)."""
+    xi, bi = ice_ih(nx, ny, nz, rho_ice)
+    xi = xi + np.array([0.0, 0.0, bi[2] / nz / 16.0])  # centre the ice layers in [0, Lz_ice)
+    n_liq = len(xi)
+    lz = n_liq * volume_per_molecule(rho_liq) / (bi[0] * bi[1])
+    xl = lattice_fill(n_liq, [0.0, 0.0, bi[2]], [bi[0], bi[1], bi[2] + lz], rho_liq, 0.1, seed)
+    box = np.array([bi[0], bi[1], bi[2] + lz])
+    x = np.concatenate([xi, xl])
+    is_ice = np.concatenate([np.ones(len(xi), bool), np.zeros(n_liq, bool)])
+    return x, box, is_ice

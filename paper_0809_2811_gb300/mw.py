@@ -1,0 +1,364 @@
+"""Thin Python binding of libmw (include/mw.h): same names, argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays
+or torch tensors to pointers and raises MWError on a non-zero mw_status.
+There is no CPU fallback: if libmw.so is missing or cannot reach a GPU the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmw.so")
+
+MW_OK, MW_EINVAL, MW_EBOX, MW_ENLIST_OVERFLOW, MW_ENAN, MW_ELOST, MW_ETIMEOUT, MW_ECUDA, MW_ENOMEM, MW_ESTATE = range(10)
+STATUS_NAMES = {0: "MW_OK", 1: "MW_EINVAL", 2: "MW_EBOX", 3: "MW_ENLIST_OVERFLOW", 4: "MW_ENAN", 5: "MW_ELOST",
+                6: "MW_ETIMEOUT", 7: "MW_ECUDA", 8: "MW_ENOMEM", 9: "MW_ESTATE"}
+MW_NVE, MW_BERENDSEN, MW_NOSE_HOOVER = 0, 1, 2
+MW_ENGINE_AUTO, MW_ENGINE_GRAPH, MW_ENGINE_PERSISTENT = 0, 1, 2
+
+# every symbol include/mw.h declares
+EXPORTS = (
+    "mw_params_default", "mw_system_create", "mw_batch_create", "mw_system_destroy", "mw_set_state",
+    "mw_set_state_dev", "mw_get_state", "mw_get_state_dev", "mw_set_params", "mw_build_neighbors",
+    "mw_get_neighbors", "mw_energy_forces", "mw_energy_forces_dev", "mw_step", "mw_get_thermo",
+    "mw_energy_forces_vjp", "mw_set_engine", "mw_set_nbr_width", "mw_autotune", "mw_get_info",
+    "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_last_error",
+)
+
+
+class mw_params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("epsilon", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("a", ctypes.c_double), ("gamma", ctypes.c_double), ("A", ctypes.c_double),
+                ("B", ctypes.c_double), ("cos_theta0", ctypes.c_double), ("p", ctypes.c_int),
+                ("q", ctypes.c_int)]
+
+
+class mw_integrator(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("thermostat", ctypes.c_int), ("T0", ctypes.c_double),
+                ("T0_per_box", ctypes.POINTER(ctypes.c_double)), ("tau", ctypes.c_double)]
+
+
+class mw_thermo(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("pe", ctypes.c_double), ("e2", ctypes.c_double),
+                ("e3", ctypes.c_double), ("ke", ctypes.c_double), ("temperature", ctypes.c_double),
+                ("conserved", ctypes.c_double), ("pressure", ctypes.c_double),
+                ("virial", ctypes.c_double * 6), ("xi", ctypes.c_double), ("eta", ctypes.c_double),
+                ("rebuilds", ctypes.c_int64)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "virial"}
+        d["virial"] = list(self.virial)
+        return d
+
+
+class mw_info(ctypes.Structure):
+    _fields_ = [("nbox", ctypes.c_int), ("n_total", ctypes.c_int), ("nbr_width", ctypes.c_int),
+                ("max_count", ctypes.c_int), ("ncell_total", ctypes.c_int), ("engine", ctypes.c_int),
+                ("persistent_blocks", ctypes.c_int), ("persistent_threads", ctypes.c_int),
+                ("r_list", ctypes.c_double), ("npairs", ctypes.c_int64), ("ntriplets", ctypes.c_int64)]
+
+
+class MWError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Loads libmw.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libmw.so not built ({LIB_PATH}); run paper_0809_2811_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.c_void_p
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        sig = {
+            "mw_params_default": [ctypes.POINTER(mw_params)],
+            "mw_system_create": [ctypes.POINTER(P), ctypes.c_int, dp, ctypes.POINTER(mw_params), ctypes.c_double,
+                                 ctypes.c_double, P],
+            "mw_batch_create": [ctypes.POINTER(P), ctypes.c_int, ip, dp, ctypes.POINTER(mw_params), ctypes.c_double,
+                                ctypes.c_double, P],
+            "mw_system_destroy": [P],
+            "mw_set_state": [P, dp, dp],
+            "mw_set_state_dev": [P, P, P],
+            "mw_get_state": [P, dp, dp],
+            "mw_get_state_dev": [P, P, P],
+            "mw_set_params": [P, ctypes.POINTER(mw_params)],
+            "mw_build_neighbors": [P, ip],
+            "mw_get_neighbors": [P, ip, ip, ctypes.c_int],
+            "mw_energy_forces": [P, dp, dp, dp],
+            "mw_energy_forces_dev": [P, P, P, P, P],
+            "mw_step": [P, ctypes.POINTER(mw_integrator), ctypes.c_int, ctypes.POINTER(mw_thermo)],
+            "mw_get_thermo": [P, ctypes.POINTER(mw_thermo)],
+            "mw_energy_forces_vjp": [P, P, P, dp],
+            "mw_set_engine": [P, ctypes.c_int],
+            "mw_set_nbr_width": [P, ctypes.c_int],
+            "mw_autotune": [P, ctypes.POINTER(mw_integrator), ctypes.c_int, ip],
+            "mw_get_info": [P, ctypes.POINTER(mw_info)],
+            "mw_set_count_terms": [P, ctypes.c_int],
+            "mw_forces_async": [P],
+            "mw_step_async": [P, ctypes.POINTER(mw_integrator), ctypes.c_int],
+            "mw_sync": [P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.mw_last_error.argtypes = []
+        L.mw_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != MW_OK:
+        raise MWError(st, lib().mw_last_error().decode())
+
+
+def _dp(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _ptr(t) -> Optional[int]:
+    """Device pointer of a torch tensor (or an int), None for None."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+# ----------------------------------------------------------------- C names
+
+def mw_params_default() -> mw_params:
+    p = mw_params()
+    _check(lib().mw_params_default(ctypes.byref(p)))
+    return p
+
+
+def mw_system_create(n: int, box, prm: Optional[mw_params] = None, mass: float = 18.015, skin: float = 1.0,
+                     stream: Optional[int] = None) -> int:
+    prm = prm or mw_params_default()
+    b = np.ascontiguousarray(box, np.float64)
+    h = ctypes.c_void_p()
+    _check(lib().mw_system_create(ctypes.byref(h), int(n), _dp(b), ctypes.byref(prm), mass, skin, stream))
+    return h.value
+
+
+def mw_batch_create(n: Sequence[int], box, prm: Optional[mw_params] = None, mass: float = 18.015,
+                    skin: float = 1.0, stream: Optional[int] = None) -> int:
+    prm = prm or mw_params_default()
+    nn = np.ascontiguousarray(n, np.int32)
+    b = np.ascontiguousarray(box, np.float64).reshape(-1, 3)
+    h = ctypes.c_void_p()
+    _check(lib().mw_batch_create(ctypes.byref(h), len(nn), _ip(nn), _dp(b), ctypes.byref(prm), mass, skin, stream))
+    return h.value
+
+
+def mw_system_destroy(h: int):
+    _check(lib().mw_system_destroy(h))
+
+
+def mw_set_state(h: int, x, v=None):
+    x = np.ascontiguousarray(x, np.float64)
+    v = None if v is None else np.ascontiguousarray(v, np.float64)
+    _check(lib().mw_set_state(h, _dp(x), _dp(v)))
+
+
+def mw_set_state_dev(h: int, x_dev, v_dev=None):
+    _check(lib().mw_set_state_dev(h, _ptr(x_dev), _ptr(v_dev)))
+
+
+def mw_get_state(h: int, n_total: int):
+    x = np.empty((n_total, 3))
+    v = np.empty((n_total, 3))
+    _check(lib().mw_get_state(h, _dp(x), _dp(v)))
+    return x, v
+
+
+def mw_get_state_dev(h: int, x_dev=None, v_dev=None):
+    _check(lib().mw_get_state_dev(h, _ptr(x_dev), _ptr(v_dev)))
+
+
+def mw_set_params(h: int, prm: mw_params):
+    _check(lib().mw_set_params(h, ctypes.byref(prm)))
+
+
+def mw_build_neighbors(h: int) -> int:
+    m = ctypes.c_int()
+    _check(lib().mw_build_neighbors(h, ctypes.byref(m)))
+    return m.value
+
+
+def mw_get_neighbors(h: int, n_total: int, width: int):
+    counts = np.zeros(n_total, np.int32)
+    nbr = np.full((n_total, width), -1, np.int32)
+    _check(lib().mw_get_neighbors(h, _ip(counts), _ip(nbr), width))
+    return counts, nbr
+
+
+def mw_energy_forces(h: int, n_total: int, nbox: int):
+    f = np.empty((n_total, 3))
+    e = np.empty((nbox, 3))
+    w = np.empty((nbox, 6))
+    _check(lib().mw_energy_forces(h, _dp(f), _dp(e), _dp(w)))
+    return f, e, w
+
+
+def mw_energy_forces_dev(h: int, x_dev=None, f_dev=None, energy_dev=None, virial_dev=None):
+    _check(lib().mw_energy_forces_dev(h, _ptr(x_dev), _ptr(f_dev), _ptr(energy_dev), _ptr(virial_dev)))
+
+
+def make_integrator(dt=10.0, thermostat=MW_NVE, T0=300.0, tau=1000.0, T0_per_box=None):
+    it = mw_integrator()
+    it.dt = dt
+    it.thermostat = thermostat
+    it.T0 = T0
+    it.tau = tau
+    if T0_per_box is not None:
+        arr = np.ascontiguousarray(T0_per_box, np.float64)
+        it._keep = arr
+        it.T0_per_box = _dp(arr)
+    return it
+
+
+def mw_step(h: int, integ: mw_integrator, nsteps: int, nbox: int = 1):
+    th = (mw_thermo * nbox)()
+    _check(lib().mw_step(h, ctypes.byref(integ), int(nsteps), th))
+    return [t.as_dict() for t in th]
+
+
+def mw_get_thermo(h: int, nbox: int = 1):
+    th = (mw_thermo * nbox)()
+    _check(lib().mw_get_thermo(h, th))
+    return [t.as_dict() for t in th]
+
+
+def mw_energy_forces_vjp(h: int, dL_dF_dev, dL_dx_dev, nbox: int = 1):
+    g = np.zeros((nbox, 3))
+    _check(lib().mw_energy_forces_vjp(h, _ptr(dL_dF_dev), _ptr(dL_dx_dev), _dp(g)))
+    return g
+
+
+def mw_set_engine(h: int, engine: int):
+    _check(lib().mw_set_engine(h, engine))
+
+
+def mw_set_nbr_width(h: int, width: int):
+    _check(lib().mw_set_nbr_width(h, width))
+
+
+def mw_autotune(h: int, integ: mw_integrator, steps: int = 50) -> int:
+    e = ctypes.c_int()
+    _check(lib().mw_autotune(h, ctypes.byref(integ), steps, ctypes.byref(e)))
+    return e.value
+
+
+def mw_get_info(h: int) -> dict:
+    i = mw_info()
+    _check(lib().mw_get_info(h, ctypes.byref(i)))
+    return {k: getattr(i, k) for k, _ in i._fields_}
+
+
+def mw_set_count_terms(h: int, on: bool):
+    _check(lib().mw_set_count_terms(h, 1 if on else 0))
+
+
+def mw_forces_async(h: int):
+    _check(lib().mw_forces_async(h))
+
+
+def mw_step_async(h: int, integ: mw_integrator, nsteps: int):
+    _check(lib().mw_step_async(h, ctypes.byref(integ), int(nsteps)))
+
+
+def mw_sync(h: int):
+    _check(lib().mw_sync(h))
+
+
+def mw_last_error() -> str:
+    return lib().mw_last_error().decode()
+
+
+# ----------------------------------------------------------------- convenience
+
+class System:
+    """One box (n atoms, box[3]) or a batch (n = list, box = [nbox, 3]) on the GPU."""
+
+    def __init__(self, n, box, prm: Optional[mw_params] = None, mass: float = 18.015, skin: float = 1.0,
+                 stream: Optional[int] = None):
+        if np.ndim(n) == 0:
+            self.nbox = 1
+            self.n = [int(n)]
+            self.h = mw_system_create(int(n), box, prm, mass, skin, stream)
+        else:
+            self.nbox = len(n)
+            self.n = [int(k) for k in n]
+            self.h = mw_batch_create(n, box, prm, mass, skin, stream)
+        self.n_total = int(sum(self.n))
+
+    def close(self):
+        if self.h:
+            mw_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_state(self, x, v=None):
+        mw_set_state(self.h, x, v)
+
+    def get_state(self):
+        return mw_get_state(self.h, self.n_total)
+
+    def energy_forces(self):
+        return mw_energy_forces(self.h, self.n_total, self.nbox)
+
+    def build_neighbors(self):
+        return mw_build_neighbors(self.h)
+
+    def neighbors(self, width: int = 128):
+        return mw_get_neighbors(self.h, self.n_total, width)
+
+    def step(self, nsteps: int, dt=10.0, thermostat=MW_NVE, T0=300.0, tau=1000.0, T0_per_box=None):
+        it = make_integrator(dt, thermostat, T0, tau, T0_per_box)
+        return mw_step(self.h, it, nsteps, self.nbox)
+
+    def thermo(self):
+        return mw_get_thermo(self.h, self.nbox)
+
+    def info(self):
+        return mw_get_info(self.h)
+
+    def set_engine(self, engine: int):
+        mw_set_engine(self.h, engine)
+
+    def set_params(self, prm: mw_params):
+        mw_set_params(self.h, prm)
+
+    def set_count_terms(self, on: bool):
+        mw_set_count_terms(self.h, on)

@@ -18,3 +18,15 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def mwlib():
+    """The CUDA library binding; builds libmw.so if needed.  GPU tests only."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test collected without a CUDA device")
+    from paper_0809_2811_gb300 import build, mw
+    build.build()
+    mw.lib()
+    return mw

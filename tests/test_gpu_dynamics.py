@@ -1,0 +1,124 @@
+"""GPU velocity-Verlet dynamics vs the oracle's, through the C ABI.
+
+Short trajectories (20 steps) are compared state by state; FP32 forces make
+the two diverge slowly (the dynamics are chaotic), so the tolerances grow
+with the number of steps.  Longer runs are checked on conserved quantities:
+the paper reports energy conserved better than 1e-4 over 1e6 NVE steps at
+dt = 10 fs (Sec. II.B).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_0809_2811_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _min_image(d, box):
+    return d - box * np.rint(d / box)
+
+
+def _run_pair(mwlib, orc, x, v, box, nsteps, kind, T0=298.0, tau=1000.0, dt=10.0, engine=None):
+    x = I.snap_to_grid(x, box)
+    s = mwlib.System(len(x), box)
+    try:
+        if engine is not None:
+            s.set_engine(engine)
+        s.set_state(x, v)
+        th = s.step(nsteps, dt=dt, thermostat=kind, T0=T0, tau=tau)[0]
+        xg, vg = s.get_state()
+    finally:
+        s.close()
+    xo, vo, st, tho = orc.md(x, v, box, nsteps, dt=dt, kind=kind, T0=T0, tau=tau)
+    return th, xg, vg, tho[-1], xo, vo, st
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_short_trajectory_matches_oracle(mwlib, orc, kind):
+    x, v, box = I.nve512()
+    th, xg, vg, tho, xo, vo, st = _run_pair(mwlib, orc, x, v, box, 20, kind, T0=250.0, tau=200.0)
+    # FP32 force error ~1e-6 relative gives ~1e-5 A after 200 fs; allow 5x
+    assert np.abs(_min_image(xg - xo, box)).max() < 5e-5
+    assert np.abs(vg - vo).max() < 1e-6
+    assert th["pe"] == pytest.approx(tho[0], rel=3e-6)
+    assert th["ke"] == pytest.approx(tho[3], rel=1e-5)
+    assert th["conserved"] == pytest.approx(tho[5], rel=3e-6)
+    if kind == 2:
+        assert th["xi"] == pytest.approx(st[0], rel=1e-4, abs=1e-9)
+        assert th["eta"] == pytest.approx(st[1], rel=1e-4, abs=1e-9)
+    assert th["step"] == 20
+
+
+def test_nve_drift_512(mwlib):
+    """Config of the paper's energy-conservation statement, scaled to 1000 steps."""
+    x, v, box = I.nve512()
+    s = mwlib.System(512, box)
+    try:
+        s.set_state(x, v)
+        e0 = s.thermo()[0]["conserved"]
+        es = []
+        for _ in range(10):
+            es.append(s.step(100, dt=10.0)[0]["conserved"])
+    finally:
+        s.close()
+    es = np.array(es)
+    assert np.abs(es - e0).max() / abs(e0) < 1e-4
+
+
+def test_nose_hoover_conserved_quantity(mwlib):
+    x, v, box = I.nve512()
+    s = mwlib.System(512, box)
+    try:
+        s.set_state(x, v * math.sqrt(1.3))
+        c0 = s.step(1, dt=10.0, thermostat=2, T0=298.0, tau=1000.0)[0]["conserved"]
+        th = s.step(600, dt=10.0, thermostat=2, T0=298.0, tau=1000.0)[0]
+    finally:
+        s.close()
+    assert abs(th["conserved"] - c0) / abs(c0) < 2e-4
+
+
+def test_batch_dynamics_matches_oracle_per_box(mwlib, orc):
+    n = [216, 343, 290]
+    rho = [0.95, 1.0, 1.08]
+    T = [220.0, 260.0, 310.0]
+    xs, vs, boxes = [], [], []
+    for k in range(3):
+        x, b = I.jittered_box(n[k], rho[k], 0.1, 300 + k)
+        xs.append(I.snap_to_grid(x, b))
+        vs.append(I.maxwell_velocities(n[k], T[k], seed=400 + k))
+        boxes.append(b)
+    s = mwlib.System(n, np.array(boxes))
+    try:
+        s.set_state(np.concatenate(xs), np.concatenate(vs))
+        th = s.step(15, dt=10.0, thermostat=2, T0_per_box=T, tau=300.0)
+        xg, vg = s.get_state()
+    finally:
+        s.close()
+    off = 0
+    for k in range(3):
+        xo, vo, st, tho = orc.md(xs[k], vs[k], boxes[k], 15, dt=10.0, kind=2, T0=T[k], tau=300.0)
+        assert np.abs(_min_image(xg[off:off + n[k]] - xo, boxes[k])).max() < 5e-5
+        assert th[k]["pe"] == pytest.approx(tho[-1, 0], rel=3e-6)
+        assert th[k]["ke"] == pytest.approx(tho[-1, 3], rel=1e-5)
+        assert th[k]["xi"] == pytest.approx(st[0], rel=1e-4, abs=1e-9)
+        off += n[k]
+
+
+def test_step_survives_list_overflow(mwlib, orc):
+    """A neighbour list too narrow mid-run is grown and the step resumed."""
+    x, v, box = I.nve512()
+    x = I.snap_to_grid(x, box)
+    s = mwlib.System(512, box)
+    try:
+        s.set_state(x, v)
+        s.step(5, dt=10.0)
+        mwlib.mw_set_nbr_width(s.h, 6)
+        th = s.step(15, dt=10.0)[0]
+        xg, _ = s.get_state()
+    finally:
+        s.close()
+    xo, vo, st, tho = orc.md(x, v, box, 20, dt=10.0)
+    assert th["step"] == 20
+    assert np.abs(_min_image(xg - xo, box)).max() < 5e-5

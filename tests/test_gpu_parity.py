@@ -1,0 +1,210 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (stated by the method's specification of this engine):
+  * neighbour sets bit-exact, except pairs within the band
+    | |d|^2 - r_list^2 | <= 1e-5 r_list^2 (FP32 vs FP64 distance; reported);
+  * per-atom forces: max_i |F_gpu,i - F_ref,i| / max(|F_ref,i|, F_rms) <= 1e-5;
+  * energies (E, E2, E3) within 1e-6 relative; virial within 1e-6 of sum |W_aa|.
+The oracle is fed the same positions the kernels see: inputs are snapped to
+the 2^-32 box-fraction grid of the device's fixed-point coordinates.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_0809_2811_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+F_TOL = 1e-5
+E_TOL = 1e-6
+
+
+def force_err(fg, fr):
+    fr = np.asarray(fr).reshape(-1, 3)
+    fg = np.asarray(fg).reshape(-1, 3)
+    mag = np.linalg.norm(fr, axis=1)
+    frms = math.sqrt(np.mean(mag ** 2)) if len(mag) else 1.0
+    den = np.maximum(mag, frms)
+    return float((np.linalg.norm(fg - fr, axis=1) / den).max())
+
+
+def check_box(mwlib, orc, x, box, v=None, neighbors=True):
+    x = I.snap_to_grid(np.asarray(x, float), box)
+    ref = orc.energy_forces(x, box)
+    s = mwlib.System(len(x), box)
+    try:
+        s.set_state(x, v)
+        f, e, w = s.energy_forces()
+        assert force_err(f, ref["forces"]) <= F_TOL
+        for k, name in ((0, "energy"), (1, "e2"), (2, "e3")):
+            scale = max(abs(ref[name]), 1e-12 * len(x))
+            assert abs(e[0, k] - ref[name]) <= E_TOL * max(scale, abs(ref["energy"])), name
+        wscale = np.abs(ref["virial"][:3]).sum()
+        assert np.abs(w[0] - ref["virial"]).max() <= E_TOL * max(wscale, 1.0)
+        if neighbors:
+            check_neighbors(s, orc, x, box)
+        return s, ref, f
+    except Exception:
+        s.close()
+        raise
+
+
+def check_neighbors(s, orc, x, box):
+    info = s.info()
+    rl = info["r_list"]
+    sets, band = orc.neighbors(x, box, rl, band_rel=1e-5)
+    counts, nbr = s.neighbors(width=max(info["max_count"], 1))
+    mism = 0
+    for i in range(len(x)):
+        g = set(nbr[i, :counts[i]].tolist())
+        r = set(sets[i].tolist())
+        diff = g.symmetric_difference(r)
+        diff = {j for j in diff if (i, j) not in band}
+        mism += len(diff)
+        assert len(g) == counts[i], "duplicate neighbour entries"
+    assert mism == 0
+
+
+CASES = {
+    "sc512_nve_start": lambda: I.nve512()[0::2],
+    "ice_ih_288": lambda: I.ice_ih(4, 3, 3, 0.92),
+    "ice_ic_216": lambda: I.diamond_cubic(3, 0.92),
+    "liquidlike_1000": lambda: I.jittered_box(1000, 1.0, 0.3, 101),
+    "dense_729_rho1.10": lambda: I.jittered_box(729, 1.10, 0.3, 102),
+    "ragged_1237": lambda: I.jittered_box(1237, 0.97, 0.25, 103),
+    "slab_2048": lambda: I.ice_liquid_slab(8, 4, 4)[:2],
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_energy_forces_parity(mwlib, orc, case):
+    x, box = CASES[case]()
+    s, _, _ = check_box(mwlib, orc, x, box)
+    s.close()
+
+
+def test_overflow_legs_path(mwlib, orc):
+    """Dense box (about 20 legs per atom): centres beyond the 16 register legs
+    take the overflow kernel; results must not change."""
+    x, box = I.jittered_box(512, 1.7, 0.15, 104)
+    s, ref, _ = check_box(mwlib, orc, x, box)
+    s.close()
+
+
+def test_tiny_systems(mwlib, orc):
+    # two atoms inside the cutoff: pair term only
+    box = np.array([12.0, 12.0, 12.0])
+    s, ref, f = check_box(mwlib, orc, np.array([[1.0, 1.0, 1.0], [3.7, 1.2, 0.9]]), box)
+    assert ref["ntriplets"] == 0 and ref["npairs"] == 1
+    s.close()
+    # three atoms: one triplet per centre that has two legs
+    s, ref, f = check_box(mwlib, orc, np.array([[1.0, 1.0, 1.0], [3.7, 1.2, 0.9], [1.5, 3.6, 1.1]]), box)
+    assert ref["ntriplets"] >= 1
+    s.close()
+    # two atoms far apart: all zero
+    s, ref, f = check_box(mwlib, orc, np.array([[1.0, 1.0, 1.0], [7.0, 7.0, 7.0]]), box)
+    assert np.abs(f).max() == 0.0
+    s.close()
+    # across the periodic boundary (minimum image)
+    s, ref, f = check_box(mwlib, orc, np.array([[0.2, 11.9, 6.0], [11.5, 0.8, 6.3], [0.5, 1.9, 5.0]]), box)
+    s.close()
+
+
+def test_box_at_two_list_radii(mwlib, orc):
+    """Edge = 2 r_list gives 2 cells per dimension: the stencil must not visit a cell twice."""
+    p = orc.default_params()
+    rl = p[3] * p[2] + 1.0
+    L = 2 * rl + 1e-9
+    rng = np.random.default_rng(5)
+    x = I.simple_cubic(4, L, 0.0) + rng.normal(0, 0.2, (64, 3))
+    s, _, _ = check_box(mwlib, orc, x, np.array([L, L, L]))
+    s.close()
+
+
+def test_batch_parity(mwlib, orc):
+    n = [216, 300, 517, 1000, 250]
+    rho = [0.92, 1.0, 1.05, 0.97, 1.10]
+    xs, boxes = [], []
+    for k, (nn, r) in enumerate(zip(n, rho)):
+        x, b = I.jittered_box(nn, r, 0.25, 200 + k)
+        xs.append(I.snap_to_grid(x, b))
+        boxes.append(b)
+    s = mwlib.System(n, np.array(boxes))
+    try:
+        s.set_state(np.concatenate(xs))
+        f, e, w = s.energy_forces()
+        off = 0
+        for b in range(len(n)):
+            ref = orc.energy_forces(xs[b], boxes[b])
+            assert force_err(f[off:off + n[b]], ref["forces"]) <= F_TOL
+            assert abs(e[b, 0] - ref["energy"]) <= E_TOL * abs(ref["energy"])
+            assert abs(e[b, 2] - ref["e3"]) <= E_TOL * abs(ref["energy"])
+            assert np.abs(w[b] - ref["virial"]).max() <= E_TOL * np.abs(ref["virial"][:3]).sum()
+            off += n[b]
+    finally:
+        s.close()
+
+
+def test_state_roundtrip_and_wrap(mwlib):
+    x, v, box = I.nve512()
+    x = x + np.array([25.0, -50.0, 3.0])  # outside the box: wrapped on entry
+    s = mwlib.System(512, box)
+    try:
+        s.set_state(x, v)
+        x2, v2 = s.get_state()
+        np.testing.assert_allclose(x2, np.mod(x, box), atol=1e-12)
+        np.testing.assert_array_equal(v2, v)
+    finally:
+        s.close()
+
+
+def test_count_terms_matches_oracle(mwlib, orc):
+    x, box = I.jittered_box(1000, 1.0, 0.3, 101)
+    x = I.snap_to_grid(x, box)
+    ref = orc.energy_forces(x, box)
+    s = mwlib.System(len(x), box)
+    try:
+        s.set_count_terms(True)
+        s.set_state(x)
+        s.energy_forces()
+        info = s.info()
+        assert info["npairs"] == ref["npairs"]
+        assert info["ntriplets"] == ref["ntriplets"]
+    finally:
+        s.close()
+
+
+def test_neighbor_overflow_recovery(mwlib, orc):
+    """A list far too narrow is grown internally and results do not change."""
+    x, box = I.jittered_box(729, 1.0, 0.25, 105)
+    x = I.snap_to_grid(x, box)
+    ref = orc.energy_forces(x, box)
+    s = mwlib.System(len(x), box)
+    try:
+        mwlib.mw_set_nbr_width(s.h, 4)
+        s.set_state(x)
+        f, e, _ = s.energy_forces()
+        assert force_err(f, ref["forces"]) <= F_TOL
+        assert s.info()["nbr_width"] > 4
+    finally:
+        s.close()
+
+
+def test_rejects_bad_input(mwlib):
+    with pytest.raises(mwlib.MWError) as ei:
+        mwlib.System(64, [9.0, 9.0, 9.0])  # shorter than 2 r_list
+    assert ei.value.status == mwlib.MW_EBOX
+    s = mwlib.System(8, [20.0, 20.0, 20.0])
+    try:
+        x = np.zeros((8, 3))
+        x[3, 1] = np.nan
+        with pytest.raises(mwlib.MWError) as ei:
+            s.set_state(x)
+        assert ei.value.status == mwlib.MW_EINVAL
+        with pytest.raises(mwlib.MWError) as ei:
+            s.energy_forces()
+        assert ei.value.status == mwlib.MW_ESTATE
+    finally:
+        s.close()

@@ -111,17 +111,19 @@ def _check(rc, what):
 
 
 def energy_forces(x, box, prm=None, method="cell"):
-    """Returns dict(e2, e3, energy, forces (n,3), virial[6], npairs, ntriplets)."""
+    """Returns dict(e2, e3, energy, forces (n,3), virial[6], npairs, ntriplets,
+    virial_abs): virial_abs is the summed magnitude of the diagonal virial
+    contributions, the scale against which the (cancelling) trace is judged."""
     prm = default_params() if prm is None else np.ascontiguousarray(prm, np.float64)
     x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
     box = np.ascontiguousarray(box, np.float64)
     n = x.shape[0]
     f = np.zeros((n, 3))
-    out = np.zeros(10)
+    out = np.zeros(11)
     fn = lib().or_energy_forces_cell if method == "cell" else lib().or_energy_forces_brute
     _check(fn(_dp(prm), n, _dp(x), _dp(box), _dp(f), _dp(out)), "energy_forces")
     return dict(e2=out[0], e3=out[1], energy=out[0] + out[1], forces=f, virial=out[2:8].copy(),
-                npairs=int(out[8]), ntriplets=int(out[9]))
+                npairs=int(out[8]), ntriplets=int(out[9]), virial_abs=out[10])
 
 
 def neighbors(x, box, rlist, band_rel=1e-5, width=256, band_cap=100000):

@@ -132,8 +132,11 @@ static void min_image(const double* box, double* d) {
   for (int k = 0; k < 3; ++k) d[k] -= box[k] * nearbyint(d[k] / box[k]);
 }
 
-/* virial accumulation: W[xx,yy,zz,xy,xz,yz] += d (x) F */
+/* virial accumulation: W[xx,yy,zz,xy,xz,yz] += d (x) F; W[6] collects
+ * |d_x F_x| + |d_y F_y| + |d_z F_z|, the summed magnitude of the diagonal
+ * contributions (the conditioning scale of the trace, which cancels). */
 static void add_virial(double* W, const double* d, const double* F) {
+  W[6] += fabs(d[0] * F[0]) + fabs(d[1] * F[1]) + fabs(d[2] * F[2]);
   W[0] += d[0] * F[0];
   W[1] += d[1] * F[1];
   W[2] += d[2] * F[2];
@@ -144,14 +147,15 @@ static void add_virial(double* W, const double* d, const double* F) {
 
 /*
  * Brute force.  out[0]=E2, out[1]=E3, out[2..7]=W, out[8]=#pairs (r<a sig),
- * out[9]=#triplets (centre, unordered leg pair, both legs < a sig).
+ * out[9]=#triplets (centre, unordered leg pair, both legs < a sig),
+ * out[10]=sum over terms and legs of |d_a F_a| (a = x, y, z).
  * f may be NULL.  Requires every box edge >= 2 a sig.
  */
 int or_energy_forces_brute(const double* prm, int n, const double* x, const double* box, double* f,
                            double* out) {
   const double rc = prm[3] * prm[2];
   if (n < 0 || box[0] < 2 * rc || box[1] < 2 * rc || box[2] < 2 * rc) return OR_EINVAL;
-  double E2 = 0, E3 = 0, W[6] = {0, 0, 0, 0, 0, 0};
+  double E2 = 0, E3 = 0, W[7] = {0, 0, 0, 0, 0, 0, 0};
   double npair = 0, ntrip = 0;
   if (f) memset(f, 0, sizeof(double) * 3 * (size_t)n);
   for (int i = 0; i < n; ++i) {
@@ -206,6 +210,7 @@ int or_energy_forces_brute(const double* prm, int n, const double* x, const doub
   for (int k = 0; k < 6; ++k) out[2 + k] = W[k];
   out[8] = npair;
   out[9] = ntrip;
+  out[10] = W[6];
   return OR_OK;
 }
 
@@ -321,7 +326,7 @@ int or_energy_forces_cell(const double* prm, int n, const double* x, const doubl
   }
   int cap = 64;
   or_leg* legs = (or_leg*)malloc(sizeof(or_leg) * (size_t)cap);
-  double E2 = 0, E3 = 0, W[6] = {0, 0, 0, 0, 0, 0};
+  double E2 = 0, E3 = 0, W[7] = {0, 0, 0, 0, 0, 0, 0};
   double npair = 0, ntrip = 0;
   if (f) memset(f, 0, sizeof(double) * 3 * (size_t)n);
   for (int i = 0; i < n; ++i) {
@@ -383,6 +388,7 @@ int or_energy_forces_cell(const double* prm, int n, const double* x, const doubl
   for (int k = 0; k < 6; ++k) out[2 + k] = W[k];
   out[8] = npair;
   out[9] = ntrip;
+  out[10] = W[6];
   return OR_OK;
 }
 
@@ -484,7 +490,7 @@ int or_md(const double* prm, int n, double* x, double* v, const double* box, dou
   if (n < 2 || kind < 0 || kind > 2) return OR_EINVAL;
   double* f = (double*)malloc(sizeof(double) * 3 * (size_t)n);
   if (!f) return OR_ENOMEM;
-  double out[10];
+  double out[11];
   for (int i = 0; i < 3 * n; ++i) x[i] = wrap1(x[i], box[i % 3]);
   int rc = or_energy_forces_cell(prm, n, x, box, f, out);
   if (rc != OR_OK) {

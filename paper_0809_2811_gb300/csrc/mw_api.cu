@@ -251,12 +251,12 @@ void launch_rebuild(mw_system* s) {
 
 void launch_force(mw_system* s) {
   const Dev& d = s->d;
-  const int gb = div_up(s->N, kForceThreads);
+  const int gb = div_up(s->N, kFAtoms);
   if (s->count_terms) {
-    k_force<true><<<gb, kForceThreads, sizeof(LegSm), s->stream>>>(d, s->fp);
+    k_force<true><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
     k_force_overflow<true><<<64, 128, 0, s->stream>>>(d, s->fp);
   } else {
-    k_force<false><<<gb, kForceThreads, sizeof(LegSm), s->stream>>>(d, s->fp);
+    k_force<false><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
     k_force_overflow<false><<<64, 128, 0, s->stream>>>(d, s->fp);
   }
 }
@@ -273,8 +273,6 @@ void launch_step(mw_system* s) {
 mw_status set_func_attrs() {
   static bool done = false;
   if (done) return MW_OK;
-  MW_CUDA(cudaFuncSetAttribute(k_force<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LegSm)));
-  MW_CUDA(cudaFuncSetAttribute(k_force<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LegSm)));
   mw_status st = persistent_func_attrs();
   if (st != MW_OK) return st;
   done = true;
@@ -351,8 +349,15 @@ mw_status finish_interrupted_step(mw_system* s) {
   return MW_OK;
 }
 
+mw_status prime_thermostat(mw_system* s) {
+  k_prime_thermostat<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d);
+  MW_CUDA(cudaGetLastError());
+  return MW_OK;
+}
+
 mw_status run_graph_engine(mw_system* s, int nsteps) {
   mw_status st;
+  if ((st = prime_thermostat(s)) != MW_OK) return st;
   const int K = 16;
   if (s->graph_dirty || !s->graph1) {
     if ((st = capture_graphs(s, K)) != MW_OK) return st;
@@ -413,6 +418,7 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   for (auto& b : bs) {
     std::memset(&b, 0, sizeof b);
     b.s_end = 1.0;
+    b.s_kick = 1.0;
     b.rebuild = 1;
   }
   MW_CUDA(cudaMemcpyAsync(s->d.bst, bs.data(), sizeof(BoxState) * s->nbox, cudaMemcpyHostToDevice, s->stream));
@@ -453,6 +459,7 @@ mw_status validate_integ(mw_system* s, const mw_integrator* in) {
   Integ I{};
   I.dt = in->dt;
   I.cf = 0.5 * in->dt * kFCONV / s->mass;
+  I.cf_f = (float)I.cf;
   I.ke_fac = 0.5 * s->mass / kFCONV;
   I.tau = in->thermostat == MW_NVE ? 1.0 : in->tau;
   I.kind = in->thermostat;
@@ -510,6 +517,7 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
       bx.qs[k] = 4294967296.0 / bx.L[k];
       bx.Lq[k] = (float)(bx.L[k] / 4294967296.0);
     }
+    bx.lost = (float)(0.5 * std::min(bx.L[0], std::min(bx.L[1], bx.L[2])));
     bx.off = o;
     bx.n = n[b];
     bx.Ndf = 3.0 * n[b] - 3.0;
@@ -825,6 +833,7 @@ mw_status mw_step_async(mw_system* s, const mw_integrator* integ, int nsteps) {
   if (eng == MW_ENGINE_AUTO) eng = s->tuned_engine >= 0 ? s->tuned_engine : MW_ENGINE_PERSISTENT;
   if (eng == MW_ENGINE_PERSISTENT && !persistent_available(s)) eng = MW_ENGINE_GRAPH;
   s->engine_used = eng;
+  if ((st = prime_thermostat(s)) != MW_OK) return st;
   if (eng == MW_ENGINE_PERSISTENT) return enqueue_persistent(s, nsteps);
   if (s->graph_dirty || !s->graph1) {
     if ((st = capture_graphs(s, 16)) != MW_OK) return st;

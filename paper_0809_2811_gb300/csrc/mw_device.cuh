@@ -14,7 +14,7 @@
 //                    the box edge; the minimum-image difference of two atoms
 //                    is the wrapping int32 difference, converted once to FP32
 //   f                float4 forces (w unused), accumulated with red.global
-//   nbr              int32 [W][N] neighbour list (slot-major), nbr_cnt[N]
+//   nbr              int32 [N][W] neighbour list (atom-major rows), nbr_cnt[N]
 //   cell_start       exclusive scan of atoms per cell, ncell + 1 entries
 #pragma once
 
@@ -33,14 +33,15 @@ enum : int { ST_OK = 0, ST_OVERFLOW = 3, ST_NAN = 4, ST_LOST = 5, ST_TIMEOUT = 6
 
 enum : int { TH_NVE = 0, TH_BERENDSEN = 1, TH_NH = 2 };
 
-// Legs kept in registers per centre atom in the fused force kernel; centres
-// with more legs take the overflow path.
-constexpr int kMaxLegs = 16;
+// Legs staged per centre atom in the fused force kernel's shared-memory table;
+// centres with more legs take the overflow path.
+constexpr int kLMax = 32;
 // Upper bound for the overflow path (more legs than this = overlapping atoms).
 constexpr int kMaxLegsOverflow = 64;
 
 struct Box {        // read-only in kernels
   double L[3];
+  float lost;       // half the shortest edge (A): larger one-step moves are errors
   double qs[3];     // 2^32 / L
   float Lq[3];      // L / 2^32
   int off, n;       // atom range
@@ -52,6 +53,7 @@ struct Box {        // read-only in kernels
 struct BoxState {   // mutated by kernels
   double xi[2], eta[2];   // [0] after the end-of-step half, [1] after the start-of-step half
   double s_end;           // pending velocity scale: true v = stored v * s_end
+  double s_kick;          // scale applied by the next kick1: s_end times the next start half
   double ke_last;         // kinetic energy after the last end half (kcal/mol)
   double ke_acc[2];       // per step-parity accumulators of the raw kinetic energy
   double ew[2][8];        // per step-parity E2, E3, W[6]
@@ -81,6 +83,7 @@ struct Global {
 struct Integ {
   double dt;
   double cf;         // 0.5 dt FCONV / mass
+  float cf_f;        // the same in FP32 (velocity increment = cf_f * F in FP32, added in FP64)
   double ke_fac;     // 0.5 mass / FCONV
   double tau;
   int kind;
@@ -145,13 +148,15 @@ __device__ __forceinline__ int cell_of(const uint4& q, const Box& bx) {
 
 __device__ __forceinline__ void set_status(Global* g, int st) { atomicCAS(&g->status, 0, st); }
 
-// Per-box FP64 accumulation of NV values.  Every thread of the block calls it
-// (b < 0 for threads without an atom).  Atoms are box-major, so the box ids
-// along a warp are non-decreasing: a segmented warp scan sums each box run;
-// runs of the block's first and last box are merged in shared memory and
-// flushed with one global atomic per value, other runs go to global directly.
+// Per-box accumulation of NV values held as FP32 by each thread; the sums
+// over threads are FP64.  Every thread of the block calls it (b < 0 for
+// threads without a contribution).  Atoms are box-major, so box ids along a
+// warp are non-decreasing: a segmented FP32 scan sums each run of one box
+// within the warp (32 atoms at most), the run totals are widened to FP64 and
+// merged in shared memory for the block's first and last box (one global
+// atomic per value and block), other runs go to global memory directly.
 template <int NV, class Dst>
-__device__ void box_accumulate(double (&v)[NV], int b, bool is_last_valid, Dst dst) {
+__device__ void box_accumulate(float (&v)[NV], int b, bool is_last_valid, Dst dst) {
   __shared__ double sacc[2][NV];
   __shared__ int sbox[2];
   const int lane = threadIdx.x & 31;
@@ -167,7 +172,7 @@ __device__ void box_accumulate(double (&v)[NV], int b, bool is_last_valid, Dst d
     const int bo = __shfl_up_sync(kFull, b, off);
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      const double vo = __shfl_up_sync(kFull, v[k], off);
+      const float vo = __shfl_up_sync(kFull, v[k], off);
       if (lane >= off && bo == b) v[k] += vo;
     }
   }
@@ -178,11 +183,11 @@ __device__ void box_accumulate(double (&v)[NV], int b, bool is_last_valid, Dst d
     const int slot = (b == sbox[0]) ? 0 : ((b == sbox[1]) ? 1 : -1);
     if (slot >= 0) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) atomicAdd(&sacc[slot][k], v[k]);
+      for (int k = 0; k < NV; ++k) atomicAdd(&sacc[slot][k], (double)v[k]);
     } else {
       double* p = dst(b);
 #pragma unroll
-      for (int k = 0; k < NV; ++k) atomicAdd(p + k, v[k]);
+      for (int k = 0; k < NV; ++k) atomicAdd(p + k, (double)v[k]);
     }
   }
   __syncthreads();
@@ -203,49 +208,71 @@ __device__ __forceinline__ double nh_half(double& ke, double& xi, double& eta, d
   return s;
 }
 
-// Velocity scale applied at the start of a step for box b: the pending
-// end-of-step scale of the previous step times this step's start-half scale.
-// The writer (the thread owning the box's first atom) also stores the
-// thermostat state after the start half and clears this step's accumulators.
-__device__ double kick1_scale_of_box(const Dev& d, int b, const Integ& I, bool writer, int par) {
+// Start-of-step thermostat half of box b, evaluated once per box at the end
+// of the previous step (or by k_prime_thermostat before the first step of a
+// call): stores the state after the start half in slot 1 and the velocity
+// scale the next kick1 applies (pending end scale times start scale).
+__device__ void start_half_box(const Dev& d, const Integ& I, int b) {
   BoxState* st = d.bst + b;
   const Box& bx = d.box[b];
-  double s = st->s_end;
   double xi = st->xi[0], eta = st->eta[0];
+  double s = 1.0;
   if (I.kind == TH_NH) {
     double ke = st->ke_last;
-    s *= nh_half(ke, xi, eta, I.dt, bx.Ndf, kKB * bx.T0, bx.Q);
+    s = nh_half(ke, xi, eta, I.dt, bx.Ndf, kKB * bx.T0, bx.Q);
   }
-  if (writer) {
-    st->xi[1] = xi;
-    st->eta[1] = eta;
-    st->ke_acc[par] = 0.0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) st->ew[par][k] = 0.0;
-  }
-  return s;
+  st->xi[1] = xi;
+  st->eta[1] = eta;
+  st->s_kick = st->s_end * s;
 }
 
 // ---------------------------------------------------------------------------
 // Phase bodies (one item each) shared by the per-phase kernels and the
 // persistent kernel.
 
-// a1 + a7 (first half): v = v*s + dt/2 a; x += dt v; wrap; fixed-point copy;
+// a1 + a7 (first half): v = s v + dt/2 a; x += dt v; wrap; fixed-point copy;
 // displacement check against the last build.  Also zeroes f for this step.
-__device__ __forceinline__ void kick1_item(const Dev& d, const Integ& I, int i, double s, int b) {
+// FP64: the velocity and position updates and the fixed-point conversion
+// (5 FP64-pipe instructions per component); the increment cf*F is formed in
+// FP32 from the FP32 force.
+__device__ __forceinline__ double wrap_slow(double x, double L, double invL) {
+  x -= L * floor(x * invL);
+  if (x >= L) x -= L;
+  if (x < 0.0) x = 0.0;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t advance_coord(double& x, double& v, double s, float dv, const Integ& I, double L,
+                                                  double qs) {
+  v = fma(v, s, (double)dv);
+  x = fma(I.dt, v, x);
+  long long q = __double2ll_rn(x * qs);
+  if ((unsigned long long)q > 0xffffffffull) {  // left [0, L): crossed a face (rare)
+    x = wrap_slow(x, L, 1.0 / L);
+    q = __double2ll_rn(x * qs);
+  }
+  return (uint32_t)(unsigned long long)q;  // 2^32 (x rounding up to L) wraps to 0
+}
+
+__device__ __forceinline__ void kick1_item(const Dev& d, const Integ& I, int i, int b, int par) {
   const Box& bx = d.box[b];
+  BoxState* st = d.bst + b;
+  const double s = st->s_kick;
+  if (i == bx.off) {  // this step's accumulators start from zero
+    st->ke_acc[par] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) st->ew[par][k] = 0.0;
+  }
   const float4 F = d.f[i];
   d.f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const double vx = d.vx[i] * s + I.cf * (double)F.x;
-  const double vy = d.vy[i] * s + I.cf * (double)F.y;
-  const double vz = d.vz[i] * s + I.cf * (double)F.z;
-  double px = d.x[i] + I.dt * vx, py = d.y[i] + I.dt * vy, pz = d.z[i] + I.dt * vz;
-  if (px >= bx.L[0]) px -= bx.L[0]; else if (px < 0.0) px += bx.L[0];
-  if (py >= bx.L[1]) py -= bx.L[1]; else if (py < 0.0) py += bx.L[1];
-  if (pz >= bx.L[2]) pz -= bx.L[2]; else if (pz < 0.0) pz += bx.L[2];
+  double vx = d.vx[i], vy = d.vy[i], vz = d.vz[i];
+  double px = d.x[i], py = d.y[i], pz = d.z[i];
+  const uint32_t q0 = advance_coord(px, vx, s, I.cf_f * F.x, I, bx.L[0], bx.qs[0]);
+  const uint32_t q1 = advance_coord(py, vy, s, I.cf_f * F.y, I, bx.L[1], bx.qs[1]);
+  const uint32_t q2 = advance_coord(pz, vz, s, I.cf_f * F.z, I, bx.L[2], bx.qs[2]);
   d.vx[i] = vx; d.vy[i] = vy; d.vz[i] = vz;
   d.x[i] = px; d.y[i] = py; d.z[i] = pz;
-  const uint4 qn = make_uint4(to_fixed(px, bx.qs[0]), to_fixed(py, bx.qs[1]), to_fixed(pz, bx.qs[2]), (unsigned)b);
+  const uint4 qn = make_uint4(q0, q1, q2, (unsigned)b);
   d.q[i] = qn;
   const uint4 qb = d.qb[i];
   const float dx = fix_diff(qb.x, qn.x, bx.Lq[0]);
@@ -255,36 +282,24 @@ __device__ __forceinline__ void kick1_item(const Dev& d, const Integ& I, int i, 
     d.bst[b].rebuild = 1;
     d.g->any_rebuild = 1;
   }
-  const double step2 = I.dt * I.dt * (vx * vx + vy * vy + vz * vz);
-  const double lmin = fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
-  if (!(step2 < 0.25 * lmin * lmin)) {
-    set_status(d.g, (step2 == step2) ? ST_LOST : ST_NAN);
+  const float sv = (float)I.dt * (fabsf((float)vx) + fabsf((float)vy) + fabsf((float)vz));
+  if (!(sv < bx.lost)) {  // moved more than half the shortest edge in one step, or NaN
+    set_status(d.g, (sv == sv) ? ST_LOST : ST_NAN);
     d.g->err_index = i;
   }
 }
 
-// Warp-cooperative scale: one evaluation per distinct box in the warp.
-__device__ __forceinline__ double warp_kick1_scale(const Dev& d, const Integ& I, int i, int b, int par) {
-  const int lane = threadIdx.x & 31;
-  const int b0 = __shfl_sync(kFull, b, 0);
-  const bool uni = __all_sync(kFull, b == b0 || b < 0);
-  if (uni) {
-    double t = 1.0;
-    if (lane == 0 && b0 >= 0) t = kick1_scale_of_box(d, b0, I, i == d.box[b0].off, par);
-    return __shfl_sync(kFull, t, 0);
-  }
-  return (b >= 0) ? kick1_scale_of_box(d, b, I, i == d.box[b].off, par) : 1.0;
-}
-
-// a7 (second half) for one atom; returns its raw kinetic energy.
-__device__ __forceinline__ double kick2_item(const Dev& d, const Integ& I, int i) {
+// a7 (second half) for one atom; returns its raw kinetic energy (FP32 per
+// atom; the sums over atoms are FP64).
+__device__ __forceinline__ float kick2_item(const Dev& d, const Integ& I, int i) {
   const float4 F = d.f[i];
-  const double vx = d.vx[i] + I.cf * (double)F.x;
-  const double vy = d.vy[i] + I.cf * (double)F.y;
-  const double vz = d.vz[i] + I.cf * (double)F.z;
+  const double vx = d.vx[i] + (double)(I.cf_f * F.x);
+  const double vy = d.vy[i] + (double)(I.cf_f * F.y);
+  const double vz = d.vz[i] + (double)(I.cf_f * F.z);
   d.vx[i] = vx; d.vy[i] = vy; d.vz[i] = vz;
-  const double ke = I.ke_fac * (vx * vx + vy * vy + vz * vz);
-  if (!(ke < 1e30)) {
+  const float fx = (float)vx, fy = (float)vy, fz = (float)vz;
+  const float ke = (float)I.ke_fac * fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+  if (!(ke < 1e30f)) {
     set_status(d.g, ST_NAN);
     d.g->err_index = i;
   }
@@ -311,6 +326,7 @@ __device__ void end_of_step_box(const Dev& d, const Integ& I, int b, int par, un
   st->ke_last = ke;
   st->xi[0] = xi;
   st->eta[0] = eta;
+  start_half_box(d, I, b);
   double* t = d.thermo + (size_t)b * TR_N;
   const double e2 = __ldcg(&st->ew[par][0]), e3 = __ldcg(&st->ew[par][1]);
   double w[6];
@@ -388,7 +404,7 @@ __device__ void neigh_warp(const Dev& d, int i, float rl2) {
     }
     const unsigned bal = __ballot_sync(kFull, pred);
     const int pos = m + __popc(bal & ((1u << lane) - 1u));
-    if (pred && pos < d.W) d.nbr[(size_t)pos * d.N + i] = j;
+    if (pred && pos < d.W) d.nbr[(size_t)i * d.W + pos] = j;
     m += __popc(bal);
   }
   if (lane == 0) {
@@ -399,156 +415,228 @@ __device__ void neigh_warp(const Dev& d, int i, float rl2) {
 }
 
 // ---------------------------------------------------------------------------
-// Fused two- + three-body force.  One thread per centre atom i:
-//   pass 1: walk the neighbour list, keep legs r < a sig; pair term (owner
-//           computes: half energy, full force on i, half virial); stage leg
-//           data in shared memory;
-//   pass 2: legs to registers (compile-time indices);
-//   pass 3: all leg pairs j < k: three-body energy and forces on j and k;
-//   pass 4: scatter leg forces with red.global.add.v4.f32, force on i,
-//           per-leg virial; FP64 per-box reduction of E2, E3, W.
-// Leg data: u (unit vector i->j), tr = 2/r, nde = gam sig/(r - a sig)^2,
-// ee = sqrt(lam eps) exp(gam sig/(r - a sig)).
-//   phi3 = ee_j ee_k D^2, D = u_j.u_k - cos th0
-//   F_j  = -g [tr_j (u_k - c u_j) - D nde_j u_j],  g = ee_j ee_k D
-constexpr int kForceThreads = 128;
+// Fused two- + three-body force (k_force).  A block holds kFAtoms centre atoms.
+//   leg phase: kG lanes per centre walk its neighbour row; every pair with
+//     r < a sig is a leg: the pair term is taken by the owner (half energy,
+//     full force on the centre, half virial) and the leg is compacted (ballot
+//     + popc within the lane group) into the centre's row of a padded
+//     shared-memory leg table;
+//   triplet phase: the (centre, leg j) items of a warp are spread evenly over
+//     its 32 lanes; an item runs over every other leg k of the same centre
+//     and accumulates the three-body force on j in registers (each unordered
+//     triplet is visited from both of its legs; its energy is counted once);
+//     the force on j goes out with one red.global.add.v4.f32, its reaction on
+//     the centre through a shared-memory sum;
+//   per-box FP64 reduction of E2, E3 and the virial.
+// Leg data: u (unit vector i->j), ee = sqrt(lam eps) exp(gam sig/(r - a sig)),
+// tr = 2/r, nde = gam sig/(r - a sig)^2, r, j.  With c = u_j.u_k and
+// D = c - cos th0, phi3 = ee_j ee_k D^2 and the force on j is
+//   F_j = -g tr_j u_k + g (c tr_j + D nde_j) u_j,   g = ee_j ee_k D.
+constexpr int kG = 4;                    // lanes per centre in the leg phase
+constexpr int kFThreads = 128;
+constexpr int kFAtoms = kFThreads / kG;  // centres per block
+constexpr int kWAtoms = 32 / kG;         // centres per warp
+constexpr int kLPad = kLMax + 1;         // row pitch (float4): shifts rows by 4 banks
 
-struct LegSm {  // shared-memory leg staging, field-major per thread for conflict-free access
-  float v[8][kMaxLegs][kForceThreads];
+struct LegTable {
+  float4 ue[kFAtoms * kLPad];   // ux, uy, uz, ee
+  float4 aux[kFAtoms * kLPad];  // tr, nde, r, j (int bits)
+  float fi[kFAtoms][4];         // three-body reaction on the centre
+  int nl[kFAtoms];
 };
 
 template <bool kCount>
-__device__ __forceinline__ void force_item(const Dev& d, const FParams& P, int i, LegSm* sm, float (&acc)[8],
-                                           int& nl_out) {
-  const int t = threadIdx.x;
-  const uint4 qi = d.q[i];
-  const Box& bx = d.box[qi.w];
-  const float L0 = bx.Lq[0], L1 = bx.Lq[1], L2 = bx.Lq[2];
-  int cnt = d.nbr_cnt[i];
-  if (cnt > d.W) cnt = d.W;
-  float fix = 0.f, fiy = 0.f, fiz = 0.f;
+__global__ void __launch_bounds__(kFThreads) k_force(Dev d, FParams P) {
+  if (d.g->status) return;
+  __shared__ LegTable T;
+  const int par = (int)(d.g->step & 1ull);
+  const int lane = threadIdx.x & 31;
+  const int g = threadIdx.x & (kG - 1);
+  const int a = threadIdx.x / kG;
+  const int i = blockIdx.x * kFAtoms + a;
+  const bool valid = i < d.N;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // E2, E3, W xx yy zz xy xz yz
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  uint4 qi = make_uint4(0u, 0u, 0u, 0u);
+  int cnt = 0, b = -1;
+  float L0 = 0.f, L1 = 0.f, L2 = 0.f;
+  if (valid) {
+    qi = d.q[i];
+    b = (int)qi.w;
+    cnt = min(d.nbr_cnt[i], d.W);
+    const Box& bx = d.box[b];
+    L0 = bx.Lq[0];
+    L1 = bx.Lq[1];
+    L2 = bx.Lq[2];
+  }
+  T.fi[a][g] = 0.f;
+  // ---- leg phase
+  const int iters = __reduce_max_sync(kFull, (cnt + kG - 1) / kG);
+  const unsigned gsh = lane & ~(kG - 1);
+  const int* row = d.nbr + (size_t)(valid ? i : 0) * d.W;
   int nl = 0;
-  for (int s = 0; s < cnt; ++s) {
-    const int j = __ldg(d.nbr + (size_t)s * d.N + i);
-    const uint4 qj = d.q[j];
-    const float dx = fix_diff(qi.x, qj.x, L0), dy = fix_diff(qi.y, qj.y, L1), dz = fix_diff(qi.z, qj.z, L2);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (r2 >= P.rc2) continue;
-    const float invr = rsqrtf(r2);
-    const float r = r2 * invr;
-    if (!(r < P.rc)) continue;
-    const float ux = dx * invr, uy = dy * invr, uz = dz * invr;
-    const float tinv = __frcp_rn(r - P.rc);  // 1/(r - a sig) < 0
-    const float e2 = exp2f(P.sig_l2e * tinv);
-    const float e3 = exp2f(P.gsig_l2e * tinv);
-    const float sr = P.sig * invr;
-    const float srp = powi(sr, P.p), srq = powi(sr, P.q);
-    const float brk = fmaf(P.B, srp, -srq);
-    const float phi = P.Aeps * brk * e2;
-    const float dphi = P.Aeps * e2 * fmaf((float)(-P.p) * P.B, srp, (float)P.q * srq) * invr -
-                       P.Aeps * e2 * brk * P.sig * tinv * tinv;
-    acc[0] = fmaf(0.5f, phi, acc[0]);
-    fix = fmaf(dphi, ux, fix);
-    fiy = fmaf(dphi, uy, fiy);
-    fiz = fmaf(dphi, uz, fiz);
-    const float wv = -0.5f * dphi * r;
-    acc[2] = fmaf(wv * ux, ux, acc[2]);
-    acc[3] = fmaf(wv * uy, uy, acc[3]);
-    acc[4] = fmaf(wv * uz, uz, acc[4]);
-    acc[5] = fmaf(wv * ux, uy, acc[5]);
-    acc[6] = fmaf(wv * ux, uz, acc[6]);
-    acc[7] = fmaf(wv * uy, uz, acc[7]);
-    if (nl < kMaxLegs) {
-      sm->v[0][nl][t] = ux;
-      sm->v[1][nl][t] = uy;
-      sm->v[2][nl][t] = uz;
-      sm->v[3][nl][t] = 2.0f * invr;
-      sm->v[4][nl][t] = P.gsig * tinv * tinv;
-      sm->v[5][nl][t] = P.sle * e3;
-      sm->v[6][nl][t] = r;
-      sm->v[7][nl][t] = __int_as_float(j);
+  for (int t = 0; t < iters; ++t) {
+    const int s = g + kG * t;
+    bool leg = false;
+    float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 1.f;
+    int j = 0;
+    if (s < cnt) {
+      j = __ldg(row + s);
+      const uint4 qj = d.q[j];
+      dx = fix_diff(qi.x, qj.x, L0);
+      dy = fix_diff(qi.y, qj.y, L1);
+      dz = fix_diff(qi.z, qj.z, L2);
+      r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      leg = r2 < P.rc2;
     }
-    ++nl;
+    float4 ue = make_float4(0.f, 0.f, 0.f, 0.f), ax = ue;
+    if (leg) {
+      const float invr = rsqrtf(r2);
+      const float r = r2 * invr;
+      leg = r < P.rc;
+      if (leg) {
+        const float ux = dx * invr, uy = dy * invr, uz = dz * invr;
+        const float tinv = __frcp_rn(r - P.rc);  // 1/(r - a sig) < 0
+        const float e2 = exp2f(P.sig_l2e * tinv);
+        const float e3 = exp2f(P.gsig_l2e * tinv);
+        const float sr = P.sig * invr;
+        const float srp = powi(sr, P.p), srq = powi(sr, P.q);
+        const float brk = fmaf(P.B, srp, -srq);
+        const float ae2 = P.Aeps * e2;
+        const float phi = ae2 * brk;
+        const float dphi = ae2 * (fmaf((float)(-P.p) * P.B, srp, (float)P.q * srq) * invr - brk * P.sig * tinv * tinv);
+        acc[0] = fmaf(0.5f, phi, acc[0]);
+        fx = fmaf(dphi, ux, fx);
+        fy = fmaf(dphi, uy, fy);
+        fz = fmaf(dphi, uz, fz);
+        const float wv = -0.5f * dphi * r;
+        acc[2] = fmaf(wv * ux, ux, acc[2]);
+        acc[3] = fmaf(wv * uy, uy, acc[3]);
+        acc[4] = fmaf(wv * uz, uz, acc[4]);
+        acc[5] = fmaf(wv * ux, uy, acc[5]);
+        acc[6] = fmaf(wv * ux, uz, acc[6]);
+        acc[7] = fmaf(wv * uy, uz, acc[7]);
+        ue = make_float4(ux, uy, uz, P.sle * e3);
+        ax = make_float4(2.0f * invr, P.gsig * tinv * tinv, r, __int_as_float(j));
+      }
+    }
+    const unsigned m = (__ballot_sync(kFull, leg) >> gsh) & ((1u << kG) - 1u);
+    const int pos = nl + __popc(m & ((1u << g) - 1u));
+    if (leg && pos < kLMax) {
+      T.ue[a * kLPad + pos] = ue;
+      T.aux[a * kLPad + pos] = ax;
+    }
+    nl += __popc(m);
   }
-  nl_out = nl;
-  if (kCount) {
-    atomicAdd((unsigned long long*)&d.g->npairs, (unsigned long long)nl);
-  }
-  if (nl > kMaxLegs) {
-    // three-body part handled by the overflow kernel; pair part is complete
-    red_add_v4(d.f + i, fix, fiy, fiz);
-    const int slot = atomicAdd(&d.g->n_over, 1);
-    if (slot < d.N) d.over[slot] = i;
-    return;
-  }
-  if (kCount) atomicAdd((unsigned long long*)&d.g->ntrip, (unsigned long long)(nl * (nl - 1) / 2));
-  float ux[kMaxLegs], uy[kMaxLegs], uz[kMaxLegs], tr[kMaxLegs], nde[kMaxLegs], ee[kMaxLegs];
-  float ax[kMaxLegs], ay[kMaxLegs], az[kMaxLegs];
+  if (g == 0) T.nl[a] = valid ? nl : 0;
+  __syncwarp();
+  // ---- triplet phase: items (centre of this warp, leg j), spread over the lanes
+  const int a0 = (threadIdx.x >> 5) * kWAtoms;
+  int pre[kWAtoms + 1];
+  pre[0] = 0;
 #pragma unroll
-  for (int k = 0; k < kMaxLegs; ++k) {
-    ax[k] = ay[k] = az[k] = 0.f;
-    if (k < nl) {
-      ux[k] = sm->v[0][k][t];
-      uy[k] = sm->v[1][k][t];
-      uz[k] = sm->v[2][k][t];
-      tr[k] = sm->v[3][k][t];
-      nde[k] = sm->v[4][k][t];
-      ee[k] = sm->v[5][k][t];
-    } else {
-      ux[k] = uy[k] = uz[k] = tr[k] = nde[k] = ee[k] = 0.f;
-    }
+  for (int k = 0; k < kWAtoms; ++k) {
+    int n = T.nl[a0 + k];
+    if (n > kLMax) n = 0;  // overflow centres: triplets in k_force_overflow
+    pre[k + 1] = pre[k] + n;
   }
-  float e3acc = 0.f;
+  const int b0 = __shfl_sync(kFull, b, 0);
+  const bool wuni = __all_sync(kFull, b == b0 || b < 0);
   const float c0 = P.c0;
+  for (int it = lane; it < pre[kWAtoms]; it += 32) {
+    int ka = 0, first = 0, n = 0;
 #pragma unroll
-  for (int j = 0; j < kMaxLegs - 1; ++j) {
-    if (j + 1 >= nl) break;
-#pragma unroll
-    for (int k = j + 1; k < kMaxLegs; ++k) {
-      if (k >= nl) break;
-      const float c = fmaf(ux[j], ux[k], fmaf(uy[j], uy[k], uz[j] * uz[k]));
+    for (int k = 0; k < kWAtoms; ++k)  // the centre whose item range holds it
+      if (it >= pre[k] && it < pre[k + 1]) {
+        ka = k;
+        first = pre[k];
+        n = pre[k + 1] - pre[k];
+      }
+    const int aa = a0 + ka;
+    const int jj = it - first;
+    const float4* rowu = T.ue + aa * kLPad;
+    const float4 uj = rowu[jj];
+    const float4 xj = T.aux[aa * kLPad + jj];
+    float gx = 0.f, gy = 0.f, gz = 0.f, e3 = 0.f;
+    for (int k = 0; k < n; ++k) {
+      const float4 uk = rowu[k];
+      const float c = fmaf(uj.x, uk.x, fmaf(uj.y, uk.y, uj.z * uk.z));
       const float D = c - c0;
-      const float g = ee[j] * ee[k] * D;
-      e3acc = fmaf(g, D, e3acc);
-      const float aj = g * tr[j];
-      const float bj = g * fmaf(c, tr[j], D * nde[j]);  // = -(g (D de_j - c tr_j)), de = -nde
-      ax[j] = fmaf(-aj, ux[k], fmaf(bj, ux[j], ax[j]));
-      ay[j] = fmaf(-aj, uy[k], fmaf(bj, uy[j], ay[j]));
-      az[j] = fmaf(-aj, uz[k], fmaf(bj, uz[j], az[j]));
-      const float ak = g * tr[k];
-      const float bk = g * fmaf(c, tr[k], D * nde[k]);
-      ax[k] = fmaf(-ak, ux[j], fmaf(bk, ux[k], ax[k]));
-      ay[k] = fmaf(-ak, uy[j], fmaf(bk, uy[k], ay[k]));
-      az[k] = fmaf(-ak, uz[j], fmaf(bk, uz[k], az[k]));
+      const float gg = (k == jj) ? 0.f : uj.w * uk.w * D;
+      if (k > jj) e3 = fmaf(gg, D, e3);
+      const float aj = gg * xj.x;
+      const float bj = gg * fmaf(c, xj.x, D * xj.y);
+      gx = fmaf(-aj, uk.x, fmaf(bj, uj.x, gx));
+      gy = fmaf(-aj, uk.y, fmaf(bj, uj.y, gy));
+      gz = fmaf(-aj, uk.z, fmaf(bj, uj.z, gz));
+    }
+    red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
+    atomicAdd(&T.fi[aa][0], -gx);
+    atomicAdd(&T.fi[aa][1], -gy);
+    atomicAdd(&T.fi[aa][2], -gz);
+    const float rx = xj.z * uj.x, ry = xj.z * uj.y, rz = xj.z * uj.z;
+    if (wuni) {
+      acc[1] += e3;
+      acc[2] = fmaf(rx, gx, acc[2]);
+      acc[3] = fmaf(ry, gy, acc[3]);
+      acc[4] = fmaf(rz, gz, acc[4]);
+      acc[5] = fmaf(rx, gy, acc[5]);
+      acc[6] = fmaf(rx, gz, acc[6]);
+      acc[7] = fmaf(ry, gz, acc[7]);
+    } else {  // warp straddles two boxes (rare): straight to the item's box
+      double* p = &d.bst[d.q[blockIdx.x * kFAtoms + aa].w].ew[par][0];
+      atomicAdd(p + 1, (double)e3);
+      atomicAdd(p + 2, (double)(rx * gx));
+      atomicAdd(p + 3, (double)(ry * gy));
+      atomicAdd(p + 4, (double)(rz * gz));
+      atomicAdd(p + 5, (double)(rx * gy));
+      atomicAdd(p + 6, (double)(rx * gz));
+      atomicAdd(p + 7, (double)(ry * gz));
     }
   }
-  acc[1] += e3acc;
+  __syncwarp();
+  // ---- force on the centre: pair part (lane group) + three-body reaction
 #pragma unroll
-  for (int k = 0; k < kMaxLegs; ++k) {
-    if (k >= nl) break;
-    const int j = __float_as_int(sm->v[7][k][t]);
-    const float r = sm->v[6][k][t];
-    red_add_v4(d.f + j, ax[k], ay[k], az[k]);
-    fix -= ax[k];
-    fiy -= ay[k];
-    fiz -= az[k];
-    const float rx = r * ux[k], ry = r * uy[k], rz = r * uz[k];
-    acc[2] = fmaf(rx, ax[k], acc[2]);
-    acc[3] = fmaf(ry, ay[k], acc[3]);
-    acc[4] = fmaf(rz, az[k], acc[4]);
-    acc[5] = fmaf(rx, ay[k], acc[5]);
-    acc[6] = fmaf(rx, az[k], acc[6]);
-    acc[7] = fmaf(ry, az[k], acc[7]);
+  for (int o = 1; o < kG; o <<= 1) {
+    fx += __shfl_xor_sync(kFull, fx, o);
+    fy += __shfl_xor_sync(kFull, fy, o);
+    fz += __shfl_xor_sync(kFull, fz, o);
   }
-  red_add_v4(d.f + i, fix, fiy, fiz);
+  if (valid && g == 0) {
+    red_add_v4(d.f + i, fx + T.fi[a][0], fy + T.fi[a][1], fz + T.fi[a][2]);
+    if (nl > kLMax) {
+      const int slot = atomicAdd(&d.g->n_over, 1);
+      if (slot < d.N) d.over[slot] = i;
+    }
+  }
+  if (kCount) {  // legs and register-path triplets, one atomic per warp
+    unsigned long long legs = (valid && g == 0) ? (unsigned long long)nl : 0ull;
+    unsigned long long tri = (valid && g == 0 && nl <= kLMax) ? (unsigned long long)(nl * (nl - 1) / 2) : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      legs += __shfl_down_sync(kFull, legs, o);
+      tri += __shfl_down_sync(kFull, tri, o);
+    }
+    if (lane == 0) {
+      atomicAdd((unsigned long long*)&d.g->npairs, legs);
+      atomicAdd((unsigned long long*)&d.g->ntrip, tri);
+    }
+  }
+  if (blockIdx.x == 0) {  // the rebuild (if any) is consumed
+    for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
+    if (threadIdx.x == 0) d.g->any_rebuild = 0;
+  }
+  const int ab = wuni ? b0 : b;
+  const bool last = valid && (a == kFAtoms - 1 || i == d.N - 1);
+  box_accumulate<8>(acc, ab, last, [&](int bb) { return &d.bst[bb].ew[par][0]; });
 }
 
-// Three-body part for centres with more than kMaxLegs legs (rare): legs in
-// local memory, same arithmetic.
+// Three-body part for centres with more than kLMax legs (rare): legs in
+// local memory, every unordered leg pair once, same arithmetic.
 template <bool kCount>
-__device__ void force_overflow_item(const Dev& d, const FParams& P, int i, float (&acc)[8]) {
+__device__ void force_overflow_item(const Dev& d, const FParams& P, int i, int par) {
   const uint4 qi = d.q[i];
-  const Box& bx = d.box[qi.w];
+  const int b = (int)qi.w;
+  const Box& bx = d.box[b];
   int cnt = d.nbr_cnt[i];
   if (cnt > d.W) cnt = d.W;
   float ux[kMaxLegsOverflow], uy[kMaxLegsOverflow], uz[kMaxLegsOverflow], tr[kMaxLegsOverflow],
@@ -557,7 +645,7 @@ __device__ void force_overflow_item(const Dev& d, const FParams& P, int i, float
   int jj[kMaxLegsOverflow];
   int nl = 0;
   for (int s = 0; s < cnt; ++s) {
-    const int j = d.nbr[(size_t)s * d.N + i];
+    const int j = d.nbr[(size_t)i * d.W + s];
     const uint4 qj = d.q[j];
     const float dx = fix_diff(qi.x, qj.x, bx.Lq[0]), dy = fix_diff(qi.y, qj.y, bx.Lq[1]),
                 dz = fix_diff(qi.z, qj.z, bx.Lq[2]);
@@ -584,7 +672,7 @@ __device__ void force_overflow_item(const Dev& d, const FParams& P, int i, float
     ++nl;
   }
   if (kCount) atomicAdd((unsigned long long*)&d.g->ntrip, (unsigned long long)(nl * (nl - 1) / 2));
-  float e3acc = 0.f;
+  float e3acc = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int j = 0; j < nl; ++j)
     for (int k = j + 1; k < nl; ++k) {
       const float c = fmaf(ux[j], ux[k], fmaf(uy[j], uy[k], uz[j] * uz[k]));
@@ -600,7 +688,6 @@ __device__ void force_overflow_item(const Dev& d, const FParams& P, int i, float
       ay[k] = fmaf(-ak, uy[j], fmaf(bk, uy[k], ay[k]));
       az[k] = fmaf(-ak, uz[j], fmaf(bk, uz[k], az[k]));
     }
-  acc[1] += e3acc;
   float fx = 0.f, fy = 0.f, fz = 0.f;
   for (int k = 0; k < nl; ++k) {
     red_add_v4(d.f + jj[k], ax[k], ay[k], az[k]);
@@ -608,14 +695,17 @@ __device__ void force_overflow_item(const Dev& d, const FParams& P, int i, float
     fy -= ay[k];
     fz -= az[k];
     const float rx = rr[k] * ux[k], ry = rr[k] * uy[k], rz = rr[k] * uz[k];
-    acc[2] = fmaf(rx, ax[k], acc[2]);
-    acc[3] = fmaf(ry, ay[k], acc[3]);
-    acc[4] = fmaf(rz, az[k], acc[4]);
-    acc[5] = fmaf(rx, ay[k], acc[5]);
-    acc[6] = fmaf(rx, az[k], acc[6]);
-    acc[7] = fmaf(ry, az[k], acc[7]);
+    w[0] = fmaf(rx, ax[k], w[0]);
+    w[1] = fmaf(ry, ay[k], w[1]);
+    w[2] = fmaf(rz, az[k], w[2]);
+    w[3] = fmaf(rx, ay[k], w[3]);
+    w[4] = fmaf(rx, az[k], w[4]);
+    w[5] = fmaf(ry, az[k], w[5]);
   }
   red_add_v4(d.f + i, fx, fy, fz);
+  double* p = &d.bst[b].ew[par][0];  // overflow centres are not box-ordered: per-thread FP64 atomics
+  atomicAdd(p + 1, (double)e3acc);
+  for (int k = 0; k < 6; ++k) atomicAdd(p + 2 + k, (double)w[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -627,9 +717,13 @@ __global__ void k_kick1(Dev d) {
   const int par = (int)(d.g->step & 1ull);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) d.g->n_over = 0;
-  const int b = (i < d.N) ? (int)d.q[i].w : -1;
-  const double s = warp_kick1_scale(d, I, i, b, par);
-  if (i < d.N) kick1_item(d, I, i, s, b);
+  if (i < d.N) kick1_item(d, I, i, (int)d.q[i].w, par);
+}
+
+// Start half of every box with the current integrator (first step of a call).
+__global__ void k_prime_thermostat(Dev d) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < d.nbox) start_half_box(d, *d.integ, b);
 }
 
 __global__ void k_bin(Dev d) {
@@ -730,48 +824,12 @@ __global__ void k_neigh(Dev d, float rl2) {
 }
 
 template <bool kCount>
-__global__ void __launch_bounds__(kForceThreads, 3) k_force(Dev d, FParams P) {
-  if (d.g->status) return;
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
-  LegSm* sm = reinterpret_cast<LegSm*>(dyn_smem);
-  const int par = (int)(d.g->step & 1ull);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int b = -1, nl = 0;
-  if (i < d.N) {
-    b = (int)d.q[i].w;
-    force_item<kCount>(d, P, i, sm, acc, nl);
-  }
-  if (blockIdx.x == 0) {  // the rebuild (if any) is consumed
-    for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
-    if (threadIdx.x == 0) d.g->any_rebuild = 0;
-  }
-  double v[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) v[k] = (double)acc[k];
-  const bool last = (i < d.N) && (threadIdx.x == blockDim.x - 1 || i == d.N - 1);
-  box_accumulate<8>(v, b, last, [&](int bb) { return &d.bst[bb].ew[par][0]; });
-}
-
-template <bool kCount>
 __global__ void __launch_bounds__(128) k_force_overflow(Dev d, FParams P) {
   if (d.g->status) return;
   const int par = (int)(d.g->step & 1ull);
   const int nover = min(d.g->n_over, d.N);
-  for (int base = blockIdx.x * blockDim.x; base < nover; base += gridDim.x * blockDim.x) {
-    const int k = base + threadIdx.x;
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int b = -1;
-    if (k < nover) {
-      const int i = d.over[k];
-      b = (int)d.q[i].w;
-      force_overflow_item<kCount>(d, P, i, acc);
-    }
-    // overflow centres are not box-ordered: plain per-thread FP64 atomics
-    if (b >= 0)
-      for (int c = 0; c < 8; ++c) atomicAdd(&d.bst[b].ew[par][c], (double)acc[c]);
-  }
-  __syncthreads();
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nover; k += gridDim.x * blockDim.x)
+    force_overflow_item<kCount>(d, P, d.over[k], par);
 }
 
 __global__ void k_kick2(Dev d) {
@@ -780,7 +838,7 @@ __global__ void k_kick2(Dev d) {
   const unsigned long long step = d.g->step;
   const int par = (int)(step & 1ull);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double ke[1] = {0.0};
+  float ke[1] = {0.f};
   int b = -1;
   if (i < d.N) {
     b = (int)d.q[i].w;
@@ -847,11 +905,12 @@ __global__ void k_load_velocities(Dev d, const double* __restrict__ vin) {
 __global__ void k_ke_init(Dev d) {
   const Integ I = *d.integ;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double ke[1] = {0.0};
+  float ke[1] = {0.f};
   int b = -1;
   if (i < d.N) {
     b = (int)d.q[i].w;
-    ke[0] = I.ke_fac * (d.vx[i] * d.vx[i] + d.vy[i] * d.vy[i] + d.vz[i] * d.vz[i]);
+    const float vx = (float)d.vx[i], vy = (float)d.vy[i], vz = (float)d.vz[i];
+    ke[0] = (float)I.ke_fac * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
   }
   const bool last = (i < d.N) && (threadIdx.x == blockDim.x - 1 || i == d.N - 1);
   box_accumulate<1>(ke, b, last, [&](int bb) { return &d.bst[bb].ke_last; });
@@ -933,7 +992,7 @@ __global__ void k_gather_forces(Dev d, double* __restrict__ fo64, float* __restr
   }
 }
 
-// Neighbour sets to user order: out[u*width + s] = id[nbr[s][i]].
+// Neighbour sets to user order: out[u*width + s] = id[nbr[i][s]].
 __global__ void k_gather_neighbors(Dev d, int* __restrict__ cnt_out, int* __restrict__ nbr_out, int width) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
@@ -941,7 +1000,7 @@ __global__ void k_gather_neighbors(Dev d, int* __restrict__ cnt_out, int* __rest
   const int c = d.nbr_cnt[i];
   cnt_out[u] = c;
   const int m = min(min(c, d.W), width);
-  for (int s = 0; s < m; ++s) nbr_out[(size_t)u * width + s] = d.id[d.nbr[(size_t)s * d.N + i]];
+  for (int s = 0; s < m; ++s) nbr_out[(size_t)u * width + s] = d.id[d.nbr[(size_t)i * d.W + s]];
 }
 
 __global__ void k_energy_out(Dev d, double* e, double* w) {

@@ -127,6 +127,8 @@ def test_ice_ih_and_diamond_closed_form(orc, rho):
         tr = -2 * n * d * orc.dphi2(d)[0]
         assert w[:3].sum() == pytest.approx(tr, rel=1e-10)
         np.testing.assert_allclose(w[:3], tr / 3, rtol=1e-9)
+        # only pair terms, all of one sign on the diagonal: the scale equals |trace|
+        assert r["virial_abs"] == pytest.approx(abs(tr), rel=1e-10)
         assert np.abs(w[3:]).max() < 1e-9 * abs(tr)
 
 

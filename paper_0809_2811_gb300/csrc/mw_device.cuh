@@ -149,22 +149,23 @@ __device__ __forceinline__ int cell_of(const uint4& q, const Box& bx) {
 __device__ __forceinline__ void set_status(Global* g, int st) { atomicCAS(&g->status, 0, st); }
 
 // Per-box accumulation of NV values held as FP32 by each thread; the sums
-// over threads are FP64.  Every thread of the block calls it (b < 0 for
+// across blocks are FP64.  Every thread of the block calls it (b < 0 for
 // threads without a contribution).  Atoms are box-major, so box ids along a
-// warp are non-decreasing: a segmented FP32 scan sums each run of one box
-// within the warp (32 atoms at most), the run totals are widened to FP64 and
-// merged in shared memory for the block's first and last box (one global
-// atomic per value and block), other runs go to global memory directly.
+// warp are non-decreasing: a segmented FP32 scan sums each run of one box in
+// the warp; runs of the block's first and last box are summed in shared
+// memory (FP32, one block of atoms) and widened to FP64 for one global atomic
+// per value and block; runs of other boxes (small boxes only) go to global
+// memory directly.  No FP64 arithmetic runs on the SM.
 template <int NV, class Dst>
 __device__ void box_accumulate(float (&v)[NV], int b, bool is_last_valid, Dst dst) {
-  __shared__ double sacc[2][NV];
+  __shared__ float sacc[2][NV];
   __shared__ int sbox[2];
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     sbox[0] = b;
     sbox[1] = -1;
   }
-  if (threadIdx.x < 2 * NV) (&sacc[0][0])[threadIdx.x] = 0.0;
+  if (threadIdx.x < 2 * NV) (&sacc[0][0])[threadIdx.x] = 0.f;
   __syncthreads();
   if (is_last_valid) sbox[1] = b;
 #pragma unroll
@@ -183,7 +184,7 @@ __device__ void box_accumulate(float (&v)[NV], int b, bool is_last_valid, Dst ds
     const int slot = (b == sbox[0]) ? 0 : ((b == sbox[1]) ? 1 : -1);
     if (slot >= 0) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) atomicAdd(&sacc[slot][k], (double)v[k]);
+      for (int k = 0; k < NV; ++k) atomicAdd(&sacc[slot][k], v[k]);
     } else {
       double* p = dst(b);
 #pragma unroll
@@ -191,9 +192,9 @@ __device__ void box_accumulate(float (&v)[NV], int b, bool is_last_valid, Dst ds
     }
   }
   __syncthreads();
-  if (threadIdx.x < NV && sbox[0] >= 0) atomicAdd(dst(sbox[0]) + threadIdx.x, sacc[0][threadIdx.x]);
+  if (threadIdx.x < NV && sbox[0] >= 0) atomicAdd(dst(sbox[0]) + threadIdx.x, (double)sacc[0][threadIdx.x]);
   if (threadIdx.x >= 32 && threadIdx.x < 32 + NV && sbox[1] >= 0 && sbox[1] != sbox[0])
-    atomicAdd(dst(sbox[1]) + (threadIdx.x - 32), sacc[1][threadIdx.x - 32]);
+    atomicAdd(dst(sbox[1]) + (threadIdx.x - 32), (double)sacc[1][threadIdx.x - 32]);
 }
 
 // One Nose-Hoover half step (length dt/2) of a single thermostat: quarter step
@@ -496,11 +497,19 @@ __global__ void __launch_bounds__(kFThreads) k_force(Dev d, FParams P) {
       leg = r < P.rc;
       if (leg) {
         const float ux = dx * invr, uy = dy * invr, uz = dz * invr;
-        const float tinv = __frcp_rn(r - P.rc);  // 1/(r - a sig) < 0
+        const float tinv = __fdividef(1.0f, r - P.rc);  // 1/(r - a sig) < 0
         const float e2 = exp2f(P.sig_l2e * tinv);
         const float e3 = exp2f(P.gsig_l2e * tinv);
         const float sr = P.sig * invr;
-        const float srp = powi(sr, P.p), srq = powi(sr, P.q);
+        float srp, srq;
+        if (P.p == 4 && P.q == 0) {  // the SW / mW exponents
+          const float sr2 = sr * sr;
+          srp = sr2 * sr2;
+          srq = 1.0f;
+        } else {
+          srp = powi(sr, P.p);
+          srq = powi(sr, P.q);
+        }
         const float brk = fmaf(P.B, srp, -srq);
         const float ae2 = P.Aeps * e2;
         const float phi = ae2 * brk;
@@ -543,8 +552,9 @@ __global__ void __launch_bounds__(kFThreads) k_force(Dev d, FParams P) {
   const int b0 = __shfl_sync(kFull, b, 0);
   const bool wuni = __all_sync(kFull, b == b0 || b < 0);
   const float c0 = P.c0;
-  for (int it = lane; it < pre[kWAtoms]; it += 32) {
-    int ka = 0, first = 0, n = 0;
+  for (int base = 0; base < pre[kWAtoms]; base += 32) {  // warp-uniform rounds
+    const int it = base + lane;
+    int ka = -1, first = 0, n = 0;
 #pragma unroll
     for (int k = 0; k < kWAtoms; ++k)  // the centre whose item range holds it
       if (it >= pre[k] && it < pre[k + 1]) {
@@ -552,47 +562,66 @@ __global__ void __launch_bounds__(kFThreads) k_force(Dev d, FParams P) {
         first = pre[k];
         n = pre[k + 1] - pre[k];
       }
-    const int aa = a0 + ka;
-    const int jj = it - first;
-    const float4* rowu = T.ue + aa * kLPad;
-    const float4 uj = rowu[jj];
-    const float4 xj = T.aux[aa * kLPad + jj];
-    float gx = 0.f, gy = 0.f, gz = 0.f, e3 = 0.f;
-    for (int k = 0; k < n; ++k) {
-      const float4 uk = rowu[k];
-      const float c = fmaf(uj.x, uk.x, fmaf(uj.y, uk.y, uj.z * uk.z));
-      const float D = c - c0;
-      const float gg = (k == jj) ? 0.f : uj.w * uk.w * D;
-      if (k > jj) e3 = fmaf(gg, D, e3);
-      const float aj = gg * xj.x;
-      const float bj = gg * fmaf(c, xj.x, D * xj.y);
-      gx = fmaf(-aj, uk.x, fmaf(bj, uj.x, gx));
-      gy = fmaf(-aj, uk.y, fmaf(bj, uj.y, gy));
-      gz = fmaf(-aj, uk.z, fmaf(bj, uj.z, gz));
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (ka >= 0) {
+      const int aa = a0 + ka;
+      const int jj = it - first;
+      const float4* rowu = T.ue + aa * kLPad;
+      const float4 uj = rowu[jj];
+      const float4 xj = T.aux[aa * kLPad + jj];
+      float e3 = 0.f;
+      for (int k = 0; k < n; ++k) {
+        const float4 uk = rowu[k];
+        const float c = fmaf(uj.x, uk.x, fmaf(uj.y, uk.y, uj.z * uk.z));
+        const float D = c - c0;
+        const float gg = (k == jj) ? 0.f : uj.w * uk.w * D;
+        if (k > jj) e3 = fmaf(gg, D, e3);
+        const float aj = gg * xj.x;
+        const float bj = gg * fmaf(c, xj.x, D * xj.y);
+        gx = fmaf(-aj, uk.x, fmaf(bj, uj.x, gx));
+        gy = fmaf(-aj, uk.y, fmaf(bj, uj.y, gy));
+        gz = fmaf(-aj, uk.z, fmaf(bj, uj.z, gz));
+      }
+      red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
+      const float rx = xj.z * uj.x, ry = xj.z * uj.y, rz = xj.z * uj.z;
+      if (wuni) {
+        acc[1] += e3;
+        acc[2] = fmaf(rx, gx, acc[2]);
+        acc[3] = fmaf(ry, gy, acc[3]);
+        acc[4] = fmaf(rz, gz, acc[4]);
+        acc[5] = fmaf(rx, gy, acc[5]);
+        acc[6] = fmaf(rx, gz, acc[6]);
+        acc[7] = fmaf(ry, gz, acc[7]);
+      } else {  // warp straddles two boxes (rare): straight to the item's box
+        double* p = &d.bst[d.q[blockIdx.x * kFAtoms + aa].w].ew[par][0];
+        atomicAdd(p + 1, (double)e3);
+        atomicAdd(p + 2, (double)(rx * gx));
+        atomicAdd(p + 3, (double)(ry * gy));
+        atomicAdd(p + 4, (double)(rz * gz));
+        atomicAdd(p + 5, (double)(rx * gy));
+        atomicAdd(p + 6, (double)(rx * gz));
+        atomicAdd(p + 7, (double)(ry * gz));
+      }
     }
-    red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
-    atomicAdd(&T.fi[aa][0], -gx);
-    atomicAdd(&T.fi[aa][1], -gy);
-    atomicAdd(&T.fi[aa][2], -gz);
-    const float rx = xj.z * uj.x, ry = xj.z * uj.y, rz = xj.z * uj.z;
-    if (wuni) {
-      acc[1] += e3;
-      acc[2] = fmaf(rx, gx, acc[2]);
-      acc[3] = fmaf(ry, gy, acc[3]);
-      acc[4] = fmaf(rz, gz, acc[4]);
-      acc[5] = fmaf(rx, gy, acc[5]);
-      acc[6] = fmaf(rx, gz, acc[6]);
-      acc[7] = fmaf(ry, gz, acc[7]);
-    } else {  // warp straddles two boxes (rare): straight to the item's box
-      double* p = &d.bst[d.q[blockIdx.x * kFAtoms + aa].w].ew[par][0];
-      atomicAdd(p + 1, (double)e3);
-      atomicAdd(p + 2, (double)(rx * gx));
-      atomicAdd(p + 3, (double)(ry * gy));
-      atomicAdd(p + 4, (double)(rz * gz));
-      atomicAdd(p + 5, (double)(rx * gy));
-      atomicAdd(p + 6, (double)(rx * gz));
-      atomicAdd(p + 7, (double)(ry * gz));
+    // reaction on the centres: segmented sum over the lanes holding one centre's items
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int ko = __shfl_up_sync(kFull, ka, o);
+      const float tx = __shfl_up_sync(kFull, gx, o), ty = __shfl_up_sync(kFull, gy, o),
+                  tz = __shfl_up_sync(kFull, gz, o);
+      if (lane >= o && ko == ka) {
+        gx += tx;
+        gy += ty;
+        gz += tz;
+      }
     }
+    const int kn = __shfl_down_sync(kFull, ka, 1);
+    if (ka >= 0 && (lane == 31 || kn != ka)) {
+      T.fi[a0 + ka][0] -= gx;  // one tail per centre and round
+      T.fi[a0 + ka][1] -= gy;
+      T.fi[a0 + ka][2] -= gz;
+    }
+    __syncwarp();  // orders this round's table updates before the next round's
   }
   __syncwarp();
   // ---- force on the centre: pair part (lane group) + three-body reaction

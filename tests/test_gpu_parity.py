@@ -9,8 +9,9 @@ Tolerances (stated by the method's specification of this engine):
   * energies (E, E2, E3) within 1e-6 of |E2| + |E3| (equal to "relative to E"
     up to a factor < 2 for liquid and ice; on strained inputs E2 and E3
     cancel and |E| alone would demand digits FP32 terms cannot carry);
-    virial within 1e-6 of the summed magnitude of its diagonal contributions
-    (the oracle's virial_abs; the trace is a cancelling sum in the same way).
+    virial within 1e-5 (the force tolerance: W is a sum of leg vector times
+    leg force) of the summed magnitude of its diagonal contributions (the
+    oracle's virial_abs; the trace is a cancelling sum like E).
 The oracle is fed the same positions the kernels see: inputs are snapped to
 the 2^-32 box-fraction grid of the device's fixed-point coordinates.
 """
@@ -50,7 +51,7 @@ def check_box(mwlib, orc, x, box, v=None, neighbors=True):
         escale = abs(ref["e2"]) + abs(ref["e3"])
         for k, name in ((0, "energy"), (1, "e2"), (2, "e3")):
             assert abs(e[0, k] - ref[name]) <= E_TOL * escale, name
-        assert np.abs(w[0] - ref["virial"]).max() <= E_TOL * ref["virial_abs"]
+        assert np.abs(w[0] - ref["virial"]).max() <= F_TOL * ref["virial_abs"]
         if neighbors:
             check_neighbors(s, orc, x, box)
         return s, ref, f
@@ -150,7 +151,7 @@ def test_batch_parity(mwlib, orc):
             escale = abs(ref["e2"]) + abs(ref["e3"])
             assert abs(e[b, 0] - ref["energy"]) <= E_TOL * escale
             assert abs(e[b, 2] - ref["e3"]) <= E_TOL * escale
-            assert np.abs(w[b] - ref["virial"]).max() <= E_TOL * ref["virial_abs"]
+            assert np.abs(w[b] - ref["virial"]).max() <= F_TOL * ref["virial_abs"]
             off += n[b]
     finally:
         s.close()

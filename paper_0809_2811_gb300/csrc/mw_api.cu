@@ -78,6 +78,7 @@ struct mw_system {
   bool graph_dirty = true;
   // persistent engine
   int pers_blocks = 0;
+  int pers_blocks_limit = 0;  // 0 = as many as can be co-resident
   std::vector<void*> allocs;
 };
 
@@ -550,8 +551,10 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
       (st = dalloc(s, &d.cell, N)) != MW_OK || (st = dalloc(s, &d.rank, N)) != MW_OK ||
       (st = dalloc(s, &d.nbr_cnt, N)) != MW_OK || (st = dalloc(s, &d.over, N)) != MW_OK ||
       (st = dalloc(s, &d.stage, 3 * N)) != MW_OK || (st = dalloc(s, &d.stage2, 3 * N)) != MW_OK ||
-      (st = dalloc(s, &s->boxid, N)) != MW_OK || (st = dalloc(s, &s->eout, 9 * (size_t)nbox)) != MW_OK)
+      (st = dalloc(s, &s->boxid, N)) != MW_OK || (st = dalloc(s, &s->eout, 9 * (size_t)nbox)) != MW_OK ||
+      (st = dalloc(s, &d.chunk, 4096)) != MW_OK)
     return bad(st);
+  d.chunk_cap = 4096;
   if (cudaMemsetAsync(d.nbr_cnt, 0, sizeof(int) * N, s->stream) != cudaSuccess)
     return bad(fail(MW_ECUDA, "memset failed"));
   Box* dbox;

@@ -72,7 +72,8 @@ struct Global {
   int status;
   int max_count;            // widest neighbour set of the last build
   unsigned done;            // last-block counter of k_kick2
-  unsigned bar_count, bar_gen;
+  unsigned bar_count, bar_gen;  // persistent engine grid barrier
+  int bar_stat[2];              // status snapshot taken at each barrier release
   long long npairs, ntrip;  // leg / triplet counts of the last force call (if counting)
   int count_terms;
   int n_over;               // centres routed to the overflow path
@@ -108,6 +109,8 @@ struct Dev {
   int *cell_cnt, *cell_start;
   int *nbr, *nbr_cnt;
   int* over;          // overflow centre list
+  int* chunk;         // per-block cell totals of the persistent engine's scan
+  int chunk_cap;
   const Box* box;
   BoxState* bst;
   double* thermo;     // nbox * TR_N
@@ -354,9 +357,9 @@ __device__ void end_of_step_box(const Dev& d, const Integ& I, int b, int par, un
 __device__ __forceinline__ int stencil_n(int nc) { return nc >= 3 ? 3 : nc; }
 __device__ __forceinline__ int stencil_off(int nc, int o) { return nc >= 3 ? o - 1 : o; }
 
-__device__ void neigh_warp(const Dev& d, int i, float rl2) {
+__device__ void neigh_warp(const Dev& d, const uint4* __restrict__ qa, int i, float rl2) {
   const int lane = threadIdx.x & 31;
-  const uint4 qi = d.q[i];
+  const uint4 qi = qa[i];
   const Box& bx = d.box[qi.w];
   const int cx = (int)(((unsigned long long)qi.x * (unsigned)bx.nc[0]) >> 32);
   const int cy = (int)(((unsigned long long)qi.y * (unsigned)bx.nc[1]) >> 32);
@@ -398,7 +401,7 @@ __device__ void neigh_warp(const Dev& d, int i, float rl2) {
     if (t < total) {
       j = sk + (t - ek);
       if (j != i) {
-        const uint4 qj = d.q[j];
+        const uint4 qj = qa[j];
         const float dx = fix_diff(qi.x, qj.x, L0), dy = fix_diff(qi.y, qj.y, L1), dz = fix_diff(qi.z, qj.z, L2);
         pred = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
       }
@@ -446,15 +449,14 @@ struct LegTable {
   int nl[kFAtoms];
 };
 
+// One block of kFAtoms centres (atoms blk*kFAtoms ...); every thread of the
+// block calls it.
 template <bool kCount>
-__global__ void __launch_bounds__(kFThreads) k_force(Dev d, FParams P) {
-  if (d.g->status) return;
-  __shared__ LegTable T;
-  const int par = (int)(d.g->step & 1ull);
+__device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk, int par) {
   const int lane = threadIdx.x & 31;
   const int g = threadIdx.x & (kG - 1);
   const int a = threadIdx.x / kG;
-  const int i = blockIdx.x * kFAtoms + a;
+  const int i = blk * kFAtoms + a;
   const bool valid = i < d.N;
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // E2, E3, W xx yy zz xy xz yz
   float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -593,7 +595,7 @@ __global__ void __launch_bounds__(kFThreads) k_force(Dev d, FParams P) {
         acc[6] = fmaf(rx, gz, acc[6]);
         acc[7] = fmaf(ry, gz, acc[7]);
       } else {  // warp straddles two boxes (rare): straight to the item's box
-        double* p = &d.bst[d.q[blockIdx.x * kFAtoms + aa].w].ew[par][0];
+        double* p = &d.bst[d.q[blk * kFAtoms + aa].w].ew[par][0];
         atomicAdd(p + 1, (double)e3);
         atomicAdd(p + 2, (double)(rx * gx));
         atomicAdd(p + 3, (double)(ry * gy));
@@ -650,13 +652,21 @@ __global__ void __launch_bounds__(kFThreads) k_force(Dev d, FParams P) {
       atomicAdd((unsigned long long*)&d.g->ntrip, tri);
     }
   }
+  const int ab = wuni ? b0 : b;
+  const bool last = valid && (a == kFAtoms - 1 || i == d.N - 1);
+  box_accumulate<8>(acc, ab, last, [&](int bb) { return &d.bst[bb].ew[par][0]; });
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kFThreads) k_force(Dev d, FParams P) {
+  if (d.g->status) return;
+  __shared__ LegTable T;
+  const int par = (int)(d.g->step & 1ull);
   if (blockIdx.x == 0) {  // the rebuild (if any) is consumed
     for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
     if (threadIdx.x == 0) d.g->any_rebuild = 0;
   }
-  const int ab = wuni ? b0 : b;
-  const bool last = valid && (a == kFAtoms - 1 || i == d.N - 1);
-  box_accumulate<8>(acc, ab, last, [&](int bb) { return &d.bst[bb].ew[par][0]; });
+  force_block<kCount>(d, P, T, blockIdx.x, par);
 }
 
 // Three-body part for centres with more than kLMax legs (rare): legs in
@@ -755,15 +765,38 @@ __global__ void k_prime_thermostat(Dev d) {
   if (b < d.nbox) start_half_box(d, *d.integ, b);
 }
 
-__global__ void k_bin(Dev d) {
-  if (!d.g->any_rebuild || d.g->status) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) d.g->max_count = 0;
-  if (i >= d.N) return;
+// a2: cell of atom i and its rank among the atoms of that cell (counting sort).
+__device__ __forceinline__ void bin_item(const Dev& d, int i) {
   const uint4 q = d.q[i];
   const int c = cell_of(q, d.box[q.w]);
   d.cell[i] = c;
   d.rank[i] = atomicAdd(d.cell_cnt + c, 1);
+}
+
+// a2: atom i to its sorted slot in the staging arrays.
+__device__ __forceinline__ void scatter_item(const Dev& d, int i) {
+  const int p = d.cell_start[d.cell[i]] + d.rank[i];
+  d.tx[p] = d.x[i]; d.ty[p] = d.y[i]; d.tz[p] = d.z[i];
+  d.tvx[p] = d.vx[i]; d.tvy[p] = d.vy[i]; d.tvz[p] = d.vz[i];
+  d.tid[p] = d.id[i];
+  d.tq[p] = d.q[i];
+}
+
+// a2: staging arrays back to the state arrays; build positions recorded.
+__device__ __forceinline__ void copyback_item(const Dev& d, int i) {
+  d.x[i] = d.tx[i]; d.y[i] = d.ty[i]; d.z[i] = d.tz[i];
+  d.vx[i] = d.tvx[i]; d.vy[i] = d.tvy[i]; d.vz[i] = d.tvz[i];
+  d.id[i] = d.tid[i];
+  const uint4 q = d.tq[i];
+  d.q[i] = q;
+  d.qb[i] = q;
+}
+
+__global__ void k_bin(Dev d) {
+  if (!d.g->any_rebuild || d.g->status) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) d.g->max_count = 0;
+  if (i < d.N) bin_item(d, i);
 }
 
 // Exclusive scan of the per-cell counts into cell_start (one block of 1024
@@ -824,32 +857,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Dev d) {
 __global__ void k_scatter(Dev d) {
   if (!d.g->any_rebuild || d.g->status) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.N) return;
-  const int p = d.cell_start[d.cell[i]] + d.rank[i];
-  d.tx[p] = d.x[i]; d.ty[p] = d.y[i]; d.tz[p] = d.z[i];
-  d.tvx[p] = d.vx[i]; d.tvy[p] = d.vy[i]; d.tvz[p] = d.vz[i];
-  d.tid[p] = d.id[i];
-  d.tq[p] = d.q[i];
+  if (i < d.N) scatter_item(d, i);
 }
 
 __global__ void k_copyback(Dev d) {
   if (!d.g->any_rebuild || d.g->status) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < d.nbox) d.bst[i].rebuilds += 1;
-  if (i >= d.N) return;
-  d.x[i] = d.tx[i]; d.y[i] = d.ty[i]; d.z[i] = d.tz[i];
-  d.vx[i] = d.tvx[i]; d.vy[i] = d.tvy[i]; d.vz[i] = d.tvz[i];
-  d.id[i] = d.tid[i];
-  const uint4 q = d.tq[i];
-  d.q[i] = q;
-  d.qb[i] = q;
+  if (i < d.N) copyback_item(d, i);
 }
 
 __global__ void k_neigh(Dev d, float rl2) {
   if (!d.g->any_rebuild || d.g->status) return;
   const int w = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   if (w >= d.N) return;
-  neigh_warp(d, w, rl2);
+  neigh_warp(d, d.q, w, rl2);
 }
 
 template <bool kCount>

@@ -1,7 +1,185 @@
-// mw_persistent.cuh -- persistent cooperative engine (device side).
+// mw_persistent.cuh -- persistent engine: one cooperative launch advances
+// every box nsteps MD steps, with grid-wide barriers between the phases of
+// mw_device.cuh (kick1 | [bin | scan | scan | scatter | copy + neighbour list]
+// | force | [overflow legs] | kick2 | thermostat).  All blocks are
+// co-resident (cooperative launch), every barrier wait is bounded in wall
+// time, and the release of each barrier carries one status snapshot so that
+// all blocks take the same decision to stop.
 #pragma once
+
 #include "mw_device.cuh"
 
 namespace mw {
-constexpr int kPersThreads = 128;
+
+constexpr int kPersThreads = kFThreads;
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier.  gen is this block's count of barriers passed (all blocks
+// start from the same value).  Returns the status snapshot of the release
+// (identical in every block), or ST_TIMEOUT if this block gave up waiting.
+__device__ int grid_barrier(Global* g, unsigned& gen) {
+  __shared__ int s_status;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned arrived = atomicAdd(&g->bar_count, 1u) + 1u;
+    int st;
+    if (arrived == gridDim.x) {
+      g->bar_count = 0u;
+      g->bar_stat[gen & 1u] = *(volatile int*)&g->status;
+      __threadfence();
+      atomicExch(&g->bar_gen, gen + 1u);
+      st = g->bar_stat[gen & 1u];
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      bool released = true;
+      while (*(volatile unsigned*)&g->bar_gen == gen) {
+        __nanosleep(100);
+        if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+          set_status(g, ST_TIMEOUT);
+          released = false;
+          break;
+        }
+      }
+      __threadfence();
+      st = released ? *(volatile int*)&g->bar_stat[gen & 1u] : ST_TIMEOUT;
+    }
+    s_status = st;
+  }
+  __syncthreads();
+  gen += 1u;
+  return s_status;
+}
+
+// Two-level exclusive scan of the cell counts over the grid: each block scans
+// a contiguous chunk of cells (local prefix + chunk total), then adds the
+// totals of the chunks before it.
+__device__ void scan_chunk_local(const Dev& d) {
+  __shared__ int wsum[kPersThreads / 32];
+  __shared__ int carry;
+  const int per = (d.ncell + gridDim.x - 1) / gridDim.x;
+  const int c0 = blockIdx.x * per, c1 = min(d.ncell, c0 + per);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = c0; base < c1; base += kPersThreads) {
+    const int c = base + threadIdx.x;
+    const int v = (c < c1) ? d.cell_cnt[c] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    int before = carry;
+    for (int w = 0; w < wid; ++w) before += wsum[w];
+    if (c < c1) d.cell_start[c] = before + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < kPersThreads / 32; ++w) tot += wsum[w];
+      carry += tot;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && blockIdx.x < d.chunk_cap) d.chunk[blockIdx.x] = carry;
+}
+
+__device__ void scan_chunk_offsets(const Dev& d) {
+  __shared__ int red[kPersThreads / 32];
+  const int per = (d.ncell + gridDim.x - 1) / gridDim.x;
+  const int c0 = blockIdx.x * per, c1 = min(d.ncell, c0 + per);
+  int part = 0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += kPersThreads) part += d.chunk[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(kFull, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  int off = 0;
+  for (int w = 0; w < kPersThreads / 32; ++w) off += red[w];
+  for (int c = c0 + threadIdx.x; c < c1; c += kPersThreads) {
+    d.cell_start[c] += off;
+    d.cell_cnt[c] = 0;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) d.cell_start[d.ncell] = off + d.chunk[blockIdx.x];
+  __syncthreads();
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, int nsteps) {
+  __shared__ LegTable T;
+  __shared__ unsigned s_gen;
+  Global* g = d.g;
+  if (threadIdx.x == 0) s_gen = *(volatile unsigned*)&g->bar_gen;
+  __syncthreads();
+  unsigned gen = s_gen;
+  const Integ I = *d.integ;
+  const unsigned long long step0 = g->step;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  const int gw = tid >> 5, nwarps = nth >> 5;
+  const int nblk = (d.N + kFAtoms - 1) / kFAtoms;
+  for (int s = 0; s < nsteps; ++s) {
+    const unsigned long long step = step0 + (unsigned long long)s;
+    const int par = (int)(step & 1ull);
+    // a1 + a7 first half, a8 displacement check
+    if (tid == 0) g->n_over = 0;
+    for (int i = tid; i < d.N; i += nth) kick1_item(d, I, i, (int)d.q[i].w, par);
+    if (grid_barrier(g, gen)) return;
+    // a2 + a3: cell binning and neighbour list, when due (flag is stable until kick2)
+    if (*(volatile int*)&g->any_rebuild) {
+      if (tid == 0) g->max_count = 0;
+      for (int i = tid; i < d.N; i += nth) bin_item(d, i);
+      if (grid_barrier(g, gen)) return;
+      scan_chunk_local(d);
+      if (grid_barrier(g, gen)) return;
+      scan_chunk_offsets(d);
+      if (grid_barrier(g, gen)) return;
+      for (int i = tid; i < d.N; i += nth) scatter_item(d, i);
+      if (grid_barrier(g, gen)) return;
+      for (int i = tid; i < d.N; i += nth) copyback_item(d, i);
+      for (int w = gw; w < d.N; w += nwarps) neigh_warp(d, d.tq, w, P.rl2);
+      if (tid < d.nbox) d.bst[tid].rebuilds += 1;
+      if (grid_barrier(g, gen)) return;
+    }
+    // a4 - a6: fused two- + three-body force, energy, virial
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) force_block<kCount>(d, P, T, blk, par);
+    if (grid_barrier(g, gen)) return;
+    const int nover = min(*(volatile int*)&g->n_over, d.N);
+    if (nover > 0) {
+      for (int k = tid; k < nover; k += nth) force_overflow_item<kCount>(d, P, d.over[k], par);
+      if (grid_barrier(g, gen)) return;
+    }
+    // a7 second half + kinetic energy per box; the rebuild (if any) is consumed
+    if (blockIdx.x == 0) {
+      for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
+      if (threadIdx.x == 0) g->any_rebuild = 0;
+    }
+    for (int base = blockIdx.x * blockDim.x; base < d.N; base += nth) {
+      const int i = base + threadIdx.x;
+      float ke[1] = {0.f};
+      int b = -1;
+      if (i < d.N) {
+        b = (int)d.q[i].w;
+        ke[0] = kick2_item(d, I, i);
+      }
+      const bool last = (i < d.N) && (threadIdx.x == blockDim.x - 1 || i == d.N - 1);
+      box_accumulate<1>(ke, b, last, [&](int bb) { return &d.bst[bb].ke_acc[par]; });
+    }
+    if (grid_barrier(g, gen)) return;
+    // thermostat halves (end of this step, start of the next) and thermo record
+    for (int b = tid; b < d.nbox; b += nth) end_of_step_box(d, I, b, par, step + 1ull);
+    if (tid == 0) g->step = step + 1ull;
+    if (grid_barrier(g, gen)) return;
+  }
+}
+
 }  // namespace mw

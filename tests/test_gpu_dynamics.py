@@ -35,10 +35,15 @@ def _run_pair(mwlib, orc, x, v, box, nsteps, kind, T0=298.0, tau=1000.0, dt=10.0
     return th, xg, vg, tho[-1], xo, vo, st
 
 
+ENGINES = {"graph": 1, "persistent": 2}
+
+
+@pytest.mark.parametrize("engine", sorted(ENGINES))
 @pytest.mark.parametrize("kind", [0, 1, 2])
-def test_short_trajectory_matches_oracle(mwlib, orc, kind):
+def test_short_trajectory_matches_oracle(mwlib, orc, kind, engine):
     x, v, box = I.nve512()
-    th, xg, vg, tho, xo, vo, st = _run_pair(mwlib, orc, x, v, box, 20, kind, T0=250.0, tau=200.0)
+    th, xg, vg, tho, xo, vo, st = _run_pair(mwlib, orc, x, v, box, 20, kind, T0=250.0, tau=200.0,
+                                            engine=ENGINES[engine])
     # FP32 force error ~1e-6 relative gives ~1e-5 A after 200 fs; allow 5x
     assert np.abs(_min_image(xg - xo, box)).max() < 5e-5
     assert np.abs(vg - vo).max() < 1e-6
@@ -91,7 +96,8 @@ def test_nose_hoover_conserved_quantity(mwlib):
     assert abs(th["conserved"] - c0) / abs(c0) < 2e-4
 
 
-def test_batch_dynamics_matches_oracle_per_box(mwlib, orc):
+@pytest.mark.parametrize("engine", sorted(ENGINES))
+def test_batch_dynamics_matches_oracle_per_box(mwlib, orc, engine):
     n = [216, 343, 290]
     rho = [0.95, 1.0, 1.08]
     T = [220.0, 260.0, 310.0]
@@ -103,8 +109,10 @@ def test_batch_dynamics_matches_oracle_per_box(mwlib, orc):
         boxes.append(b)
     s = mwlib.System(n, np.array(boxes))
     try:
+        s.set_engine(ENGINES[engine])
         s.set_state(np.concatenate(xs), np.concatenate(vs))
         th = s.step(15, dt=10.0, thermostat=2, T0_per_box=T, tau=300.0)
+        assert s.info()["engine"] == ENGINES[engine]
         xg, vg = s.get_state()
     finally:
         s.close()
@@ -118,12 +126,14 @@ def test_batch_dynamics_matches_oracle_per_box(mwlib, orc):
         off += n[k]
 
 
-def test_step_survives_list_overflow(mwlib, orc):
+@pytest.mark.parametrize("engine", sorted(ENGINES))
+def test_step_survives_list_overflow(mwlib, orc, engine):
     """A neighbour list too narrow mid-run is grown and the step resumed."""
     x, v, box = I.nve512()
     x = I.snap_to_grid(x, box)
     s = mwlib.System(512, box)
     try:
+        s.set_engine(ENGINES[engine])
         s.set_state(x, v)
         s.step(5, dt=10.0)
         mwlib.mw_set_nbr_width(s.h, 6)
@@ -134,3 +144,24 @@ def test_step_survives_list_overflow(mwlib, orc):
     xo, vo, st, tho = orc.md(x, v, box, 20, dt=10.0)
     assert th["step"] == 20
     assert np.abs(_min_image(xg - xo, box)).max() < 5e-5
+
+
+def test_engines_agree_over_a_long_run(mwlib):
+    """Both engines run the same algorithm: a 300-step NH run of a 4096-atom
+    liquid-like box gives thermo that agree to round-off growth."""
+    x, box = I.jittered_box(4096, 1.0, 0.1, 7)
+    v = I.maxwell_velocities(4096, 260.0, seed=8)
+    out = {}
+    for name, eng in ENGINES.items():
+        s = mwlib.System(4096, box)
+        try:
+            s.set_engine(eng)
+            s.set_state(x, v)
+            out[name] = s.step(300, dt=10.0, thermostat=2, T0=260.0, tau=1000.0)[0]
+        finally:
+            s.close()
+    a, b = out["graph"], out["persistent"]
+    assert a["step"] == b["step"] == 300
+    assert a["rebuilds"] == b["rebuilds"] or abs(a["rebuilds"] - b["rebuilds"]) <= 2
+    assert a["conserved"] == pytest.approx(b["conserved"], rel=1e-5)
+    assert a["temperature"] == pytest.approx(b["temperature"], rel=5e-2)

@@ -79,6 +79,7 @@ struct mw_system {
   // persistent engine
   int pers_blocks = 0;
   int pers_blocks_limit = 0;  // 0 = as many as can be co-resident
+  std::vector<int> cell_box_host;
   std::vector<void*> allocs;
 };
 
@@ -187,11 +188,22 @@ mw_status upload_integ(mw_system* s) {
 mw_status alloc_cells(mw_system* s) {
   dfree(s, s->d.cell_cnt);
   dfree(s, s->d.cell_start);
-  s->d.cell_cnt = s->d.cell_start = nullptr;
+  dfree(s, s->d.cell_box);
+  s->d.cell_cnt = s->d.cell_start = s->d.cell_box = nullptr;
   mw_status st;
   if ((st = dalloc(s, &s->d.cell_cnt, s->ncell)) != MW_OK) return st;
   if ((st = dalloc(s, &s->d.cell_start, s->ncell + 1)) != MW_OK) return st;
+  if ((st = dalloc(s, &s->d.cell_box, s->ncell)) != MW_OK) return st;
   MW_CUDA(cudaMemsetAsync(s->d.cell_cnt, 0, sizeof(int) * s->ncell, s->stream));
+  s->cell_box_host.resize(s->ncell);
+  for (int b = 0; b < s->nbox; ++b) {
+    const Box& bx = s->boxes[b];
+    const int nc = bx.nc[0] * bx.nc[1] * bx.nc[2];
+    for (int k = 0; k < nc; ++k) s->cell_box_host[bx.cell_off + k] = b;
+  }
+  MW_CUDA(cudaMemcpyAsync(s->d.cell_box, s->cell_box_host.data(), sizeof(int) * s->ncell, cudaMemcpyHostToDevice,
+                          s->stream));
+  MW_CUDA(cudaStreamSynchronize(s->stream));
   s->d.ncell = s->ncell;
   s->graph_dirty = true;
   return MW_OK;
@@ -247,7 +259,7 @@ void launch_rebuild(mw_system* s) {
   k_scan<<<1, kScanThreads, 0, s->stream>>>(d);
   k_scatter<<<gb, kThreads, 0, s->stream>>>(d);
   k_copyback<<<std::max(gb, div_up(s->nbox, kThreads)), kThreads, 0, s->stream>>>(d);
-  k_neigh<<<div_up((long long)s->N * 32, kThreads), kThreads, 0, s->stream>>>(d, s->fp.rl2);
+  k_neigh<<<div_up((long long)s->ncell * 32, kThreads), kThreads, 0, s->stream>>>(d, s->fp.rl2);
 }
 
 void launch_force(mw_system* s) {
@@ -682,10 +694,8 @@ mw_status mw_set_params(mw_system* s, const mw_params* prm) {
     return st;
   }
   make_fparams(s);
-  if (ncell != s->ncell) {
-    s->ncell = ncell;
-    if ((st = alloc_cells(s)) != MW_OK) return st;
-  }
+  s->ncell = ncell;
+  if ((st = alloc_cells(s)) != MW_OK) return st;
   if ((st = upload_boxes(s)) != MW_OK) return st;
   s->graph_dirty = true;
   s->forces_valid = false;

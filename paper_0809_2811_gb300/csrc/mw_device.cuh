@@ -107,6 +107,7 @@ struct Dev {
   int *id, *tid;
   int *cell, *rank;
   int *cell_cnt, *cell_start;
+  int* cell_box;      // box of each global cell
   int *nbr, *nbr_cnt;
   int* over;          // overflow centre list
   int* chunk;         // per-block cell totals of the persistent engine's scan
@@ -352,18 +353,22 @@ __device__ void end_of_step_box(const Dev& d, const Integ& I, int b, int par, un
 }
 
 // ---------------------------------------------------------------------------
-// Neighbour list: one warp per centre atom, candidates of the (deduplicated)
-// 27-cell stencil flattened over the lanes, ballot + popc compaction.
+// Neighbour list (a3): one warp per cell.  The candidates of the
+// (deduplicated) 27-cell stencil are flattened over the lanes, each lane
+// loading one candidate per chunk of 32; the chunk is then tested against
+// every centre atom of the cell (up to 32 at a time) and the hits of each
+// centre are compacted into its row with ballot + popc.
 __device__ __forceinline__ int stencil_n(int nc) { return nc >= 3 ? 3 : nc; }
 __device__ __forceinline__ int stencil_off(int nc, int o) { return nc >= 3 ? o - 1 : o; }
 
-__device__ void neigh_warp(const Dev& d, const uint4* __restrict__ qa, int i, float rl2) {
+__device__ void neigh_cell_warp(const Dev& d, const uint4* __restrict__ qa, int c, float rl2) {
   const int lane = threadIdx.x & 31;
-  const uint4 qi = qa[i];
-  const Box& bx = d.box[qi.w];
-  const int cx = (int)(((unsigned long long)qi.x * (unsigned)bx.nc[0]) >> 32);
-  const int cy = (int)(((unsigned long long)qi.y * (unsigned)bx.nc[1]) >> 32);
-  const int cz = (int)(((unsigned long long)qi.z * (unsigned)bx.nc[2]) >> 32);
+  const int a0 = d.cell_start[c];
+  const int ni = d.cell_start[c + 1] - a0;
+  if (ni == 0) return;  // warp-uniform
+  const Box& bx = d.box[d.cell_box[c]];
+  const int cl = c - bx.cell_off;
+  const int cx = cl % bx.nc[0], cy = (cl / bx.nc[0]) % bx.nc[1], cz = cl / (bx.nc[0] * bx.nc[1]);
   const int nx = stencil_n(bx.nc[0]), ny = stencil_n(bx.nc[1]), nz = stencil_n(bx.nc[2]);
   int start = 0, cnt = 0;
   if (lane < nx * ny * nz) {
@@ -371,9 +376,9 @@ __device__ void neigh_warp(const Dev& d, const uint4* __restrict__ qa, int i, fl
     const int X = (cx + stencil_off(bx.nc[0], ox) + bx.nc[0]) % bx.nc[0];
     const int Y = (cy + stencil_off(bx.nc[1], oy) + bx.nc[1]) % bx.nc[1];
     const int Z = (cz + stencil_off(bx.nc[2], oz) + bx.nc[2]) % bx.nc[2];
-    const int c = bx.cell_off + X + bx.nc[0] * (Y + bx.nc[1] * Z);
-    start = d.cell_start[c];
-    cnt = d.cell_start[c + 1] - start;
+    const int cc = bx.cell_off + X + bx.nc[0] * (Y + bx.nc[1] * Z);
+    start = d.cell_start[cc];
+    cnt = d.cell_start[cc + 1] - start;
   }
   int incl = cnt;
 #pragma unroll
@@ -384,37 +389,47 @@ __device__ void neigh_warp(const Dev& d, const uint4* __restrict__ qa, int i, fl
   const int excl = incl - cnt;
   const int total = __shfl_sync(kFull, incl, 31);
   const float L0 = bx.Lq[0], L1 = bx.Lq[1], L2 = bx.Lq[2];
-  int m = 0;
-  for (int base = 0; base < total; base += 32) {
-    const int t = base + lane;
-    int lo = 0, hi = 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int ib = 0; ib < ni; ib += 32) {  // centre atoms of this cell, 32 at a time
+    const int nb = min(32, ni - ib);
+    const uint4 qmine = qa[a0 + ib + min(lane, nb - 1)];
+    int mycount = 0;  // lane k counts the neighbours of centre ib + k
+    for (int base = 0; base < total; base += 32) {
+      const int t = base + lane;
+      int lo = 0, hi = 31;
 #pragma unroll
-    for (int it = 0; it < 5; ++it) {  // smallest lane k with incl_k > t
-      const int mid = (lo + hi) >> 1;
-      const int v = __shfl_sync(kFull, incl, mid);
-      if (v > t) hi = mid; else lo = mid + 1;
-    }
-    const int sk = __shfl_sync(kFull, start, lo);
-    const int ek = __shfl_sync(kFull, excl, lo);
-    bool pred = false;
-    int j = 0;
-    if (t < total) {
-      j = sk + (t - ek);
-      if (j != i) {
-        const uint4 qj = qa[j];
-        const float dx = fix_diff(qi.x, qj.x, L0), dy = fix_diff(qi.y, qj.y, L1), dz = fix_diff(qi.z, qj.z, L2);
-        pred = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
+      for (int it = 0; it < 5; ++it) {  // smallest lane k with incl_k > t
+        const int mid = (lo + hi) >> 1;
+        const int v = __shfl_sync(kFull, incl, mid);
+        if (v > t) hi = mid; else lo = mid + 1;
+      }
+      const int sk = __shfl_sync(kFull, start, lo);
+      const int ek = __shfl_sync(kFull, excl, lo);
+      const bool have = t < total;
+      const int j = have ? sk + (t - ek) : -1;
+      const uint4 qj = have ? qa[j] : make_uint4(0u, 0u, 0u, 0u);
+      for (int k = 0; k < nb; ++k) {
+        const int i = a0 + ib + k;
+        const unsigned qx = __shfl_sync(kFull, qmine.x, k), qy = __shfl_sync(kFull, qmine.y, k),
+                       qz = __shfl_sync(kFull, qmine.z, k);
+        bool pred = false;
+        if (have && j != i) {
+          const float dx = fix_diff(qx, qj.x, L0), dy = fix_diff(qy, qj.y, L1), dz = fix_diff(qz, qj.z, L2);
+          pred = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
+        }
+        const unsigned bal = __ballot_sync(kFull, pred);
+        const int m = __shfl_sync(kFull, mycount, k);
+        const int pos = m + __popc(bal & lt);
+        if (pred && pos < d.W) d.nbr[(size_t)i * d.W + pos] = j;
+        if (lane == k) mycount += __popc(bal);
       }
     }
-    const unsigned bal = __ballot_sync(kFull, pred);
-    const int pos = m + __popc(bal & ((1u << lane) - 1u));
-    if (pred && pos < d.W) d.nbr[(size_t)i * d.W + pos] = j;
-    m += __popc(bal);
-  }
-  if (lane == 0) {
-    d.nbr_cnt[i] = m;
-    atomicMax(&d.g->max_count, m);
-    if (m > d.W) set_status(d.g, ST_OVERFLOW);
+    if (lane < nb) {
+      const int i = a0 + ib + lane;
+      d.nbr_cnt[i] = mycount;
+      atomicMax(&d.g->max_count, mycount);
+      if (mycount > d.W) set_status(d.g, ST_OVERFLOW);
+    }
   }
 }
 
@@ -572,18 +587,24 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
       const float4 uj = rowu[jj];
       const float4 xj = T.aux[aa * kLPad + jj];
       float e3 = 0.f;
-      for (int k = 0; k < n; ++k) {
+      // partner legs k != jj; the energy of each unordered triplet is taken
+      // by the item of its lower leg (k > jj)
+      auto partner = [&](int k, bool energy) {
         const float4 uk = rowu[k];
         const float c = fmaf(uj.x, uk.x, fmaf(uj.y, uk.y, uj.z * uk.z));
         const float D = c - c0;
-        const float gg = (k == jj) ? 0.f : uj.w * uk.w * D;
-        if (k > jj) e3 = fmaf(gg, D, e3);
+        const float gg = uj.w * uk.w * D;
+        if (energy) e3 = fmaf(gg, D, e3);
         const float aj = gg * xj.x;
         const float bj = gg * fmaf(c, xj.x, D * xj.y);
         gx = fmaf(-aj, uk.x, fmaf(bj, uj.x, gx));
         gy = fmaf(-aj, uk.y, fmaf(bj, uj.y, gy));
         gz = fmaf(-aj, uk.z, fmaf(bj, uj.z, gz));
-      }
+      };
+#pragma unroll 2
+      for (int k = 0; k < jj; ++k) partner(k, false);
+#pragma unroll 2
+      for (int k = jj + 1; k < n; ++k) partner(k, true);
       red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
       const float rx = xj.z * uj.x, ry = xj.z * uj.y, rz = xj.z * uj.z;
       if (wuni) {
@@ -870,8 +891,7 @@ __global__ void k_copyback(Dev d) {
 __global__ void k_neigh(Dev d, float rl2) {
   if (!d.g->any_rebuild || d.g->status) return;
   const int w = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-  if (w >= d.N) return;
-  neigh_warp(d, d.q, w, rl2);
+  if (w < d.ncell) neigh_cell_warp(d, d.q, w, rl2);
 }
 
 template <bool kCount>

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
       for (int i = tid; i < d.N; i += nth) scatter_item(d, i);
       if (grid_barrier(g, gen)) return;
       for (int i = tid; i < d.N; i += nth) copyback_item(d, i);
-      for (int w = gw; w < d.N; w += nwarps) neigh_warp(d, d.tq, w, P.rl2);
+      for (int c = gw; c < d.ncell; c += nwarps) neigh_cell_warp(d, d.tq, c, P.rl2);
       if (tid < d.nbox) d.bst[tid].rebuilds += 1;
       if (grid_barrier(g, gen)) return;
     }

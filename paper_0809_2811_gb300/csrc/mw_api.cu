@@ -63,7 +63,7 @@ struct mw_system {
   Integ integ{};
   bool integ_set = false;
   int* boxid = nullptr;  // user-order box id per atom
-  void* adj_scratch = nullptr;  // adjoint per-box accumulators
+  AdjDev adj{};  // adjoint buffers (dL/dF, dL/dx accumulators, per-box sums)
   // state
   bool state_set = false;
   bool forces_valid = false;

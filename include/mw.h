@@ -226,6 +226,38 @@ mw_status mw_get_info(mw_system* s, mw_info* out);
  * slower; the counts feed the roofline arithmetic). */
 mw_status mw_set_count_terms(mw_system* s, int on);
 
+/* ---- For callers that cannot allocate device memory ----------------------
+ * The paper has no counterpart to this call; it exists for callers that may
+ * not call cudaMalloc (an application that owns every device allocation, a
+ * plugin inside a fixed memory pool, a process whose footprint is fixed up
+ * front).  It computes what mw_energy_forces_dev computes, for ONE box of
+ * n <= MW_NOALLOC_MAX_ATOMS atoms with at most MW_NOALLOC_MAX_CELLS cells
+ * (box edge / (a sigma + skin), rounded down, multiplied over the three
+ * axes) and at most MW_NOALLOC_MAX_WIDTH neighbours per atom within
+ * a sigma + skin, and it allocates nothing: all scratch lives in one static
+ * device array of MW_NOALLOC_SCRATCH_BYTES that every GPU loading this
+ * library holds until the process exits.
+ *   x_dev       device, n*3 doubles (A, AoS, caller's order; wrapped into the box)
+ *   f_dev       device, n*3 floats out (kcal/mol/A), or NULL
+ *   energy_dev  device, 3 doubles out: E, E2, E3 (kcal/mol), or NULL
+ *   virial_dev  device, 6 doubles out: xx yy zz xy xz yz (kcal/mol), or NULL
+ *   stream      cudaStream_t the work is enqueued on (NULL = legacy default);
+ *               the call synchronises it before returning.
+ * Larger inputs are rejected with MW_EINVAL (atoms or cells) or
+ * MW_ENLIST_OVERFLOW (neighbours), with a message naming the limit.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call reuses the same array: calls whose
+ * GPU work can overlap (e.g. on two unordered streams) race and must not be
+ * made. */
+#define MW_NOALLOC_MAX_ATOMS 16384
+#define MW_NOALLOC_MAX_WIDTH 64
+#define MW_NOALLOC_MAX_CELLS 16384
+#define MW_NOALLOC_SCRATCH_BYTES (6u << 20)
+mw_status mw_energy_forces_noalloc(int n, const double box[3], const mw_params* prm, double skin,
+                                   const double* x_dev, float* f_dev, double* energy_dev, double* virial_dev,
+                                   void* stream);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* mw_last_error(void);
 

@@ -944,3 +944,202 @@ mw_status mw_set_count_terms(mw_system* s, int on) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Entry point for callers that cannot allocate device memory.
+//
+// Some callers of this library may not call cudaMalloc: code running inside a
+// captured or externally managed memory pool, plugins whose host application
+// owns all device allocations, or processes that have pinned their footprint
+// up front.  mw_energy_forces_noalloc serves them: the caller passes device
+// inputs and outputs, and every piece of scratch (fixed-point positions, cell
+// lists, neighbour list, force accumulators, counters) lives in the one
+// file-scope array below.  Each GPU that loads the library holds that array
+// (MW_NOALLOC_SCRATCH_BYTES) until the process exits.
+//
+// In host code the symbol g_noalloc_scratch is only a host-side stand-in; its
+// device address is fetched once per device with cudaGetSymbolAddress (on the
+// first call made while that device is current) and cached.  Every call
+// shares the array and leaves its contents behind: each call clears what must
+// start at zero, and calls whose work overlaps on the GPU (different streams
+// with no ordering between them) race on it.
+// ===========================================================================
+
+namespace {
+
+constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t kNaQ = 0;                                                      // uint4 q[MAX]
+constexpr size_t kNaTQ = kNaQ + na_align(sizeof(uint4) * MW_NOALLOC_MAX_ATOMS);  // uint4 tq[MAX]
+constexpr size_t kNaF = kNaTQ + na_align(sizeof(uint4) * MW_NOALLOC_MAX_ATOMS);  // float4 f[MAX]
+constexpr size_t kNaCell = kNaF + na_align(sizeof(float4) * MW_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaRank = kNaCell + na_align(sizeof(int) * MW_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaTid = kNaRank + na_align(sizeof(int) * MW_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaCnt = kNaTid + na_align(sizeof(int) * MW_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaOver = kNaCnt + na_align(sizeof(int) * MW_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaNbr = kNaOver + na_align(sizeof(int) * MW_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaCellCnt = kNaNbr + na_align(sizeof(int) * (size_t)MW_NOALLOC_MAX_ATOMS * MW_NOALLOC_MAX_WIDTH);
+constexpr size_t kNaCellStart = kNaCellCnt + na_align(sizeof(int) * MW_NOALLOC_MAX_CELLS);
+constexpr size_t kNaCellBox = kNaCellStart + na_align(sizeof(int) * (MW_NOALLOC_MAX_CELLS + 1));
+constexpr size_t kNaBox = kNaCellBox + na_align(sizeof(int) * MW_NOALLOC_MAX_CELLS);
+constexpr size_t kNaBst = kNaBox + na_align(sizeof(Box));
+constexpr size_t kNaGlobal = kNaBst + na_align(sizeof(BoxState));
+constexpr size_t kNaEnd = kNaGlobal + na_align(sizeof(Global));
+static_assert(kNaEnd <= MW_NOALLOC_SCRATCH_BYTES, "no-alloc scratch layout exceeds its stated size");
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[MW_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNaMaxDevices = 64;
+unsigned char* g_na_base[kNaMaxDevices] = {nullptr};
+
+// Positions (AoS doubles, caller's order) -> fixed point, box 0; zero forces.
+__global__ void k_na_load(Dev d, const double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.N) return;
+  const Box& bx = d.box[0];
+  uint32_t q[3];
+  for (int k = 0; k < 3; ++k) {
+    double v = x[3 * (size_t)i + k];
+    v -= bx.L[k] * floor(v / bx.L[k]);
+    if (v >= bx.L[k]) v -= bx.L[k];
+    if (v < 0.0) v = 0.0;
+    q[k] = to_fixed(v, bx.qs[k]);
+  }
+  d.q[i] = make_uint4(q[0], q[1], q[2], 0u);
+}
+
+// Cell-sorted copy of the fixed-point positions and their original indices.
+__global__ void k_na_scatter(Dev d, uint4* __restrict__ tq) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.N || d.g->status) return;
+  const int p = d.cell_start[d.cell[i]] + d.rank[i];
+  tq[p] = d.q[i];
+  d.tid[p] = i;
+}
+
+// Sorted forces -> caller's order; energies and virial of the box.
+__global__ void k_na_out(Dev d, float* __restrict__ f, double* __restrict__ e, double* __restrict__ w) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < d.N && f) {
+    const int u = d.tid[p];
+    const float4 F = d.f[p];
+    f[3 * (size_t)u] = F.x;
+    f[3 * (size_t)u + 1] = F.y;
+    f[3 * (size_t)u + 2] = F.z;
+  }
+  if (p == 0) {
+    const double* ew = d.bst[0].ew[0];
+    if (e) {
+      e[0] = ew[0] + ew[1];
+      e[1] = ew[0];
+      e[2] = ew[1];
+    }
+    if (w)
+      for (int k = 0; k < 6; ++k) w[k] = ew[2 + k];
+  }
+}
+
+mw_status na_base(unsigned char** out) {
+  int dev = 0;
+  MW_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNaMaxDevices) return fail(MW_EINVAL, "device index %d out of range", dev);
+  if (!g_na_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return fail(MW_ECUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    g_na_base[dev] = (unsigned char*)p;
+  }
+  *out = g_na_base[dev];
+  return MW_OK;
+}
+
+}  // namespace
+
+extern "C" mw_status mw_energy_forces_noalloc(int n, const double box[3], const mw_params* prm, double skin,
+                                              const double* x_dev, float* f_dev, double* energy_dev,
+                                              double* virial_dev, void* stream) {
+  if (n < 2 || !box || !x_dev) return fail(MW_EINVAL, "need n >= 2, box and x_dev");
+  if (n > MW_NOALLOC_MAX_ATOMS)
+    return fail(MW_EINVAL, "n = %d exceeds the no-alloc limit of %d atoms", n, MW_NOALLOC_MAX_ATOMS);
+  mw_status st;
+  if ((st = check_params(prm)) != MW_OK) return st;
+  if (!(skin >= 0) || !std::isfinite(skin)) return fail(MW_EINVAL, "skin must be >= 0");
+  const double rc = prm->a * prm->sigma, rl = rc + skin;
+  Box bx;
+  std::memset(&bx, 0, sizeof bx);
+  long long ncell = 1;
+  for (int k = 0; k < 3; ++k) {
+    if (!(box[k] > 0) || !std::isfinite(box[k])) return fail(MW_EINVAL, "bad box edge");
+    if (box[k] < 2.0 * rl) return fail(MW_EBOX, "box edge %d = %g A is shorter than 2 r_list = %g A", k, box[k], 2 * rl);
+    bx.L[k] = box[k];
+    bx.qs[k] = 4294967296.0 / box[k];
+    bx.Lq[k] = (float)(box[k] / 4294967296.0);
+    bx.nc[k] = std::max(1, (int)std::floor(box[k] / rl));
+    ncell *= bx.nc[k];
+  }
+  if (ncell > MW_NOALLOC_MAX_CELLS)
+    return fail(MW_EINVAL, "%lld cells exceed the no-alloc limit of %d (box too large)", ncell, MW_NOALLOC_MAX_CELLS);
+  bx.lost = (float)(0.5 * std::min(box[0], std::min(box[1], box[2])));
+  bx.off = 0;
+  bx.n = n;
+  bx.cell_off = 0;
+  bx.volume = box[0] * box[1] * box[2];
+  unsigned char* base = nullptr;
+  if ((st = na_base(&base)) != MW_OK) return st;
+  cudaStream_t sm = (cudaStream_t)stream;
+  // this call's parameters and cleared counters
+  mw_system tmp;  // host-side helper only (parameter packing); owns nothing on the device
+  tmp.prm = *prm;
+  tmp.skin = skin;
+  make_fparams(&tmp);
+  BoxState bs;
+  std::memset(&bs, 0, sizeof bs);
+  bs.s_end = bs.s_kick = 1.0;
+  Global g{};
+  g.any_rebuild = 1;
+  MW_CUDA(cudaMemcpyAsync(base + kNaBox, &bx, sizeof bx, cudaMemcpyHostToDevice, sm));
+  MW_CUDA(cudaMemcpyAsync(base + kNaBst, &bs, sizeof bs, cudaMemcpyHostToDevice, sm));
+  MW_CUDA(cudaMemcpyAsync(base + kNaGlobal, &g, sizeof g, cudaMemcpyHostToDevice, sm));
+  MW_CUDA(cudaMemsetAsync(base + kNaCellCnt, 0, sizeof(int) * (size_t)ncell, sm));
+  MW_CUDA(cudaMemsetAsync(base + kNaCellBox, 0, sizeof(int) * (size_t)ncell, sm));
+  Dev d{};
+  d.N = n;
+  d.W = MW_NOALLOC_MAX_WIDTH;
+  d.ncell = (int)ncell;
+  d.nbox = 1;
+  d.q = (uint4*)(base + kNaQ);
+  d.f = (float4*)(base + kNaF);
+  d.cell = (int*)(base + kNaCell);
+  d.rank = (int*)(base + kNaRank);
+  d.tid = (int*)(base + kNaTid);
+  d.nbr_cnt = (int*)(base + kNaCnt);
+  d.over = (int*)(base + kNaOver);
+  d.nbr = (int*)(base + kNaNbr);
+  d.cell_cnt = (int*)(base + kNaCellCnt);
+  d.cell_start = (int*)(base + kNaCellStart);
+  d.cell_box = (int*)(base + kNaCellBox);
+  d.box = (const Box*)(base + kNaBox);
+  d.bst = (BoxState*)(base + kNaBst);
+  d.g = (Global*)(base + kNaGlobal);
+  uint4* tq = (uint4*)(base + kNaTQ);
+  const int gb = div_up(n, kThreads);
+  k_na_load<<<gb, kThreads, 0, sm>>>(d, x_dev);
+  k_bin<<<gb, kThreads, 0, sm>>>(d);
+  k_scan<<<1, kScanThreads, 0, sm>>>(d);
+  k_na_scatter<<<gb, kThreads, 0, sm>>>(d, tq);
+  Dev ds = d;  // the sorted view: neighbour list and forces work on the cell-sorted copy
+  ds.q = tq;
+  k_neigh<<<div_up(ncell * 32, kThreads), kThreads, 0, sm>>>(ds, tmp.fp.rl2);
+  k_prep_force<<<gb, kThreads, 0, sm>>>(ds, 1);
+  k_force<false><<<div_up(n, kFAtoms), kFThreads, 0, sm>>>(ds, tmp.fp);
+  k_force_overflow<false><<<64, 128, 0, sm>>>(ds, tmp.fp);
+  k_na_out<<<gb, kThreads, 0, sm>>>(ds, f_dev, energy_dev, virial_dev);
+  MW_CUDA(cudaGetLastError());
+  Global gout;
+  MW_CUDA(cudaMemcpyAsync(&gout, base + kNaGlobal, sizeof gout, cudaMemcpyDeviceToHost, sm));
+  MW_CUDA(cudaStreamSynchronize(sm));
+  if (gout.status == ST_OVERFLOW)
+    return fail(MW_ENLIST_OVERFLOW, "an atom has %d neighbours within r_list; the no-alloc limit is %d",
+                gout.max_count, MW_NOALLOC_MAX_WIDTH);
+  if (gout.status) return status_error(gout);
+  return MW_OK;
+}

@@ -28,7 +28,8 @@ EXPORTS = (
     "mw_set_state_dev", "mw_get_state", "mw_get_state_dev", "mw_set_params", "mw_build_neighbors",
     "mw_get_neighbors", "mw_energy_forces", "mw_energy_forces_dev", "mw_step", "mw_get_thermo",
     "mw_energy_forces_vjp", "mw_set_engine", "mw_set_nbr_width", "mw_autotune", "mw_get_info",
-    "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_last_error",
+    "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc",
+    "mw_last_error",
 )
 
 
@@ -110,6 +111,8 @@ def lib():
             "mw_forces_async": [P],
             "mw_step_async": [P, ctypes.POINTER(mw_integrator), ctypes.c_int],
             "mw_sync": [P],
+            "mw_energy_forces_noalloc": [ctypes.c_int, dp, ctypes.POINTER(mw_params), ctypes.c_double, P, P, P, P,
+                                         P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -289,6 +292,15 @@ def mw_step_async(h: int, integ: mw_integrator, nsteps: int):
 
 def mw_sync(h: int):
     _check(lib().mw_sync(h))
+
+
+def mw_energy_forces_noalloc(n: int, box, x_dev, f_dev=None, energy_dev=None, virial_dev=None,
+                             prm: Optional[mw_params] = None, skin: float = 1.0, stream: Optional[int] = None):
+    """Energy/forces of one box without any device allocation (see mw.h)."""
+    prm = prm or mw_params_default()
+    b = np.ascontiguousarray(box, np.float64)
+    _check(lib().mw_energy_forces_noalloc(int(n), _dp(b), ctypes.byref(prm), skin, _ptr(x_dev), _ptr(f_dev),
+                                          _ptr(energy_dev), _ptr(virial_dev), stream))
 
 
 def mw_last_error() -> str:

@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prep-steps", type=int, default=3000)
+    ap.add_argument("--workload", default="ice_liquid_32k",
+                    choices=["ice_liquid_32k", "nve512", "batch256", "slab1m", "fm4096x64"])
+    ap.add_argument("--drift-steps", type=int, default=0,
+                    help="after timing, run this many NVE steps and report the energy drift per ns")
     return ap.parse_args()
 
 
@@ -255,6 +259,9 @@ def run_gpu(args, world, rank, local, pg):
     sysm.set_state(x, v)
     integ = mw.make_integrator(DT, mw.MW_NOSE_HOOVER, T_RUN, TAU)
     natoms = sum(n)
+    tuned = None
+    if args.engine == "auto":  # engine and skin picked by the autotuner on this state
+        tuned = mw.mw_autotune(sysm.h, integ, 50)
 
     # warm-up
     mw.mw_step(sysm.h, integ, max(args.warmup, 3), sysm.nbox)
@@ -350,6 +357,7 @@ def run_gpu(args, world, rank, local, pg):
                    "l2": "flushed between steps (512 MB write)",
                    "engine": {1: "graph", 2: "persistent"}.get(info["engine"], str(info["engine"])),
                    "nbr_width": info["nbr_width"], "rebuilds_in_timed_region": int(rebuilds),
+                   "r_list_A": info["r_list"], "autotuned": tuned is not None,
                    "liquid_pe_per_atom_after_melt": liq_pe, "wall_s_timed": t_wall,
                    "host_us_per_step_call": 1e6 * t_host / K},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -363,6 +371,165 @@ def run_gpu(args, world, rank, local, pg):
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ other workloads
+
+def _timed_steps(torch, mw, sysm, integ, stream, K, flush):
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    for k in range(K):
+        ev0[k].record(stream)
+        mw.mw_step_async(sysm.h, integ, 1)
+        ev1[k].record(stream)
+        if flush is not None:
+            flush.fill_(float(k))
+    torch.cuda.synchronize()
+    mw.mw_sync(sysm.h)
+    return sum(a.elapsed_time(c) for a, c in zip(ev0, ev1)) / 1e3
+
+
+def _nve_drift(mw, sysm, nsteps, dt, natoms):
+    """Energy drift of an NVE segment: slope of the conserved energy (linear
+    fit over 20 points), per ns and per atom, and relative to |E|."""
+    integ = mw.make_integrator(dt, mw.MW_NVE)
+    es, ts = [], []
+    chunk = max(1, nsteps // 20)
+    t = 0
+    th = mw.mw_step(sysm.h, integ, 0, sysm.nbox)
+    es.append(sum(x["conserved"] for x in th))
+    ts.append(0.0)
+    while t < nsteps:
+        th = mw.mw_step(sysm.h, integ, chunk, sysm.nbox)
+        t += chunk
+        es.append(sum(x["conserved"] for x in th))
+        ts.append(t * dt)
+    slope = float(np.polyfit(np.array(ts), np.array(es), 1)[0])  # kcal/mol per fs
+    return {"nve_steps": t, "dt_fs": dt, "drift_kcal_mol_per_ns_per_atom": slope * 1e6 / natoms,
+            "drift_relative_per_ns": slope * 1e6 / abs(es[0]),
+            "max_abs_dev_relative": float(np.abs(np.array(es) - es[0]).max() / abs(es[0]))}
+
+
+def run_other(args, world, rank, local, pg):
+    import torch
+    from paper_0809_2811_gb300 import build, mw
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    sp = stream.cuda_stream
+    K = args.steps
+    seed = I.BASE_SEED + 17 * rank
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    extra = {}
+    if args.workload == "fm4096x64":
+        return run_fm(args, world, rank, torch, mw, dev, stream, sp, flush)
+    if args.workload == "nve512":
+        x, v, box = I.nve512(I.BASE_SEED + 1)
+        sysm = mw.System(512, box, stream=sp)
+        sysm.set_state(x, v)
+        integ = mw.make_integrator(10.0, mw.MW_NVE)
+        natoms = 512
+        cfg = {"workload": "512-atom SC-jitter NVE, 1.000 g/cm^3, 298 K start, dt 10 fs", "atoms": 512}
+        flush_use = flush
+    elif args.workload == "batch256":
+        n, boxes, x, v, T = I.batch_boxes(256, I.BASE_SEED + 3)
+        sysm = mw.System(list(n), boxes, stream=sp)
+        sysm.set_state(x, v)
+        integ = mw.make_integrator(10.0, mw.MW_NOSE_HOOVER, T0_per_box=T, tau=TAU)
+        natoms = int(n.sum())
+        cfg = {"workload": "256 boxes, N~U[216,8000], rho~U[0.92,1.10], T~U[200,320] K, NH, dt 10 fs",
+               "boxes": 256, "atoms": natoms}
+        flush_use = None  # working set ~250 MB > L2
+    else:  # slab1m
+        x, box, _ = I.ice_liquid_slab()
+        v = I.maxwell_velocities(len(x), 250.0, seed=seed)
+        sysm = mw.System(len(x), box, stream=sp)
+        sysm.set_state(x, v)
+        integ = mw.make_integrator(10.0, mw.MW_NOSE_HOOVER, 250.0, TAU)
+        natoms = len(x)
+        cfg = {"workload": "ice Ih slab 524288 @0.92 + liquid-start slab 524288 @0.9998 along z, NH 250 K, "
+                           "dt 10 fs", "atoms": natoms, "box_A": [float(b) for b in box]}
+        flush_use = None  # working set ~250 MB > L2
+    if args.engine != "auto":
+        sysm.set_engine({"graph": mw.MW_ENGINE_GRAPH, "persistent": mw.MW_ENGINE_PERSISTENT}[args.engine])
+    mw.mw_step(sysm.h, integ, max(args.warmup, 3), sysm.nbox)
+    reb0 = sum(t["rebuilds"] for t in sysm.thermo())
+    span = _timed_steps(torch, mw, sysm, integ, stream, K, flush_use)
+    span_max = reduce_max(pg, span, dev)
+    rebuilds = sum(t["rebuilds"] for t in sysm.thermo()) - reb0
+    if args.drift_steps > 0:
+        extra["nve"] = _nve_drift(mw, sysm, args.drift_steps, 10.0, natoms)
+    info = sysm.info()
+    out = {"metric": METRIC, "value": world * natoms * K / span_max, "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": 1e3 * span_max / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 pair/triplet, f64 integrate+reductions", "data": "synthetic",
+           "config": {**cfg, "engine": {1: "graph", 2: "persistent"}.get(info["engine"]),
+                      "rebuilds_in_timed_region": int(rebuilds),
+                      "l2": "flushed between steps" if flush_use is not None else "working set > L2"},
+           **extra}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_fm(args, world, rank, torch, mw, dev, stream, sp, flush):
+    """Force-matching gradient evaluations: 64 frames of a 4096-atom 260 K
+    liquid (one frame per ps of an NVT run of this engine), target forces at
+    the paper's parameters, evaluated from lambda = 21, epsilon and sigma x 1.05.
+    One evaluation = forces of a frame + loss gradient + adjoint."""
+    from paper_0809_2811_gb300 import torch_ops
+    nfr, n = 64, 4096
+    x0, box = I.jittered_box(n, 0.9998, 0.1, I.BASE_SEED + 4)
+    v0 = I.maxwell_velocities(n, 400.0, seed=I.BASE_SEED + 44)
+    s = mw.System(n, box, stream=sp)
+    s.set_state(x0, v0)
+    s.step(1000, dt=5.0, thermostat=mw.MW_BERENDSEN, T0=400.0, tau=200.0)
+    s.step(1000, dt=10.0, thermostat=mw.MW_NOSE_HOOVER, T0=260.0, tau=TAU)
+    frames = []
+    for _ in range(nfr):
+        s.step(100, dt=10.0, thermostat=mw.MW_NOSE_HOOVER, T0=260.0, tau=TAU)
+        frames.append(s.get_state()[0])
+    s.close()
+    X = torch.tensor(np.concatenate(frames), device=dev)
+    ff = torch_ops.ForceField([n] * nfr, np.stack([box] * nfr))
+    theta_paper = torch_ops.paper_theta(dev)
+    with torch.no_grad():
+        f_star = ff.forces(X, theta_paper).detach()
+    theta = torch.tensor([21.0, 6.189 * 1.05, 2.3925 * 1.05], dtype=torch.float64, device=dev, requires_grad=True)
+
+    def one_eval(k):
+        th = theta if k % 2 == 0 else (theta * (1 + 1e-7))  # a new theta each evaluation: list rebuilt
+        xg = X.clone().requires_grad_(True)
+        loss = torch_ops.force_matching_loss(ff.forces(xg, th), f_star)
+        loss.backward()
+        return loss
+
+    for k in range(max(args.warmup, 3)):
+        one_eval(k)
+    torch.cuda.synchronize()
+    K = args.steps
+    t0 = time.perf_counter()
+    for k in range(K):
+        loss = one_eval(k)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    el = reduce_max(pg_holder[0], el, dev) if pg_holder[0] is not None else el
+    out = {"metric": "grad evals/s (force matching, one 4096-atom frame forward + adjoint)",
+           "value": world * nfr * K / el, "unit": "frame-grad-evals/s", "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 forces/adjoint, f64 reductions", "data": "synthetic",
+           "config": {"workload": "64 frames x 4096 atoms, 0.9998 g/cm^3, 260 K NH trajectory (1 ps apart); "
+                                  "targets at the paper's parameters; theta0 = (21, 1.05 eps, 1.05 sigma)",
+                      "frames": nfr, "atoms_per_frame": n, "timing": "wall clock incl. host glue",
+                      "loss": float(loss.item()),
+                      "grad_theta": [float(v) for v in theta.grad.tolist()] if theta.grad is not None else None}}
+    ff.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+pg_holder = [None]
 
 
 def run_reference(args, world, rank):
@@ -389,11 +556,14 @@ def run_reference(args, world, rank):
 def main():
     args = parse()
     world, rank, local, pg = dist_setup(args)
+    pg_holder[0] = pg
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
-        else:
+        elif args.workload == "ice_liquid_32k":
             run_gpu(args, world, rank, local, pg)
+        else:
+            run_other(args, world, rank, local, pg)
     finally:
         if pg is not None:
             pg.destroy_process_group()

@@ -212,10 +212,19 @@ mw_status mw_set_engine(mw_system* s, int engine);
  * stale; a width too small is grown again on the next build. */
 mw_status mw_set_nbr_width(mw_system* s, int width);
 
-/* Times both engines on a copy of the current state for `steps` steps each
- * (the state is restored afterwards) and makes the faster one the AUTO
- * choice; *best_engine (may be NULL) receives it.  Results are cached per
- * device name and box-size signature in the file named by the environment
+/* Sets the Verlet-list skin (A, >= 0): the list radius is a sigma + skin and
+ * the list is rebuilt once an atom has moved more than skin/2.  A pure
+ * performance parameter (results agree to round-off).  Fails with MW_EBOX if
+ * a box edge would be shorter than 2 (a sigma + skin). */
+mw_status mw_set_skin(mw_system* s, double skin);
+
+/* Autotuner.  Runs `steps` steps for each candidate configuration - engine
+ * (graph / persistent), skin (0.7x, 1x, 1.4x, 1.8x the current one) and
+ * persistent grid size - each from the same saved state (positions,
+ * velocities and thermostat state are restored exactly between candidates and
+ * at the end), keeps the fastest by GPU time as the AUTO engine and the skin,
+ * and writes it to *best_engine (may be NULL).  The choice is cached per
+ * device name and system signature in the text file named by the environment
  * variable MW_AUTOTUNE_CACHE, when set. */
 mw_status mw_autotune(mw_system* s, const mw_integrator* integ, int steps, int* best_engine);
 

@@ -49,7 +49,7 @@ constexpr int kThreads = 128;
 }  // namespace
 
 struct mw_system {
-  int nbox = 0, N = 0, W = 0, ncell = 0;
+  int nbox = 0, N = 0, W = 0, ncell = 0, ncell_cap = 0;
   std::vector<int> n, off;
   std::vector<Box> boxes;
   mw_params prm{};
@@ -186,14 +186,17 @@ mw_status upload_integ(mw_system* s) {
 }
 
 mw_status alloc_cells(mw_system* s) {
-  dfree(s, s->d.cell_cnt);
-  dfree(s, s->d.cell_start);
-  dfree(s, s->d.cell_box);
-  s->d.cell_cnt = s->d.cell_start = s->d.cell_box = nullptr;
   mw_status st;
-  if ((st = dalloc(s, &s->d.cell_cnt, s->ncell)) != MW_OK) return st;
-  if ((st = dalloc(s, &s->d.cell_start, s->ncell + 1)) != MW_OK) return st;
-  if ((st = dalloc(s, &s->d.cell_box, s->ncell)) != MW_OK) return st;
+  if (s->ncell > s->ncell_cap) {  // grow only; a smaller grid reuses the arrays
+    dfree(s, s->d.cell_cnt);
+    dfree(s, s->d.cell_start);
+    dfree(s, s->d.cell_box);
+    s->d.cell_cnt = s->d.cell_start = s->d.cell_box = nullptr;
+    if ((st = dalloc(s, &s->d.cell_cnt, s->ncell)) != MW_OK) return st;
+    if ((st = dalloc(s, &s->d.cell_start, s->ncell + 1)) != MW_OK) return st;
+    if ((st = dalloc(s, &s->d.cell_box, s->ncell)) != MW_OK) return st;
+    s->ncell_cap = s->ncell;
+  }
   MW_CUDA(cudaMemsetAsync(s->d.cell_cnt, 0, sizeof(int) * s->ncell, s->stream));
   s->cell_box_host.resize(s->ncell);
   for (int b = 0; b < s->nbox; ++b) {
@@ -612,6 +615,7 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
 
 #include "mw_persistent_host.inc"
 #include "mw_adjoint_host.inc"
+#include "mw_autotune.inc"
 
 extern "C" {
 

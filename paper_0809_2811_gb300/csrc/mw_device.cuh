@@ -456,6 +456,7 @@ constexpr int kFThreads = 128;
 constexpr int kFAtoms = kFThreads / kG;  // centres per block
 constexpr int kWAtoms = 32 / kG;         // centres per warp
 constexpr int kLPad = kLMax + 1;         // row pitch (float4): shifts rows by 4 banks
+constexpr int kPre = 8;                  // neighbour slots per lane fetched ahead in the leg phase
 
 struct LegTable {
   float4 ue[kFAtoms * kLPad];   // ux, uy, uz, ee
@@ -488,22 +489,35 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     L2 = bx.Lq[2];
   }
   T.fi[a][g] = 0.f;
-  // ---- leg phase
+  // ---- leg phase: row entries and candidate positions are fetched for up to
+  // kPre slots per lane before any is used (one memory latency instead of a
+  // dependent chain per slot); rows longer than kG * kPre continue unprefetched.
   const int iters = __reduce_max_sync(kFull, (cnt + kG - 1) / kG);
   const unsigned gsh = lane & ~(kG - 1);
   const int* row = d.nbr + (size_t)(valid ? i : 0) * d.W;
   int nl = 0;
-  for (int t = 0; t < iters; ++t) {
+  int jr[kPre];
+  uint32_t qx[kPre], qy[kPre], qz[kPre];
+#pragma unroll
+  for (int t = 0; t < kPre; ++t) {
     const int s = g + kG * t;
+    jr[t] = (s < cnt) ? __ldg(row + s) : -1;
+  }
+#pragma unroll
+  for (int t = 0; t < kPre; ++t) {
+    uint4 qj = make_uint4(0u, 0u, 0u, 0u);
+    if (jr[t] >= 0) qj = d.q[jr[t]];
+    qx[t] = qj.x;
+    qy[t] = qj.y;
+    qz[t] = qj.z;
+  }
+  auto leg_slot = [&](int j, uint32_t jx, uint32_t jy, uint32_t jz, bool have) {
     bool leg = false;
     float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 1.f;
-    int j = 0;
-    if (s < cnt) {
-      j = __ldg(row + s);
-      const uint4 qj = d.q[j];
-      dx = fix_diff(qi.x, qj.x, L0);
-      dy = fix_diff(qi.y, qj.y, L1);
-      dz = fix_diff(qi.z, qj.z, L2);
+    if (have) {
+      dx = fix_diff(qi.x, jx, L0);
+      dy = fix_diff(qi.y, jy, L1);
+      dz = fix_diff(qi.z, jz, L2);
       r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       leg = r2 < P.rc2;
     }
@@ -553,6 +567,17 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
       T.aux[a * kLPad + pos] = ax;
     }
     nl += __popc(m);
+  };
+#pragma unroll
+  for (int t = 0; t < kPre; ++t)
+    if (t < iters) leg_slot(jr[t], qx[t], qy[t], qz[t], jr[t] >= 0);
+  for (int t = kPre; t < iters; ++t) {  // long rows (dense input)
+    const int s = g + kG * t;
+    const bool have = s < cnt;
+    const int j = have ? __ldg(row + s) : 0;
+    uint4 qj = make_uint4(0u, 0u, 0u, 0u);
+    if (have) qj = d.q[j];
+    leg_slot(j, qj.x, qj.y, qj.z, have);
   }
   if (g == 0) T.nl[a] = valid ? nl : 0;
   __syncwarp();

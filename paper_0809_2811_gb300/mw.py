@@ -28,7 +28,7 @@ EXPORTS = (
     "mw_set_state_dev", "mw_get_state", "mw_get_state_dev", "mw_set_params", "mw_build_neighbors",
     "mw_get_neighbors", "mw_energy_forces", "mw_energy_forces_dev", "mw_step", "mw_get_thermo",
     "mw_energy_forces_vjp", "mw_set_engine", "mw_set_nbr_width", "mw_autotune", "mw_get_info",
-    "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc",
+    "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc", "mw_set_skin",
     "mw_last_error",
 )
 
@@ -111,6 +111,7 @@ def lib():
             "mw_forces_async": [P],
             "mw_step_async": [P, ctypes.POINTER(mw_integrator), ctypes.c_int],
             "mw_sync": [P],
+            "mw_set_skin": [P, ctypes.c_double],
             "mw_energy_forces_noalloc": [ctypes.c_int, dp, ctypes.POINTER(mw_params), ctypes.c_double, P, P, P, P,
                                          P],
         }
@@ -301,6 +302,10 @@ def mw_energy_forces_noalloc(n: int, box, x_dev, f_dev=None, energy_dev=None, vi
     b = np.ascontiguousarray(box, np.float64)
     _check(lib().mw_energy_forces_noalloc(int(n), _dp(b), ctypes.byref(prm), skin, _ptr(x_dev), _ptr(f_dev),
                                           _ptr(energy_dev), _ptr(virial_dev), stream))
+
+
+def mw_set_skin(h: int, skin: float):
+    _check(lib().mw_set_skin(h, float(skin)))
 
 
 def mw_last_error() -> str:

@@ -6,7 +6,8 @@ adjoint forms the Hessian-vector product and the (lambda, epsilon, sigma)
 derivatives analytically in FP32 from recomputed leg and triplet terms.
 Tolerance (derived from the arithmetic): second derivatives carry the FP32
 cancellation of the forces once more, so dL/dx is held to 1e-4 per atom
-relative to max(|ref_i|, rms(ref)) and dL/dtheta to 1e-4 relative.
+relative to max(|ref_i|, rms(ref)) and dL/dtheta to 1e-4 relative (dL/depsilon
+against the magnitude of its two cancelling parts, see _check_theta).
 """
 import math
 
@@ -24,6 +25,21 @@ def _rel_err_rows(g, r):
     mag = np.linalg.norm(r, axis=1)
     den = np.maximum(mag, math.sqrt(np.mean(mag ** 2)))
     return float((np.linalg.norm(g - r, axis=1) / den).max())
+
+
+def _check_theta(orc, x, box, w, gt, gt_ref, prm=None):
+    """dL/dlambda and dL/dsigma relative; dL/depsilon = -(D2 + D3)/epsilon is a
+    cancelling sum like E2 + E3, so it is judged against (|D2| + |D3|)/epsilon
+    (D2 from the oracle at lambda = 0, D3 = -lambda dL/dlambda)."""
+    p = orc.default_params() if prm is None else prm
+    p0 = p.copy()
+    p0[0] = 0.0
+    _, g2 = orc.force_vjp(x, box, w, p0)
+    d2 = -p[1] * g2[1]
+    d3 = -p[0] * gt_ref[0]
+    assert abs(gt[0] - gt_ref[0]) <= G_TOL * abs(gt_ref[0])
+    assert abs(gt[1] - gt_ref[1]) <= G_TOL * (abs(d2) + abs(d3)) / p[1]
+    assert abs(gt[2] - gt_ref[2]) <= G_TOL * abs(gt_ref[2])
 
 
 def _gpu_vjp(mwlib, torch, n, box, x, w, prm=None):
@@ -61,7 +77,7 @@ def test_adjoint_matches_oracle(mwlib, orc, case):
     gx_ref, gt_ref = orc.force_vjp(x, box, w)
     gx, gt = _gpu_vjp(mwlib, torch, len(x), box, x, w)
     assert _rel_err_rows(gx, gx_ref) <= G_TOL
-    np.testing.assert_allclose(gt[0], gt_ref, rtol=G_TOL)
+    _check_theta(orc, x, box, w, gt[0], gt_ref)
 
 
 def test_adjoint_dense_overflow_path(mwlib, orc):
@@ -73,7 +89,7 @@ def test_adjoint_dense_overflow_path(mwlib, orc):
     gx_ref, gt_ref = orc.force_vjp(x, box, w)
     gx, gt = _gpu_vjp(mwlib, torch, len(x), box, x, w)
     assert _rel_err_rows(gx, gx_ref) <= G_TOL
-    np.testing.assert_allclose(gt[0], gt_ref, rtol=G_TOL)
+    _check_theta(orc, x, box, w, gt[0], gt_ref)
 
 
 def test_adjoint_at_perturbed_parameters_batch(mwlib, orc):
@@ -94,7 +110,7 @@ def test_adjoint_at_perturbed_parameters_batch(mwlib, orc):
     for b in range(3):
         gx_ref, gt_ref = orc.force_vjp(xs[b], boxes[b], w[off:off + n[b]], po)
         assert _rel_err_rows(gx[off:off + n[b]], gx_ref) <= G_TOL
-        np.testing.assert_allclose(gt[b], gt_ref, rtol=G_TOL)
+        _check_theta(orc, xs[b], boxes[b], w[off:off + n[b]], gt[b], gt_ref, po)
         off += n[b]
 
 
@@ -123,4 +139,4 @@ def test_autograd_force_matching_step(mwlib, orc):
     w = 2.0 * (f_cur - f_target) / f_cur.size
     gx_ref, gt_ref = orc.force_vjp(x, box, w, po)
     assert _rel_err_rows(gx, gx_ref) <= G_TOL
-    np.testing.assert_allclose(gth, gt_ref, rtol=G_TOL)
+    _check_theta(orc, x, box, w, gth, gt_ref, po)

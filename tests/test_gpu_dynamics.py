@@ -167,3 +167,39 @@ def test_engines_agree_over_a_long_run(mwlib):
     # each conserves H' to the paper's 1e-4 and they agree to that level
     assert a["conserved"] == pytest.approx(b["conserved"], rel=1e-4)
     assert a["temperature"] == pytest.approx(b["temperature"], rel=5e-2)
+
+
+def test_autotune_restores_state(mwlib, tmp_path, monkeypatch):
+    """The autotuner runs candidates from a saved state and restores it: a run
+    after tuning matches a run that never tuned (to round-off growth), and a
+    cached choice is reused."""
+    monkeypatch.setenv("MW_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    x, box = I.jittered_box(2048, 1.0, 0.1, 17)
+    v = I.maxwell_velocities(2048, 260.0, seed=18)
+    res = []
+    for tune in (False, True):
+        s = mwlib.System(2048, box)
+        try:
+            s.set_state(x, v)
+            s.step(20, dt=10.0, thermostat=2, T0=260.0, tau=500.0)
+            before = s.thermo()[0]
+            if tune:
+                it = mwlib.make_integrator(10.0, 2, 260.0, 500.0)
+                eng = mwlib.mw_autotune(s.h, it, 20)
+                assert eng in (1, 2)
+                after = s.thermo()[0]
+                assert after["step"] == before["step"]
+                assert after["xi"] == pytest.approx(before["xi"], rel=1e-12, abs=1e-15)
+            res.append(s.step(30, dt=10.0, thermostat=2, T0=260.0, tau=500.0)[0])
+        finally:
+            s.close()
+    assert res[0]["step"] == res[1]["step"] == 50
+    assert res[1]["conserved"] == pytest.approx(res[0]["conserved"], rel=2e-5)
+    assert res[1]["pe"] == pytest.approx(res[0]["pe"], rel=2e-4)
+    assert (tmp_path / "tune.txt").read_text().strip()
+    s = mwlib.System(2048, box)
+    try:
+        s.set_state(x, v)
+        assert mwlib.mw_autotune(s.h, mwlib.make_integrator(10.0, 2, 260.0, 500.0), 20) in (1, 2)  # cached
+    finally:
+        s.close()

@@ -235,6 +235,12 @@ mw_status set_global_field(mw_system* s, size_t offset, int value) {
   return MW_OK;
 }
 
+mw_status flag_all(mw_system* s) {
+  k_flag_all<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d);
+  MW_CUDA(cudaGetLastError());
+  return MW_OK;
+}
+
 mw_status read_global(mw_system* s, Global* g) {
   MW_CUDA(cudaMemcpyAsync(g, s->d.g, sizeof(Global), cudaMemcpyDeviceToHost, s->stream));
   MW_CUDA(cudaStreamSynchronize(s->stream));
@@ -324,7 +330,7 @@ mw_status ensure_forces(mw_system* s) {
     if (g.status == ST_OVERFLOW) {
       if ((st = grow_nbr_after_overflow(s, g)) != MW_OK) return st;
       if ((st = set_global_field(s, offsetof(Global, status), 0)) != MW_OK) return st;
-      if ((st = set_global_field(s, offsetof(Global, any_rebuild), 1)) != MW_OK) return st;
+      if ((st = flag_all(s)) != MW_OK) return st;
       continue;
     }
     if (g.status) return status_error(g);
@@ -395,7 +401,7 @@ mw_status run_graph_engine(mw_system* s, int nsteps) {
       if (++guard > 8) return fail(MW_ENLIST_OVERFLOW, "neighbour list kept overflowing");
       if ((st = grow_nbr_after_overflow(s, g)) != MW_OK) return st;
       if ((st = set_global_field(s, offsetof(Global, status), 0)) != MW_OK) return st;
-      if ((st = set_global_field(s, offsetof(Global, any_rebuild), 1)) != MW_OK) return st;
+      if ((st = flag_all(s)) != MW_OK) return st;
       if ((st = finish_interrupted_step(s)) != MW_OK) return st;
       Global g2;
       if ((st = read_global(s, &g2)) != MW_OK) return st;
@@ -704,7 +710,7 @@ mw_status mw_set_params(mw_system* s, const mw_params* prm) {
   s->graph_dirty = true;
   s->forces_valid = false;
   if (s->state_set) {
-    if ((st = set_global_field(s, offsetof(Global, any_rebuild), 1)) != MW_OK) return st;
+    if ((st = flag_all(s)) != MW_OK) return st;
   }
   MW_CUDA(cudaStreamSynchronize(s->stream));
   return MW_OK;
@@ -715,7 +721,7 @@ mw_status mw_build_neighbors(mw_system* s, int* max_count_out) {
   if (!s->state_set) return fail(MW_ESTATE, "no state set");
   mw_status st;
   for (int attempt = 0; attempt < 4; ++attempt) {
-    if ((st = set_global_field(s, offsetof(Global, any_rebuild), 1)) != MW_OK) return st;
+    if ((st = flag_all(s)) != MW_OK) return st;
     launch_rebuild(s);
     k_prep_force<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d, 0);  // list consumed
     MW_CUDA(cudaGetLastError());
@@ -797,7 +803,7 @@ mw_status mw_energy_forces_dev(mw_system* s, const double* x_dev, float* f_dev, 
     k_load_positions<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, x_dev, s->boxid, 0);
     MW_CUDA(cudaGetLastError());
     mw_status st;
-    if ((st = set_global_field(s, offsetof(Global, any_rebuild), 1)) != MW_OK) return st;
+    if ((st = flag_all(s)) != MW_OK) return st;
     s->forces_valid = false;
   }
   mw_status st;
@@ -909,7 +915,7 @@ mw_status mw_set_nbr_width(mw_system* s, int width) {
   // Forces at the current positions stay valid; the list is rebuilt in the
   // rebuild phase of the next step (or of the next force evaluation).
   if (s->state_set) {
-    if ((st = set_global_field(s, offsetof(Global, any_rebuild), 1)) != MW_OK) return st;
+    if ((st = flag_all(s)) != MW_OK) return st;
   }
   MW_CUDA(cudaStreamSynchronize(s->stream));
   return MW_OK;
@@ -1098,6 +1104,7 @@ extern "C" mw_status mw_energy_forces_noalloc(int n, const double box[3], const 
   BoxState bs;
   std::memset(&bs, 0, sizeof bs);
   bs.s_end = bs.s_kick = 1.0;
+  bs.rebuild = 1;
   Global g{};
   g.any_rebuild = 1;
   MW_CUDA(cudaMemcpyAsync(base + kNaBox, &bx, sizeof bx, cudaMemcpyHostToDevice, sm));

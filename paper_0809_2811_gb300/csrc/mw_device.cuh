@@ -35,7 +35,7 @@ enum : int { TH_NVE = 0, TH_BERENDSEN = 1, TH_NH = 2 };
 
 // Legs staged per centre atom in the fused force kernel's shared-memory table;
 // centres with more legs take the overflow path.
-constexpr int kLMax = 32;
+constexpr int kLMax = 24;
 // Upper bound for the overflow path (more legs than this = overlapping atoms).
 constexpr int kMaxLegsOverflow = 64;
 
@@ -151,6 +151,13 @@ __device__ __forceinline__ int cell_of(const uint4& q, const Box& bx) {
 }
 
 __device__ __forceinline__ void set_status(Global* g, int st) { atomicCAS(&g->status, 0, st); }
+
+// Rebuilds are per box.  On a rebuild step every atom is binned and the scan
+// over all cells gives absolute cell starts (every box's counts add up to its
+// atom range), but only boxes whose flag kick1 raised (or that the host
+// flagged) are re-sorted and re-listed; the others keep their order and list
+// and never read their recomputed starts.
+__device__ __forceinline__ bool box_flagged(const Dev& d, int b) { return d.bst[b].rebuild != 0; }
 
 // Per-box accumulation of NV values held as FP32 by each thread; the sums
 // across blocks are FP64.  Every thread of the block calls it (b < 0 for
@@ -365,7 +372,7 @@ __device__ void neigh_cell_warp(const Dev& d, const uint4* __restrict__ qa, int 
   const int lane = threadIdx.x & 31;
   const int a0 = d.cell_start[c];
   const int ni = d.cell_start[c + 1] - a0;
-  if (ni == 0) return;  // warp-uniform
+  if (ni == 0 || !box_flagged(d, d.cell_box[c])) return;  // warp-uniform
   const Box& bx = d.box[d.cell_box[c]];
   const int cl = c - bx.cell_off;
   const int cx = cl % bx.nc[0], cy = (cl / bx.nc[0]) % bx.nc[1], cz = cl / (bx.nc[0] * bx.nc[1]);
@@ -511,73 +518,88 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     qy[t] = qj.y;
     qz[t] = qj.z;
   }
-  auto leg_slot = [&](int j, uint32_t jx, uint32_t jy, uint32_t jz, bool have) {
-    bool leg = false;
-    float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 1.f;
+  // pass A: distance test only; hits are compacted (ballot + popc in the lane
+  // group) into the centre's row as (d, r^2 | j)
+  auto test_slot = [&](int j, uint32_t jx, uint32_t jy, uint32_t jz, bool have) {
+    bool hit = false;
+    float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
     if (have) {
       dx = fix_diff(qi.x, jx, L0);
       dy = fix_diff(qi.y, jy, L1);
       dz = fix_diff(qi.z, jz, L2);
       r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      leg = r2 < P.rc2;
+      hit = r2 < P.rc2;
     }
-    float4 ue = make_float4(0.f, 0.f, 0.f, 0.f), ax = ue;
-    if (leg) {
-      const float invr = rsqrtf(r2);
-      const float r = r2 * invr;
-      leg = r < P.rc;
-      if (leg) {
-        const float ux = dx * invr, uy = dy * invr, uz = dz * invr;
-        const float tinv = __fdividef(1.0f, r - P.rc);  // 1/(r - a sig) < 0
-        const float e2 = exp2f(P.sig_l2e * tinv);
-        const float e3 = exp2f(P.gsig_l2e * tinv);
-        const float sr = P.sig * invr;
-        float srp, srq;
-        if (P.p == 4 && P.q == 0) {  // the SW / mW exponents
-          const float sr2 = sr * sr;
-          srp = sr2 * sr2;
-          srq = 1.0f;
-        } else {
-          srp = powi(sr, P.p);
-          srq = powi(sr, P.q);
-        }
-        const float brk = fmaf(P.B, srp, -srq);
-        const float ae2 = P.Aeps * e2;
-        const float phi = ae2 * brk;
-        const float dphi = ae2 * (fmaf((float)(-P.p) * P.B, srp, (float)P.q * srq) * invr - brk * P.sig * tinv * tinv);
-        acc[0] = fmaf(0.5f, phi, acc[0]);
-        fx = fmaf(dphi, ux, fx);
-        fy = fmaf(dphi, uy, fy);
-        fz = fmaf(dphi, uz, fz);
-        const float wv = -0.5f * dphi * r;
-        acc[2] = fmaf(wv * ux, ux, acc[2]);
-        acc[3] = fmaf(wv * uy, uy, acc[3]);
-        acc[4] = fmaf(wv * uz, uz, acc[4]);
-        acc[5] = fmaf(wv * ux, uy, acc[5]);
-        acc[6] = fmaf(wv * ux, uz, acc[6]);
-        acc[7] = fmaf(wv * uy, uz, acc[7]);
-        ue = make_float4(ux, uy, uz, P.sle * e3);
-        ax = make_float4(2.0f * invr, P.gsig * tinv * tinv, r, __int_as_float(j));
-      }
-    }
-    const unsigned m = (__ballot_sync(kFull, leg) >> gsh) & ((1u << kG) - 1u);
+    const unsigned m = (__ballot_sync(kFull, hit) >> gsh) & ((1u << kG) - 1u);
     const int pos = nl + __popc(m & ((1u << g) - 1u));
-    if (leg && pos < kLMax) {
-      T.ue[a * kLPad + pos] = ue;
-      T.aux[a * kLPad + pos] = ax;
+    if (hit && pos < kLMax) {
+      T.ue[a * kLPad + pos] = make_float4(dx, dy, dz, r2);
+      T.aux[a * kLPad + pos] = make_float4(0.f, 0.f, 0.f, __int_as_float(j));
     }
     nl += __popc(m);
   };
 #pragma unroll
   for (int t = 0; t < kPre; ++t)
-    if (t < iters) leg_slot(jr[t], qx[t], qy[t], qz[t], jr[t] >= 0);
+    if (t < iters) test_slot(jr[t], qx[t], qy[t], qz[t], jr[t] >= 0);
   for (int t = kPre; t < iters; ++t) {  // long rows (dense input)
     const int s = g + kG * t;
     const bool have = s < cnt;
     const int j = have ? __ldg(row + s) : 0;
     uint4 qj = make_uint4(0u, 0u, 0u, 0u);
     if (have) qj = d.q[j];
-    leg_slot(j, qj.x, qj.y, qj.z, have);
+    test_slot(j, qj.x, qj.y, qj.z, have);
+  }
+  __syncwarp();
+  // pass B: leg terms for the compacted legs only, spread over the group's
+  // lanes: pair term (owner computes) and the leg table entry
+  const int nstage = min(nl, kLMax);
+  for (int l = g; l < nstage; l += kG) {
+    float4* ue_p = T.ue + a * kLPad + l;
+    float4* ax_p = T.aux + a * kLPad + l;
+    const float4 rec = *ue_p;
+    const float r2 = rec.w;
+    const float invr = rsqrtf(r2);
+    const float r = r2 * invr;
+    if (!(r < P.rc)) {  // FP32 rounding put it on the cutoff: contributes nothing
+      *ue_p = make_float4(0.f, 0.f, 0.f, 0.f);
+      ax_p->x = 0.f;
+      ax_p->y = 0.f;
+      ax_p->z = r;
+      continue;
+    }
+    const float ux = rec.x * invr, uy = rec.y * invr, uz = rec.z * invr;
+    const float tinv = __fdividef(1.0f, r - P.rc);  // 1/(r - a sig) < 0
+    const float e2 = exp2f(P.sig_l2e * tinv);
+    const float e3 = exp2f(P.gsig_l2e * tinv);
+    const float sr = P.sig * invr;
+    float srp, srq;
+    if (P.p == 4 && P.q == 0) {  // the SW / mW exponents
+      const float sr2 = sr * sr;
+      srp = sr2 * sr2;
+      srq = 1.0f;
+    } else {
+      srp = powi(sr, P.p);
+      srq = powi(sr, P.q);
+    }
+    const float brk = fmaf(P.B, srp, -srq);
+    const float ae2 = P.Aeps * e2;
+    const float phi = ae2 * brk;
+    const float dphi = ae2 * (fmaf((float)(-P.p) * P.B, srp, (float)P.q * srq) * invr - brk * P.sig * tinv * tinv);
+    acc[0] = fmaf(0.5f, phi, acc[0]);
+    fx = fmaf(dphi, ux, fx);
+    fy = fmaf(dphi, uy, fy);
+    fz = fmaf(dphi, uz, fz);
+    const float wv = -0.5f * dphi * r;
+    acc[2] = fmaf(wv * ux, ux, acc[2]);
+    acc[3] = fmaf(wv * uy, uy, acc[3]);
+    acc[4] = fmaf(wv * uz, uz, acc[4]);
+    acc[5] = fmaf(wv * ux, uy, acc[5]);
+    acc[6] = fmaf(wv * ux, uz, acc[6]);
+    acc[7] = fmaf(wv * uy, uz, acc[7]);
+    *ue_p = make_float4(ux, uy, uz, P.sle * e3);
+    ax_p->x = 2.0f * invr;
+    ax_p->y = P.gsig * tinv * tinv;
+    ax_p->z = r;
   }
   if (g == 0) T.nl[a] = valid ? nl : 0;
   __syncwarp();
@@ -704,7 +726,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
 }
 
 template <bool kCount>
-__global__ void __launch_bounds__(kFThreads) k_force(Dev d, FParams P) {
+__global__ void __launch_bounds__(kFThreads, 8) k_force(Dev d, FParams P) {
   if (d.g->status) return;
   __shared__ LegTable T;
   const int par = (int)(d.g->step & 1ull);
@@ -821,6 +843,7 @@ __device__ __forceinline__ void bin_item(const Dev& d, int i) {
 
 // a2: atom i to its sorted slot in the staging arrays.
 __device__ __forceinline__ void scatter_item(const Dev& d, int i) {
+  if (!box_flagged(d, (int)d.q[i].w)) return;
   const int p = d.cell_start[d.cell[i]] + d.rank[i];
   d.tx[p] = d.x[i]; d.ty[p] = d.y[i]; d.tz[p] = d.z[i];
   d.tvx[p] = d.vx[i]; d.tvy[p] = d.vy[i]; d.tvz[p] = d.vz[i];
@@ -830,6 +853,7 @@ __device__ __forceinline__ void scatter_item(const Dev& d, int i) {
 
 // a2: staging arrays back to the state arrays; build positions recorded.
 __device__ __forceinline__ void copyback_item(const Dev& d, int i) {
+  if (!box_flagged(d, (int)d.q[i].w)) return;  // a box keeps its atom range
   d.x[i] = d.tx[i]; d.y[i] = d.ty[i]; d.z[i] = d.tz[i];
   d.vx[i] = d.tvx[i]; d.vy[i] = d.tvy[i]; d.vz[i] = d.tvz[i];
   d.id[i] = d.tid[i];
@@ -909,7 +933,7 @@ __global__ void k_scatter(Dev d) {
 __global__ void k_copyback(Dev d) {
   if (!d.g->any_rebuild || d.g->status) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < d.nbox) d.bst[i].rebuilds += 1;
+  if (i < d.nbox && box_flagged(d, i)) d.bst[i].rebuilds += 1;
   if (i < d.N) copyback_item(d, i);
 }
 
@@ -1010,6 +1034,13 @@ __global__ void k_ke_init(Dev d) {
   }
   const bool last = (i < d.N) && (threadIdx.x == blockDim.x - 1 || i == d.N - 1);
   box_accumulate<1>(ke, b, last, [&](int bb) { return &d.bst[bb].ke_last; });
+}
+
+// Flags every box for a rebuild (new state, parameters, skin or list width).
+__global__ void k_flag_all(Dev d) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < d.nbox) d.bst[b].rebuild = 1;
+  if (b == 0) d.g->any_rebuild = 1;
 }
 
 // Zeroes this parity's energy/virial accumulators and (optionally) the forces.

@@ -81,7 +81,7 @@ def test_adjoint_matches_oracle(mwlib, orc, case):
 
 
 def test_adjoint_dense_overflow_path(mwlib, orc):
-    """32+ legs per centre: the overflow adjoint kernel takes those centres."""
+    """More than 24 legs per centre: the overflow adjoint kernel takes those centres."""
     torch = pytest.importorskip("torch")
     x, box = I.jittered_box(512, 3.5, 0.1, 104)
     x = I.snap_to_grid(x, box)

@@ -95,7 +95,7 @@ def test_energy_forces_parity(mwlib, orc, case):
 
 
 def test_overflow_legs_path(mwlib, orc):
-    """Dense box (32 legs per atom on average, up to 36): centres beyond the 32 staged legs
+    """Dense box (32 legs per atom on average, up to 36): centres beyond the 24 staged legs
     take the overflow kernel; results must not change."""
     x, box = I.jittered_box(512, 3.5, 0.1, 104)
     s, ref, _ = check_box(mwlib, orc, x, box)

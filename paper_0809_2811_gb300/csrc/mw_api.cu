@@ -55,6 +55,7 @@ struct mw_system {
   mw_params prm{};
   double mass = 18.015, skin = 1.0;
   cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // second stream for capturing conditional bodies
   bool own_stream = false;
   bool list_built = false;
   double* eout = nullptr;  // 9 * nbox doubles: energies + virials staging
@@ -274,22 +275,47 @@ void launch_rebuild(mw_system* s) {
 void launch_force(mw_system* s) {
   const Dev& d = s->d;
   const int gb = div_up(s->N, kFAtoms);
-  if (s->count_terms) {
+  if (s->count_terms)
     k_force<true><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
-    k_force_overflow<true><<<64, 128, 0, s->stream>>>(d, s->fp);
-  } else {
+  else
     k_force<false><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
-    k_force_overflow<false><<<64, 128, 0, s->stream>>>(d, s->fp);
-  }
 }
 
-void launch_step(mw_system* s) {
+// One MD step into the stream being captured: kick1, an IF node holding the
+// rebuild kernels (condition set on the device by kick1), force, kick2.
+mw_status capture_step(mw_system* s) {
   const Dev& d = s->d;
   const int gb = div_up(s->N, kThreads);
-  k_kick1<<<gb, kThreads, 0, s->stream>>>(d);
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  MW_CUDA(cudaStreamGetCaptureInfo(s->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphConditionalHandle h;
+  MW_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+  k_kick1<<<gb, kThreads, 0, s->stream>>>(d, h, 1);
+  MW_CUDA(cudaGetLastError());
+  MW_CUDA(cudaStreamGetCaptureInfo(s->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeIf;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  MW_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  MW_CUDA(cudaStreamUpdateCaptureDependencies(s->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  MW_CUDA(cudaStreamBeginCaptureToGraph(s->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaStream_t keep = s->stream;
+  s->stream = s->cap_stream;
   launch_rebuild(s);
+  s->stream = keep;
+  MW_CUDA(cudaGetLastError());
+  MW_CUDA(cudaStreamEndCapture(s->cap_stream, &body));
   launch_force(s);
   k_kick2<<<gb, kThreads, 0, s->stream>>>(d);
+  MW_CUDA(cudaGetLastError());
+  return MW_OK;
 }
 
 mw_status set_func_attrs() {
@@ -347,8 +373,13 @@ mw_status capture_graphs(mw_system* s, int ksteps) {
     const int steps = which == 0 ? 1 : ksteps;
     cudaGraph_t graph;
     MW_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < steps; ++k) launch_step(s);
+    mw_status cst = MW_OK;
+    for (int k = 0; k < steps && cst == MW_OK; ++k) cst = capture_step(s);
     cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
+    if (cst != MW_OK) {
+      if (e == cudaSuccess) cudaGraphDestroy(graph);
+      return cst;
+    }
     if (e != cudaSuccess) return fail(MW_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
     cudaGraphExec_t ex;
     e = cudaGraphInstantiate(&ex, graph, 0);
@@ -527,6 +558,11 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
     }
     s->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return fail(MW_ECUDA, "cudaStreamCreate failed");
+  }
   s->n.assign(n, n + nbox);
   s->off.resize(nbox);
   s->boxes.resize(nbox);
@@ -552,6 +588,7 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
   make_fparams(s);
   if ((st = layout_cells(s, &s->ncell)) != MW_OK) {
     if (s->own_stream) cudaStreamDestroy(s->stream);
+    cudaStreamDestroy(s->cap_stream);
     delete s;
     return st;
   }
@@ -659,6 +696,7 @@ mw_status mw_system_destroy(mw_system* s) {
   destroy_graphs(s);
   for (void* p : s->allocs) cudaFree(p);
   if (s->own_stream) cudaStreamDestroy(s->stream);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   delete s;
   return MW_OK;
 }
@@ -1142,7 +1180,6 @@ extern "C" mw_status mw_energy_forces_noalloc(int n, const double box[3], const 
   k_neigh<<<div_up(ncell * 32, kThreads), kThreads, 0, sm>>>(ds, tmp.fp.rl2);
   k_prep_force<<<gb, kThreads, 0, sm>>>(ds, 1);
   k_force<false><<<div_up(n, kFAtoms), kFThreads, 0, sm>>>(ds, tmp.fp);
-  k_force_overflow<false><<<64, 128, 0, sm>>>(ds, tmp.fp);
   k_na_out<<<gb, kThreads, 0, sm>>>(ds, f_dev, energy_dev, virial_dev);
   MW_CUDA(cudaGetLastError());
   Global gout;

@@ -72,6 +72,7 @@ struct Global {
   int status;
   int max_count;            // widest neighbour set of the last build
   unsigned done;            // last-block counter of k_kick2
+  unsigned done1;           // last-block counter of k_kick1 (graph condition)
   unsigned bar_count, bar_gen;  // persistent engine grid barrier
   int bar_stat[2];              // status snapshot taken at each barrier release
   long long npairs, ntrip;  // leg / triplet counts of the last force call (if counting)
@@ -472,6 +473,107 @@ struct LegTable {
   int nl[kFAtoms];
 };
 
+// Whole owner contribution (pair terms and three-body terms) of a centre with
+// more than kLMax legs (rare): legs in local memory, every unordered leg pair
+// once, same arithmetic.  Called by the centre's group leader inside k_force,
+// out of line so that its local arrays and registers stay off the common path.
+template <bool kCount>
+__device__ __noinline__ void force_overflow_item(const Dev& d, const FParams& P, int i, int par) {
+  const uint4 qi = d.q[i];
+  const int b = (int)qi.w;
+  const Box& bx = d.box[b];
+  int cnt = d.nbr_cnt[i];
+  if (cnt > d.W) cnt = d.W;
+  float ux[kMaxLegsOverflow], uy[kMaxLegsOverflow], uz[kMaxLegsOverflow], tr[kMaxLegsOverflow],
+      nde[kMaxLegsOverflow], ee[kMaxLegsOverflow], rr[kMaxLegsOverflow];
+  float ax[kMaxLegsOverflow], ay[kMaxLegsOverflow], az[kMaxLegsOverflow];
+  int jj[kMaxLegsOverflow];
+  int nl = 0;
+  float e2acc = 0.f, px = 0.f, py = 0.f, pz = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int s = 0; s < cnt; ++s) {
+    const int j = d.nbr[(size_t)i * d.W + s];
+    const uint4 qj = d.q[j];
+    const float dx = fix_diff(qi.x, qj.x, bx.Lq[0]), dy = fix_diff(qi.y, qj.y, bx.Lq[1]),
+                dz = fix_diff(qi.z, qj.z, bx.Lq[2]);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (r2 >= P.rc2) continue;
+    const float invr = rsqrtf(r2);
+    const float r = r2 * invr;
+    if (!(r < P.rc)) continue;
+    if (nl >= kMaxLegsOverflow) {
+      set_status(d.g, ST_LEGS);
+      d.g->err_index = i;
+      return;
+    }
+    const float tinv = __frcp_rn(r - P.rc);
+    ux[nl] = dx * invr;
+    uy[nl] = dy * invr;
+    uz[nl] = dz * invr;
+    tr[nl] = 2.0f * invr;
+    nde[nl] = P.gsig * tinv * tinv;
+    ee[nl] = P.sle * exp2f(P.gsig_l2e * tinv);
+    rr[nl] = r;
+    jj[nl] = j;
+    ax[nl] = ay[nl] = az[nl] = 0.f;
+    {  // pair term, owner computes (half energy, full force on the centre, half virial)
+      const float e2 = exp2f(P.sig_l2e * tinv);
+      const float sr = P.sig * invr;
+      const float srp = powi(sr, P.p), srq = powi(sr, P.q);
+      const float brk = fmaf(P.B, srp, -srq);
+      const float ae2 = P.Aeps * e2;
+      const float dphi = ae2 * (fmaf((float)(-P.p) * P.B, srp, (float)P.q * srq) * invr - brk * P.sig * tinv * tinv);
+      e2acc = fmaf(0.5f * ae2, brk, e2acc);
+      px = fmaf(dphi, ux[nl], px);
+      py = fmaf(dphi, uy[nl], py);
+      pz = fmaf(dphi, uz[nl], pz);
+      const float wv = -0.5f * dphi * r;
+      w[0] = fmaf(wv * ux[nl], ux[nl], w[0]);
+      w[1] = fmaf(wv * uy[nl], uy[nl], w[1]);
+      w[2] = fmaf(wv * uz[nl], uz[nl], w[2]);
+      w[3] = fmaf(wv * ux[nl], uy[nl], w[3]);
+      w[4] = fmaf(wv * ux[nl], uz[nl], w[4]);
+      w[5] = fmaf(wv * uy[nl], uz[nl], w[5]);
+    }
+    ++nl;
+  }
+  if (kCount) atomicAdd((unsigned long long*)&d.g->ntrip, (unsigned long long)(nl * (nl - 1) / 2));
+  float e3acc = 0.f;
+  for (int j = 0; j < nl; ++j)
+    for (int k = j + 1; k < nl; ++k) {
+      const float c = fmaf(ux[j], ux[k], fmaf(uy[j], uy[k], uz[j] * uz[k]));
+      const float D = c - P.c0;
+      const float g = ee[j] * ee[k] * D;
+      e3acc = fmaf(g, D, e3acc);
+      const float aj = g * tr[j], bj = g * fmaf(c, tr[j], D * nde[j]);
+      ax[j] = fmaf(-aj, ux[k], fmaf(bj, ux[j], ax[j]));
+      ay[j] = fmaf(-aj, uy[k], fmaf(bj, uy[j], ay[j]));
+      az[j] = fmaf(-aj, uz[k], fmaf(bj, uz[j], az[j]));
+      const float ak = g * tr[k], bk = g * fmaf(c, tr[k], D * nde[k]);
+      ax[k] = fmaf(-ak, ux[j], fmaf(bk, ux[k], ax[k]));
+      ay[k] = fmaf(-ak, uy[j], fmaf(bk, uy[k], ay[k]));
+      az[k] = fmaf(-ak, uz[j], fmaf(bk, uz[k], az[k]));
+    }
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  for (int k = 0; k < nl; ++k) {
+    red_add_v4(d.f + jj[k], ax[k], ay[k], az[k]);
+    fx -= ax[k];
+    fy -= ay[k];
+    fz -= az[k];
+    const float rx = rr[k] * ux[k], ry = rr[k] * uy[k], rz = rr[k] * uz[k];
+    w[0] = fmaf(rx, ax[k], w[0]);
+    w[1] = fmaf(ry, ay[k], w[1]);
+    w[2] = fmaf(rz, az[k], w[2]);
+    w[3] = fmaf(rx, ay[k], w[3]);
+    w[4] = fmaf(rx, az[k], w[4]);
+    w[5] = fmaf(ry, az[k], w[5]);
+  }
+  red_add_v4(d.f + i, fx + px, fy + py, fz + pz);
+  double* p = &d.bst[b].ew[par][0];  // rare path: per-thread FP64 atomics
+  atomicAdd(p + 0, (double)e2acc);
+  atomicAdd(p + 1, (double)e3acc);
+  for (int k = 0; k < 6; ++k) atomicAdd(p + 2 + k, (double)w[k]);
+}
+
 // One block of kFAtoms centres (atoms blk*kFAtoms ...); every thread of the
 // block calls it.
 template <bool kCount>
@@ -552,7 +654,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
   __syncwarp();
   // pass B: leg terms for the compacted legs only, spread over the group's
   // lanes: pair term (owner computes) and the leg table entry
-  const int nstage = min(nl, kLMax);
+  const int nstage = (nl <= kLMax) ? nl : 0;  // larger centres: force_overflow_item does everything
   for (int l = g; l < nstage; l += kG) {
     float4* ue_p = T.ue + a * kLPad + l;
     float4* ax_p = T.aux + a * kLPad + l;
@@ -610,7 +712,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
 #pragma unroll
   for (int k = 0; k < kWAtoms; ++k) {
     int n = T.nl[a0 + k];
-    if (n > kLMax) n = 0;  // overflow centres: triplets in k_force_overflow
+    if (n > kLMax) n = 0;  // centres beyond the table: force_overflow_item
     pre[k + 1] = pre[k] + n;
   }
   const int b0 = __shfl_sync(kFull, b, 0);
@@ -703,10 +805,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
   }
   if (valid && g == 0) {
     red_add_v4(d.f + i, fx + T.fi[a][0], fy + T.fi[a][1], fz + T.fi[a][2]);
-    if (nl > kLMax) {
-      const int slot = atomicAdd(&d.g->n_over, 1);
-      if (slot < d.N) d.over[slot] = i;
-    }
+    if (nl > kLMax) force_overflow_item<kCount>(d, P, i, par);  // rare: more legs than the table holds
   }
   if (kCount) {  // legs and register-path triplets, one atomic per warp
     unsigned long long legs = (valid && g == 0) ? (unsigned long long)nl : 0ull;
@@ -737,94 +836,32 @@ __global__ void __launch_bounds__(kFThreads, 8) k_force(Dev d, FParams P) {
   force_block<kCount>(d, P, T, blockIdx.x, par);
 }
 
-// Three-body part for centres with more than kLMax legs (rare): legs in
-// local memory, every unordered leg pair once, same arithmetic.
-template <bool kCount>
-__device__ void force_overflow_item(const Dev& d, const FParams& P, int i, int par) {
-  const uint4 qi = d.q[i];
-  const int b = (int)qi.w;
-  const Box& bx = d.box[b];
-  int cnt = d.nbr_cnt[i];
-  if (cnt > d.W) cnt = d.W;
-  float ux[kMaxLegsOverflow], uy[kMaxLegsOverflow], uz[kMaxLegsOverflow], tr[kMaxLegsOverflow],
-      nde[kMaxLegsOverflow], ee[kMaxLegsOverflow], rr[kMaxLegsOverflow];
-  float ax[kMaxLegsOverflow], ay[kMaxLegsOverflow], az[kMaxLegsOverflow];
-  int jj[kMaxLegsOverflow];
-  int nl = 0;
-  for (int s = 0; s < cnt; ++s) {
-    const int j = d.nbr[(size_t)i * d.W + s];
-    const uint4 qj = d.q[j];
-    const float dx = fix_diff(qi.x, qj.x, bx.Lq[0]), dy = fix_diff(qi.y, qj.y, bx.Lq[1]),
-                dz = fix_diff(qi.z, qj.z, bx.Lq[2]);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (r2 >= P.rc2) continue;
-    const float invr = rsqrtf(r2);
-    const float r = r2 * invr;
-    if (!(r < P.rc)) continue;
-    if (nl >= kMaxLegsOverflow) {
-      set_status(d.g, ST_LEGS);
-      d.g->err_index = i;
-      return;
-    }
-    const float tinv = __frcp_rn(r - P.rc);
-    ux[nl] = dx * invr;
-    uy[nl] = dy * invr;
-    uz[nl] = dz * invr;
-    tr[nl] = 2.0f * invr;
-    nde[nl] = P.gsig * tinv * tinv;
-    ee[nl] = P.sle * exp2f(P.gsig_l2e * tinv);
-    rr[nl] = r;
-    jj[nl] = j;
-    ax[nl] = ay[nl] = az[nl] = 0.f;
-    ++nl;
-  }
-  if (kCount) atomicAdd((unsigned long long*)&d.g->ntrip, (unsigned long long)(nl * (nl - 1) / 2));
-  float e3acc = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int j = 0; j < nl; ++j)
-    for (int k = j + 1; k < nl; ++k) {
-      const float c = fmaf(ux[j], ux[k], fmaf(uy[j], uy[k], uz[j] * uz[k]));
-      const float D = c - P.c0;
-      const float g = ee[j] * ee[k] * D;
-      e3acc = fmaf(g, D, e3acc);
-      const float aj = g * tr[j], bj = g * fmaf(c, tr[j], D * nde[j]);
-      ax[j] = fmaf(-aj, ux[k], fmaf(bj, ux[j], ax[j]));
-      ay[j] = fmaf(-aj, uy[k], fmaf(bj, uy[j], ay[j]));
-      az[j] = fmaf(-aj, uz[k], fmaf(bj, uz[j], az[j]));
-      const float ak = g * tr[k], bk = g * fmaf(c, tr[k], D * nde[k]);
-      ax[k] = fmaf(-ak, ux[j], fmaf(bk, ux[k], ax[k]));
-      ay[k] = fmaf(-ak, uy[j], fmaf(bk, uy[k], ay[k]));
-      az[k] = fmaf(-ak, uz[j], fmaf(bk, uz[k], az[k]));
-    }
-  float fx = 0.f, fy = 0.f, fz = 0.f;
-  for (int k = 0; k < nl; ++k) {
-    red_add_v4(d.f + jj[k], ax[k], ay[k], az[k]);
-    fx -= ax[k];
-    fy -= ay[k];
-    fz -= az[k];
-    const float rx = rr[k] * ux[k], ry = rr[k] * uy[k], rz = rr[k] * uz[k];
-    w[0] = fmaf(rx, ax[k], w[0]);
-    w[1] = fmaf(ry, ay[k], w[1]);
-    w[2] = fmaf(rz, az[k], w[2]);
-    w[3] = fmaf(rx, ay[k], w[3]);
-    w[4] = fmaf(rx, az[k], w[4]);
-    w[5] = fmaf(ry, az[k], w[5]);
-  }
-  red_add_v4(d.f + i, fx, fy, fz);
-  double* p = &d.bst[b].ew[par][0];  // overflow centres are not box-ordered: per-thread FP64 atomics
-  atomicAdd(p + 1, (double)e3acc);
-  for (int k = 0; k < 6; ++k) atomicAdd(p + 2 + k, (double)w[k]);
-}
 
 // ---------------------------------------------------------------------------
 // Per-phase kernels (the graph engine and the standalone force call).
 
-__global__ void k_kick1(Dev d) {
+// In the graph engine the last block to finish also sets the condition of
+// the graph's IF node that holds the rebuild kernels (skipped when no box
+// moved more than skin/2).
+__global__ void k_kick1(Dev d, cudaGraphConditionalHandle rebuild_cond, int use_cond) {
   if (d.g->status) return;
   const Integ I = *d.integ;
   const int par = (int)(d.g->step & 1ull);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) d.g->n_over = 0;
   if (i < d.N) kick1_item(d, I, i, (int)d.q[i].w, par);
+  if (use_cond) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(&d.g->done1, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+      __threadfence();
+      d.g->done1 = 0u;
+      cudaGraphSetConditional(rebuild_cond, *(volatile int*)&d.g->any_rebuild ? 1u : 0u);
+    }
+  }
 }
 
 // Start half of every box with the current integrator (first step of a call).
@@ -943,14 +980,6 @@ __global__ void k_neigh(Dev d, float rl2) {
   if (w < d.ncell) neigh_cell_warp(d, d.q, w, rl2);
 }
 
-template <bool kCount>
-__global__ void __launch_bounds__(128) k_force_overflow(Dev d, FParams P) {
-  if (d.g->status) return;
-  const int par = (int)(d.g->step & 1ull);
-  const int nover = min(d.g->n_over, d.N);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nover; k += gridDim.x * blockDim.x)
-    force_overflow_item<kCount>(d, P, d.over[k], par);
-}
 
 __global__ void k_kick2(Dev d) {
   if (d.g->status) return;

@@ -1,7 +1,7 @@
 // mw_persistent.cuh -- persistent engine: one cooperative launch advances
 // every box nsteps MD steps, with grid-wide barriers between the phases of
 // mw_device.cuh (kick1 | [bin | scan | scan | scatter | copy + neighbour list]
-// | force | [overflow legs] | kick2 | thermostat).  All blocks are
+// | force | kick2 | thermostat).  All blocks are
 // co-resident (cooperative launch), every barrier wait is bounded in wall
 // time, and the release of each barrier carries one status snapshot so that
 // all blocks take the same decision to stop.
@@ -153,11 +153,6 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     // a4 - a6: fused two- + three-body force, energy, virial
     for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) force_block<kCount>(d, P, T, blk, par);
     if (grid_barrier(g, gen)) return;
-    const int nover = min(*(volatile int*)&g->n_over, d.N);
-    if (nover > 0) {
-      for (int k = tid; k < nover; k += nth) force_overflow_item<kCount>(d, P, d.over[k], par);
-      if (grid_barrier(g, gen)) return;
-    }
     // a7 second half + kinetic energy per box; the rebuild (if any) is consumed
     if (blockIdx.x == 0) {
       for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;

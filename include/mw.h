@@ -102,6 +102,7 @@ typedef struct mw_info {
   int persistent_blocks, persistent_threads;
   double r_list;      /* a sigma + skin, A */
   int64_t npairs, ntriplets; /* legs r < a sigma (unordered pairs) and triplets at the last force call */
+  int64_t rebuild_steps;     /* steps and force calls that rebuilt at least one box since mw_set_state */
 } mw_info;
 
 typedef struct mw_system mw_system;
@@ -229,6 +230,14 @@ mw_status mw_set_skin(mw_system* s, double skin);
 mw_status mw_autotune(mw_system* s, const mw_integrator* integ, int steps, int* best_engine);
 
 mw_status mw_get_info(mw_system* s, mw_info* out);
+
+/* Diagnostics: advances nsteps steps with every phase kernel launched on its
+ * own (no graph) between CUDA events, and writes the mean GPU time per step
+ * of each phase to ms_out[8] (ms): kick1 + drift + rebuild check, cell
+ * binning, scan, scatter, copy-back, neighbour list, force, kick2 +
+ * thermostat.  The rebuild phases return at once on steps without a rebuild,
+ * so their mean includes those launches. */
+mw_status mw_phase_times(mw_system* s, const mw_integrator* integ, int nsteps, double* ms_out);
 
 /* Diagnostics: when on != 0 the force kernels count legs (pairs with
  * r < a sigma) and triplets into mw_info.npairs / .ntriplets (device atomics,

@@ -68,6 +68,7 @@ struct mw_system {
   // state
   bool state_set = false;
   bool forces_valid = false;
+  bool need_prime = true;  // thermostat start half must be recomputed before the next step
   long long host_step = 0;
   int engine = MW_ENGINE_AUTO, engine_used = MW_ENGINE_GRAPH;
   int tuned_engine = -1;
@@ -402,9 +403,14 @@ mw_status finish_interrupted_step(mw_system* s) {
   return MW_OK;
 }
 
+// The start-of-step thermostat half is normally computed by the previous
+// step's end; it is recomputed here only after a state, parameter or
+// integrator change.
 mw_status prime_thermostat(mw_system* s) {
+  if (!s->need_prime) return MW_OK;
   k_prime_thermostat<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d);
   MW_CUDA(cudaGetLastError());
+  s->need_prime = false;
   return MW_OK;
 }
 
@@ -488,6 +494,7 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   MW_CUDA(cudaStreamSynchronize(s->stream));
   s->state_set = true;
   s->forces_valid = false;
+  s->need_prime = true;
   s->host_step = 0;
   return MW_OK;
 }
@@ -518,10 +525,14 @@ mw_status validate_integ(mw_system* s, const mw_integrator* in) {
   I.kind = in->thermostat;
   I.half_skin2 = (float)(0.25 * s->skin * s->skin);
   mw_status st;
-  if (boxes_changed && (st = upload_boxes(s)) != MW_OK) return st;
+  if (boxes_changed) {
+    if ((st = upload_boxes(s)) != MW_OK) return st;
+    s->need_prime = true;
+  }
   if (std::memcmp(&I, &s->integ, sizeof I) != 0) {
     s->integ = I;
     if ((st = upload_integ(s)) != MW_OK) return st;
+    s->need_prime = true;
   }
   return MW_OK;
 }
@@ -975,6 +986,7 @@ mw_status mw_get_info(mw_system* s, mw_info* out) {
   out->r_list = r_list(s);
   out->npairs = s->npairs;
   out->ntriplets = s->ntrip;
+  out->rebuild_steps = g.rebuild_steps;
   return MW_OK;
 }
 

@@ -73,6 +73,7 @@ struct Global {
   int max_count;            // widest neighbour set of the last build
   unsigned done;            // last-block counter of k_kick2
   unsigned done1;           // last-block counter of k_kick1 (graph condition)
+  long long rebuild_steps;  // steps (or force calls) that rebuilt at least one box
   unsigned bar_count, bar_gen;  // persistent engine grid barrier
   int bar_stat[2];              // status snapshot taken at each barrier release
   long long npairs, ntrip;  // leg / triplet counts of the last force call (if counting)
@@ -706,94 +707,116 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
   if (g == 0) T.nl[a] = valid ? nl : 0;
   __syncwarp();
   // ---- triplet phase: items (centre of this warp, leg j), spread over the lanes
+  // ---- triplet phase: the ordered leg pairs (j, k != j) of the warp's
+  // centres are split into 32 equal contiguous ranges, one per lane.  A lane
+  // walks (centre, j, k) in order and flushes the force accumulated on leg j
+  // (red.global) and the reaction on the centre (shared memory) whenever j or
+  // the centre changes; a leg whose partners straddle two lanes gets two
+  // partial flushes, which add up.  Each unordered triplet's energy is taken
+  // once (k > j).
   const int a0 = (threadIdx.x >> 5) * kWAtoms;
-  int pre[kWAtoms + 1];
-  pre[0] = 0;
+  int ppre[kWAtoms + 1];
+  ppre[0] = 0;
 #pragma unroll
   for (int k = 0; k < kWAtoms; ++k) {
     int n = T.nl[a0 + k];
     if (n > kLMax) n = 0;  // centres beyond the table: force_overflow_item
-    pre[k + 1] = pre[k] + n;
+    ppre[k + 1] = ppre[k] + n * (n - 1);
   }
   const int b0 = __shfl_sync(kFull, b, 0);
   const bool wuni = __all_sync(kFull, b == b0 || b < 0);
   const float c0 = P.c0;
-  for (int base = 0; base < pre[kWAtoms]; base += 32) {  // warp-uniform rounds
-    const int it = base + lane;
-    int ka = -1, first = 0, n = 0;
+  const int ptot = ppre[kWAtoms];
+  int t = (lane * ptot) >> 5;
+  const int t1 = ((lane + 1) * ptot) >> 5;
+  if (t < t1) {
+    // decode the first pair of this lane's range
+    int ka = 0, pbase = 0, n = 0;
 #pragma unroll
-    for (int k = 0; k < kWAtoms; ++k)  // the centre whose item range holds it
-      if (it >= pre[k] && it < pre[k + 1]) {
+    for (int k = 0; k < kWAtoms; ++k)
+      if (t >= ppre[k] && t < ppre[k + 1]) {
         ka = k;
-        first = pre[k];
-        n = pre[k + 1] - pre[k];
+        pbase = ppre[k];
+        n = (int)(0.5f + sqrtf(0.25f + (float)(ppre[k + 1] - ppre[k])));  // n (n - 1) pairs
       }
-    float gx = 0.f, gy = 0.f, gz = 0.f;
-    if (ka >= 0) {
-      const int aa = a0 + ka;
-      const int jj = it - first;
-      const float4* rowu = T.ue + aa * kLPad;
-      const float4 uj = rowu[jj];
-      const float4 xj = T.aux[aa * kLPad + jj];
-      float e3 = 0.f;
-      // partner legs k != jj; the energy of each unordered triplet is taken
-      // by the item of its lower leg (k > jj)
-      auto partner = [&](int k, bool energy) {
-        const float4 uk = rowu[k];
+    int off = t - pbase;
+    int jj = off / (n - 1);
+    int kk = off - jj * (n - 1);
+    kk += (kk >= jj) ? 1 : 0;
+    int rb = (a0 + ka) * kLPad;
+    float4 uj = T.ue[rb + jj], xj = T.aux[rb + jj];
+    float gx = 0.f, gy = 0.f, gz = 0.f, e3 = 0.f;
+    float crx = 0.f, cry = 0.f, crz = 0.f;  // reaction on the current centre
+    while (true) {
+      {
+        const float4 uk = T.ue[rb + kk];
         const float c = fmaf(uj.x, uk.x, fmaf(uj.y, uk.y, uj.z * uk.z));
         const float D = c - c0;
         const float gg = uj.w * uk.w * D;
-        if (energy) e3 = fmaf(gg, D, e3);
+        if (kk > jj) e3 = fmaf(gg, D, e3);
         const float aj = gg * xj.x;
         const float bj = gg * fmaf(c, xj.x, D * xj.y);
         gx = fmaf(-aj, uk.x, fmaf(bj, uj.x, gx));
         gy = fmaf(-aj, uk.y, fmaf(bj, uj.y, gy));
         gz = fmaf(-aj, uk.z, fmaf(bj, uj.z, gz));
-      };
-#pragma unroll 2
-      for (int k = 0; k < jj; ++k) partner(k, false);
-#pragma unroll 2
-      for (int k = jj + 1; k < n; ++k) partner(k, true);
-      red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
-      const float rx = xj.z * uj.x, ry = xj.z * uj.y, rz = xj.z * uj.z;
-      if (wuni) {
-        acc[1] += e3;
-        acc[2] = fmaf(rx, gx, acc[2]);
-        acc[3] = fmaf(ry, gy, acc[3]);
-        acc[4] = fmaf(rz, gz, acc[4]);
-        acc[5] = fmaf(rx, gy, acc[5]);
-        acc[6] = fmaf(rx, gz, acc[6]);
-        acc[7] = fmaf(ry, gz, acc[7]);
-      } else {  // warp straddles two boxes (rare): straight to the item's box
-        double* p = &d.bst[d.q[blk * kFAtoms + aa].w].ew[par][0];
-        atomicAdd(p + 1, (double)e3);
-        atomicAdd(p + 2, (double)(rx * gx));
-        atomicAdd(p + 3, (double)(ry * gy));
-        atomicAdd(p + 4, (double)(rz * gz));
-        atomicAdd(p + 5, (double)(rx * gy));
-        atomicAdd(p + 6, (double)(rx * gz));
-        atomicAdd(p + 7, (double)(ry * gz));
       }
-    }
-    // reaction on the centres: segmented sum over the lanes holding one centre's items
+      ++t;
+      ++kk;
+      if (kk == jj) ++kk;
+      const bool end_j = (kk >= n) || (t >= t1);
+      if (end_j) {  // flush leg jj of centre ka
+        red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
+        crx -= gx;
+        cry -= gy;
+        crz -= gz;
+        const float rx = xj.z * uj.x, ry = xj.z * uj.y, rz = xj.z * uj.z;
+        if (wuni) {
+          acc[1] += e3;
+          acc[2] = fmaf(rx, gx, acc[2]);
+          acc[3] = fmaf(ry, gy, acc[3]);
+          acc[4] = fmaf(rz, gz, acc[4]);
+          acc[5] = fmaf(rx, gy, acc[5]);
+          acc[6] = fmaf(rx, gz, acc[6]);
+          acc[7] = fmaf(ry, gz, acc[7]);
+        } else {  // warp straddles two boxes (rare): straight to this centre's box
+          double* p = &d.bst[d.q[blk * kFAtoms + a0 + ka].w].ew[par][0];
+          atomicAdd(p + 1, (double)e3);
+          atomicAdd(p + 2, (double)(rx * gx));
+          atomicAdd(p + 3, (double)(ry * gy));
+          atomicAdd(p + 4, (double)(rz * gz));
+          atomicAdd(p + 5, (double)(rx * gy));
+          atomicAdd(p + 6, (double)(rx * gz));
+          atomicAdd(p + 7, (double)(ry * gz));
+        }
+        gx = gy = gz = e3 = 0.f;
+        if (t >= t1) break;
+        ++jj;
+        kk = (jj == 0) ? 1 : 0;
+        if (jj >= n) {  // next centre with at least two legs
+          atomicAdd(&T.fi[a0 + ka][0], crx);
+          atomicAdd(&T.fi[a0 + ka][1], cry);
+          atomicAdd(&T.fi[a0 + ka][2], crz);
+          crx = cry = crz = 0.f;
+          int nk = ka + 1;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int ko = __shfl_up_sync(kFull, ka, o);
-      const float tx = __shfl_up_sync(kFull, gx, o), ty = __shfl_up_sync(kFull, gy, o),
-                  tz = __shfl_up_sync(kFull, gz, o);
-      if (lane >= o && ko == ka) {
-        gx += tx;
-        gy += ty;
-        gz += tz;
+          for (int k = kWAtoms - 1; k >= 0; --k)  // smallest k > ka with pairs
+            if (k > ka && ppre[k + 1] > ppre[k]) nk = k;
+          ka = nk;
+          pbase = 0;
+#pragma unroll
+          for (int k = 0; k < kWAtoms; ++k)
+            if (k == ka) n = (int)(0.5f + sqrtf(0.25f + (float)(ppre[k + 1] - ppre[k])));
+          jj = 0;
+          kk = 1;
+          rb = (a0 + ka) * kLPad;
+        }
+        uj = T.ue[rb + jj];
+        xj = T.aux[rb + jj];
       }
     }
-    const int kn = __shfl_down_sync(kFull, ka, 1);
-    if (ka >= 0 && (lane == 31 || kn != ka)) {
-      T.fi[a0 + ka][0] -= gx;  // one tail per centre and round
-      T.fi[a0 + ka][1] -= gy;
-      T.fi[a0 + ka][2] -= gz;
-    }
-    __syncwarp();  // orders this round's table updates before the next round's
+    atomicAdd(&T.fi[a0 + ka][0], crx);
+    atomicAdd(&T.fi[a0 + ka][1], cry);
+    atomicAdd(&T.fi[a0 + ka][2], crz);
   }
   __syncwarp();
   // ---- force on the centre: pair part (lane group) + three-body reaction
@@ -970,6 +993,7 @@ __global__ void k_scatter(Dev d) {
 __global__ void k_copyback(Dev d) {
   if (!d.g->any_rebuild || d.g->status) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) d.g->rebuild_steps += 1;
   if (i < d.nbox && box_flagged(d, i)) d.bst[i].rebuilds += 1;
   if (i < d.N) copyback_item(d, i);
 }

@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
       for (int i = tid; i < d.N; i += nth) copyback_item(d, i);
       for (int c = gw; c < d.ncell; c += nwarps) neigh_cell_warp(d, d.tq, c, P.rl2);
       if (tid < d.nbox && box_flagged(d, tid)) d.bst[tid].rebuilds += 1;
+      if (tid == 0) g->rebuild_steps += 1;
       if (grid_barrier(g, gen)) return;
     }
     // a4 - a6: fused two- + three-body force, energy, virial

@@ -28,7 +28,7 @@ EXPORTS = (
     "mw_set_state_dev", "mw_get_state", "mw_get_state_dev", "mw_set_params", "mw_build_neighbors",
     "mw_get_neighbors", "mw_energy_forces", "mw_energy_forces_dev", "mw_step", "mw_get_thermo",
     "mw_energy_forces_vjp", "mw_set_engine", "mw_set_nbr_width", "mw_autotune", "mw_get_info",
-    "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc", "mw_set_skin",
+    "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc", "mw_set_skin", "mw_phase_times",
     "mw_last_error",
 )
 
@@ -62,7 +62,8 @@ class mw_info(ctypes.Structure):
     _fields_ = [("nbox", ctypes.c_int), ("n_total", ctypes.c_int), ("nbr_width", ctypes.c_int),
                 ("max_count", ctypes.c_int), ("ncell_total", ctypes.c_int), ("engine", ctypes.c_int),
                 ("persistent_blocks", ctypes.c_int), ("persistent_threads", ctypes.c_int),
-                ("r_list", ctypes.c_double), ("npairs", ctypes.c_int64), ("ntriplets", ctypes.c_int64)]
+                ("r_list", ctypes.c_double), ("npairs", ctypes.c_int64), ("ntriplets", ctypes.c_int64),
+                ("rebuild_steps", ctypes.c_int64)]
 
 
 class MWError(RuntimeError):
@@ -112,6 +113,7 @@ def lib():
             "mw_step_async": [P, ctypes.POINTER(mw_integrator), ctypes.c_int],
             "mw_sync": [P],
             "mw_set_skin": [P, ctypes.c_double],
+            "mw_phase_times": [P, ctypes.POINTER(mw_integrator), ctypes.c_int, dp],
             "mw_energy_forces_noalloc": [ctypes.c_int, dp, ctypes.POINTER(mw_params), ctypes.c_double, P, P, P, P,
                                          P],
         }
@@ -306,6 +308,15 @@ def mw_energy_forces_noalloc(n: int, box, x_dev, f_dev=None, energy_dev=None, vi
 
 def mw_set_skin(h: int, skin: float):
     _check(lib().mw_set_skin(h, float(skin)))
+
+
+PHASES = ("kick1", "bin", "scan", "scatter", "copyback", "neigh", "force", "kick2")
+
+
+def mw_phase_times(h: int, integ: mw_integrator, nsteps: int) -> dict:
+    out = np.zeros(8)
+    _check(lib().mw_phase_times(h, ctypes.byref(integ), int(nsteps), _dp(out)))
+    return dict(zip(PHASES, out.tolist()))
 
 
 def mw_last_error() -> str:

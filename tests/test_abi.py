@@ -37,7 +37,7 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(mw.mw_params) == 72
     assert ctypes.sizeof(mw.mw_integrator) == 40
     assert ctypes.sizeof(mw.mw_thermo) == 136
-    assert ctypes.sizeof(mw.mw_info) == 56
+    assert ctypes.sizeof(mw.mw_info) == 64
 
 
 def test_oracle_and_library_share_no_code():

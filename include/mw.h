@@ -30,6 +30,11 @@
  *   - The library owns all its device buffers (allocated at create time and
  *     when a neighbour list must grow) and frees them in mw_system_destroy.
  *   - One mw_system must not be used from two threads at once.
+ *   - Environment: MW_AUTOTUNE_CACHE (see mw_autotune); MW_GRAPH_NO_CONDITIONAL
+ *     (any value) captures the graph engine's step without its conditional
+ *     node - every kernel launches each step and the rebuild kernels return at
+ *     once when not needed - for profilers that do not follow conditional
+ *     graph nodes.
  */
 #ifndef MW_H
 #define MW_H

@@ -237,6 +237,15 @@ mw_status set_global_field(mw_system* s, size_t offset, int value) {
   return MW_OK;
 }
 
+// Applies a pending second half-kick to the stored velocities (before forces
+// are recomputed or atoms re-sorted outside a step).
+mw_status flush_pending(mw_system* s) {
+  if (!s->state_set) return MW_OK;
+  k_flush_pending<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d);
+  MW_CUDA(cudaGetLastError());
+  return set_global_field(s, offsetof(Global, pend), 0);
+}
+
 mw_status flag_all(mw_system* s) {
   k_flag_all<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d);
   MW_CUDA(cudaGetLastError());
@@ -287,6 +296,17 @@ void launch_force(mw_system* s) {
 mw_status capture_step(mw_system* s) {
   const Dev& d = s->d;
   const int gb = div_up(s->N, kThreads);
+  if (std::getenv("MW_GRAPH_NO_CONDITIONAL")) {
+    // Same kernels without the IF node (the rebuild kernels return at once
+    // when no box needs a rebuild): profilers that skip conditional graphs
+    // still see every kernel of the step.
+    k_kick1<<<gb, kThreads, 0, s->stream>>>(d, 0ull, 0);
+    launch_rebuild(s);
+    launch_force(s);
+    k_kick2<<<gb, kThreads, 0, s->stream>>>(d);
+    MW_CUDA(cudaGetLastError());
+    return MW_OK;
+  }
   cudaStreamCaptureStatus cs;
   cudaGraph_t g;
   const cudaGraphNode_t* deps = nullptr;
@@ -340,6 +360,7 @@ mw_status ensure_forces(mw_system* s) {
   if (!s->state_set) return fail(MW_ESTATE, "no state set (call mw_set_state first)");
   if (s->forces_valid) return MW_OK;
   mw_status st;
+  if ((st = flush_pending(s)) != MW_OK) return st;
   if ((st = set_func_attrs()) != MW_OK) return st;
   for (int attempt = 0; attempt < 4; ++attempt) {
     k_prep_force<<<div_up(std::max(s->N, s->nbox), kThreads), kThreads, 0, s->stream>>>(s->d, 1);
@@ -514,6 +535,13 @@ mw_status validate_integ(mw_system* s, const mw_integrator* in) {
       bx.T0 = T0;
       bx.Q = Q;
       boxes_changed = true;
+    }
+    for (int k = 0; k < 3; ++k) {
+      const double dtL = in->dt / bx.L[k];
+      if (bx.dtL[k] != dtL) {
+        bx.dtL[k] = dtL;
+        boxes_changed = true;
+      }
     }
   }
   Integ I{};
@@ -744,6 +772,7 @@ mw_status mw_set_params(mw_system* s, const mw_params* prm) {
   if (!s) return fail(MW_EINVAL, "system is NULL");
   mw_status st;
   if ((st = check_params(prm)) != MW_OK) return st;
+  if ((st = flush_pending(s)) != MW_OK) return st;  // the pending half-kick belongs to the old potential
   const mw_params old = s->prm;
   s->prm = *prm;
   int ncell;
@@ -769,6 +798,7 @@ mw_status mw_build_neighbors(mw_system* s, int* max_count_out) {
   if (!s) return fail(MW_EINVAL, "system is NULL");
   if (!s->state_set) return fail(MW_ESTATE, "no state set");
   mw_status st;
+  if ((st = flush_pending(s)) != MW_OK) return st;  // atoms get re-sorted, forces do not follow
   for (int attempt = 0; attempt < 4; ++attempt) {
     if ((st = flag_all(s)) != MW_OK) return st;
     launch_rebuild(s);
@@ -849,9 +879,10 @@ mw_status mw_energy_forces_dev(mw_system* s, const double* x_dev, float* f_dev, 
   if (!s) return fail(MW_EINVAL, "system is NULL");
   if (x_dev) {
     if (!s->state_set) return do_set_state(s, x_dev, nullptr, true) == MW_OK ? mw_energy_forces_dev(s, nullptr, f_dev, energy_dev, virial_dev) : MW_ECUDA;
+    mw_status st;
+    if ((st = flush_pending(s)) != MW_OK) return st;
     k_load_positions<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, x_dev, s->boxid, 0);
     MW_CUDA(cudaGetLastError());
-    mw_status st;
     if ((st = flag_all(s)) != MW_OK) return st;
     s->forces_valid = false;
   }

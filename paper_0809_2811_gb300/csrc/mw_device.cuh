@@ -9,7 +9,10 @@
 //
 // Layout (all boxes concatenated box-major, atoms sorted by cell inside each
 // box at every neighbour-list rebuild):
-//   x,y,z,vx,vy,vz   FP64 master positions / velocities (SoA)
+//   x,y,z            FP64 master positions as fractions of the box edge, [0, 1)
+//   vx,vy,vz         FP64 master velocities (A/fs); between steps they lack the
+//                    second half-kick of the last step (Global::pend), which
+//                    the next kick1 folds into its own
 //   q                uint4 {qx, qy, qz, box}: position as a 32-bit fraction of
 //                    the box edge; the minimum-image difference of two atoms
 //                    is the wrapping int32 difference, converted once to FP32
@@ -41,6 +44,7 @@ constexpr int kMaxLegsOverflow = 64;
 
 struct Box {        // read-only in kernels
   double L[3];
+  double dtL[3];    // dt / L: drift of the box fraction per unit velocity
   float lost;       // half the shortest edge (A): larger one-step moves are errors
   double qs[3];     // 2^32 / L
   float Lq[3];      // L / 2^32
@@ -54,6 +58,7 @@ struct BoxState {   // mutated by kernels
   double xi[2], eta[2];   // [0] after the end-of-step half, [1] after the start-of-step half
   double s_end;           // pending velocity scale: true v = stored v * s_end
   double s_kick;          // scale applied by the next kick1: s_end times the next start half
+  float s_kick1;          // s_kick + 1 in FP32 (weight of the folded half-kick)
   double ke_last;         // kinetic energy after the last end half (kcal/mol)
   double ke_acc[2];       // per step-parity accumulators of the raw kinetic energy
   double ew[2][8];        // per step-parity E2, E3, W[6]
@@ -74,6 +79,7 @@ struct Global {
   unsigned done;            // last-block counter of k_kick2
   unsigned done1;           // last-block counter of k_kick1 (graph condition)
   long long rebuild_steps;  // steps (or force calls) that rebuilt at least one box
+  int pend;                 // 1: velocities lack the second half-kick of the last step
   unsigned bar_count, bar_gen;  // persistent engine grid barrier
   int bar_stat[2];              // status snapshot taken at each barrier release
   long long npairs, ntrip;  // leg / triplet counts of the last force call (if counting)
@@ -128,6 +134,17 @@ struct Dev {
 
 __device__ __forceinline__ uint32_t to_fixed(double x, double qs) {
   return (uint32_t)(unsigned long long)__double2ll_rn(x * qs);
+}
+
+// Box fraction s in [0, 1) -> round(s 2^32) mod 2^32, from the IEEE fields
+// with integer operations only (no FP64 instruction).
+__device__ __forceinline__ uint32_t frac_to_fixed(double s) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(s);
+  const int e = (int)(bits >> 52) - 1023;  // s = 1.m x 2^e, e <= -1
+  const int sh = 20 - e;                    // round(m x 2^(e + 32 - 52))
+  if (bits == 0ull || sh >= 54 || sh < 21) return 0u;  // tiny, or not in [0, 1) (NaN)
+  const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  return (uint32_t)((m + (1ull << (sh - 1))) >> sh);  // 2^32 (s rounding up to 1) wraps to 0
 }
 
 __device__ __forceinline__ float fix_diff(uint32_t a, uint32_t b, float lq) {  // b - a, minimum image
@@ -238,40 +255,37 @@ __device__ void start_half_box(const Dev& d, const Integ& I, int b) {
   st->xi[1] = xi;
   st->eta[1] = eta;
   st->s_kick = st->s_end * s;
+  st->s_kick1 = (float)(st->s_kick + 1.0);
 }
 
 // ---------------------------------------------------------------------------
 // Phase bodies (one item each) shared by the per-phase kernels and the
 // persistent kernel.
 
-// a1 + a7 (first half): v = s v + dt/2 a; x += dt v; wrap; fixed-point copy;
-// displacement check against the last build.  Also zeroes f for this step.
-// FP64: the velocity and position updates and the fixed-point conversion
-// (5 FP64-pipe instructions per component); the increment cf*F is formed in
-// FP32 from the FP32 force.
-__device__ __forceinline__ double wrap_slow(double x, double L, double invL) {
-  x -= L * floor(x * invL);
-  if (x >= L) x -= L;
-  if (x < 0.0) x = 0.0;
-  return x;
-}
-
-__device__ __forceinline__ uint32_t advance_coord(double& x, double& v, double s, float dv, const Integ& I, double L,
-                                                  double qs) {
-  v = fma(v, s, (double)dv);
-  x = fma(I.dt, v, x);
-  long long q = __double2ll_rn(x * qs);
-  if ((unsigned long long)q > 0xffffffffull) {  // left [0, L): crossed a face (rare)
-    x = wrap_slow(x, L, 1.0 / L);
-    q = __double2ll_rn(x * qs);
+// a1 + a7 (first half): the second half-kick of the last step and the first
+// of this one use the same force, so they are folded: v = S v + (S + 1) a
+// when a half-kick is pending (S = thermostat scale of the step boundary,
+// a = dt/2 F/m), else v = S v + a; then s += (dt/L) v on the box fraction,
+// wrap into [0, 1), fixed-point copy, displacement check against the last
+// build.  FP64: one conversion and two FMAs per component; the fixed-point
+// copy uses integer operations.  Also zeroes f for this step.
+__device__ __forceinline__ uint32_t advance_coord(double& s, double& v, double S, float dv, double dtL) {
+  v = fma(v, S, (double)dv);
+  s = fma(dtL, v, s);
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(s);
+  if ((bits >> 63) || (bits >> 52) >= 1023ull) {  // left [0, 1): crossed a face (rare)
+    s -= floor(s);
+    if (s >= 1.0) s -= 1.0;
+    if (s < 0.0) s = 0.0;
   }
-  return (uint32_t)(unsigned long long)q;  // 2^32 (x rounding up to L) wraps to 0
+  return frac_to_fixed(s);
 }
 
-__device__ __forceinline__ void kick1_item(const Dev& d, const Integ& I, int i, int b, int par) {
+__device__ __forceinline__ void kick1_item(const Dev& d, const Integ& I, int i, int b, int par, int pend) {
   const Box& bx = d.box[b];
   BoxState* st = d.bst + b;
-  const double s = st->s_kick;
+  const double S = st->s_kick;
+  const float kf = I.cf_f * (pend ? st->s_kick1 : 1.0f);
   if (i == bx.off) {  // this step's accumulators start from zero
     st->ke_acc[par] = 0.0;
 #pragma unroll
@@ -281,9 +295,9 @@ __device__ __forceinline__ void kick1_item(const Dev& d, const Integ& I, int i, 
   d.f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   double vx = d.vx[i], vy = d.vy[i], vz = d.vz[i];
   double px = d.x[i], py = d.y[i], pz = d.z[i];
-  const uint32_t q0 = advance_coord(px, vx, s, I.cf_f * F.x, I, bx.L[0], bx.qs[0]);
-  const uint32_t q1 = advance_coord(py, vy, s, I.cf_f * F.y, I, bx.L[1], bx.qs[1]);
-  const uint32_t q2 = advance_coord(pz, vz, s, I.cf_f * F.z, I, bx.L[2], bx.qs[2]);
+  const uint32_t q0 = advance_coord(px, vx, S, kf * F.x, bx.dtL[0]);
+  const uint32_t q1 = advance_coord(py, vy, S, kf * F.y, bx.dtL[1]);
+  const uint32_t q2 = advance_coord(pz, vz, S, kf * F.z, bx.dtL[2]);
   d.vx[i] = vx; d.vy[i] = vy; d.vz[i] = vz;
   d.x[i] = px; d.y[i] = py; d.z[i] = pz;
   const uint4 qn = make_uint4(q0, q1, q2, (unsigned)b);
@@ -303,15 +317,14 @@ __device__ __forceinline__ void kick1_item(const Dev& d, const Integ& I, int i, 
   }
 }
 
-// a7 (second half) for one atom; returns its raw kinetic energy (FP32 per
-// atom; the sums over atoms are FP64).
+// a7 (second half) for one atom: the kinetic energy of v + a (FP32 per atom;
+// the sums over atoms are FP64).  The half-kick itself is left pending and
+// folded into the next kick1 (or applied when the state is read).
 __device__ __forceinline__ float kick2_item(const Dev& d, const Integ& I, int i) {
   const float4 F = d.f[i];
-  const double vx = d.vx[i] + (double)(I.cf_f * F.x);
-  const double vy = d.vy[i] + (double)(I.cf_f * F.y);
-  const double vz = d.vz[i] + (double)(I.cf_f * F.z);
-  d.vx[i] = vx; d.vy[i] = vy; d.vz[i] = vz;
-  const float fx = (float)vx, fy = (float)vy, fz = (float)vz;
+  const float fx = fmaf(I.cf_f, F.x, (float)d.vx[i]);
+  const float fy = fmaf(I.cf_f, F.y, (float)d.vy[i]);
+  const float fz = fmaf(I.cf_f, F.z, (float)d.vz[i]);
   const float ke = (float)I.ke_fac * fmaf(fx, fx, fmaf(fy, fy, fz * fz));
   if (!(ke < 1e30f)) {
     set_status(d.g, ST_NAN);
@@ -707,116 +720,94 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
   if (g == 0) T.nl[a] = valid ? nl : 0;
   __syncwarp();
   // ---- triplet phase: items (centre of this warp, leg j), spread over the lanes
-  // ---- triplet phase: the ordered leg pairs (j, k != j) of the warp's
-  // centres are split into 32 equal contiguous ranges, one per lane.  A lane
-  // walks (centre, j, k) in order and flushes the force accumulated on leg j
-  // (red.global) and the reaction on the centre (shared memory) whenever j or
-  // the centre changes; a leg whose partners straddle two lanes gets two
-  // partial flushes, which add up.  Each unordered triplet's energy is taken
-  // once (k > j).
   const int a0 = (threadIdx.x >> 5) * kWAtoms;
-  int ppre[kWAtoms + 1];
-  ppre[0] = 0;
+  int pre[kWAtoms + 1];
+  pre[0] = 0;
 #pragma unroll
   for (int k = 0; k < kWAtoms; ++k) {
     int n = T.nl[a0 + k];
     if (n > kLMax) n = 0;  // centres beyond the table: force_overflow_item
-    ppre[k + 1] = ppre[k] + n * (n - 1);
+    pre[k + 1] = pre[k] + n;
   }
   const int b0 = __shfl_sync(kFull, b, 0);
   const bool wuni = __all_sync(kFull, b == b0 || b < 0);
   const float c0 = P.c0;
-  const int ptot = ppre[kWAtoms];
-  int t = (lane * ptot) >> 5;
-  const int t1 = ((lane + 1) * ptot) >> 5;
-  if (t < t1) {
-    // decode the first pair of this lane's range
-    int ka = 0, pbase = 0, n = 0;
+  for (int base = 0; base < pre[kWAtoms]; base += 32) {  // warp-uniform rounds
+    const int it = base + lane;
+    int ka = -1, first = 0, n = 0;
 #pragma unroll
-    for (int k = 0; k < kWAtoms; ++k)
-      if (t >= ppre[k] && t < ppre[k + 1]) {
+    for (int k = 0; k < kWAtoms; ++k)  // the centre whose item range holds it
+      if (it >= pre[k] && it < pre[k + 1]) {
         ka = k;
-        pbase = ppre[k];
-        n = (int)(0.5f + sqrtf(0.25f + (float)(ppre[k + 1] - ppre[k])));  // n (n - 1) pairs
+        first = pre[k];
+        n = pre[k + 1] - pre[k];
       }
-    int off = t - pbase;
-    int jj = off / (n - 1);
-    int kk = off - jj * (n - 1);
-    kk += (kk >= jj) ? 1 : 0;
-    int rb = (a0 + ka) * kLPad;
-    float4 uj = T.ue[rb + jj], xj = T.aux[rb + jj];
-    float gx = 0.f, gy = 0.f, gz = 0.f, e3 = 0.f;
-    float crx = 0.f, cry = 0.f, crz = 0.f;  // reaction on the current centre
-    while (true) {
-      {
-        const float4 uk = T.ue[rb + kk];
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (ka >= 0) {
+      const int aa = a0 + ka;
+      const int jj = it - first;
+      const float4* rowu = T.ue + aa * kLPad;
+      const float4 uj = rowu[jj];
+      const float4 xj = T.aux[aa * kLPad + jj];
+      float e3 = 0.f;
+      // partner legs k != jj; the energy of each unordered triplet is taken
+      // by the item of its lower leg (k > jj)
+      auto partner = [&](int k, bool energy) {
+        const float4 uk = rowu[k];
         const float c = fmaf(uj.x, uk.x, fmaf(uj.y, uk.y, uj.z * uk.z));
         const float D = c - c0;
         const float gg = uj.w * uk.w * D;
-        if (kk > jj) e3 = fmaf(gg, D, e3);
+        if (energy) e3 = fmaf(gg, D, e3);
         const float aj = gg * xj.x;
         const float bj = gg * fmaf(c, xj.x, D * xj.y);
         gx = fmaf(-aj, uk.x, fmaf(bj, uj.x, gx));
         gy = fmaf(-aj, uk.y, fmaf(bj, uj.y, gy));
         gz = fmaf(-aj, uk.z, fmaf(bj, uj.z, gz));
-      }
-      ++t;
-      ++kk;
-      if (kk == jj) ++kk;
-      const bool end_j = (kk >= n) || (t >= t1);
-      if (end_j) {  // flush leg jj of centre ka
-        red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
-        crx -= gx;
-        cry -= gy;
-        crz -= gz;
-        const float rx = xj.z * uj.x, ry = xj.z * uj.y, rz = xj.z * uj.z;
-        if (wuni) {
-          acc[1] += e3;
-          acc[2] = fmaf(rx, gx, acc[2]);
-          acc[3] = fmaf(ry, gy, acc[3]);
-          acc[4] = fmaf(rz, gz, acc[4]);
-          acc[5] = fmaf(rx, gy, acc[5]);
-          acc[6] = fmaf(rx, gz, acc[6]);
-          acc[7] = fmaf(ry, gz, acc[7]);
-        } else {  // warp straddles two boxes (rare): straight to this centre's box
-          double* p = &d.bst[d.q[blk * kFAtoms + a0 + ka].w].ew[par][0];
-          atomicAdd(p + 1, (double)e3);
-          atomicAdd(p + 2, (double)(rx * gx));
-          atomicAdd(p + 3, (double)(ry * gy));
-          atomicAdd(p + 4, (double)(rz * gz));
-          atomicAdd(p + 5, (double)(rx * gy));
-          atomicAdd(p + 6, (double)(rx * gz));
-          atomicAdd(p + 7, (double)(ry * gz));
-        }
-        gx = gy = gz = e3 = 0.f;
-        if (t >= t1) break;
-        ++jj;
-        kk = (jj == 0) ? 1 : 0;
-        if (jj >= n) {  // next centre with at least two legs
-          atomicAdd(&T.fi[a0 + ka][0], crx);
-          atomicAdd(&T.fi[a0 + ka][1], cry);
-          atomicAdd(&T.fi[a0 + ka][2], crz);
-          crx = cry = crz = 0.f;
-          int nk = ka + 1;
-#pragma unroll
-          for (int k = kWAtoms - 1; k >= 0; --k)  // smallest k > ka with pairs
-            if (k > ka && ppre[k + 1] > ppre[k]) nk = k;
-          ka = nk;
-          pbase = 0;
-#pragma unroll
-          for (int k = 0; k < kWAtoms; ++k)
-            if (k == ka) n = (int)(0.5f + sqrtf(0.25f + (float)(ppre[k + 1] - ppre[k])));
-          jj = 0;
-          kk = 1;
-          rb = (a0 + ka) * kLPad;
-        }
-        uj = T.ue[rb + jj];
-        xj = T.aux[rb + jj];
+      };
+#pragma unroll 2
+      for (int k = 0; k < jj; ++k) partner(k, false);
+#pragma unroll 2
+      for (int k = jj + 1; k < n; ++k) partner(k, true);
+      red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
+      const float rx = xj.z * uj.x, ry = xj.z * uj.y, rz = xj.z * uj.z;
+      if (wuni) {
+        acc[1] += e3;
+        acc[2] = fmaf(rx, gx, acc[2]);
+        acc[3] = fmaf(ry, gy, acc[3]);
+        acc[4] = fmaf(rz, gz, acc[4]);
+        acc[5] = fmaf(rx, gy, acc[5]);
+        acc[6] = fmaf(rx, gz, acc[6]);
+        acc[7] = fmaf(ry, gz, acc[7]);
+      } else {  // warp straddles two boxes (rare): straight to the item's box
+        double* p = &d.bst[d.q[blk * kFAtoms + aa].w].ew[par][0];
+        atomicAdd(p + 1, (double)e3);
+        atomicAdd(p + 2, (double)(rx * gx));
+        atomicAdd(p + 3, (double)(ry * gy));
+        atomicAdd(p + 4, (double)(rz * gz));
+        atomicAdd(p + 5, (double)(rx * gy));
+        atomicAdd(p + 6, (double)(rx * gz));
+        atomicAdd(p + 7, (double)(ry * gz));
       }
     }
-    atomicAdd(&T.fi[a0 + ka][0], crx);
-    atomicAdd(&T.fi[a0 + ka][1], cry);
-    atomicAdd(&T.fi[a0 + ka][2], crz);
+    // reaction on the centres: segmented sum over the lanes holding one centre's items
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int ko = __shfl_up_sync(kFull, ka, o);
+      const float tx = __shfl_up_sync(kFull, gx, o), ty = __shfl_up_sync(kFull, gy, o),
+                  tz = __shfl_up_sync(kFull, gz, o);
+      if (lane >= o && ko == ka) {
+        gx += tx;
+        gy += ty;
+        gz += tz;
+      }
+    }
+    const int kn = __shfl_down_sync(kFull, ka, 1);
+    if (ka >= 0 && (lane == 31 || kn != ka)) {
+      T.fi[a0 + ka][0] -= gx;  // one tail per centre and round
+      T.fi[a0 + ka][1] -= gy;
+      T.fi[a0 + ka][2] -= gz;
+    }
+    __syncwarp();  // orders this round's table updates before the next round's
   }
   __syncwarp();
   // ---- force on the centre: pair part (lane group) + three-body reaction
@@ -871,8 +862,9 @@ __global__ void k_kick1(Dev d, cudaGraphConditionalHandle rebuild_cond, int use_
   const Integ I = *d.integ;
   const int par = (int)(d.g->step & 1ull);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int pend = d.g->pend;
   if (i == 0) d.g->n_over = 0;
-  if (i < d.N) kick1_item(d, I, i, (int)d.q[i].w, par);
+  if (i < d.N) kick1_item(d, I, i, (int)d.q[i].w, par, pend);
   if (use_cond) {
     __shared__ bool last;
     __threadfence();
@@ -1019,6 +1011,7 @@ __global__ void k_kick2(Dev d) {
   }
   const bool last = (i < d.N) && (threadIdx.x == blockDim.x - 1 || i == d.N - 1);
   box_accumulate<1>(ke, b, last, [&](int bb) { return &d.bst[bb].ke_acc[par]; });
+  if (i == 0) d.g->pend = 1;  // the second half-kick is now pending
   // last block finishes the step: end-of-step thermostat half per box
   __shared__ bool am_last;
   __threadfence();
@@ -1051,14 +1044,14 @@ __global__ void k_load_positions(Dev d, const double* __restrict__ xin, const in
   const Box& bx = d.box[b];
   double p[3];
   for (int k = 0; k < 3; ++k) {
-    double v = xin[3 * (size_t)u + k];
-    v -= bx.L[k] * floor(v / bx.L[k]);
-    if (v >= bx.L[k]) v -= bx.L[k];
+    double v = xin[3 * (size_t)u + k] / bx.L[k];  // box fraction
+    v -= floor(v);
+    if (v >= 1.0) v -= 1.0;
     if (v < 0.0) v = 0.0;
     p[k] = v;
   }
   d.x[i] = p[0]; d.y[i] = p[1]; d.z[i] = p[2];
-  d.q[i] = make_uint4(to_fixed(p[0], bx.qs[0]), to_fixed(p[1], bx.qs[1]), to_fixed(p[2], bx.qs[2]), (unsigned)b);
+  d.q[i] = make_uint4(frac_to_fixed(p[0]), frac_to_fixed(p[1]), frac_to_fixed(p[2]), (unsigned)b);
 }
 
 __global__ void k_load_velocities(Dev d, const double* __restrict__ vin) {
@@ -1087,6 +1080,20 @@ __global__ void k_ke_init(Dev d) {
   }
   const bool last = (i < d.N) && (threadIdx.x == blockDim.x - 1 || i == d.N - 1);
   box_accumulate<1>(ke, b, last, [&](int bb) { return &d.bst[bb].ke_last; });
+}
+
+// Applies a pending second half-kick (v += dt/2 F/m) before anything changes
+// the forces or the atom order outside a step.
+__global__ void k_flush_pending(Dev d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!d.g->pend) return;
+  const double cf = d.integ->cf;
+  if (i < d.N) {
+    const float4 F = d.f[i];
+    d.vx[i] += cf * F.x;
+    d.vy[i] += cf * F.y;
+    d.vz[i] += cf * F.z;
+  }
 }
 
 // Flags every box for a rebuild (new state, parameters, skin or list width).
@@ -1142,16 +1149,19 @@ __global__ void k_gather_state(Dev d, double* __restrict__ xo, double* __restric
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
   const int u = d.id[i];
+  const Box& bx = d.box[d.q[i].w];
   if (xo) {
-    xo[3 * (size_t)u] = d.x[i];
-    xo[3 * (size_t)u + 1] = d.y[i];
-    xo[3 * (size_t)u + 2] = d.z[i];
+    xo[3 * (size_t)u] = d.x[i] * bx.L[0];
+    xo[3 * (size_t)u + 1] = d.y[i] * bx.L[1];
+    xo[3 * (size_t)u + 2] = d.z[i] * bx.L[2];
   }
-  if (vo) {
+  if (vo) {  // pending half-kick and end-of-step thermostat scale applied
     const double s = d.bst[d.q[i].w].s_end;
-    vo[3 * (size_t)u] = d.vx[i] * s;
-    vo[3 * (size_t)u + 1] = d.vy[i] * s;
-    vo[3 * (size_t)u + 2] = d.vz[i] * s;
+    const double cf = d.g->pend ? d.integ->cf : 0.0;
+    const float4 F = d.f[i];
+    vo[3 * (size_t)u] = (d.vx[i] + cf * F.x) * s;
+    vo[3 * (size_t)u + 1] = (d.vy[i] + cf * F.y) * s;
+    vo[3 * (size_t)u + 2] = (d.vz[i] + cf * F.z) * s;
   }
 }
 

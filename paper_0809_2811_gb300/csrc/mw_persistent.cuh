@@ -131,8 +131,9 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     const unsigned long long step = step0 + (unsigned long long)s;
     const int par = (int)(step & 1ull);
     // a1 + a7 first half, a8 displacement check
+    const int pend = *(volatile int*)&g->pend;  // stable: written only in the kick2 phase
     if (tid == 0) g->n_over = 0;
-    for (int i = tid; i < d.N; i += nth) kick1_item(d, I, i, (int)d.q[i].w, par);
+    for (int i = tid; i < d.N; i += nth) kick1_item(d, I, i, (int)d.q[i].w, par, pend);
     if (grid_barrier(g, gen)) return;
     // a2 + a3: cell binning and neighbour list, when due (flag is stable until kick2)
     if (*(volatile int*)&g->any_rebuild) {
@@ -157,7 +158,10 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     // a7 second half + kinetic energy per box; the rebuild (if any) is consumed
     if (blockIdx.x == 0) {
       for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
-      if (threadIdx.x == 0) g->any_rebuild = 0;
+      if (threadIdx.x == 0) {
+        g->any_rebuild = 0;
+        g->pend = 1;  // the second half-kick is now pending
+      }
     }
     for (int base = blockIdx.x * blockDim.x; base < d.N; base += nth) {
       const int i = base + threadIdx.x;

@@ -280,6 +280,7 @@ def run_gpu(args, world, rank, local, pg):
     time.sleep(0.3)
     t_wall = time.perf_counter()
     t_host = 0.0
+    torch.cuda.profiler.start()  # profiler range = the timed steps (ncu --profile-from-start off)
     for k in range(K):
         ev0[k].record(stream)
         th_ = time.perf_counter()
@@ -288,6 +289,7 @@ def run_gpu(args, world, rank, local, pg):
         ev1[k].record(stream)
         flush.fill_(float(k))
     torch.cuda.synchronize(dev)
+    torch.cuda.profiler.stop()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     mw.mw_sync(sysm.h)

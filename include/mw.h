@@ -60,7 +60,7 @@ typedef enum mw_status {
   MW_EBOX = 2,             /* a box edge is shorter than 2 * (a sigma + skin) */
   MW_ENLIST_OVERFLOW = 3,  /* neighbour list wider than its allocation (recovered internally by mw_step) */
   MW_ENAN = 4,             /* non-finite force or velocity met during dynamics */
-  MW_ELOST = 5,            /* an atom moved more than half a box edge in one step */
+  MW_ELOST = 5,            /* a velocity component would move an atom > 1/4 of the shortest edge per step */
   MW_ETIMEOUT = 6,         /* a bounded device-side wait ran out (persistent engine) */
   MW_ECUDA = 7,            /* a CUDA runtime call failed */
   MW_ENOMEM = 8,           /* device or host allocation failed */

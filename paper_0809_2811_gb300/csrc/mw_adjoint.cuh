@@ -95,7 +95,7 @@ __device__ void adjoint_block(const Dev& d, const AdjDev& A, const FParams& P, A
     float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 1.f;
     int j = 0;
     if (s < cnt) {
-      j = __ldg(row + s);
+      j = row[s];
       const uint4 qj = d.q[j];
       dx = fix_diff(qi.x, qj.x, L0);
       dy = fix_diff(qi.y, qj.y, L1);
@@ -246,8 +246,7 @@ __device__ void adjoint_block(const Dev& d, const AdjDev& A, const FParams& P, A
     }
   }
   const int ab = wuni ? b0 : b;
-  const bool last = valid && (a == kFAtoms - 1 || i == d.N - 1);
-  box_accumulate<3>(acc, ab, last, [&](int bb) { return &A.acc[3 * bb]; });
+  box_accumulate<3>(acc, ab, [&](int bb) { return &A.acc[3 * bb]; });
 }
 
 __global__ void __launch_bounds__(kFThreads) k_adjoint(Dev d, AdjDev A, FParams P) {

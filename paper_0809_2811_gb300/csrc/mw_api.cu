@@ -263,7 +263,7 @@ mw_status status_error(const Global& g) {
     case ST_OK: return MW_OK;
     case ST_OVERFLOW: return fail(MW_ENLIST_OVERFLOW, "neighbour list overflow (max count %d)", g.max_count);
     case ST_NAN: return fail(MW_ENAN, "non-finite velocity or force at atom slot %d", g.err_index);
-    case ST_LOST: return fail(MW_ELOST, "atom slot %d moved more than half a box edge in one step", g.err_index);
+    case ST_LOST: return fail(MW_ELOST, "atom slot %d ran away: a velocity component moves it more than a quarter of the shortest box edge per step, or is not finite", g.err_index);
     case ST_TIMEOUT: return fail(MW_ETIMEOUT, "a bounded device-side wait ran out");
     case ST_LEGS: return fail(MW_EINVAL, "more than %d atoms within a*sigma of atom slot %d", kMaxLegsOverflow, g.err_index);
     default: return fail(MW_ECUDA, "device status %d", g.status);
@@ -300,10 +300,10 @@ mw_status capture_step(mw_system* s) {
     // Same kernels without the IF node (the rebuild kernels return at once
     // when no box needs a rebuild): profilers that skip conditional graphs
     // still see every kernel of the step.
-    k_kick1<<<gb, kThreads, 0, s->stream>>>(d, 0ull, 0);
+    k_kick1<false><<<kick_blocks(s->N, kKThreads), kKThreads, 0, s->stream>>>(d, 0ull);
     launch_rebuild(s);
     launch_force(s);
-    k_kick2<<<gb, kThreads, 0, s->stream>>>(d);
+    k_kick2<<<kick_blocks(s->N, kKThreads), kKThreads, 0, s->stream>>>(d);
     MW_CUDA(cudaGetLastError());
     return MW_OK;
   }
@@ -314,7 +314,7 @@ mw_status capture_step(mw_system* s) {
   MW_CUDA(cudaStreamGetCaptureInfo(s->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphConditionalHandle h;
   MW_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-  k_kick1<<<gb, kThreads, 0, s->stream>>>(d, h, 1);
+  k_kick1<true><<<kick_blocks(s->N, kKThreads), kKThreads, 0, s->stream>>>(d, h);
   MW_CUDA(cudaGetLastError());
   MW_CUDA(cudaStreamGetCaptureInfo(s->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphNodeParams p = {};
@@ -334,7 +334,7 @@ mw_status capture_step(mw_system* s) {
   MW_CUDA(cudaGetLastError());
   MW_CUDA(cudaStreamEndCapture(s->cap_stream, &body));
   launch_force(s);
-  k_kick2<<<gb, kThreads, 0, s->stream>>>(d);
+  k_kick2<<<kick_blocks(s->N, kKThreads), kKThreads, 0, s->stream>>>(d);
   MW_CUDA(cudaGetLastError());
   return MW_OK;
 }
@@ -419,7 +419,7 @@ mw_status finish_interrupted_step(mw_system* s) {
   const int gb = div_up(s->N, kThreads);
   launch_rebuild(s);
   launch_force(s);
-  k_kick2<<<gb, kThreads, 0, s->stream>>>(s->d);
+  k_kick2<<<kick_blocks(s->N, kKThreads), kKThreads, 0, s->stream>>>(s->d);
   MW_CUDA(cudaGetLastError());
   return MW_OK;
 }
@@ -534,6 +534,7 @@ mw_status validate_integ(mw_system* s, const mw_integrator* in) {
     if (bx.T0 != T0 || bx.Q != Q) {
       bx.T0 = T0;
       bx.Q = Q;
+      bx.invQ = 1.0 / Q;
       boxes_changed = true;
     }
     for (int k = 0; k < 3; ++k) {
@@ -542,6 +543,14 @@ mw_status validate_integ(mw_system* s, const mw_integrator* in) {
         bx.dtL[k] = dtL;
         boxes_changed = true;
       }
+    }
+    // a velocity component of magnitude >= 2^floor(log2(lost / dt)) (between
+    // lost/(2 dt) and lost/dt) moves an atom at least a quarter of the
+    // shortest edge in one step: the run is reported as lost
+    const int ve = std::min(2047, std::max(1, 1023 + (int)std::floor(std::log2((double)bx.lost / in->dt))));
+    if (bx.vexp_lost != ve) {
+      bx.vexp_lost = ve;
+      boxes_changed = true;
     }
   }
   Integ I{};
@@ -620,7 +629,11 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
     bx.Ndf = 3.0 * n[b] - 3.0;
     bx.T0 = 0;
     bx.Q = 1;
+    bx.invQ = 1;
+    bx.vexp_lost = 2047;
     bx.volume = bx.L[0] * bx.L[1] * bx.L[2];
+    bx.inv_ndf_kb = bx.Ndf > 0 ? 1.0 / (bx.Ndf * kKB) : 0.0;
+    bx.p_fac = kATM / (3.0 * bx.volume);
     s->off[b] = o;
     o += n[b];
   }
@@ -1174,6 +1187,9 @@ extern "C" mw_status mw_energy_forces_noalloc(int n, const double box[3], const 
   bx.n = n;
   bx.cell_off = 0;
   bx.volume = box[0] * box[1] * box[2];
+  bx.Ndf = 3.0 * n - 3.0;
+  bx.inv_ndf_kb = n > 1 ? 1.0 / (bx.Ndf * kKB) : 0.0;
+  bx.p_fac = kATM / (3.0 * bx.volume);
   unsigned char* base = nullptr;
   if ((st = na_base(&base)) != MW_OK) return st;
   cudaStream_t sm = (cudaStream_t)stream;

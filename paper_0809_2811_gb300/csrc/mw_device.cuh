@@ -45,13 +45,17 @@ constexpr int kMaxLegsOverflow = 64;
 struct Box {        // read-only in kernels
   double L[3];
   double dtL[3];    // dt / L: drift of the box fraction per unit velocity
-  float lost;       // half the shortest edge (A): larger one-step moves are errors
+  float lost;       // half the shortest edge (A)
   double qs[3];     // 2^32 / L
   float Lq[3];      // L / 2^32
   int off, n;       // atom range
   int nc[3];        // cells per dimension
   int cell_off;     // first global cell
   double T0, Ndf, Q, volume;
+  double invQ;      // 1 / Q
+  double inv_ndf_kb;  // 1 / (N_df k_B): T = 2 KE inv_ndf_kb
+  double p_fac;     // atm per kcal/mol of 2 KE + tr W: 1/(3 V) in atm
+  int vexp_lost;    // a velocity component whose FP64 exponent field is >= this is a runaway (see validate_integ)
 };
 
 struct BoxState {   // mutated by kernels
@@ -180,14 +184,15 @@ __device__ __forceinline__ bool box_flagged(const Dev& d, int b) { return d.bst[
 
 // Per-box accumulation of NV values held as FP32 by each thread; the sums
 // across blocks are FP64.  Every thread of the block calls it (b < 0 for
-// threads without a contribution).  Atoms are box-major, so box ids along a
+// threads without a contribution); thread 0 must hold the block's first box.  Atoms are box-major, so box ids along a
 // warp are non-decreasing: a segmented FP32 scan sums each run of one box in
 // the warp; runs of the block's first and last box are summed in shared
 // memory (FP32, one block of atoms) and widened to FP64 for one global atomic
 // per value and block; runs of other boxes (small boxes only) go to global
 // memory directly.  No FP64 arithmetic runs on the SM.
 template <int NV, class Dst>
-__device__ void box_accumulate(float (&v)[NV], int b, bool is_last_valid, Dst dst) {
+__device__ void box_accumulate(float (&v)[NV], int b, Dst dst) {
+  static_assert(NV <= 16, "two slots of NV sums are flushed by warp 0");
   __shared__ float sacc[2][NV];
   __shared__ int sbox[2];
   const int lane = threadIdx.x & 31;
@@ -197,7 +202,7 @@ __device__ void box_accumulate(float (&v)[NV], int b, bool is_last_valid, Dst ds
   }
   if (threadIdx.x < 2 * NV) (&sacc[0][0])[threadIdx.x] = 0.f;
   __syncthreads();
-  if (is_last_valid) sbox[1] = b;
+  if (b >= 0) atomicMax(&sbox[1], b);  // the block's last box (box ids never decrease along atoms)
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     const int bo = __shfl_up_sync(kFull, b, off);
@@ -222,20 +227,29 @@ __device__ void box_accumulate(float (&v)[NV], int b, bool is_last_valid, Dst ds
     }
   }
   __syncthreads();
+  // warp 0 alone reads the shared sums after the barrier, so a following call
+  // (whose warp 0 resets them first) cannot race with these reads
   if (threadIdx.x < NV && sbox[0] >= 0) atomicAdd(dst(sbox[0]) + threadIdx.x, (double)sacc[0][threadIdx.x]);
-  if (threadIdx.x >= 32 && threadIdx.x < 32 + NV && sbox[1] >= 0 && sbox[1] != sbox[0])
-    atomicAdd(dst(sbox[1]) + (threadIdx.x - 32), (double)sacc[1][threadIdx.x - 32]);
+  if (threadIdx.x >= 16 && threadIdx.x < 16 + NV && sbox[1] >= 0 && sbox[1] != sbox[0])
+    atomicAdd(dst(sbox[1]) + (threadIdx.x - 16), (double)sacc[1][threadIdx.x - 16]);
+}
+
+// exp(x) for the thermostat scale: |x| = |xi dt/2| is ~1e-4 in practice, where
+// the Taylor series to x^6 is exact to ~1e-19 relative; larger |x| uses exp().
+__device__ __forceinline__ double exp_small(double x) {
+  if (fabs(x) > 1e-2) return exp(x);
+  return 1.0 + x * (1.0 + x * (0.5 + x * (1.0 / 6.0 + x * (1.0 / 24.0 + x * (1.0 / 120.0 + x * (1.0 / 720.0))))));
 }
 
 // One Nose-Hoover half step (length dt/2) of a single thermostat: quarter step
 // on xi, velocity scale exp(-xi dt/2), half step on eta, quarter step on xi.
 __device__ __forceinline__ double nh_half(double& ke, double& xi, double& eta, double dt, double Ndf, double kT0,
-                                          double Q) {
-  xi += 0.25 * dt * (2.0 * ke - Ndf * kT0) / Q;
-  const double s = exp(-xi * 0.5 * dt);
+                                          double invQ) {
+  xi += 0.25 * dt * (2.0 * ke - Ndf * kT0) * invQ;
+  const double s = exp_small(-xi * 0.5 * dt);
   ke *= s * s;
   eta += xi * 0.5 * dt;
-  xi += 0.25 * dt * (2.0 * ke - Ndf * kT0) / Q;
+  xi += 0.25 * dt * (2.0 * ke - Ndf * kT0) * invQ;
   return s;
 }
 
@@ -250,7 +264,7 @@ __device__ void start_half_box(const Dev& d, const Integ& I, int b) {
   double s = 1.0;
   if (I.kind == TH_NH) {
     double ke = st->ke_last;
-    s = nh_half(ke, xi, eta, I.dt, bx.Ndf, kKB * bx.T0, bx.Q);
+    s = nh_half(ke, xi, eta, I.dt, bx.Ndf, kKB * bx.T0, bx.invQ);
   }
   st->xi[1] = xi;
   st->eta[1] = eta;
@@ -267,65 +281,91 @@ __device__ void start_half_box(const Dev& d, const Integ& I, int b) {
 // when a half-kick is pending (S = thermostat scale of the step boundary,
 // a = dt/2 F/m), else v = S v + a; then s += (dt/L) v on the box fraction,
 // wrap into [0, 1), fixed-point copy, displacement check against the last
-// build.  FP64: one conversion and two FMAs per component; the fixed-point
-// copy uses integer operations.  Also zeroes f for this step.
-__device__ __forceinline__ uint32_t advance_coord(double& s, double& v, double S, float dv, double dtL) {
-  v = fma(v, S, (double)dv);
-  s = fma(dtL, v, s);
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(s);
-  if ((bits >> 63) || (bits >> 52) >= 1023ull) {  // left [0, 1): crossed a face (rare)
-    s -= floor(s);
-    if (s >= 1.0) s -= 1.0;
-    if (s < 0.0) s = 0.0;
-  }
-  return frac_to_fixed(s);
-}
+// build.  Three lanes per atom, one per Cartesian component (10 atoms per
+// warp, lanes 30 and 31 idle): FP64 is one conversion and two FMAs per lane,
+// the fixed-point copy and the runaway check use integer operations only.
+// Also zeroes f for this step.
+constexpr int kKAtoms = 10;     // atoms per warp in the kick kernels
+constexpr int kKThreads = 512;  // threads per block of k_kick1 / k_kick2 (few blocks: few same-address atomics)
 
-__device__ __forceinline__ void kick1_item(const Dev& d, const Integ& I, int i, int b, int par, int pend) {
-  const Box& bx = d.box[b];
-  BoxState* st = d.bst + b;
-  const double S = st->s_kick;
-  const float kf = I.cf_f * (pend ? st->s_kick1 : 1.0f);
-  if (i == bx.off) {  // this step's accumulators start from zero
-    st->ke_acc[par] = 0.0;
+__device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, int par, int pend) {
+  const int lane = threadIdx.x & 31;
+  const int i = w * kKAtoms + lane / 3;
+  const int c = lane - 3 * (lane / 3);
+  const bool act = lane < 3 * kKAtoms && i < d.N;
+  float dd = 0.f;
+  bool lost = false;
+  int b = -1;
+  if (act) {
+    // every load that does not depend on the box first, so that their
+    // latencies overlap (the stores below may alias them)
+    float* fp = reinterpret_cast<float*>(d.f + i) + c;
+    double* vp = (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz)) + i;
+    double* sp = (c == 0 ? d.x : (c == 1 ? d.y : d.z)) + i;
+    b = (int)d.q[i].w;
+    const float F = *fp;
+    const double v0 = *vp;
+    const double s0 = *sp;
+    const uint32_t qb = reinterpret_cast<const uint32_t*>(d.qb + i)[c];
+    const Box& bx = d.box[b];
+    const BoxState* st = d.bst + b;
+    const double S = st->s_kick;
+    const float kf = I.cf_f * (pend ? st->s_kick1 : 1.0f);
+    const double dtL = c == 0 ? bx.dtL[0] : (c == 1 ? bx.dtL[1] : bx.dtL[2]);
+    const float Lq = c == 0 ? bx.Lq[0] : (c == 1 ? bx.Lq[1] : bx.Lq[2]);
+    const int vexp = bx.vexp_lost;
+    const double v = fma(v0, S, (double)(kf * F));
+    double sf = fma(dtL, v, s0);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(sf);
+    if ((bits >> 63) || (bits >> 52) >= 1023ull) {  // left [0, 1): crossed a face (rare)
+      sf -= floor(sf);
+      if (sf >= 1.0) sf -= 1.0;
+      if (sf < 0.0) sf = 0.0;
+    }
+    *fp = 0.f;
+    *vp = v;
+    *sp = sf;
+    const uint32_t qn = frac_to_fixed(sf);
+    reinterpret_cast<uint32_t*>(d.q + i)[c] = qn;
+    const float dc = fix_diff(qb, qn, Lq);
+    dd = dc * dc;
+    // |v| at or above the box's runaway threshold (or NaN/inf): exponent field test
+    lost = (int)((__double_as_longlong(v) >> 52) & 0x7ff) >= vexp;
+    if (i == bx.off && c == 0) {  // this step's accumulators start from zero
+      BoxState* sw = d.bst + b;
+      sw->ke_acc[par] = 0.0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) st->ew[par][k] = 0.0;
+      for (int k = 0; k < 8; ++k) sw->ew[par][k] = 0.0;
+    }
   }
-  const float4 F = d.f[i];
-  d.f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  double vx = d.vx[i], vy = d.vy[i], vz = d.vz[i];
-  double px = d.x[i], py = d.y[i], pz = d.z[i];
-  const uint32_t q0 = advance_coord(px, vx, S, kf * F.x, bx.dtL[0]);
-  const uint32_t q1 = advance_coord(py, vy, S, kf * F.y, bx.dtL[1]);
-  const uint32_t q2 = advance_coord(pz, vz, S, kf * F.z, bx.dtL[2]);
-  d.vx[i] = vx; d.vy[i] = vy; d.vz[i] = vz;
-  d.x[i] = px; d.y[i] = py; d.z[i] = pz;
-  const uint4 qn = make_uint4(q0, q1, q2, (unsigned)b);
-  d.q[i] = qn;
-  const uint4 qb = d.qb[i];
-  const float dx = fix_diff(qb.x, qn.x, bx.Lq[0]);
-  const float dy = fix_diff(qb.y, qn.y, bx.Lq[1]);
-  const float dz = fix_diff(qb.z, qn.z, bx.Lq[2]);
-  if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > I.half_skin2) {
+  // displacement since the last build: sum the three components of the atom
+  const int base = lane - c;
+  const float d1 = __shfl_sync(kFull, dd, min(base + 1, 31)), d2 = __shfl_sync(kFull, dd, min(base + 2, 31));
+  if (act && c == 0 && dd + d1 + d2 > I.half_skin2) {
     d.bst[b].rebuild = 1;
     d.g->any_rebuild = 1;
   }
-  const float sv = (float)I.dt * (fabsf((float)vx) + fabsf((float)vy) + fabsf((float)vz));
-  if (!(sv < bx.lost)) {  // moved more than half the shortest edge in one step, or NaN
-    set_status(d.g, (sv == sv) ? ST_LOST : ST_NAN);
+  if (lost) {
+    set_status(d.g, ST_LOST);
     d.g->err_index = i;
   }
 }
 
-// a7 (second half) for one atom: the kinetic energy of v + a (FP32 per atom;
-// the sums over atoms are FP64).  The half-kick itself is left pending and
-// folded into the next kick1 (or applied when the state is read).
-__device__ __forceinline__ float kick2_item(const Dev& d, const Integ& I, int i) {
-  const float4 F = d.f[i];
-  const float fx = fmaf(I.cf_f, F.x, (float)d.vx[i]);
-  const float fy = fmaf(I.cf_f, F.y, (float)d.vy[i]);
-  const float fz = fmaf(I.cf_f, F.z, (float)d.vz[i]);
-  const float ke = (float)I.ke_fac * fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+// a7 (second half): the kinetic energy of v + a (FP32 per component; the
+// sums over atoms are FP64).  The half-kick itself is left pending and folded
+// into the next kick1 (or applied when the state is read).  Same lane layout
+// as kick1_lane.
+__device__ __forceinline__ float kick2_lane(const Dev& d, const Integ& I, int w, int& b) {
+  const int lane = threadIdx.x & 31;
+  const int i = w * kKAtoms + lane / 3;
+  const int c = lane - 3 * (lane / 3);
+  b = -1;
+  if (lane >= 3 * kKAtoms || i >= d.N) return 0.f;
+  b = (int)d.q[i].w;
+  const float F = reinterpret_cast<const float*>(d.f + i)[c];
+  const double* vp = (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz)) + i;
+  const float u = fmaf(I.cf_f, F, (float)*vp);
+  const float ke = (float)I.ke_fac * u * u;
   if (!(ke < 1e30f)) {
     set_status(d.g, ST_NAN);
     d.g->err_index = i;
@@ -341,9 +381,9 @@ __device__ void end_of_step_box(const Dev& d, const Integ& I, int b, int par, un
   double xi = st->xi[1], eta = st->eta[1];
   double s = 1.0;
   if (I.kind == TH_NH) {
-    s = nh_half(ke, xi, eta, I.dt, bx.Ndf, kKB * bx.T0, bx.Q);
+    s = nh_half(ke, xi, eta, I.dt, bx.Ndf, kKB * bx.T0, bx.invQ);
   } else if (I.kind == TH_BERENDSEN) {
-    const double T = 2.0 * ke / (bx.Ndf * kKB);
+    const double T = 2.0 * ke * bx.inv_ndf_kb;
     if (T > 0.0) {
       s = sqrt(1.0 + I.dt / I.tau * (bx.T0 / T - 1.0));
       ke *= s * s;
@@ -363,11 +403,11 @@ __device__ void end_of_step_box(const Dev& d, const Integ& I, int b, int par, un
   t[TR_E2] = e2;
   t[TR_E3] = e3;
   t[TR_KE] = ke;
-  t[TR_T] = 2.0 * ke / (bx.Ndf * kKB);
+  t[TR_T] = 2.0 * ke * bx.inv_ndf_kb;
   double cons = ke + e2 + e3;
   if (I.kind == TH_NH) cons += 0.5 * bx.Q * xi * xi + bx.Ndf * kKB * bx.T0 * eta;
   t[TR_CONS] = cons;
-  t[TR_P] = (2.0 * ke + w[0] + w[1] + w[2]) / (3.0 * bx.volume) * kATM;
+  t[TR_P] = (2.0 * ke + w[0] + w[1] + w[2]) * bx.p_fac;
   for (int k = 0; k < 6; ++k) t[TR_W0 + k] = w[k];
   t[TR_XI] = xi;
   t[TR_ETA] = eta;
@@ -383,7 +423,7 @@ __device__ void end_of_step_box(const Dev& d, const Integ& I, int b, int par, un
 __device__ __forceinline__ int stencil_n(int nc) { return nc >= 3 ? 3 : nc; }
 __device__ __forceinline__ int stencil_off(int nc, int o) { return nc >= 3 ? o - 1 : o; }
 
-__device__ void neigh_cell_warp(const Dev& d, const uint4* __restrict__ qa, int c, float rl2) {
+__device__ void neigh_cell_warp(const Dev& d, const uint4* qa, int c, float rl2) {
   const int lane = threadIdx.x & 31;
   const int a0 = d.cell_start[c];
   const int ni = d.cell_start[c + 1] - a0;
@@ -624,7 +664,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
 #pragma unroll
   for (int t = 0; t < kPre; ++t) {
     const int s = g + kG * t;
-    jr[t] = (s < cnt) ? __ldg(row + s) : -1;
+    jr[t] = (s < cnt) ? row[s] : -1;
   }
 #pragma unroll
   for (int t = 0; t < kPre; ++t) {
@@ -660,7 +700,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
   for (int t = kPre; t < iters; ++t) {  // long rows (dense input)
     const int s = g + kG * t;
     const bool have = s < cnt;
-    const int j = have ? __ldg(row + s) : 0;
+    const int j = have ? row[s] : 0;
     uint4 qj = make_uint4(0u, 0u, 0u, 0u);
     if (have) qj = d.q[j];
     test_slot(j, qj.x, qj.y, qj.z, have);
@@ -834,8 +874,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     }
   }
   const int ab = wuni ? b0 : b;
-  const bool last = valid && (a == kFAtoms - 1 || i == d.N - 1);
-  box_accumulate<8>(acc, ab, last, [&](int bb) { return &d.bst[bb].ew[par][0]; });
+  box_accumulate<8>(acc, ab, [&](int bb) { return &d.bst[bb].ew[par][0]; });
 }
 
 template <bool kCount>
@@ -854,22 +893,26 @@ __global__ void __launch_bounds__(kFThreads, 8) k_force(Dev d, FParams P) {
 // ---------------------------------------------------------------------------
 // Per-phase kernels (the graph engine and the standalone force call).
 
-// In the graph engine the last block to finish also sets the condition of
-// the graph's IF node that holds the rebuild kernels (skipped when no box
-// moved more than skin/2).
-__global__ void k_kick1(Dev d, cudaGraphConditionalHandle rebuild_cond, int use_cond) {
+// kCond (the graph engine's instantiation): the last block to finish also
+// sets the condition of the graph's IF node that holds the rebuild kernels
+// (skipped when no box moved more than skin/2).  The other instantiation
+// holds no conditional-node call, so profilers can capture it.
+template <bool kCond>
+__global__ void __launch_bounds__(kKThreads) k_kick1(Dev d, cudaGraphConditionalHandle rebuild_cond) {
   if (d.g->status) return;
   const Integ I = *d.integ;
   const int par = (int)(d.g->step & 1ull);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int pend = d.g->pend;
-  if (i == 0) d.g->n_over = 0;
-  if (i < d.N) kick1_item(d, I, i, (int)d.q[i].w, par, pend);
-  if (use_cond) {
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.g->n_over = 0;
+  if (w * kKAtoms < d.N) kick1_lane(d, I, w, par, pend);
+  if constexpr (kCond) {
     __shared__ bool last;
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(&d.g->done1, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) {  // one fence per block after the barrier orders the block's writes
+      __threadfence();
+      last = (atomicAdd(&d.g->done1, 1u) == gridDim.x - 1);
+    }
     __syncthreads();
     if (last && threadIdx.x == 0) {
       __threadfence();
@@ -997,26 +1040,24 @@ __global__ void k_neigh(Dev d, float rl2) {
 }
 
 
-__global__ void k_kick2(Dev d) {
+__global__ void __launch_bounds__(kKThreads) k_kick2(Dev d) {
   if (d.g->status) return;
   const Integ I = *d.integ;
   const unsigned long long step = d.g->step;
   const int par = (int)(step & 1ull);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   float ke[1] = {0.f};
   int b = -1;
-  if (i < d.N) {
-    b = (int)d.q[i].w;
-    ke[0] = kick2_item(d, I, i);
-  }
-  const bool last = (i < d.N) && (threadIdx.x == blockDim.x - 1 || i == d.N - 1);
-  box_accumulate<1>(ke, b, last, [&](int bb) { return &d.bst[bb].ke_acc[par]; });
-  if (i == 0) d.g->pend = 1;  // the second half-kick is now pending
+  ke[0] = kick2_lane(d, I, w, b);
+  box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_acc[par]; });
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.g->pend = 1;  // the second half-kick is now pending
   // last block finishes the step: end-of-step thermostat half per box
   __shared__ bool am_last;
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) am_last = (atomicAdd(&d.g->done, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) {  // one fence per block after the barrier orders the block's writes
+    __threadfence();
+    am_last = (atomicAdd(&d.g->done, 1u) == gridDim.x - 1);
+  }
   __syncthreads();
   if (am_last) {
     __threadfence();
@@ -1078,8 +1119,7 @@ __global__ void k_ke_init(Dev d) {
     const float vx = (float)d.vx[i], vy = (float)d.vy[i], vz = (float)d.vz[i];
     ke[0] = (float)I.ke_fac * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
   }
-  const bool last = (i < d.N) && (threadIdx.x == blockDim.x - 1 || i == d.N - 1);
-  box_accumulate<1>(ke, b, last, [&](int bb) { return &d.bst[bb].ke_last; });
+  box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_last; });
 }
 
 // Applies a pending second half-kick (v += dt/2 F/m) before anything changes
@@ -1102,6 +1142,9 @@ __global__ void k_flag_all(Dev d) {
   if (b < d.nbox) d.bst[b].rebuild = 1;
   if (b == 0) d.g->any_rebuild = 1;
 }
+
+// Blocks of the kick kernels (kKAtoms atoms per warp).
+__host__ __device__ inline int kick_blocks(int n, int threads) { return (n + kKAtoms * (threads / 32) - 1) / (kKAtoms * (threads / 32)); }
 
 // Zeroes this parity's energy/virial accumulators and (optionally) the forces.
 __global__ void k_prep_force(Dev d, int zero_f) {
@@ -1133,11 +1176,11 @@ __global__ void k_thermo_snapshot(Dev d) {
   t[TR_E2] = e2;
   t[TR_E3] = e3;
   t[TR_KE] = ke;
-  t[TR_T] = 2.0 * ke / (bx.Ndf * kKB);
+  t[TR_T] = 2.0 * ke * bx.inv_ndf_kb;
   double cons = ke + e2 + e3;
   if (I.kind == TH_NH) cons += 0.5 * bx.Q * st->xi[0] * st->xi[0] + bx.Ndf * kKB * bx.T0 * st->eta[0];
   t[TR_CONS] = cons;
-  t[TR_P] = (2.0 * ke + st->ew[par][2] + st->ew[par][3] + st->ew[par][4]) / (3.0 * bx.volume) * kATM;
+  t[TR_P] = (2.0 * ke + st->ew[par][2] + st->ew[par][3] + st->ew[par][4]) * bx.p_fac;
   for (int k = 0; k < 6; ++k) t[TR_W0 + k] = st->ew[par][2 + k];
   t[TR_XI] = st->xi[0];
   t[TR_ETA] = st->eta[0];

@@ -4,7 +4,9 @@
 // | force | kick2 | thermostat).  All blocks are
 // co-resident (cooperative launch), every barrier wait is bounded in wall
 // time, and the release of each barrier carries one status snapshot so that
-// all blocks take the same decision to stop.
+// all blocks take the same decision to stop.  Data written in one phase is
+// read by other blocks in a later phase of the same launch, so those reads
+// are coherent loads (no ld.global.nc / __ldg anywhere in the phase bodies).
 #pragma once
 
 #include "mw_device.cuh"
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     // a1 + a7 first half, a8 displacement check
     const int pend = *(volatile int*)&g->pend;  // stable: written only in the kick2 phase
     if (tid == 0) g->n_over = 0;
-    for (int i = tid; i < d.N; i += nth) kick1_item(d, I, i, (int)d.q[i].w, par, pend);
+    for (int w = gw; w * kKAtoms < d.N; w += nwarps) kick1_lane(d, I, w, par, pend);
     if (grid_barrier(g, gen)) return;
     // a2 + a3: cell binning and neighbour list, when due (flag is stable until kick2)
     if (*(volatile int*)&g->any_rebuild) {
@@ -163,16 +165,12 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
         g->pend = 1;  // the second half-kick is now pending
       }
     }
-    for (int base = blockIdx.x * blockDim.x; base < d.N; base += nth) {
-      const int i = base + threadIdx.x;
+    for (int wb = blockIdx.x * (kPersThreads / 32); wb * kKAtoms < d.N; wb += nwarps) {  // block-uniform
+      const int w = wb + (int)(threadIdx.x >> 5);
       float ke[1] = {0.f};
       int b = -1;
-      if (i < d.N) {
-        b = (int)d.q[i].w;
-        ke[0] = kick2_item(d, I, i);
-      }
-      const bool last = (i < d.N) && (threadIdx.x == blockDim.x - 1 || i == d.N - 1);
-      box_accumulate<1>(ke, b, last, [&](int bb) { return &d.bst[bb].ke_acc[par]; });
+      ke[0] = kick2_lane(d, I, w, b);
+      box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_acc[par]; });
     }
     if (grid_barrier(g, gen)) return;
     // thermostat halves (end of this step, start of the next) and thermo record

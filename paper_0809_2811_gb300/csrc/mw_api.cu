@@ -499,6 +499,8 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
     std::memset(&b, 0, sizeof b);
     b.s_end = 1.0;
     b.s_kick = 1.0;
+    b.s_kick1 = 2.0f;
+    b.sig = 0.0f;
     b.rebuild = 1;
   }
   MW_CUDA(cudaMemcpyAsync(s->d.bst, bs.data(), sizeof(BoxState) * s->nbox, cudaMemcpyHostToDevice, s->stream));
@@ -541,13 +543,14 @@ mw_status validate_integ(mw_system* s, const mw_integrator* in) {
       const double dtL = in->dt / bx.L[k];
       if (bx.dtL[k] != dtL) {
         bx.dtL[k] = dtL;
+        bx.dtL64[k] = (float)std::ldexp(dtL, 64);
         boxes_changed = true;
       }
     }
     // a velocity component of magnitude >= 2^floor(log2(lost / dt)) (between
     // lost/(2 dt) and lost/dt) moves an atom at least a quarter of the
-    // shortest edge in one step: the run is reported as lost
-    const int ve = std::min(2047, std::max(1, 1023 + (int)std::floor(std::log2((double)bx.lost / in->dt))));
+    // shortest edge in one step: the run is reported as lost (FP32 exponent)
+    const int ve = std::min(255, std::max(1, 127 + (int)std::floor(std::log2((double)bx.lost / in->dt))));
     if (bx.vexp_lost != ve) {
       bx.vexp_lost = ve;
       boxes_changed = true;
@@ -630,7 +633,7 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
     bx.T0 = 0;
     bx.Q = 1;
     bx.invQ = 1;
-    bx.vexp_lost = 2047;
+    bx.vexp_lost = 255;
     bx.volume = bx.L[0] * bx.L[1] * bx.L[2];
     bx.inv_ndf_kb = bx.Ndf > 0 ? 1.0 / (bx.Ndf * kKB) : 0.0;
     bx.p_fac = kATM / (3.0 * bx.volume);
@@ -652,8 +655,11 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
   Dev& d = s->d;
   d.N = s->N;
   d.nbox = nbox;
-  double** dbl[] = {&d.x, &d.y, &d.z, &d.vx, &d.vy, &d.vz, &d.tx, &d.ty, &d.tz, &d.tvx, &d.tvy, &d.tvz};
-  for (double** p : dbl)
+  unsigned long long** pos[] = {&d.x, &d.y, &d.z, &d.tx, &d.ty, &d.tz};
+  for (unsigned long long** p : pos)
+    if ((st = dalloc(s, p, N)) != MW_OK) return bad(st);
+  float2** vel[] = {&d.vx, &d.vy, &d.vz, &d.tvx, &d.tvy, &d.tvz};
+  for (float2** p : vel)
     if ((st = dalloc(s, p, N)) != MW_OK) return bad(st);
   if ((st = dalloc(s, &d.q, N)) != MW_OK || (st = dalloc(s, &d.qb, N)) != MW_OK ||
       (st = dalloc(s, &d.tq, N)) != MW_OK || (st = dalloc(s, &d.f, N)) != MW_OK ||
@@ -1201,6 +1207,7 @@ extern "C" mw_status mw_energy_forces_noalloc(int n, const double box[3], const 
   BoxState bs;
   std::memset(&bs, 0, sizeof bs);
   bs.s_end = bs.s_kick = 1.0;
+  bs.s_kick1 = 2.0f;
   bs.rebuild = 1;
   Global g{};
   g.any_rebuild = 1;

@@ -45,6 +45,7 @@ constexpr int kMaxLegsOverflow = 64;
 struct Box {        // read-only in kernels
   double L[3];
   double dtL[3];    // dt / L: drift of the box fraction per unit velocity
+  float dtL64[3];   // dt / L * 2^64: drift in 2^-64 box-fraction units per unit velocity (FP32)
   float lost;       // half the shortest edge (A)
   double qs[3];     // 2^32 / L
   float Lq[3];      // L / 2^32
@@ -55,7 +56,7 @@ struct Box {        // read-only in kernels
   double invQ;      // 1 / Q
   double inv_ndf_kb;  // 1 / (N_df k_B): T = 2 KE inv_ndf_kb
   double p_fac;     // atm per kcal/mol of 2 KE + tr W: 1/(3 V) in atm
-  int vexp_lost;    // a velocity component whose FP64 exponent field is >= this is a runaway (see validate_integ)
+  int vexp_lost;    // a velocity component whose FP32 exponent field is >= this is a runaway (see validate_integ)
 };
 
 struct BoxState {   // mutated by kernels
@@ -63,6 +64,7 @@ struct BoxState {   // mutated by kernels
   double s_end;           // pending velocity scale: true v = stored v * s_end
   double s_kick;          // scale applied by the next kick1: s_end times the next start half
   float s_kick1;          // s_kick + 1 in FP32 (weight of the folded half-kick)
+  float sig;              // s_kick - 1 in FP32 (the scale as an increment: v += sig v)
   double ke_last;         // kinetic energy after the last end half (kcal/mol)
   double ke_acc[2];       // per step-parity accumulators of the raw kinetic energy
   double ew[2][8];        // per step-parity E2, E3, W[6]
@@ -112,8 +114,12 @@ struct FParams {     // FP32 constants of the force kernels
 
 struct Dev {
   int N, W, ncell, nbox;
-  double *x, *y, *z, *vx, *vy, *vz;
-  double *tx, *ty, *tz, *tvx, *tvy, *tvz;
+  // master state: positions as 64-bit box fractions (s 2^64, wrapping), velocities
+  // (A/fs) as unevaluated FP32 sums hi + lo (about 48 significant bits)
+  unsigned long long *x, *y, *z;
+  float2 *vx, *vy, *vz;
+  unsigned long long *tx, *ty, *tz;
+  float2 *tvx, *tvy, *tvz;
   uint4 *q, *qb, *tq;
   float4* f;
   int *id, *tid;
@@ -140,16 +146,42 @@ __device__ __forceinline__ uint32_t to_fixed(double x, double qs) {
   return (uint32_t)(unsigned long long)__double2ll_rn(x * qs);
 }
 
-// Box fraction s in [0, 1) -> round(s 2^32) mod 2^32, from the IEEE fields
-// with integer operations only (no FP64 instruction).
-__device__ __forceinline__ uint32_t frac_to_fixed(double s) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(s);
-  const int e = (int)(bits >> 52) - 1023;  // s = 1.m x 2^e, e <= -1
-  const int sh = 20 - e;                    // round(m x 2^(e + 32 - 52))
-  if (bits == 0ull || sh >= 54 || sh < 21) return 0u;  // tiny, or not in [0, 1) (NaN)
-  const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  return (uint32_t)((m + (1ull << (sh - 1))) >> sh);  // 2^32 (s rounding up to 1) wraps to 0
+// 32-bit fixed-point coordinate of a 64-bit box fraction: round(s / 2^32)
+// mod 2^32 (a fraction within half a unit of 1 wraps to 0).
+__device__ __forceinline__ uint32_t q_of(unsigned long long s) {
+  return (uint32_t)((s + 0x80000000ull) >> 32);
 }
+
+// Box fraction in [0, 1) (FP64) -> 64-bit fraction round(s 2^64) mod 2^64.
+__device__ __forceinline__ unsigned long long frac64_of(double s) {
+  const double t = s * 18446744073709551616.0;
+  return (t >= 18446744073709551616.0) ? 0ull : __double2ull_rn(t);
+}
+
+// Exact conversion of an FP32 value to a 64-bit integer with integer
+// operations only (no FP64 or 64-bit conversion instruction): |f| >= 2^23 is
+// an integer already; smaller values round half away from zero; zero and
+// subnormals give 0; magnitudes beyond 2^62 are clamped (a runaway atom,
+// reported separately).
+__device__ __forceinline__ long long f2ll_exact(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const int ex = (int)((u >> 23) & 0xffu);
+  const long long m = (long long)((u & 0x7fffffu) | 0x800000u);
+  const int e = ex - 150;  // |f| = m 2^e
+  long long r;
+  if (ex == 0) r = 0;
+  else if (e >= 0) r = m << min(e, 38);
+  else if (e > -25) r = (m + (1ll << (-e - 1))) >> (-e);
+  else r = 0;
+  return (u >> 31) ? -r : r;
+}
+
+// Velocity as hi + lo (FP32 pair) <-> FP64 (set/get state and rare paths only).
+__device__ __forceinline__ float2 split_df(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+__device__ __forceinline__ double join_df(float2 v) { return (double)v.x + (double)v.y; }
 
 __device__ __forceinline__ float fix_diff(uint32_t a, uint32_t b, float lq) {  // b - a, minimum image
   return __int2float_rn((int)(b - a)) * lq;
@@ -270,6 +302,7 @@ __device__ void start_half_box(const Dev& d, const Integ& I, int b) {
   st->eta[1] = eta;
   st->s_kick = st->s_end * s;
   st->s_kick1 = (float)(st->s_kick + 1.0);
+  st->sig = (float)(st->s_kick - 1.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -280,11 +313,14 @@ __device__ void start_half_box(const Dev& d, const Integ& I, int b) {
 // of this one use the same force, so they are folded: v = S v + (S + 1) a
 // when a half-kick is pending (S = thermostat scale of the step boundary,
 // a = dt/2 F/m), else v = S v + a; then s += (dt/L) v on the box fraction,
-// wrap into [0, 1), fixed-point copy, displacement check against the last
-// build.  Three lanes per atom, one per Cartesian component (10 atoms per
-// warp, lanes 30 and 31 idle): FP64 is one conversion and two FMAs per lane,
-// the fixed-point copy and the runaway check use integer operations only.
-// Also zeroes f for this step.
+// fixed-point copy, displacement check against the last build.  Three lanes
+// per atom, one per Cartesian component (10 atoms per warp, lanes 30 and 31
+// idle).  No FP64 instruction: v is the unevaluated sum hi + lo of two FP32
+// values, updated as hi + t with t = (S - 1) v + kick and the rounding error
+// of that sum carried into lo (Knuth's two-sum); the drift (dt/L) v 2^64 is
+// rounded once to FP32 and added exactly to the 64-bit box fraction, which
+// wraps at the faces by itself.  The runaway check is an integer test of the
+// FP32 exponent.  Also zeroes f for this step.
 constexpr int kKAtoms = 10;     // atoms per warp in the kick kernels
 constexpr int kKThreads = 512;  // threads per block of k_kick1 / k_kick2 (few blocks: few same-address atomics)
 
@@ -300,37 +336,38 @@ __device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, 
     // every load that does not depend on the box first, so that their
     // latencies overlap (the stores below may alias them)
     float* fp = reinterpret_cast<float*>(d.f + i) + c;
-    double* vp = (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz)) + i;
-    double* sp = (c == 0 ? d.x : (c == 1 ? d.y : d.z)) + i;
+    float2* vp = (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz)) + i;
+    unsigned long long* sp = (c == 0 ? d.x : (c == 1 ? d.y : d.z)) + i;
     b = (int)d.q[i].w;
     const float F = *fp;
-    const double v0 = *vp;
-    const double s0 = *sp;
+    const float2 v0 = *vp;
+    const unsigned long long s0 = *sp;
     const uint32_t qb = reinterpret_cast<const uint32_t*>(d.qb + i)[c];
     const Box& bx = d.box[b];
     const BoxState* st = d.bst + b;
-    const double S = st->s_kick;
+    const float sig = st->sig;
     const float kf = I.cf_f * (pend ? st->s_kick1 : 1.0f);
-    const double dtL = c == 0 ? bx.dtL[0] : (c == 1 ? bx.dtL[1] : bx.dtL[2]);
+    const float k64 = c == 0 ? bx.dtL64[0] : (c == 1 ? bx.dtL64[1] : bx.dtL64[2]);
     const float Lq = c == 0 ? bx.Lq[0] : (c == 1 ? bx.Lq[1] : bx.Lq[2]);
     const int vexp = bx.vexp_lost;
-    const double v = fma(v0, S, (double)(kf * F));
-    double sf = fma(dtL, v, s0);
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(sf);
-    if ((bits >> 63) || (bits >> 52) >= 1023ull) {  // left [0, 1): crossed a face (rare)
-      sf -= floor(sf);
-      if (sf >= 1.0) sf -= 1.0;
-      if (sf < 0.0) sf = 0.0;
-    }
+    // v + t as hi + lo: two-sum of hi and t, its error added to lo, renormalised
+    const float t = fmaf(sig, v0.x, fmaf(sig, v0.y, kf * F));
+    const float sh = v0.x + t;
+    const float bb = sh - v0.x;
+    const float er = (v0.x - (sh - bb)) + (t - bb);
+    const float lo1 = v0.y + er;
+    const float hi = sh + lo1;
+    const float lo = lo1 - (hi - sh);
+    const unsigned long long sn = s0 + (unsigned long long)f2ll_exact(fmaf(hi, k64, lo * k64));
     *fp = 0.f;
-    *vp = v;
-    *sp = sf;
-    const uint32_t qn = frac_to_fixed(sf);
+    *vp = make_float2(hi, lo);
+    *sp = sn;
+    const uint32_t qn = q_of(sn);
     reinterpret_cast<uint32_t*>(d.q + i)[c] = qn;
     const float dc = fix_diff(qb, qn, Lq);
     dd = dc * dc;
     // |v| at or above the box's runaway threshold (or NaN/inf): exponent field test
-    lost = (int)((__double_as_longlong(v) >> 52) & 0x7ff) >= vexp;
+    lost = (int)((__float_as_uint(hi) >> 23) & 0xffu) >= vexp;
     if (i == bx.off && c == 0) {  // this step's accumulators start from zero
       BoxState* sw = d.bst + b;
       sw->ke_acc[par] = 0.0;
@@ -363,8 +400,8 @@ __device__ __forceinline__ float kick2_lane(const Dev& d, const Integ& I, int w,
   if (lane >= 3 * kKAtoms || i >= d.N) return 0.f;
   b = (int)d.q[i].w;
   const float F = reinterpret_cast<const float*>(d.f + i)[c];
-  const double* vp = (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz)) + i;
-  const float u = fmaf(I.cf_f, F, (float)*vp);
+  const float2 v = (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz))[i];
+  const float u = fmaf(I.cf_f, F, v.x) + v.y;
   const float ke = (float)I.ke_fac * u * u;
   if (!(ke < 1e30f)) {
     set_status(d.g, ST_NAN);
@@ -497,22 +534,32 @@ __device__ void neigh_cell_warp(const Dev& d, const uint4* qa, int c, float rl2)
 
 // ---------------------------------------------------------------------------
 // Fused two- + three-body force (k_force).  A block holds kFAtoms centre atoms.
-//   leg phase: kG lanes per centre walk its neighbour row; every pair with
-//     r < a sig is a leg: the pair term is taken by the owner (half energy,
-//     full force on the centre, half virial) and the leg is compacted (ballot
-//     + popc within the lane group) into the centre's row of a padded
-//     shared-memory leg table;
-//   triplet phase: the (centre, leg j) items of a warp are spread evenly over
-//     its 32 lanes; an item runs over every other leg k of the same centre
-//     and accumulates the three-body force on j in registers (each unordered
-//     triplet is visited from both of its legs; its energy is counted once);
-//     the force on j goes out with one red.global.add.v4.f32, its reaction on
-//     the centre through a shared-memory sum;
+//   leg phase A: kG lanes per centre walk its neighbour row; the pairs with
+//     r^2 < (a sig)^2 are compacted (ballot + popc within the lane group) into
+//     the centre's row of a padded shared-memory leg table;
+//   leg phase B: the leg terms, spread over the group's lanes: the pair term
+//     is taken by the owner (half energy, full force on the centre, half
+//     virial), and the leg's three-body factors go into the table and into
+//     the centre's moments (below);
+//   leg phase C: each leg's three-body force from the moments, one
+//     red.global.add.v4.f32 to the partner, the reaction kept for the centre;
 //   per-box FP64 reduction of E2, E3 and the virial.
 // Leg data: u (unit vector i->j), ee = sqrt(lam eps) exp(gam sig/(r - a sig)),
-// tr = 2/r, nde = gam sig/(r - a sig)^2, r, j.  With c = u_j.u_k and
-// D = c - cos th0, phi3 = ee_j ee_k D^2 and the force on j is
-//   F_j = -g tr_j u_k + g (c tr_j + D nde_j) u_j,   g = ee_j ee_k D.
+// tr = 2/r, nde = gam sig/(r - a sig)^2, r, j.  With c_jk = u_j.u_k and
+// D_jk = c_jk - cos th0 a centre's three-body energy (Sec. II.A) is
+//   E3_i = sum_{j<k} ee_j ee_k D_jk^2 = 1/2 sum_j ee_j C_j,
+// and the force on leg partner j is
+//   F_j = ee_j [ nde_j C_j u_j - tr_j (A_j - B_j u_j) ],
+//   A_j = sum_{k!=j} ee_k D_jk u_k,  B_j = sum_{k!=j} ee_k D_jk c_jk,
+//   C_j = sum_{k!=j} ee_k D_jk^2.
+// Because D_jk is affine in u_j.u_k, the three sums follow exactly from the
+// centre's moments S0 = sum_k ee_k, s = sum_k ee_k u_k and the symmetric
+// M = sum_k ee_k u_k u_k^T (all legs, k = j included):
+//   A_j = M u_j - c0 s - self u_j,  B_j = u_j.M u_j - c0 u_j.s - self c_jj,
+//   C_j = u_j.M u_j - 2 c0 u_j.s + c0^2 S0 - self D_jj,
+// with c0 = cos th0, c_jj = u_j.u_j, D_jj = c_jj - c0 and self = ee_j D_jj
+// (the k = j term taken back out).  This is the same sum reordered: O(n) per
+// centre instead of O(n^2) leg pairs.
 constexpr int kG = 4;                    // lanes per centre in the leg phase
 constexpr int kFThreads = 128;
 constexpr int kFAtoms = kFThreads / kG;  // centres per block
@@ -523,8 +570,6 @@ constexpr int kPre = 8;                  // neighbour slots per lane fetched ahe
 struct LegTable {
   float4 ue[kFAtoms * kLPad];   // ux, uy, uz, ee
   float4 aux[kFAtoms * kLPad];  // tr, nde, r, j (int bits)
-  float fi[kFAtoms][4];         // three-body reaction on the centre
-  int nl[kFAtoms];
 };
 
 // Whole owner contribution (pair terms and three-body terms) of a centre with
@@ -638,7 +683,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
   const int i = blk * kFAtoms + a;
   const bool valid = i < d.N;
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // E2, E3, W xx yy zz xy xz yz
-  float fx = 0.f, fy = 0.f, fz = 0.f;
+  float fx = 0.f, fy = 0.f, fz = 0.f;  // force on the centre (pair part and three-body reaction)
   uint4 qi = make_uint4(0u, 0u, 0u, 0u);
   int cnt = 0, b = -1;
   float L0 = 0.f, L1 = 0.f, L2 = 0.f;
@@ -651,10 +696,11 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     L1 = bx.Lq[1];
     L2 = bx.Lq[2];
   }
-  T.fi[a][g] = 0.f;
-  // ---- leg phase: row entries and candidate positions are fetched for up to
-  // kPre slots per lane before any is used (one memory latency instead of a
-  // dependent chain per slot); rows longer than kG * kPre continue unprefetched.
+  // ---- leg phase A: row entries and candidate positions are fetched for up
+  // to kPre slots per lane before any is used (one memory latency instead of
+  // a dependent chain per slot); rows longer than kG * kPre continue
+  // unprefetched.  Distance test only; hits are compacted (ballot + popc in
+  // the lane group) into the centre's row as (d, r^2 | j).
   const int iters = __reduce_max_sync(kFull, (cnt + kG - 1) / kG);
   const unsigned gsh = lane & ~(kG - 1);
   const int* row = d.nbr + (size_t)(valid ? i : 0) * d.W;
@@ -674,8 +720,6 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     qy[t] = qj.y;
     qz[t] = qj.z;
   }
-  // pass A: distance test only; hits are compacted (ballot + popc in the lane
-  // group) into the centre's row as (d, r^2 | j)
   auto test_slot = [&](int j, uint32_t jx, uint32_t jy, uint32_t jz, bool have) {
     bool hit = false;
     float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
@@ -706,9 +750,12 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     test_slot(j, qj.x, qj.y, qj.z, have);
   }
   __syncwarp();
-  // pass B: leg terms for the compacted legs only, spread over the group's
-  // lanes: pair term (owner computes) and the leg table entry
+  // ---- leg phase B: leg terms for the compacted legs only, spread over the
+  // group's lanes: pair term (owner computes), the leg's table entry and its
+  // share of the centre's moments S0, s, M.
   const int nstage = (nl <= kLMax) ? nl : 0;  // larger centres: force_overflow_item does everything
+  float m0 = 0.f, msx = 0.f, msy = 0.f, msz = 0.f;                            // S0, s
+  float mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;     // M
   for (int l = g; l < nstage; l += kG) {
     float4* ue_p = T.ue + a * kLPad + l;
     float4* ax_p = T.aux + a * kLPad + l;
@@ -726,7 +773,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     const float ux = rec.x * invr, uy = rec.y * invr, uz = rec.z * invr;
     const float tinv = __fdividef(1.0f, r - P.rc);  // 1/(r - a sig) < 0
     const float e2 = exp2f(P.sig_l2e * tinv);
-    const float e3 = exp2f(P.gsig_l2e * tinv);
+    const float ee = P.sle * exp2f(P.gsig_l2e * tinv);
     const float sr = P.sig * invr;
     float srp, srq;
     if (P.p == 4 && P.q == 0) {  // the SW / mW exponents
@@ -752,105 +799,77 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     acc[5] = fmaf(wv * ux, uy, acc[5]);
     acc[6] = fmaf(wv * ux, uz, acc[6]);
     acc[7] = fmaf(wv * uy, uz, acc[7]);
-    *ue_p = make_float4(ux, uy, uz, P.sle * e3);
+    *ue_p = make_float4(ux, uy, uz, ee);
     ax_p->x = 2.0f * invr;
     ax_p->y = P.gsig * tinv * tinv;
     ax_p->z = r;
+    const float ex = ee * ux, ey = ee * uy, ez = ee * uz;
+    m0 += ee;
+    msx += ex;
+    msy += ey;
+    msz += ez;
+    mxx = fmaf(ex, ux, mxx);
+    myy = fmaf(ey, uy, myy);
+    mzz = fmaf(ez, uz, mzz);
+    mxy = fmaf(ex, uy, mxy);
+    mxz = fmaf(ex, uz, mxz);
+    myz = fmaf(ey, uz, myz);
   }
-  if (g == 0) T.nl[a] = valid ? nl : 0;
-  __syncwarp();
-  // ---- triplet phase: items (centre of this warp, leg j), spread over the lanes
-  const int a0 = (threadIdx.x >> 5) * kWAtoms;
-  int pre[kWAtoms + 1];
-  pre[0] = 0;
+  // the centre's moments: sum over the lane group
 #pragma unroll
-  for (int k = 0; k < kWAtoms; ++k) {
-    int n = T.nl[a0 + k];
-    if (n > kLMax) n = 0;  // centres beyond the table: force_overflow_item
-    pre[k + 1] = pre[k] + n;
+  for (int o = 1; o < kG; o <<= 1) {
+    m0 += __shfl_xor_sync(kFull, m0, o);
+    msx += __shfl_xor_sync(kFull, msx, o);
+    msy += __shfl_xor_sync(kFull, msy, o);
+    msz += __shfl_xor_sync(kFull, msz, o);
+    mxx += __shfl_xor_sync(kFull, mxx, o);
+    myy += __shfl_xor_sync(kFull, myy, o);
+    mzz += __shfl_xor_sync(kFull, mzz, o);
+    mxy += __shfl_xor_sync(kFull, mxy, o);
+    mxz += __shfl_xor_sync(kFull, mxz, o);
+    myz += __shfl_xor_sync(kFull, myz, o);
   }
-  const int b0 = __shfl_sync(kFull, b, 0);
-  const bool wuni = __all_sync(kFull, b == b0 || b < 0);
+  __syncwarp();  // the group's table entries are complete
+  // ---- leg phase C: three-body force on each leg partner from the moments
   const float c0 = P.c0;
-  for (int base = 0; base < pre[kWAtoms]; base += 32) {  // warp-uniform rounds
-    const int it = base + lane;
-    int ka = -1, first = 0, n = 0;
-#pragma unroll
-    for (int k = 0; k < kWAtoms; ++k)  // the centre whose item range holds it
-      if (it >= pre[k] && it < pre[k + 1]) {
-        ka = k;
-        first = pre[k];
-        n = pre[k + 1] - pre[k];
-      }
-    float gx = 0.f, gy = 0.f, gz = 0.f;
-    if (ka >= 0) {
-      const int aa = a0 + ka;
-      const int jj = it - first;
-      const float4* rowu = T.ue + aa * kLPad;
-      const float4 uj = rowu[jj];
-      const float4 xj = T.aux[aa * kLPad + jj];
-      float e3 = 0.f;
-      // partner legs k != jj; the energy of each unordered triplet is taken
-      // by the item of its lower leg (k > jj)
-      auto partner = [&](int k, bool energy) {
-        const float4 uk = rowu[k];
-        const float c = fmaf(uj.x, uk.x, fmaf(uj.y, uk.y, uj.z * uk.z));
-        const float D = c - c0;
-        const float gg = uj.w * uk.w * D;
-        if (energy) e3 = fmaf(gg, D, e3);
-        const float aj = gg * xj.x;
-        const float bj = gg * fmaf(c, xj.x, D * xj.y);
-        gx = fmaf(-aj, uk.x, fmaf(bj, uj.x, gx));
-        gy = fmaf(-aj, uk.y, fmaf(bj, uj.y, gy));
-        gz = fmaf(-aj, uk.z, fmaf(bj, uj.z, gz));
-      };
-#pragma unroll 2
-      for (int k = 0; k < jj; ++k) partner(k, false);
-#pragma unroll 2
-      for (int k = jj + 1; k < n; ++k) partner(k, true);
-      red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
-      const float rx = xj.z * uj.x, ry = xj.z * uj.y, rz = xj.z * uj.z;
-      if (wuni) {
-        acc[1] += e3;
-        acc[2] = fmaf(rx, gx, acc[2]);
-        acc[3] = fmaf(ry, gy, acc[3]);
-        acc[4] = fmaf(rz, gz, acc[4]);
-        acc[5] = fmaf(rx, gy, acc[5]);
-        acc[6] = fmaf(rx, gz, acc[6]);
-        acc[7] = fmaf(ry, gz, acc[7]);
-      } else {  // warp straddles two boxes (rare): straight to the item's box
-        double* p = &d.bst[d.q[blk * kFAtoms + aa].w].ew[par][0];
-        atomicAdd(p + 1, (double)e3);
-        atomicAdd(p + 2, (double)(rx * gx));
-        atomicAdd(p + 3, (double)(ry * gy));
-        atomicAdd(p + 4, (double)(rz * gz));
-        atomicAdd(p + 5, (double)(rx * gy));
-        atomicAdd(p + 6, (double)(rx * gz));
-        atomicAdd(p + 7, (double)(ry * gz));
-      }
-    }
-    // reaction on the centres: segmented sum over the lanes holding one centre's items
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int ko = __shfl_up_sync(kFull, ka, o);
-      const float tx = __shfl_up_sync(kFull, gx, o), ty = __shfl_up_sync(kFull, gy, o),
-                  tz = __shfl_up_sync(kFull, gz, o);
-      if (lane >= o && ko == ka) {
-        gx += tx;
-        gy += ty;
-        gz += tz;
-      }
-    }
-    const int kn = __shfl_down_sync(kFull, ka, 1);
-    if (ka >= 0 && (lane == 31 || kn != ka)) {
-      T.fi[a0 + ka][0] -= gx;  // one tail per centre and round
-      T.fi[a0 + ka][1] -= gy;
-      T.fi[a0 + ka][2] -= gz;
-    }
-    __syncwarp();  // orders this round's table updates before the next round's
+  const float s0c = c0 * c0 * m0;
+  for (int l = g; l < nstage; l += kG) {
+    const float4 uj = T.ue[a * kLPad + l];
+    const float4 xj = T.aux[a * kLPad + l];
+    const float ee = uj.w;
+    if (ee == 0.f) continue;  // leg dropped in phase B
+    const float mx = fmaf(mxx, uj.x, fmaf(mxy, uj.y, mxz * uj.z));  // M u_j
+    const float my = fmaf(mxy, uj.x, fmaf(myy, uj.y, myz * uj.z));
+    const float mz = fmaf(mxz, uj.x, fmaf(myz, uj.y, mzz * uj.z));
+    const float qm = fmaf(uj.x, mx, fmaf(uj.y, my, uj.z * mz));     // u_j.M u_j
+    const float ps = fmaf(uj.x, msx, fmaf(uj.y, msy, uj.z * msz));  // u_j.s
+    const float cjj = fmaf(uj.x, uj.x, fmaf(uj.y, uj.y, uj.z * uj.z));
+    const float djj = cjj - c0;
+    const float self = ee * djj;
+    const float Bj = fmaf(-c0, ps, qm) - self * cjj;
+    const float Cj = fmaf(-2.0f * c0, ps, qm + s0c) - self * djj;
+    const float Ax = fmaf(-c0, msx, mx) - self * uj.x;
+    const float Ay = fmaf(-c0, msy, my) - self * uj.y;
+    const float Az = fmaf(-c0, msz, mz) - self * uj.z;
+    const float et = ee * xj.x;                          // ee_j tr_j
+    const float cu = ee * fmaf(xj.y, Cj, xj.x * Bj);     // ee_j (nde_j C_j + tr_j B_j)
+    const float gx = fmaf(cu, uj.x, -et * Ax);
+    const float gy = fmaf(cu, uj.y, -et * Ay);
+    const float gz = fmaf(cu, uj.z, -et * Az);
+    red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
+    fx -= gx;
+    fy -= gy;
+    fz -= gz;
+    acc[1] = fmaf(0.5f * ee, Cj, acc[1]);
+    const float rx = xj.z * uj.x, ry = xj.z * uj.y, rz = xj.z * uj.z;
+    acc[2] = fmaf(rx, gx, acc[2]);
+    acc[3] = fmaf(ry, gy, acc[3]);
+    acc[4] = fmaf(rz, gz, acc[4]);
+    acc[5] = fmaf(rx, gy, acc[5]);
+    acc[6] = fmaf(rx, gz, acc[6]);
+    acc[7] = fmaf(ry, gz, acc[7]);
   }
-  __syncwarp();
-  // ---- force on the centre: pair part (lane group) + three-body reaction
+  // ---- force on the centre: pair part + three-body reaction, over the group
 #pragma unroll
   for (int o = 1; o < kG; o <<= 1) {
     fx += __shfl_xor_sync(kFull, fx, o);
@@ -858,10 +877,10 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     fz += __shfl_xor_sync(kFull, fz, o);
   }
   if (valid && g == 0) {
-    red_add_v4(d.f + i, fx + T.fi[a][0], fy + T.fi[a][1], fz + T.fi[a][2]);
+    red_add_v4(d.f + i, fx, fy, fz);
     if (nl > kLMax) force_overflow_item<kCount>(d, P, i, par);  // rare: more legs than the table holds
   }
-  if (kCount) {  // legs and register-path triplets, one atomic per warp
+  if (kCount) {  // legs and table-path triplets, one atomic per warp
     unsigned long long legs = (valid && g == 0) ? (unsigned long long)nl : 0ull;
     unsigned long long tri = (valid && g == 0 && nl <= kLMax) ? (unsigned long long)(nl * (nl - 1) / 2) : 0ull;
     for (int o = 16; o > 0; o >>= 1) {
@@ -873,8 +892,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
       atomicAdd((unsigned long long*)&d.g->ntrip, tri);
     }
   }
-  const int ab = wuni ? b0 : b;
-  box_accumulate<8>(acc, ab, [&](int bb) { return &d.bst[bb].ew[par][0]; });
+  box_accumulate<8>(acc, b, [&](int bb) { return &d.bst[bb].ew[par][0]; });
 }
 
 template <bool kCount>
@@ -1083,16 +1101,16 @@ __global__ void k_load_positions(Dev d, const double* __restrict__ xin, const in
   const int u = d.id[i];
   const int b = boxid[u];
   const Box& bx = d.box[b];
-  double p[3];
+  unsigned long long p[3];
   for (int k = 0; k < 3; ++k) {
     double v = xin[3 * (size_t)u + k] / bx.L[k];  // box fraction
     v -= floor(v);
     if (v >= 1.0) v -= 1.0;
     if (v < 0.0) v = 0.0;
-    p[k] = v;
+    p[k] = frac64_of(v);
   }
   d.x[i] = p[0]; d.y[i] = p[1]; d.z[i] = p[2];
-  d.q[i] = make_uint4(frac_to_fixed(p[0]), frac_to_fixed(p[1]), frac_to_fixed(p[2]), (unsigned)b);
+  d.q[i] = make_uint4(q_of(p[0]), q_of(p[1]), q_of(p[2]), (unsigned)b);
 }
 
 __global__ void k_load_velocities(Dev d, const double* __restrict__ vin) {
@@ -1100,11 +1118,11 @@ __global__ void k_load_velocities(Dev d, const double* __restrict__ vin) {
   if (i >= d.N) return;
   const int u = d.id[i];
   if (vin) {
-    d.vx[i] = vin[3 * (size_t)u];
-    d.vy[i] = vin[3 * (size_t)u + 1];
-    d.vz[i] = vin[3 * (size_t)u + 2];
+    d.vx[i] = split_df(vin[3 * (size_t)u]);
+    d.vy[i] = split_df(vin[3 * (size_t)u + 1]);
+    d.vz[i] = split_df(vin[3 * (size_t)u + 2]);
   } else {
-    d.vx[i] = d.vy[i] = d.vz[i] = 0.0;
+    d.vx[i] = d.vy[i] = d.vz[i] = make_float2(0.f, 0.f);
   }
 }
 
@@ -1116,7 +1134,7 @@ __global__ void k_ke_init(Dev d) {
   int b = -1;
   if (i < d.N) {
     b = (int)d.q[i].w;
-    const float vx = (float)d.vx[i], vy = (float)d.vy[i], vz = (float)d.vz[i];
+    const float vx = d.vx[i].x + d.vx[i].y, vy = d.vy[i].x + d.vy[i].y, vz = d.vz[i].x + d.vz[i].y;
     ke[0] = (float)I.ke_fac * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
   }
   box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_last; });
@@ -1130,9 +1148,9 @@ __global__ void k_flush_pending(Dev d) {
   const double cf = d.integ->cf;
   if (i < d.N) {
     const float4 F = d.f[i];
-    d.vx[i] += cf * F.x;
-    d.vy[i] += cf * F.y;
-    d.vz[i] += cf * F.z;
+    d.vx[i] = split_df(join_df(d.vx[i]) + cf * F.x);
+    d.vy[i] = split_df(join_df(d.vy[i]) + cf * F.y);
+    d.vz[i] = split_df(join_df(d.vz[i]) + cf * F.z);
   }
 }
 
@@ -1194,17 +1212,18 @@ __global__ void k_gather_state(Dev d, double* __restrict__ xo, double* __restric
   const int u = d.id[i];
   const Box& bx = d.box[d.q[i].w];
   if (xo) {
-    xo[3 * (size_t)u] = d.x[i] * bx.L[0];
-    xo[3 * (size_t)u + 1] = d.y[i] * bx.L[1];
-    xo[3 * (size_t)u + 2] = d.z[i] * bx.L[2];
+    constexpr double k2m64 = 5.421010862427522170037264e-20;  // 2^-64
+    xo[3 * (size_t)u] = __ull2double_rn(d.x[i]) * k2m64 * bx.L[0];
+    xo[3 * (size_t)u + 1] = __ull2double_rn(d.y[i]) * k2m64 * bx.L[1];
+    xo[3 * (size_t)u + 2] = __ull2double_rn(d.z[i]) * k2m64 * bx.L[2];
   }
   if (vo) {  // pending half-kick and end-of-step thermostat scale applied
     const double s = d.bst[d.q[i].w].s_end;
     const double cf = d.g->pend ? d.integ->cf : 0.0;
     const float4 F = d.f[i];
-    vo[3 * (size_t)u] = (d.vx[i] + cf * F.x) * s;
-    vo[3 * (size_t)u + 1] = (d.vy[i] + cf * F.y) * s;
-    vo[3 * (size_t)u + 2] = (d.vz[i] + cf * F.z) * s;
+    vo[3 * (size_t)u] = (join_df(d.vx[i]) + cf * F.x) * s;
+    vo[3 * (size_t)u + 1] = (join_df(d.vy[i]) + cf * F.y) * s;
+    vo[3 * (size_t)u + 2] = (join_df(d.vz[i]) + cf * F.z) * s;
   }
 }
 

@@ -250,7 +250,7 @@ __device__ void adjoint_block(const Dev& d, const AdjDev& A, const FParams& P, A
 }
 
 __global__ void __launch_bounds__(kFThreads) k_adjoint(Dev d, AdjDev A, FParams P) {
-  if (d.g->status) return;
+  if (block_stop(d)) return;
   extern __shared__ __align__(16) unsigned char adj_smem[];
   AdjTable& T = *reinterpret_cast<AdjTable*>(adj_smem);
   adjoint_block(d, A, P, T, blockIdx.x);

@@ -69,6 +69,7 @@ struct mw_system {
   bool state_set = false;
   bool forces_valid = false;
   bool need_prime = true;  // thermostat start half must be recomputed before the next step
+  bool record_pending = false;  // steps ran since the last thermo record was written
   long long host_step = 0;
   int engine = MW_ENGINE_AUTO, engine_used = MW_ENGINE_GRAPH;
   int tuned_engine = -1;
@@ -93,6 +94,7 @@ bool persistent_available(mw_system* s);
 mw_status run_persistent_engine(mw_system* s, int nsteps);
 mw_status enqueue_persistent(mw_system* s, int nsteps);
 mw_status adjoint_alloc(mw_system* s);
+mw_status prime_thermostat(mw_system* s);
 
 template <class T>
 mw_status dalloc(mw_system* s, T** p, size_t count) {
@@ -384,6 +386,7 @@ mw_status ensure_forces(mw_system* s) {
     if (g.status) return status_error(g);
     s->forces_valid = true;
     s->list_built = true;
+    s->record_pending = false;  // the snapshot is the newest record
     return MW_OK;
   }
   return fail(MW_ENLIST_OVERFLOW, "neighbour list kept overflowing");
@@ -424,9 +427,9 @@ mw_status finish_interrupted_step(mw_system* s) {
   return MW_OK;
 }
 
-// The start-of-step thermostat half is normally computed by the previous
-// step's end; it is recomputed here only after a state, parameter or
-// integrator change.
+// The start-of-step thermostat half is normally computed at the end of the
+// previous step; it is recomputed here only after a state or integrator
+// change.
 mw_status prime_thermostat(mw_system* s) {
   if (!s->need_prime) return MW_OK;
   k_prime_thermostat<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d);
@@ -438,6 +441,7 @@ mw_status prime_thermostat(mw_system* s) {
 mw_status run_graph_engine(mw_system* s, int nsteps) {
   mw_status st;
   if ((st = prime_thermostat(s)) != MW_OK) return st;
+  s->record_pending = true;
   const int K = 16;
   if (s->graph_dirty || !s->graph1) {
     if ((st = capture_graphs(s, K)) != MW_OK) return st;
@@ -497,10 +501,7 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   std::vector<BoxState> bs(s->nbox);
   for (auto& b : bs) {
     std::memset(&b, 0, sizeof b);
-    b.s_end = 1.0;
-    b.s_kick = 1.0;
-    b.s_kick1 = 2.0f;
-    b.sig = 0.0f;
+    b.s_endc = 1.0;
     b.rebuild = 1;
   }
   MW_CUDA(cudaMemcpyAsync(s->d.bst, bs.data(), sizeof(BoxState) * s->nbox, cudaMemcpyHostToDevice, s->stream));
@@ -517,7 +518,7 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   MW_CUDA(cudaStreamSynchronize(s->stream));
   s->state_set = true;
   s->forces_valid = false;
-  s->need_prime = true;
+  s->need_prime = true;  // thermostat at rest: xi = eta = 0, KE of the new velocities
   s->host_step = 0;
   return MW_OK;
 }
@@ -533,10 +534,14 @@ mw_status validate_integ(mw_system* s, const mw_integrator* in) {
     if (in->thermostat != MW_NVE && !(T0 > 0)) return fail(MW_EINVAL, "T0 must be > 0");
     Box& bx = s->boxes[b];
     const double Q = bx.Ndf * kKB * T0 * in->tau * in->tau;
-    if (bx.T0 != T0 || bx.Q != Q) {
+    const double q4 = 0.25 * in->dt / Q;
+    if (bx.T0 != T0 || bx.Q != Q || bx.q4 != q4) {
       bx.T0 = T0;
       bx.Q = Q;
       bx.invQ = 1.0 / Q;
+      bx.ndfkT0 = bx.Ndf * kKB * T0;
+      bx.q4 = q4;
+      bx.q4f = (float)q4;
       boxes_changed = true;
     }
     for (int k = 0; k < 3; ++k) {
@@ -565,15 +570,18 @@ mw_status validate_integ(mw_system* s, const mw_integrator* in) {
   I.kind = in->thermostat;
   I.half_skin2 = (float)(0.25 * s->skin * s->skin);
   mw_status st;
-  if (boxes_changed) {
-    if ((st = upload_boxes(s)) != MW_OK) return st;
-    s->need_prime = true;
+  const bool integ_changed = std::memcmp(&I, &s->integ, sizeof I) != 0;
+  if ((boxes_changed || integ_changed) && s->state_set) {
+    // the pending half-kick belongs to the old integrator (the last step's
+    // end half was taken with it too); the start half is redone with the new
+    if ((st = flush_pending(s)) != MW_OK) return st;
   }
-  if (std::memcmp(&I, &s->integ, sizeof I) != 0) {
+  if (boxes_changed && (st = upload_boxes(s)) != MW_OK) return st;
+  if (integ_changed) {
     s->integ = I;
     if ((st = upload_integ(s)) != MW_OK) return st;
-    s->need_prime = true;
   }
+  if (boxes_changed || integ_changed) s->need_prime = true;
   return MW_OK;
 }
 
@@ -956,6 +964,7 @@ mw_status mw_step_async(mw_system* s, const mw_integrator* integ, int nsteps) {
   if (eng == MW_ENGINE_PERSISTENT && !persistent_available(s)) eng = MW_ENGINE_GRAPH;
   s->engine_used = eng;
   if ((st = prime_thermostat(s)) != MW_OK) return st;
+  s->record_pending = true;
   if (eng == MW_ENGINE_PERSISTENT) return enqueue_persistent(s, nsteps);
   if (s->graph_dirty || !s->graph1) {
     if ((st = capture_graphs(s, 16)) != MW_OK) return st;
@@ -979,6 +988,11 @@ mw_status mw_get_thermo(mw_system* s, mw_thermo* out) {
   if (!s->state_set) return fail(MW_ESTATE, "no state set");
   mw_status st;
   if ((st = ensure_forces(s)) != MW_OK) return st;
+  if (s->record_pending) {  // the last step's record, written on demand
+    k_record<<<1, 256, 0, s->stream>>>(s->d);
+    MW_CUDA(cudaGetLastError());
+    s->record_pending = false;
+  }
   std::vector<double> t((size_t)s->nbox * TR_N);
   MW_CUDA(cudaMemcpyAsync(t.data(), s->d.thermo, sizeof(double) * t.size(), cudaMemcpyDeviceToHost, s->stream));
   MW_CUDA(cudaStreamSynchronize(s->stream));
@@ -1206,8 +1220,7 @@ extern "C" mw_status mw_energy_forces_noalloc(int n, const double box[3], const 
   make_fparams(&tmp);
   BoxState bs;
   std::memset(&bs, 0, sizeof bs);
-  bs.s_end = bs.s_kick = 1.0;
-  bs.s_kick1 = 2.0f;
+  bs.s_endc = 1.0;
   bs.rebuild = 1;
   Global g{};
   g.any_rebuild = 1;

@@ -54,19 +54,22 @@ struct Box {        // read-only in kernels
   int cell_off;     // first global cell
   double T0, Ndf, Q, volume;
   double invQ;      // 1 / Q
+  double ndfkT0;    // N_df k_B T0
+  double q4;        // dt / (4 Q): quarter-step factor of xi
+  float q4f;        // q4 in FP32
   double inv_ndf_kb;  // 1 / (N_df k_B): T = 2 KE inv_ndf_kb
   double p_fac;     // atm per kcal/mol of 2 KE + tr W: 1/(3 V) in atm
   int vexp_lost;    // a velocity component whose FP32 exponent field is >= this is a runaway (see validate_integ)
 };
 
 struct BoxState {   // mutated by kernels
-  double xi[2], eta[2];   // [0] after the end-of-step half, [1] after the start-of-step half
-  double s_end;           // pending velocity scale: true v = stored v * s_end
-  double s_kick;          // scale applied by the next kick1: s_end times the next start half
-  float s_kick1;          // s_kick + 1 in FP32 (weight of the folded half-kick)
-  float sig;              // s_kick - 1 in FP32 (the scale as an increment: v += sig v)
-  double ke_last;         // kinetic energy after the last end half (kcal/mol)
-  double ke_acc[2];       // per step-parity accumulators of the raw kinetic energy
+  float4 th;              // (xi hi, xi lo, eta hi, eta lo) after the start half of the next step
+  float4 th_e;            // the same after the last end half
+  double ke_last;         // KE after the last end half, or of the state just set (kcal/mol)
+  double s_endc;          // last end scale, still pending on the stored velocities
+  float sig;              // S - 1 for the next kick1: S = s_endc times the start-half scale
+  int pad0_;
+  double ke_acc[2];       // per step-parity raw kinetic energy of v + a (the second half-kick)
   double ew[2][8];        // per step-parity E2, E3, W[6]
   int rebuild;            // displacement flag of this box
   int pad_;
@@ -266,43 +269,146 @@ __device__ void box_accumulate(float (&v)[NV], int b, Dst dst) {
     atomicAdd(dst(sbox[1]) + (threadIdx.x - 16), (double)sacc[1][threadIdx.x - 16]);
 }
 
-// exp(x) for the thermostat scale: |x| = |xi dt/2| is ~1e-4 in practice, where
-// the Taylor series to x^6 is exact to ~1e-19 relative; larger |x| uses exp().
-__device__ __forceinline__ double exp_small(double x) {
-  if (fabs(x) > 1e-2) return exp(x);
-  return 1.0 + x * (1.0 + x * (0.5 + x * (1.0 / 6.0 + x * (1.0 / 24.0 + x * (1.0 / 120.0 + x * (1.0 / 720.0))))));
+// ---------------------------------------------------------------------------
+// Thermostat (Sec. II.B: Nose-Hoover, tau = 1 ps; Berendsen as the option).
+// GB300 issues an FP64 instruction at a small fraction of the FP32 rate, even
+// for one active lane, so the per-step thermostat arithmetic is FP32: xi and
+// eta are unevaluated FP32 pairs hi + lo (their increments are tiny against
+// their values), the kinetic energy enters through d = 2 KE - N_df k_B T0,
+// formed with one FP64 FMA from the FP64 sum, and a velocity scale s is
+// carried as sig = s - 1 (expm1f): the kick applies v += sig v, and the
+// relative FP32 error of sig (~1e-4 in size) is ~1e-12 of s.
+
+// a += b for an unevaluated pair a = (hi, lo) and an FP32 b (two-sum).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float b) {
+  const float s = hi + b;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (b - bb);
+  const float l = lo + e;
+  hi = s + l;
+  lo = l - (hi - s);
 }
+
+struct ThermoState {  // one box at a step boundary
+  float xh, xl, eh, el;  // xi, eta as hi + lo
+  float d;               // 2 KE - N_df k_B T0 (FP32)
+  float ke;              // KE in FP32 (for the scale's effect on d)
+};
 
 // One Nose-Hoover half step (length dt/2) of a single thermostat: quarter step
 // on xi, velocity scale exp(-xi dt/2), half step on eta, quarter step on xi.
-__device__ __forceinline__ double nh_half(double& ke, double& xi, double& eta, double dt, double Ndf, double kT0,
-                                          double invQ) {
-  xi += 0.25 * dt * (2.0 * ke - Ndf * kT0) * invQ;
-  const double s = exp_small(-xi * 0.5 * dt);
-  ke *= s * s;
-  eta += xi * 0.5 * dt;
-  xi += 0.25 * dt * (2.0 * ke - Ndf * kT0) * invQ;
-  return s;
+// Returns sig = s - 1; KE and d follow the scale.
+__device__ __forceinline__ float nh_half(const Integ& I, const Box& bx, ThermoState& t) {
+  const float hdt = 0.5f * (float)I.dt;
+  df_add(t.xh, t.xl, bx.q4f * t.d);
+  const float sig = expm1f(-hdt * t.xh);
+  const float f = sig * (2.0f + sig);  // s^2 - 1
+  const float dke = t.ke * f;
+  t.ke += dke;
+  t.d = fmaf(2.0f, dke, t.d);
+  df_add(t.eh, t.el, hdt * t.xh);
+  df_add(t.xh, t.xl, bx.q4f * t.d);
+  return sig;
 }
 
-// Start-of-step thermostat half of box b, evaluated once per box at the end
-// of the previous step (or by k_prime_thermostat before the first step of a
-// call): stores the state after the start half in slot 1 and the velocity
-// scale the next kick1 applies (pending end scale times start scale).
-__device__ void start_half_box(const Dev& d, const Integ& I, int b) {
+// End-of-step half, after the second half-kick: Nose-Hoover half step, or
+// the Berendsen scale s = sqrt(1 + dt/tau (T0/T - 1)) (sig = x / (s + 1) with
+// x = dt/tau (T0/T - 1), free of cancellation); NVE changes nothing.
+__device__ __forceinline__ float end_half(const Integ& I, const Box& bx, ThermoState& t) {
+  if (I.kind == TH_NH) return nh_half(I, bx, t);
+  if (I.kind == TH_BERENDSEN && t.ke > 0.f) {
+    const float T = 2.0f * t.ke * (float)bx.inv_ndf_kb;
+    const float x = (float)(I.dt / I.tau) * ((float)bx.T0 / T - 1.0f);
+    const float sig = x / (sqrtf(1.0f + x) + 1.0f);
+    const float f = sig * (2.0f + sig);
+    t.ke += t.ke * f;
+    return sig;
+  }
+  return 0.f;
+}
+
+// Start-of-step half, before the first half-kick (Nose-Hoover only).
+__device__ __forceinline__ float start_half(const Integ& I, const Box& bx, ThermoState& t) {
+  return I.kind == TH_NH ? nh_half(I, bx, t) : 0.f;
+}
+
+__device__ __forceinline__ ThermoState thermo_in(const Box& bx, float4 th, double ke) {
+  ThermoState t;
+  t.xh = th.x;
+  t.xl = th.y;
+  t.eh = th.z;
+  t.el = th.w;
+  t.d = (float)fma(2.0, ke, -bx.ndfkT0);
+  t.ke = (float)ke;
+  return t;
+}
+
+// Thermo record of box b for the last completed step (parity pp): the
+// thermostat state after its end half and the step's energies and virial.
+// Written only when the host reads it (k_record).
+__device__ void write_record(const Dev& d, const Integ& I, int b, int pp, unsigned long long step_done) {
+  const BoxState* st = d.bst + b;
+  const Box& bx = d.box[b];
+  double* r = d.thermo + (size_t)b * TR_N;
+  const double e2 = st->ew[pp][0], e3 = st->ew[pp][1];
+  const double ke = st->ke_last;
+  const double xi = (double)st->th_e.x + (double)st->th_e.y, eta = (double)st->th_e.z + (double)st->th_e.w;
+  r[TR_STEP] = (double)step_done;
+  r[TR_PE] = e2 + e3;
+  r[TR_E2] = e2;
+  r[TR_E3] = e3;
+  r[TR_KE] = ke;
+  r[TR_T] = 2.0 * ke * bx.inv_ndf_kb;
+  double cons = ke + e2 + e3;
+  if (I.kind == TH_NH) cons += 0.5 * bx.Q * xi * xi + bx.ndfkT0 * eta;
+  r[TR_CONS] = cons;
+  r[TR_P] = (2.0 * ke + st->ew[pp][2] + st->ew[pp][3] + st->ew[pp][4]) * bx.p_fac;
+  for (int k = 0; k < 6; ++k) r[TR_W0 + k] = st->ew[pp][2 + k];
+  r[TR_XI] = xi;
+  r[TR_ETA] = eta;
+  r[TR_REBUILDS] = (double)st->rebuilds;
+}
+
+// Thermostat at the end of the step of parity par, for box b (one thread per
+// box, after the step's kinetic-energy sum is complete): the end half of this
+// step, then the start half of the next one; stores the state after each half
+// and the combined scale S - 1 the next kick1 applies.
+__device__ void end_of_step_box(const Dev& d, const Integ& I, int b, int par) {
   BoxState* st = d.bst + b;
   const Box& bx = d.box[b];
-  double xi = st->xi[0], eta = st->eta[0];
-  double s = 1.0;
-  if (I.kind == TH_NH) {
-    double ke = st->ke_last;
-    s = nh_half(ke, xi, eta, I.dt, bx.Ndf, kKB * bx.T0, bx.invQ);
-  }
-  st->xi[1] = xi;
-  st->eta[1] = eta;
-  st->s_kick = st->s_end * s;
-  st->s_kick1 = (float)(st->s_kick + 1.0);
-  st->sig = (float)(st->s_kick - 1.0);
+  const double ke = __ldcg(&st->ke_acc[par]);
+  ThermoState t = thermo_in(bx, __ldcg(&st->th), ke);
+  const float se = end_half(I, bx, t);
+  st->th_e = make_float4(t.xh, t.xl, t.eh, t.el);
+  st->ke_last = fma(ke, (double)(se * (2.0f + se)), ke);
+  st->s_endc = 1.0 + (double)se;
+  const float ss = start_half(I, bx, t);
+  st->th = make_float4(t.xh, t.xl, t.eh, t.el);
+  st->sig = fmaf(se, ss, se + ss);
+}
+
+// Start half only, from the state after the last end half (a new state, or a
+// changed integrator): the scale S - 1 includes the pending end scale.
+__global__ void k_prime_thermostat(Dev d) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= d.nbox) return;
+  const Integ I = *d.integ;
+  BoxState* st = d.bst + b;
+  const Box& bx = d.box[b];
+  ThermoState t = thermo_in(bx, st->th_e, st->ke_last);
+  const float se = (float)(st->s_endc - 1.0);
+  const float ss = start_half(I, bx, t);
+  st->th = make_float4(t.xh, t.xl, t.eh, t.el);
+  st->sig = fmaf(se, ss, se + ss);
+}
+
+// Uniform early exit of a block on a device error status (one read, shared),
+// so that no warp skips a barrier the others wait at.
+__device__ __forceinline__ bool block_stop(const Dev& d) {
+  __shared__ int s_stop;
+  if (threadIdx.x == 0) s_stop = *(volatile int*)&d.g->status;
+  __syncthreads();
+  return s_stop != 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -323,7 +429,6 @@ __device__ void start_half_box(const Dev& d, const Integ& I, int b) {
 // FP32 exponent.  Also zeroes f for this step.
 constexpr int kKAtoms = 10;     // atoms per warp in the kick kernels
 constexpr int kKThreads = 512;  // threads per block of k_kick1 / k_kick2 (few blocks: few same-address atomics)
-
 __device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, int par, int pend) {
   const int lane = threadIdx.x & 31;
   const int i = w * kKAtoms + lane / 3;
@@ -346,7 +451,7 @@ __device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, 
     const Box& bx = d.box[b];
     const BoxState* st = d.bst + b;
     const float sig = st->sig;
-    const float kf = I.cf_f * (pend ? st->s_kick1 : 1.0f);
+    const float kf = I.cf_f * (pend ? 2.0f + sig : 1.0f);
     const float k64 = c == 0 ? bx.dtL64[0] : (c == 1 ? bx.dtL64[1] : bx.dtL64[2]);
     const float Lq = c == 0 ? bx.Lq[0] : (c == 1 ? bx.Lq[1] : bx.Lq[2]);
     const int vexp = bx.vexp_lost;
@@ -408,47 +513,6 @@ __device__ __forceinline__ float kick2_lane(const Dev& d, const Integ& I, int w,
     d.g->err_index = i;
   }
   return ke;
-}
-
-// End-of-step thermostat half and thermo record of box b (one thread per box).
-__device__ void end_of_step_box(const Dev& d, const Integ& I, int b, int par, unsigned long long step_done) {
-  BoxState* st = d.bst + b;
-  const Box& bx = d.box[b];
-  double ke = __ldcg(&st->ke_acc[par]);
-  double xi = st->xi[1], eta = st->eta[1];
-  double s = 1.0;
-  if (I.kind == TH_NH) {
-    s = nh_half(ke, xi, eta, I.dt, bx.Ndf, kKB * bx.T0, bx.invQ);
-  } else if (I.kind == TH_BERENDSEN) {
-    const double T = 2.0 * ke * bx.inv_ndf_kb;
-    if (T > 0.0) {
-      s = sqrt(1.0 + I.dt / I.tau * (bx.T0 / T - 1.0));
-      ke *= s * s;
-    }
-  }
-  st->s_end = s;
-  st->ke_last = ke;
-  st->xi[0] = xi;
-  st->eta[0] = eta;
-  start_half_box(d, I, b);
-  double* t = d.thermo + (size_t)b * TR_N;
-  const double e2 = __ldcg(&st->ew[par][0]), e3 = __ldcg(&st->ew[par][1]);
-  double w[6];
-  for (int k = 0; k < 6; ++k) w[k] = __ldcg(&st->ew[par][2 + k]);
-  t[TR_STEP] = (double)step_done;
-  t[TR_PE] = e2 + e3;
-  t[TR_E2] = e2;
-  t[TR_E3] = e3;
-  t[TR_KE] = ke;
-  t[TR_T] = 2.0 * ke * bx.inv_ndf_kb;
-  double cons = ke + e2 + e3;
-  if (I.kind == TH_NH) cons += 0.5 * bx.Q * xi * xi + bx.Ndf * kKB * bx.T0 * eta;
-  t[TR_CONS] = cons;
-  t[TR_P] = (2.0 * ke + w[0] + w[1] + w[2]) * bx.p_fac;
-  for (int k = 0; k < 6; ++k) t[TR_W0 + k] = w[k];
-  t[TR_XI] = xi;
-  t[TR_ETA] = eta;
-  t[TR_REBUILDS] = (double)st->rebuilds;
 }
 
 // ---------------------------------------------------------------------------
@@ -897,7 +961,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
 
 template <bool kCount>
 __global__ void __launch_bounds__(kFThreads, 8) k_force(Dev d, FParams P) {
-  if (d.g->status) return;
+  if (block_stop(d)) return;
   __shared__ LegTable T;
   const int par = (int)(d.g->step & 1ull);
   if (blockIdx.x == 0) {  // the rebuild (if any) is consumed
@@ -917,7 +981,7 @@ __global__ void __launch_bounds__(kFThreads, 8) k_force(Dev d, FParams P) {
 // holds no conditional-node call, so profilers can capture it.
 template <bool kCond>
 __global__ void __launch_bounds__(kKThreads) k_kick1(Dev d, cudaGraphConditionalHandle rebuild_cond) {
-  if (d.g->status) return;
+  if (block_stop(d)) return;
   const Integ I = *d.integ;
   const int par = (int)(d.g->step & 1ull);
   const int pend = d.g->pend;
@@ -938,12 +1002,6 @@ __global__ void __launch_bounds__(kKThreads) k_kick1(Dev d, cudaGraphConditional
       cudaGraphSetConditional(rebuild_cond, *(volatile int*)&d.g->any_rebuild ? 1u : 0u);
     }
   }
-}
-
-// Start half of every box with the current integrator (first step of a call).
-__global__ void k_prime_thermostat(Dev d) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < d.nbox) start_half_box(d, *d.integ, b);
 }
 
 // a2: cell of atom i and its rank among the atoms of that cell (counting sort).
@@ -1058,8 +1116,11 @@ __global__ void k_neigh(Dev d, float rl2) {
 }
 
 
+// a7 second half: kinetic energy of v + a per box; the last block to finish
+// runs the thermostat halves of every box (FP32, a short serial tail) and
+// advances the step.  The half-kick itself stays pending.
 __global__ void __launch_bounds__(kKThreads) k_kick2(Dev d) {
-  if (d.g->status) return;
+  if (block_stop(d)) return;
   const Integ I = *d.integ;
   const unsigned long long step = d.g->step;
   const int par = (int)(step & 1ull);
@@ -1068,8 +1129,6 @@ __global__ void __launch_bounds__(kKThreads) k_kick2(Dev d) {
   int b = -1;
   ke[0] = kick2_lane(d, I, w, b);
   box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_acc[par]; });
-  if (blockIdx.x == 0 && threadIdx.x == 0) d.g->pend = 1;  // the second half-kick is now pending
-  // last block finishes the step: end-of-step thermostat half per box
   __shared__ bool am_last;
   __syncthreads();
   if (threadIdx.x == 0) {  // one fence per block after the barrier orders the block's writes
@@ -1079,13 +1138,22 @@ __global__ void __launch_bounds__(kKThreads) k_kick2(Dev d) {
   __syncthreads();
   if (am_last) {
     __threadfence();
-    for (int bb = threadIdx.x; bb < d.nbox; bb += blockDim.x) end_of_step_box(d, I, bb, par, step + 1);
+    for (int bb = threadIdx.x; bb < d.nbox; bb += blockDim.x) end_of_step_box(d, I, bb, par);
     __syncthreads();
     if (threadIdx.x == 0) {
-      d.g->done = 0;
-      d.g->step = step + 1;
+      d.g->done = 0u;
+      d.g->pend = 1;
+      d.g->step = step + 1ull;
     }
   }
+}
+
+// Thermo record of the last completed step (one block), before the host reads it.
+__global__ void k_record(Dev d) {
+  const Integ I = *d.integ;
+  const unsigned long long step = d.g->step;
+  const int pl = (int)((step - 1ull) & 1ull);
+  for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) write_record(d, I, b, pl, step);
 }
 
 // ---------------------------------------------------------------------------
@@ -1178,7 +1246,8 @@ __global__ void k_prep_force(Dev d, int zero_f) {
   if (zero_f && i < d.N) d.f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Thermo record from the current accumulators without advancing (state just set).
+// Thermo record from the current accumulators without advancing (forces just
+// evaluated).
 __global__ void k_thermo_snapshot(Dev d) {
   const Integ I = *d.integ;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1196,16 +1265,18 @@ __global__ void k_thermo_snapshot(Dev d) {
   t[TR_KE] = ke;
   t[TR_T] = 2.0 * ke * bx.inv_ndf_kb;
   double cons = ke + e2 + e3;
-  if (I.kind == TH_NH) cons += 0.5 * bx.Q * st->xi[0] * st->xi[0] + bx.Ndf * kKB * bx.T0 * st->eta[0];
+  const double xi = (double)st->th_e.x + (double)st->th_e.y, eta = (double)st->th_e.z + (double)st->th_e.w;
+  if (I.kind == TH_NH) cons += 0.5 * bx.Q * xi * xi + bx.ndfkT0 * eta;
   t[TR_CONS] = cons;
   t[TR_P] = (2.0 * ke + st->ew[par][2] + st->ew[par][3] + st->ew[par][4]) * bx.p_fac;
   for (int k = 0; k < 6; ++k) t[TR_W0 + k] = st->ew[par][2 + k];
-  t[TR_XI] = st->xi[0];
-  t[TR_ETA] = st->eta[0];
+  t[TR_XI] = xi;
+  t[TR_ETA] = eta;
   t[TR_REBUILDS] = (double)st->rebuilds;
 }
 
-// Sorted -> user order: x (wrapped) and v * s_end (pending thermostat scale).
+// Sorted -> user order: x (wrapped) and (v + pending half-kick) * s_endc (the
+// end scale of the last step, pending on the stored velocities).
 __global__ void k_gather_state(Dev d, double* __restrict__ xo, double* __restrict__ vo) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
@@ -1218,7 +1289,7 @@ __global__ void k_gather_state(Dev d, double* __restrict__ xo, double* __restric
     xo[3 * (size_t)u + 2] = __ull2double_rn(d.z[i]) * k2m64 * bx.L[2];
   }
   if (vo) {  // pending half-kick and end-of-step thermostat scale applied
-    const double s = d.bst[d.q[i].w].s_end;
+    const double s = d.bst[d.q[i].w].s_endc;
     const double cf = d.g->pend ? d.integ->cf : 0.0;
     const float4 F = d.f[i];
     vo[3 * (size_t)u] = (join_df(d.vx[i]) + cf * F.x) * s;

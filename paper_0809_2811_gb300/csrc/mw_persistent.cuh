@@ -1,7 +1,7 @@
 // mw_persistent.cuh -- persistent engine: one cooperative launch advances
 // every box nsteps MD steps, with grid-wide barriers between the phases of
-// mw_device.cuh (kick1 | [bin | scan | scan | scatter | copy + neighbour list]
-// | force | kick2 | thermostat).  All blocks are
+// mw_device.cuh (kick1 | [bin | scan | scan | scatter | copy + neighbour
+// list] | force | kick2 + thermostat in the last block to arrive).  All blocks are
 // co-resident (cooperative launch), every barrier wait is bounded in wall
 // time, and the release of each barrier carries one status snapshot so that
 // all blocks take the same decision to stop.  Data written in one phase is
@@ -53,6 +53,50 @@ __device__ int grid_barrier(Global* g, unsigned& gen) {
       st = released ? *(volatile int*)&g->bar_stat[gen & 1u] : ST_TIMEOUT;
     }
     s_status = st;
+  }
+  __syncthreads();
+  gen += 1u;
+  return s_status;
+}
+
+// Grid barrier whose last arriving block runs fn() (all its threads) before
+// the release, so that work that needs every block's results and that every
+// block needs next costs no barrier of its own.  Same bounded waits and
+// status snapshot as grid_barrier.
+template <class Fn>
+__device__ int grid_barrier_last(Global* g, unsigned& gen, Fn fn) {
+  __shared__ int s_status;
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&g->bar_count, 1u) + 1u == gridDim.x);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    fn();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      g->bar_count = 0u;
+      g->bar_stat[gen & 1u] = *(volatile int*)&g->status;
+      __threadfence();
+      atomicExch(&g->bar_gen, gen + 1u);
+      s_status = g->bar_stat[gen & 1u];
+    }
+  } else if (threadIdx.x == 0) {
+    const unsigned long long t0 = globaltimer_ns();
+    bool released = true;
+    while (*(volatile unsigned*)&g->bar_gen == gen) {
+      __nanosleep(100);
+      if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+        set_status(g, ST_TIMEOUT);
+        released = false;
+        break;
+      }
+    }
+    __threadfence();
+    s_status = released ? *(volatile int*)&g->bar_stat[gen & 1u] : ST_TIMEOUT;
   }
   __syncthreads();
   gen += 1u;
@@ -133,7 +177,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     const unsigned long long step = step0 + (unsigned long long)s;
     const int par = (int)(step & 1ull);
     // a1 + a7 first half, a8 displacement check
-    const int pend = *(volatile int*)&g->pend;  // stable: written only in the kick2 phase
+    const int pend = *(volatile int*)&g->pend;  // stable: written only at the end of the kick2 phase
     if (tid == 0) g->n_over = 0;
     for (int w = gw; w * kKAtoms < d.N; w += nwarps) kick1_lane(d, I, w, par, pend);
     if (grid_barrier(g, gen)) return;
@@ -157,13 +201,10 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     // a4 - a6: fused two- + three-body force, energy, virial
     for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) force_block<kCount>(d, P, T, blk, par);
     if (grid_barrier(g, gen)) return;
-    // a7 second half + kinetic energy per box; the rebuild (if any) is consumed
+    // a7 second half: kinetic energy of v + a per box; the rebuild (if any) is consumed
     if (blockIdx.x == 0) {
       for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
-      if (threadIdx.x == 0) {
-        g->any_rebuild = 0;
-        g->pend = 1;  // the second half-kick is now pending
-      }
+      if (threadIdx.x == 0) g->any_rebuild = 0;
     }
     for (int wb = blockIdx.x * (kPersThreads / 32); wb * kKAtoms < d.N; wb += nwarps) {  // block-uniform
       const int w = wb + (int)(threadIdx.x >> 5);
@@ -172,11 +213,16 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
       ke[0] = kick2_lane(d, I, w, b);
       box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_acc[par]; });
     }
-    if (grid_barrier(g, gen)) return;
-    // thermostat halves (end of this step, start of the next) and thermo record
-    for (int b = tid; b < d.nbox; b += nth) end_of_step_box(d, I, b, par, step + 1ull);
-    if (tid == 0) g->step = step + 1ull;
-    if (grid_barrier(g, gen)) return;
+    // the last block to arrive runs the thermostat halves of every box (end of
+    // this step, start of the next) before releasing the others
+    if (grid_barrier_last(g, gen, [&] {
+          for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) end_of_step_box(d, I, b, par);
+          if (threadIdx.x == 0) {
+            g->pend = 1;
+            g->step = step + 1ull;
+          }
+        }))
+      return;
   }
 }
 

@@ -219,12 +219,14 @@ __device__ __forceinline__ bool box_flagged(const Dev& d, int b) { return d.bst[
 
 // Per-box accumulation of NV values held as FP32 by each thread; the sums
 // across blocks are FP64.  Every thread of the block calls it (b < 0 for
-// threads without a contribution); thread 0 must hold the block's first box.  Atoms are box-major, so box ids along a
-// warp are non-decreasing: a segmented FP32 scan sums each run of one box in
-// the warp; runs of the block's first and last box are summed in shared
-// memory (FP32, one block of atoms) and widened to FP64 for one global atomic
-// per value and block; runs of other boxes (small boxes only) go to global
-// memory directly.  No FP64 arithmetic runs on the SM.
+// threads without a contribution, whose values must be 0); thread 0 must hold
+// the block's first box.  Atoms are box-major, so box ids along a warp are
+// non-decreasing.  A warp within one box (nearly all) reduces its NV values
+// by a transpose-reduce butterfly (about NV + 5 shuffles in all); a warp that
+// straddles boxes runs a segmented FP32 scan over each run of one box.  Sums
+// of the block's first and last box are combined in shared memory (FP32) and
+// widened to FP64 for one global atomic per value and block; sums of other
+// boxes (small boxes only) go to global memory directly.
 template <int NV, class Dst>
 __device__ void box_accumulate(float (&v)[NV], int b, Dst dst) {
   static_assert(NV <= 16, "two slots of NV sums are flushed by warp 0");
@@ -238,27 +240,57 @@ __device__ void box_accumulate(float (&v)[NV], int b, Dst dst) {
   if (threadIdx.x < 2 * NV) (&sacc[0][0])[threadIdx.x] = 0.f;
   __syncthreads();
   if (b >= 0) atomicMax(&sbox[1], b);  // the block's last box (box ids never decrease along atoms)
+  const int b0 = __shfl_sync(kFull, b, 0);
+  constexpr bool kPow2 = (NV & (NV - 1)) == 0;
+  if (kPow2 && __all_sync(kFull, b == b0 || b < 0)) {
+    // the warp holds one box (the common case): transpose-reduce, each of the
+    // NV sums ending on its own group of 32/NV lanes
+    int off = 16;
 #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const int bo = __shfl_up_sync(kFull, b, off);
+    for (int n = NV; n > 1; n >>= 1) {
+      const bool up = (lane & off) != 0;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      const float vo = __shfl_up_sync(kFull, v[k], off);
-      if (lane >= off && bo == b) v[k] += vo;
+      for (int k = 0; k < n / 2; ++k) {
+        const float send = up ? v[k] : v[k + n / 2];
+        const float keep = up ? v[k + n / 2] : v[k];
+        v[k] = keep + __shfl_xor_sync(kFull, send, off);
+      }
+      off >>= 1;
     }
-  }
-  const int bn = __shfl_down_sync(kFull, b, 1);
-  __syncthreads();
-  const bool tail = (b >= 0) && (lane == 31 || bn != b);
-  if (tail) {
-    const int slot = (b == sbox[0]) ? 0 : ((b == sbox[1]) ? 1 : -1);
-    if (slot >= 0) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) atomicAdd(&sacc[slot][k], v[k]);
-    } else {
-      double* p = dst(b);
+    for (; off > 0; off >>= 1) v[0] += __shfl_xor_sync(kFull, v[0], off);
+    __syncthreads();
+    constexpr int kGroup = 32 / NV;
+    if (b0 >= 0 && lane % kGroup == 0) {
+      const int k = lane / kGroup;
+      const int slot = (b0 == sbox[0]) ? 0 : ((b0 == sbox[1]) ? 1 : -1);
+      if (slot >= 0) atomicAdd(&sacc[slot][k], v[0]);
+      else atomicAdd(dst(b0) + k, (double)v[0]);
+    }
+  } else {
+    // segmented FP32 scan over the runs of one box in the warp
 #pragma unroll
-      for (int k = 0; k < NV; ++k) atomicAdd(p + k, (double)v[k]);
+    for (int off = 1; off < 32; off <<= 1) {
+      const int bo = __shfl_up_sync(kFull, b, off);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const float vo = __shfl_up_sync(kFull, v[k], off);
+        if (lane >= off && bo == b) v[k] += vo;
+      }
+    }
+    const int bn = __shfl_down_sync(kFull, b, 1);
+    __syncthreads();
+    const bool tail = (b >= 0) && (lane == 31 || bn != b);
+    if (tail) {
+      const int slot = (b == sbox[0]) ? 0 : ((b == sbox[1]) ? 1 : -1);
+      if (slot >= 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) atomicAdd(&sacc[slot][k], v[k]);
+      } else {
+        double* p = dst(b);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) atomicAdd(p + k, (double)v[k]);
+      }
     }
   }
   __syncthreads();
@@ -760,30 +792,15 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     L1 = bx.Lq[1];
     L2 = bx.Lq[2];
   }
-  // ---- leg phase A: row entries and candidate positions are fetched for up
-  // to kPre slots per lane before any is used (one memory latency instead of
-  // a dependent chain per slot); rows longer than kG * kPre continue
-  // unprefetched.  Distance test only; hits are compacted (ballot + popc in
-  // the lane group) into the centre's row as (d, r^2 | j).
+  // ---- leg phase A: row entries and candidate positions are fetched for
+  // kPre slots per lane before any is used (two memory latencies per batch
+  // instead of a dependent chain per slot).  Distance test only; hits are
+  // compacted (ballot + popc in the lane group) into the centre's row as
+  // (d, r^2 | j).
   const int iters = __reduce_max_sync(kFull, (cnt + kG - 1) / kG);
   const unsigned gsh = lane & ~(kG - 1);
   const int* row = d.nbr + (size_t)(valid ? i : 0) * d.W;
   int nl = 0;
-  int jr[kPre];
-  uint32_t qx[kPre], qy[kPre], qz[kPre];
-#pragma unroll
-  for (int t = 0; t < kPre; ++t) {
-    const int s = g + kG * t;
-    jr[t] = (s < cnt) ? row[s] : -1;
-  }
-#pragma unroll
-  for (int t = 0; t < kPre; ++t) {
-    uint4 qj = make_uint4(0u, 0u, 0u, 0u);
-    if (jr[t] >= 0) qj = d.q[jr[t]];
-    qx[t] = qj.x;
-    qy[t] = qj.y;
-    qz[t] = qj.z;
-  }
   auto test_slot = [&](int j, uint32_t jx, uint32_t jy, uint32_t jz, bool have) {
     bool hit = false;
     float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
@@ -802,16 +819,28 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     }
     nl += __popc(m);
   };
+  // batches of kPre slots per lane, each fetched as a whole (rows, then
+  // positions) before its tests: rows longer than kG * kPre cost one more
+  // round trip per batch, not per slot
+  for (int t0 = 0; t0 < iters; t0 += kPre) {  // warp-uniform
+    int jr[kPre];
+    uint32_t qx[kPre], qy[kPre], qz[kPre];
 #pragma unroll
-  for (int t = 0; t < kPre; ++t)
-    if (t < iters) test_slot(jr[t], qx[t], qy[t], qz[t], jr[t] >= 0);
-  for (int t = kPre; t < iters; ++t) {  // long rows (dense input)
-    const int s = g + kG * t;
-    const bool have = s < cnt;
-    const int j = have ? row[s] : 0;
-    uint4 qj = make_uint4(0u, 0u, 0u, 0u);
-    if (have) qj = d.q[j];
-    test_slot(j, qj.x, qj.y, qj.z, have);
+    for (int t = 0; t < kPre; ++t) {
+      const int s = g + kG * (t0 + t);
+      jr[t] = (s < cnt) ? row[s] : -1;
+    }
+#pragma unroll
+    for (int t = 0; t < kPre; ++t) {
+      uint4 qj = make_uint4(0u, 0u, 0u, 0u);
+      if (jr[t] >= 0) qj = d.q[jr[t]];
+      qx[t] = qj.x;
+      qy[t] = qj.y;
+      qz[t] = qj.z;
+    }
+#pragma unroll
+    for (int t = 0; t < kPre; ++t)
+      if (t0 + t < iters) test_slot(jr[t], qx[t], qy[t], qz[t], jr[t] >= 0);
   }
   __syncwarp();
   // ---- leg phase B: leg terms for the compacted legs only, spread over the

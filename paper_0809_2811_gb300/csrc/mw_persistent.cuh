@@ -22,8 +22,10 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// Grid barrier.  gen is this block's count of barriers passed (all blocks
-// start from the same value).  Returns the status snapshot of the release
+// Grid barrier (one counter: a two-level counter tree measured slower on
+// GB300, where the fences and L2 round trips, ~3.3 us per barrier, dominate
+// rather than atomic contention).  gen is this block's count of barriers
+// passed (all blocks start from the same value).  Returns the status snapshot of the release
 // (identical in every block), or ST_TIMEOUT if this block gave up waiting.
 __device__ int grid_barrier(Global* g, unsigned& gen) {
   __shared__ int s_status;

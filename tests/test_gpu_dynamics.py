@@ -57,11 +57,15 @@ def test_short_trajectory_matches_oracle(mwlib, orc, kind, engine):
 
 
 def test_nve_energy_conservation_512(mwlib, orc):
-    """1000 NVE steps at dt = 10 fs from the jittered 512-atom start.  The
-    total energy fluctuates at O(dt^2) while the start relaxes; the FP32-force
-    run must (a) fluctuate no more than the FP64 oracle's own run of the same
-    steps (+ 20%), and (b) show a fitted drift below 1e-4 of |E| over the run
-    (Sec. II.B: better than 1/10000)."""
+    """NVE at dt = 10 fs from the jittered 512-atom start.  (a) Over the first
+    1000 steps the FP32-force run fluctuates no more than the FP64 oracle's own
+    run of the same steps (+ 20%).  (b) Over 1e5 steps (1 ns) the fitted drift
+    of the total energy stays below 1e-4 of |E| (Sec. II.B: energy conserved
+    better than 1/10000 over a run).  The drift is fitted over the long run:
+    within 1000 steps the O(dt^2) fluctuation of the total energy (the oracle's
+    own FP64 run moves by ~1.7e-4 |E| there) decides any fitted slope, and the
+    GPU trajectory, chaotic and summed in nondeterministic order, differs from
+    run to run."""
     x, v, box = I.nve512()
     x = I.snap_to_grid(x, box)
     s = mwlib.System(512, box)
@@ -71,6 +75,9 @@ def test_nve_energy_conservation_512(mwlib, orc):
         es = [e0]
         for _ in range(20):
             es.append(s.step(50, dt=10.0)[0]["conserved"])
+        el = [es[-1]]
+        for _ in range(198):
+            el.append(s.step(500, dt=10.0)[0]["conserved"])
     finally:
         s.close()
     es = np.array(es)
@@ -79,9 +86,10 @@ def test_nve_energy_conservation_512(mwlib, orc):
     dev_gpu = np.abs(es - es[0]).max()
     dev_orc = np.abs(eo - eo[0]).max()
     assert dev_gpu <= 1.2 * dev_orc + 1e-6 * abs(e0)
-    t = np.arange(len(es)) * 50.0
-    slope = np.polyfit(t[5:], es[5:], 1)[0]  # after the initial relaxation
-    assert abs(slope * 1000.0) / abs(e0) < 1e-4
+    el = np.array(el)
+    t = 1000.0 + 500.0 * np.arange(len(el))
+    slope = np.polyfit(t, el, 1)[0]
+    assert abs(slope * 1e5) / abs(e0) < 1e-4
 
 
 def test_nose_hoover_conserved_quantity(mwlib):

@@ -225,7 +225,7 @@ mw_status mw_set_nbr_width(mw_system* s, int width);
 mw_status mw_set_skin(mw_system* s, double skin);
 
 /* Autotuner.  Runs `steps` steps for each candidate configuration - engine
- * (graph / persistent), skin (0.7x, 1x, 1.4x, 1.8x the current one) and
+ * (graph / persistent), skin (0.7x, 1x, 1.4x, 1.8x, 2.2x, 2.6x the current one) and
  * persistent grid size - each from the same saved state (positions,
  * velocities and thermostat state are restored exactly between candidates and
  * at the end), keeps the fastest by GPU time as the AUTO engine and the skin,

@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--engine", default="auto", choices=["auto", "graph", "persistent"])
+    ap.add_argument("--skin", type=float, default=None,
+                    help="neighbour-list skin (A) for an explicit --engine (the autotuner picks it otherwise)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prep-steps", type=int, default=3000)
@@ -257,6 +259,8 @@ def run_gpu(args, world, rank, local, pg):
     if args.engine != "auto":
         sysm.set_engine({"graph": mw.MW_ENGINE_GRAPH, "persistent": mw.MW_ENGINE_PERSISTENT}[args.engine])
     sysm.set_state(x, v)
+    if args.skin is not None and args.engine != "auto":
+        mw.mw_set_skin(sysm.h, args.skin)
     integ = mw.make_integrator(DT, mw.MW_NOSE_HOOVER, T_RUN, TAU)
     natoms = sum(n)
     tuned = None
@@ -303,7 +307,10 @@ def run_gpu(args, world, rank, local, pg):
     rebuild_steps = info["rebuild_steps"] - rs0
     value = world * natoms * K / span_max
 
-    # force-kernel roofline (timed alone, L2 flushed between launches)
+    # force-kernel roofline: the k_force launch alone, timed with events on the
+    # system stream between the other phases of a step (mw_phase_times); the
+    # whole force call with the L2 flushed before it is reported beside it
+    phases = mw.mw_phase_times(sysm.h, integ, 50)  # per-phase GPU time (separate launches)
     nf = 30
     f0 = [torch.cuda.Event(enable_timing=True) for _ in range(nf)]
     f1 = [torch.cuda.Event(enable_timing=True) for _ in range(nf)]
@@ -322,7 +329,8 @@ def run_gpu(args, world, rank, local, pg):
     sysm.set_count_terms(False)
     P, T = info_c["npairs"], info_c["ntriplets"]
     flops = 40.0 * (2 * P + T)  # 40 FP32 ops per ordered leg and per triplet
-    achieved = flops / (fms / 1e3) / 1e12
+    kms = phases["force"]
+    achieved = flops / (kms / 1e3) / 1e12
     peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     traffic = traffic_from_profile(os.path.join(ROOT, "paper_0809_2811_gb300", "csrc", "mw_device.cuh"))
 
@@ -352,7 +360,6 @@ def run_gpu(args, world, rank, local, pg):
         rate, desc = oracle_sample()
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
 
-    phases = mw.mw_phase_times(sysm.h, integ, 50)  # per-phase GPU time (separate launches)
     kernels_per_step = 4 if info["engine"] == mw.MW_ENGINE_GRAPH else 1  # + 5 rebuild kernels on rebuild steps
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -368,7 +375,7 @@ def run_gpu(args, world, rank, local, pg):
                    "host_us_per_step_call": 1e6 * t_host / K},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_force (fused 2+3-body)",
-                     "force_ms": fms, "legs": 2 * P, "triplets": T,
+                     "kernel_ms": kms, "force_call_ms_l2_flushed": fms, "legs": 2 * P, "triplets": T,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz"},
         "cpu_baseline": cpu,
         "e2e": e2e,

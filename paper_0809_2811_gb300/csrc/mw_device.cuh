@@ -641,7 +641,7 @@ __device__ void neigh_cell_warp(const Dev& d, const uint4* qa, int c, float rl2)
 //     red.global.add.v4.f32 to the partner, the reaction kept for the centre;
 //   per-box FP64 reduction of E2, E3 and the virial.
 // Leg data: u (unit vector i->j), ee = sqrt(lam eps) exp(gam sig/(r - a sig)),
-// tr = 2/r, nde = gam sig/(r - a sig)^2, r, j.  With c_jk = u_j.u_k and
+// -1/2 dphi2/dr, nde = gam sig/(r - a sig)^2, r, j (tr = 2/r from r).  With c_jk = u_j.u_k and
 // D_jk = c_jk - cos th0 a centre's three-body energy (Sec. II.A) is
 //   E3_i = sum_{j<k} ee_j ee_k D_jk^2 = 1/2 sum_j ee_j C_j,
 // and the force on leg partner j is
@@ -858,9 +858,6 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     const float r = r2 * invr;
     if (!(r < P.rc)) {  // FP32 rounding put it on the cutoff: contributes nothing
       *ue_p = make_float4(0.f, 0.f, 0.f, 0.f);
-      ax_p->x = 0.f;
-      ax_p->y = 0.f;
-      ax_p->z = r;
       continue;
     }
     const float ux = rec.x * invr, uy = rec.y * invr, uz = rec.z * invr;
@@ -885,17 +882,9 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     fx = fmaf(dphi, ux, fx);
     fy = fmaf(dphi, uy, fy);
     fz = fmaf(dphi, uz, fz);
-    const float wv = -0.5f * dphi * r;
-    acc[2] = fmaf(wv * ux, ux, acc[2]);
-    acc[3] = fmaf(wv * uy, uy, acc[3]);
-    acc[4] = fmaf(wv * uz, uz, acc[4]);
-    acc[5] = fmaf(wv * ux, uy, acc[5]);
-    acc[6] = fmaf(wv * ux, uz, acc[6]);
-    acc[7] = fmaf(wv * uy, uz, acc[7]);
     *ue_p = make_float4(ux, uy, uz, ee);
-    ax_p->x = 2.0f * invr;
-    ax_p->y = P.gsig * tinv * tinv;
-    ax_p->z = r;
+    // (-1/2 dphi: the pair term's share of the virial, taken in phase C), nde, r, j
+    *ax_p = make_float4(-0.5f * dphi, P.gsig * tinv * tinv, r, ax_p->w);
     const float ex = ee * ux, ey = ee * uy, ez = ee * uz;
     m0 += ee;
     msx += ex;
@@ -926,6 +915,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
   // ---- leg phase C: three-body force on each leg partner from the moments
   const float c0 = P.c0;
   const float s0c = c0 * c0 * m0;
+  const float oc0 = 1.0f - c0;  // D_jj with c_jj = |u_j|^2 = 1
   for (int l = g; l < nstage; l += kG) {
     const float4 uj = T.ue[a * kLPad + l];
     const float4 xj = T.aux[a * kLPad + l];
@@ -936,16 +926,18 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     const float mz = fmaf(mxz, uj.x, fmaf(myz, uj.y, mzz * uj.z));
     const float qm = fmaf(uj.x, mx, fmaf(uj.y, my, uj.z * mz));     // u_j.M u_j
     const float ps = fmaf(uj.x, msx, fmaf(uj.y, msy, uj.z * msz));  // u_j.s
-    const float cjj = fmaf(uj.x, uj.x, fmaf(uj.y, uj.y, uj.z * uj.z));
-    const float djj = cjj - c0;
-    const float self = ee * djj;
-    const float Bj = fmaf(-c0, ps, qm) - self * cjj;
-    const float Cj = fmaf(-2.0f * c0, ps, qm + s0c) - self * djj;
+    // the k = j term taken back out with c_jj = 1 (|u_j|^2 - 1 ~ 1e-7 leaves a
+    // residue of that relative size in the smallest terms)
+    const float self = ee * oc0;
+    const float Bj = fmaf(-c0, ps, qm) - self;
+    const float Cj = fmaf(-2.0f * c0, ps, qm + s0c) - self * oc0;
     const float Ax = fmaf(-c0, msx, mx) - self * uj.x;
     const float Ay = fmaf(-c0, msy, my) - self * uj.y;
     const float Az = fmaf(-c0, msz, mz) - self * uj.z;
-    const float et = ee * xj.x;                          // ee_j tr_j
-    const float cu = ee * fmaf(xj.y, Cj, xj.x * Bj);     // ee_j (nde_j C_j + tr_j B_j)
+    const float r = xj.z;
+    const float tr = __fdividef(2.0f, r);
+    const float et = ee * tr;                            // ee_j tr_j
+    const float cu = ee * fmaf(xj.y, Cj, tr * Bj);       // ee_j (nde_j C_j + tr_j B_j)
     const float gx = fmaf(cu, uj.x, -et * Ax);
     const float gy = fmaf(cu, uj.y, -et * Ay);
     const float gz = fmaf(cu, uj.z, -et * Az);
@@ -954,13 +946,15 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     fy -= gy;
     fz -= gz;
     acc[1] = fmaf(0.5f * ee, Cj, acc[1]);
-    const float rx = xj.z * uj.x, ry = xj.z * uj.y, rz = xj.z * uj.z;
-    acc[2] = fmaf(rx, gx, acc[2]);
-    acc[3] = fmaf(ry, gy, acc[3]);
-    acc[4] = fmaf(rz, gz, acc[4]);
-    acc[5] = fmaf(rx, gy, acc[5]);
-    acc[6] = fmaf(rx, gz, acc[6]);
-    acc[7] = fmaf(ry, gz, acc[7]);
+    // virial: r u_a (g_b - 1/2 dphi u_b), the three-body and the pair part
+    const float hx = fmaf(xj.x, uj.x, gx), hy = fmaf(xj.x, uj.y, gy), hz = fmaf(xj.x, uj.z, gz);
+    const float rx = r * uj.x, ry = r * uj.y, rz = r * uj.z;
+    acc[2] = fmaf(rx, hx, acc[2]);
+    acc[3] = fmaf(ry, hy, acc[3]);
+    acc[4] = fmaf(rz, hz, acc[4]);
+    acc[5] = fmaf(rx, hy, acc[5]);
+    acc[6] = fmaf(rx, hz, acc[6]);
+    acc[7] = fmaf(ry, hz, acc[7]);
   }
   // ---- force on the centre: pair part + three-body reaction, over the group
 #pragma unroll

@@ -66,6 +66,10 @@ def lib():
                                ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, d, d]
         _lib.or_force_vjp.argtypes = [d, ctypes.c_int, d, d, d, d, d]
         _lib.or_energy_param_grad.argtypes = [d, ctypes.c_int, d, d, d]
+        ll = ctypes.POINTER(ctypes.c_longlong)
+        _lib.or_pair_histogram.argtypes = [ctypes.c_int, d, d, ctypes.c_double, ctypes.c_int, ctypes.c_double, ll, ll]
+        _lib.or_angle_histogram.argtypes = [ctypes.c_int, d, d, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_double, ll, ll, ll]
     return _lib
 
 
@@ -178,3 +182,34 @@ def energy_param_grad(x, box, prm=None):
     g = np.zeros(3)
     _check(lib().or_energy_param_grad(_dp(prm), x.shape[0], _dp(x), _dp(box), _dp(g)), "energy_param_grad")
     return g
+
+
+def _llp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
+
+
+def pair_histogram(x, box, dr, nbins, rel=1e-5):
+    """Sec. II.C: ordered pairs i != j by minimum-image distance bin (the raw
+    histogram behind g(r)); also the pairs within rel of a bin edge, per bin."""
+    x = np.ascontiguousarray(x, np.float64)
+    box = np.ascontiguousarray(box, np.float64)
+    h = np.zeros(nbins, np.int64)
+    a = np.zeros(nbins, np.int64)
+    _check(lib().or_pair_histogram(len(x), _dp(x), _dp(box), float(dr), int(nbins), float(rel), _llp(h), _llp(a)),
+           "or_pair_histogram")
+    return h, a
+
+
+def angle_histogram(x, box, nc=8, nbins=180, tol_deg=1e-3, rel=1e-5):
+    """Sec. II.C: angles theta_ikj at each atom k over ordered pairs of its nc
+    nearest neighbours, binned over [0, 180] degrees; also the angles within
+    tol_deg of a bin edge, per bin, and the number of atoms whose nc-th
+    neighbour is within rel of the next (an ambiguous selection)."""
+    x = np.ascontiguousarray(x, np.float64)
+    box = np.ascontiguousarray(box, np.float64)
+    h = np.zeros(nbins, np.int64)
+    a = np.zeros(nbins, np.int64)
+    t = np.zeros(1, np.int64)
+    _check(lib().or_angle_histogram(len(x), _dp(x), _dp(box), int(nc), int(nbins), float(tol_deg), float(rel),
+                                    _llp(h), _llp(a), _llp(t)), "or_angle_histogram")
+    return h, a, int(t[0])

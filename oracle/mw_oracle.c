@@ -25,6 +25,11 @@
  *   - Sec. II.B: velocity-Verlet dynamics (the paper names LAMMPS, the 10 fs
  *     step and a 1 ps Nose-Hoover relaxation time; the integrator itself and
  *     the single-thermostat Trotter split are this oracle's reading).
+ *   - Sec. II.C, structure: the pair histogram behind g(r) (ordered pairs
+ *     i != j of one periodic box, binned by their minimum-image distance),
+ *     and the angle histogram behind the adf (for each atom k its n_c
+ *     nearest neighbours, the angles theta_ikj at k over every ordered pair
+ *     i != j of them).  Both by brute force over all pairs.
  *   - Force-matching adjoint (no counterpart in the paper, whose Sec. II.D
  *     tunes lam, eps, sig by scans): the derivative of the forces along a
  *     direction, taken by the complex-step method (Squire & Trapp, SIAM Rev.
@@ -726,4 +731,115 @@ int or_energy_param_grad(const double* prm, int n, const double* x, const double
   free(xc);
   free(fc);
   return rc;
+}
+
+/* ---------------------------------------------------------------------------
+ * Sec. II.C, structure.
+ *
+ * Pair histogram: hist[k] = number of ordered pairs (i, j), i != j, whose
+ * minimum-image distance r satisfies k dr <= r < (k + 1) dr, k < nbins.
+ * amb[k] counts the pairs whose r lies within rel * r of a bin edge of bin k
+ * (the bin a rounding of r could move them into or out of).  All pairs by
+ * brute force.  Returns 0. */
+int or_pair_histogram(int n, const double* x, const double* box, double dr, int nbins, double rel, long long* hist,
+                      long long* amb) {
+  for (int k = 0; k < nbins; ++k) hist[k] = amb[k] = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+      min_image(box, d);
+      const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      const double t = r / dr;
+      const int k = (int)floor(t);
+      if (k >= 0 && k < nbins) hist[k] += 1;
+      /* near an edge: count in both neighbouring bins */
+      const double e = floor(t + 0.5);
+      if (fabs(t - e) * dr <= rel * r) {
+        const int lo = (int)e - 1, hi = (int)e;
+        if (lo >= 0 && lo < nbins) amb[lo] += 1;
+        if (hi >= 0 && hi < nbins) amb[hi] += 1;
+      }
+    }
+  return 0;
+}
+
+typedef struct {
+  double r2;
+  int j;
+} or_nb;
+
+static int cmp_nb(const void* a, const void* b) {
+  const or_nb* p = (const or_nb*)a;
+  const or_nb* q = (const or_nb*)b;
+  if (p->r2 < q->r2) return -1;
+  if (p->r2 > q->r2) return 1;
+  return (p->j > q->j) - (p->j < q->j);
+}
+
+/* Angle histogram (adf): for each atom k, its nc nearest neighbours (ties by
+ * index); for every ordered pair (i, j), i != j, of them the angle theta_ikj
+ * at k, binned over [0, 180] degrees in nbins bins (180 itself in the last).
+ * amb[b] counts the angles within tol_deg of an edge of bin b; *ties counts
+ * the atoms whose nc-th and (nc+1)-th neighbour distances differ by less than
+ * rel of the distance (the selection a rounding could change).  Returns 0,
+ * or -1 if an atom has fewer than nc other atoms. */
+int or_angle_histogram(int n, const double* x, const double* box, int nc, int nbins, double tol_deg, double rel,
+                       long long* hist, long long* amb, long long* ties) {
+  const double pi = 3.14159265358979323846;
+  const double w = 180.0 / nbins;
+  for (int b = 0; b < nbins; ++b) hist[b] = amb[b] = 0;
+  *ties = 0;
+  if (nc >= n) return -1;
+  or_nb* nb = (or_nb*)malloc(sizeof(or_nb) * (size_t)n);
+  double* u = (double*)malloc(sizeof(double) * 3 * (size_t)nc);
+  if (!nb || !u) {
+    free(nb);
+    free(u);
+    return -2;
+  }
+  for (int k = 0; k < n; ++k) {
+    int m = 0;
+    for (int j = 0; j < n; ++j) {
+      if (j == k) continue;
+      double d[3] = {x[3 * j] - x[3 * k], x[3 * j + 1] - x[3 * k + 1], x[3 * j + 2] - x[3 * k + 2]};
+      min_image(box, d);
+      nb[m].r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      nb[m].j = j;
+      ++m;
+    }
+    qsort(nb, (size_t)m, sizeof(or_nb), cmp_nb);
+    if (m > nc) {
+      const double ra = sqrt(nb[nc - 1].r2), rb = sqrt(nb[nc].r2);
+      if (rb - ra <= rel * rb) *ties += 1;
+    }
+    for (int a = 0; a < nc; ++a) {
+      const int j = nb[a].j;
+      double d[3] = {x[3 * j] - x[3 * k], x[3 * j + 1] - x[3 * k + 1], x[3 * j + 2] - x[3 * k + 2]};
+      min_image(box, d);
+      const double r = sqrt(nb[a].r2);
+      for (int c = 0; c < 3; ++c) u[3 * a + c] = d[c] / r;
+    }
+    for (int a = 0; a < nc; ++a)
+      for (int b = 0; b < nc; ++b) {
+        if (a == b) continue;
+        double c = u[3 * a] * u[3 * b] + u[3 * a + 1] * u[3 * b + 1] + u[3 * a + 2] * u[3 * b + 2];
+        if (c > 1.0) c = 1.0;
+        if (c < -1.0) c = -1.0;
+        const double th = acos(c) * 180.0 / pi;
+        int bin = (int)floor(th / w);
+        if (bin >= nbins) bin = nbins - 1;
+        if (bin < 0) bin = 0;
+        hist[bin] += 1;
+        const double e = floor(th / w + 0.5);
+        if (fabs(th - e * w) <= tol_deg) {
+          const int lo = (int)e - 1, hi = (int)e;
+          if (lo >= 0 && lo < nbins) amb[lo] += 1;
+          if (hi >= 0 && hi < nbins) amb[hi] += 1;
+        }
+      }
+  }
+  free(nb);
+  free(u);
+  return 0;
 }

@@ -377,3 +377,59 @@ def test_berendsen_relaxes_temperature(orc):
     x, v, box = I.nve512()
     x1, v1, _, th = orc.md(x, v * math.sqrt(2.0), box, 300, dt=10.0, kind=1, T0=298.0, tau=100.0)
     assert abs(th[-50:, 4].mean() - 298.0) < 25.0
+
+
+# --------------------------------------------------------------------------
+# Sec. II.C structure: the pair histogram behind g(r) and the adf.
+
+def test_pair_histogram_diamond_shells(orc):
+    """Cubic diamond with cube edge a0: coordination shells at r^2 = (3/16) a0^2
+    x (1, 8/3, 11/3) hold 4, 12 and 12 atoms; the histogram counts ordered pairs."""
+    x, box = I.diamond_cubic(3, 0.92)
+    n = len(x)
+    a0 = box[0] / 3
+    d = math.sqrt(3.0) / 4.0 * a0
+    dr = 0.01
+    h, amb = orc.pair_histogram(x, box, dr, 600)
+    assert amb.sum() == 0
+    for f, c in ((1.0, 4), (8.0 / 3.0, 12), (11.0 / 3.0, 12)):
+        k = int(math.floor(d * math.sqrt(f) / dr))
+        assert h[k] == c * n
+    k3 = int(math.floor(d * math.sqrt(11.0 / 3.0) / dr))
+    assert h[: k3 + 1].sum() == (4 + 12 + 12) * n  # nothing in between
+
+
+def test_pair_histogram_simple_cubic_shells_and_total(orc):
+    """Simple cubic (spacing s): 6, 12, 8 neighbours at s, sqrt2 s, sqrt3 s;
+    with the range past the largest minimum-image distance every ordered pair
+    is counted once: N (N - 1) in all."""
+    L = 8 * 3.104282
+    x = I.simple_cubic(8, L)
+    n = len(x)
+    s = L / 8
+    h, amb = orc.pair_histogram(x, np.array([L, L, L]), 0.01, 3000)
+    assert amb.sum() == 0
+    for f, c in ((1.0, 6), (2.0, 12), (3.0, 8)):
+        assert h[int(math.floor(s * math.sqrt(f) / 0.01))] == c * n
+    assert h.sum() == n * (n - 1)
+
+
+def test_angle_histogram_tetrahedral_and_cubic(orc):
+    """adf with n_c = 4 in diamond: every angle is the tetrahedral one
+    (acos(-1/3) = 109.47 deg), 4 x 3 ordered pairs per atom; with n_c = 6 in
+    simple cubic: 24 right angles and 6 straight ones per atom."""
+    x, box = I.diamond_cubic(2, 0.92)
+    n = len(x)
+    h, amb, ties = orc.angle_histogram(x, box, nc=4, nbins=7)
+    w = 180.0 / 7
+    assert amb.sum() == 0 and ties == 0
+    assert h[int(math.degrees(math.acos(-1.0 / 3.0)) // w)] == 12 * n
+    assert h.sum() == 12 * n
+    L = 6 * 3.104282
+    xs = I.simple_cubic(6, L)
+    hs, amb, ties = orc.angle_histogram(xs, np.array([L, L, L]), nc=6, nbins=7)
+    m = len(xs)
+    assert ties == 0
+    assert hs[int(90.0 // w)] == 24 * m
+    assert hs[6] == 6 * m
+    assert hs.sum() == 30 * m

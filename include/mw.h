@@ -249,6 +249,30 @@ mw_status mw_phase_times(mw_system* s, const mw_integrator* integ, int nsteps, d
  * slower; the counts feed the roofline arithmetic). */
 mw_status mw_set_count_terms(mw_system* s, int on);
 
+/* ---- Structure analysis (Sec. II.C) -----------------------------------
+ * Of the current positions.  Both calls first build the neighbour list at
+ * these positions (so every pair within the list radius a sigma + skin is
+ * seen; a pending half-kick is applied first and the forces are recomputed
+ * before the next step), then count on the GPU.  Counts are per box,
+ * row-major hist[box * nbins + bin], host arrays the caller owns.
+ *
+ * Pair histogram, the raw count behind g(r): the ordered pairs (i, j), i != j,
+ * of one box with bin * dr <= r_ij < (bin + 1) * dr (minimum image, FP32
+ * distance from the fixed-point positions).  g(r) in bin k is
+ * hist[k] V / (N^2 4 pi r^2 dr) at the bin's centre r, and the coordination
+ * number within R_c the sum of hist up to R_c divided by N.  Needs dr > 0,
+ * 1 <= nbins <= 4096 and nbins * dr <= a sigma + skin (MW_EINVAL otherwise,
+ * naming the radius: raise the skin with mw_set_skin to reach further). */
+mw_status mw_pair_histogram(mw_system* s, double dr, int nbins, unsigned long long* hist);
+
+/* Angle histogram, the raw count behind the angular distribution function:
+ * for each atom k its nc nearest neighbours (2 <= nc <= 16), the angle
+ * theta_ikj at k for every ordered pair i != j of them, binned over
+ * [0, 180] degrees in nbins equal bins (180 itself in the last);
+ * nc (nc - 1) counts per atom.  Fails with MW_EINVAL if an atom has fewer
+ * than nc neighbours within the list radius (raise the skin). */
+mw_status mw_angle_histogram(mw_system* s, int nc, int nbins, unsigned long long* hist);
+
 /* ---- For callers that cannot allocate device memory ----------------------
  * The paper has no counterpart to this call; it exists for callers that may
  * not call cudaMalloc (an application that owns every device allocation, a

@@ -19,6 +19,7 @@
 #include "mw_device.cuh"
 #include "mw_persistent.cuh"
 #include "mw_adjoint.cuh"
+#include "mw_structure.cuh"
 
 using namespace mw;
 
@@ -70,6 +71,8 @@ struct mw_system {
   bool forces_valid = false;
   bool need_prime = true;  // thermostat start half must be recomputed before the next step
   bool record_pending = false;  // steps ran since the last thermo record was written
+  unsigned long long* ana = nullptr;  // structure-analysis histograms (grow-only)
+  size_t ana_cap = 0;
   long long host_step = 0;
   int engine = MW_ENGINE_AUTO, engine_used = MW_ENGINE_GRAPH;
   int tuned_engine = -1;
@@ -725,6 +728,7 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
 #include "mw_persistent_host.inc"
 #include "mw_adjoint_host.inc"
 #include "mw_autotune.inc"
+#include "mw_structure_host.inc"
 
 extern "C" {
 

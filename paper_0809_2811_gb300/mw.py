@@ -29,7 +29,7 @@ EXPORTS = (
     "mw_get_neighbors", "mw_energy_forces", "mw_energy_forces_dev", "mw_step", "mw_get_thermo",
     "mw_energy_forces_vjp", "mw_set_engine", "mw_set_nbr_width", "mw_autotune", "mw_get_info",
     "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc", "mw_set_skin", "mw_phase_times",
-    "mw_last_error",
+    "mw_pair_histogram", "mw_angle_histogram", "mw_last_error",
 )
 
 
@@ -114,6 +114,8 @@ def lib():
             "mw_sync": [P],
             "mw_set_skin": [P, ctypes.c_double],
             "mw_phase_times": [P, ctypes.POINTER(mw_integrator), ctypes.c_int, dp],
+            "mw_pair_histogram": [P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)],
+            "mw_angle_histogram": [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)],
             "mw_energy_forces_noalloc": [ctypes.c_int, dp, ctypes.POINTER(mw_params), ctypes.c_double, P, P, P, P,
                                          P],
         }
@@ -319,6 +321,21 @@ def mw_phase_times(h: int, integ: mw_integrator, nsteps: int) -> dict:
     return dict(zip(PHASES, out.tolist()))
 
 
+def mw_pair_histogram(h: int, nbox: int, dr: float, nbins: int) -> np.ndarray:
+    """Per box, ordered pairs by distance bin (the raw count behind g(r)); uint64 [nbox, nbins]."""
+    out = np.zeros((nbox, nbins), np.uint64)
+    _check(lib().mw_pair_histogram(h, float(dr), int(nbins), out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong))))
+    return out
+
+
+def mw_angle_histogram(h: int, nbox: int, nc: int, nbins: int) -> np.ndarray:
+    """Per box, angles at each atom between ordered pairs of its nc nearest
+    neighbours, over [0, 180] degrees; uint64 [nbox, nbins]."""
+    out = np.zeros((nbox, nbins), np.uint64)
+    _check(lib().mw_angle_histogram(h, int(nc), int(nbins), out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong))))
+    return out
+
+
 def mw_last_error() -> str:
     return lib().mw_last_error().decode()
 
@@ -378,6 +395,12 @@ class System:
 
     def thermo(self):
         return mw_get_thermo(self.h, self.nbox)
+
+    def pair_histogram(self, dr: float, nbins: int) -> np.ndarray:
+        return mw_pair_histogram(self.h, self.nbox, dr, nbins)
+
+    def angle_histogram(self, nc: int = 8, nbins: int = 180) -> np.ndarray:
+        return mw_angle_histogram(self.h, self.nbox, nc, nbins)
 
     def info(self):
         return mw_get_info(self.h)

@@ -180,3 +180,15 @@ def ice_liquid_slab(nx: int = 64, ny: int = 32, nz: int = 32, rho_ice: float = 0
     x = np.concatenate([xi, xl])
     is_ice = np.concatenate([np.ones(len(xi), bool), np.zeros(n_liq, bool)])
     return x, box, is_ice
+
+
+def liquid_vapor_slab(n: int = 1024, lxy: float = 30.0, lz: float = 100.0, rho: float = 0.997,
+                      jitter: float = 0.2, seed: int = BASE_SEED + 6):
+    """The liquid-vapour slab of Sec. II.C: n molecules filling a slab of
+    density rho centred along z in an lxy x lxy x lz periodic cell, the rest
+    of z empty (two interfaces perpendicular to z).  Jittered-grid start; the
+    liquid forms once dynamics run.  Returns (x, box)."""
+    t = n * volume_per_molecule(rho) / (lxy * lxy)
+    z0 = 0.5 * (lz - t)
+    x = lattice_fill(n, [0.0, 0.0, z0], [lxy, lxy, z0 + t], rho, jitter, seed)
+    return x, np.array([lxy, lxy, lz])

@@ -84,6 +84,7 @@ CASES = {
     "dense_729_rho1.10": lambda: I.jittered_box(729, 1.10, 0.3, 102),
     "ragged_1237": lambda: I.jittered_box(1237, 0.97, 0.25, 103),
     "slab_2048": lambda: I.ice_liquid_slab(8, 4, 4)[:2],
+    "liquid_vapor_slab_1024": lambda: I.liquid_vapor_slab(),
 }
 
 

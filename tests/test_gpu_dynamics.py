@@ -244,7 +244,7 @@ def test_liquid_vapor_slab_surface_tension(mwlib):
     V = float(np.prod(box))
     g = 0.5 * box[2] * 1e-10 * (w[:, 2] - 0.5 * (w[:, 0] + w[:, 1])) / V * KCAL_PER_A3_PA * 1e3  # mJ/m^2
     gamma, err = g.mean(), g.std(ddof=1) / math.sqrt(len(g))
-    assert 20.0 < gamma < 140.0, (gamma, err)
+    assert 40.0 < gamma < 95.0, (gamma, err)  # 1 ns of this run gives 66.2 +- 1.0; 100 ps: stderr ~3
     assert abs(np.mean(temps) - 300.0) < 10.0
     z = np.mod(xf[:, 2], box[2])
     assert z.min() > 5.0 and z.max() < box[2] - 5.0  # still a slab in the middle of the cell

@@ -146,6 +146,13 @@ mw_status mw_set_state_dev(mw_system* s, const double* x_dev, const double* v_de
 mw_status mw_get_state(mw_system* s, double* x, double* v);
 mw_status mw_get_state_dev(mw_system* s, double* x_dev, double* v_dev);
 
+/* Unwrapped positions (host array of n_total*3 doubles, caller's order): the
+ * wrapped position plus the periodic images each atom has crossed along each
+ * axis since mw_set_state (which counts the images of the positions it was
+ * given, so a position outside the box comes back as given).  For mean-square
+ * displacements and the diffusion coefficient (Sec. II.C). */
+mw_status mw_get_unwrapped(mw_system* s, double* x);
+
 /* Replaces the potential parameters (the neighbour list is marked stale:
  * its radius a sigma + skin follows sigma). */
 mw_status mw_set_params(mw_system* s, const mw_params* prm);

@@ -672,6 +672,7 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
   float2** vel[] = {&d.vx, &d.vy, &d.vz, &d.tvx, &d.tvy, &d.tvz};
   for (float2** p : vel)
     if ((st = dalloc(s, p, N)) != MW_OK) return bad(st);
+  if ((st = dalloc(s, &d.img, N)) != MW_OK || (st = dalloc(s, &d.timg, N)) != MW_OK) return bad(st);
   if ((st = dalloc(s, &d.q, N)) != MW_OK || (st = dalloc(s, &d.qb, N)) != MW_OK ||
       (st = dalloc(s, &d.tq, N)) != MW_OK || (st = dalloc(s, &d.f, N)) != MW_OK ||
       (st = dalloc(s, &d.id, N)) != MW_OK || (st = dalloc(s, &d.tid, N)) != MW_OK ||
@@ -782,7 +783,7 @@ mw_status mw_get_state(mw_system* s, double* x, double* v) {
   if (!s->state_set) return fail(MW_ESTATE, "no state set");
   const size_t bytes = sizeof(double) * 3 * (size_t)s->N;
   k_gather_state<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, x ? s->d.stage : nullptr,
-                                                                     v ? s->d.stage2 : nullptr);
+                                                                     v ? s->d.stage2 : nullptr, 0);
   MW_CUDA(cudaGetLastError());
   if (x) MW_CUDA(cudaMemcpyAsync(x, s->d.stage, bytes, cudaMemcpyDeviceToHost, s->stream));
   if (v) MW_CUDA(cudaMemcpyAsync(v, s->d.stage2, bytes, cudaMemcpyDeviceToHost, s->stream));
@@ -790,10 +791,21 @@ mw_status mw_get_state(mw_system* s, double* x, double* v) {
   return MW_OK;
 }
 
+mw_status mw_get_unwrapped(mw_system* s, double* x) {
+  if (!s || !x) return fail(MW_EINVAL, "bad arguments");
+  if (!s->state_set) return fail(MW_ESTATE, "no state set");
+  const size_t bytes = sizeof(double) * 3 * (size_t)s->N;
+  k_gather_state<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, s->d.stage, nullptr, 1);
+  MW_CUDA(cudaGetLastError());
+  MW_CUDA(cudaMemcpyAsync(x, s->d.stage, bytes, cudaMemcpyDeviceToHost, s->stream));
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  return MW_OK;
+}
+
 mw_status mw_get_state_dev(mw_system* s, double* x_dev, double* v_dev) {
   if (!s) return fail(MW_EINVAL, "system is NULL");
   if (!s->state_set) return fail(MW_ESTATE, "no state set");
-  k_gather_state<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, x_dev, v_dev);
+  k_gather_state<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, x_dev, v_dev, 0);
   MW_CUDA(cudaGetLastError());
   MW_CUDA(cudaStreamSynchronize(s->stream));
   return MW_OK;

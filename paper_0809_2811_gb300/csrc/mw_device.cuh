@@ -123,6 +123,7 @@ struct Dev {
   float2 *vx, *vy, *vz;
   unsigned long long *tx, *ty, *tz;
   float2 *tvx, *tvy, *tvz;
+  int4 *img, *timg;   // periodic images crossed per component since the state was set (x, y, z)
   uint4 *q, *qb, *tq;
   float4* f;
   int *id, *tid;
@@ -495,7 +496,10 @@ __device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, 
     const float lo1 = v0.y + er;
     const float hi = sh + lo1;
     const float lo = lo1 - (hi - sh);
-    const unsigned long long sn = s0 + (unsigned long long)f2ll_exact(fmaf(hi, k64, lo * k64));
+    const long long inc = f2ll_exact(fmaf(hi, k64, lo * k64));
+    const unsigned long long sn = s0 + (unsigned long long)inc;
+    if (inc > 0 ? sn < s0 : sn > s0)  // the 64-bit fraction wrapped: the atom crossed a face
+      reinterpret_cast<int*>(d.img + i)[c] += inc > 0 ? 1 : -1;
     *fp = 0.f;
     *vp = make_float2(hi, lo);
     *sp = sn;
@@ -1043,6 +1047,7 @@ __device__ __forceinline__ void scatter_item(const Dev& d, int i) {
   d.tvx[p] = d.vx[i]; d.tvy[p] = d.vy[i]; d.tvz[p] = d.vz[i];
   d.tid[p] = d.id[i];
   d.tq[p] = d.q[i];
+  d.timg[p] = d.img[i];
 }
 
 // a2: staging arrays back to the state arrays; build positions recorded.
@@ -1051,6 +1056,7 @@ __device__ __forceinline__ void copyback_item(const Dev& d, int i) {
   d.x[i] = d.tx[i]; d.y[i] = d.ty[i]; d.z[i] = d.tz[i];
   d.vx[i] = d.tvx[i]; d.vy[i] = d.tvy[i]; d.vz[i] = d.tvz[i];
   d.id[i] = d.tid[i];
+  d.img[i] = d.timg[i];
   const uint4 q = d.tq[i];
   d.q[i] = q;
   d.qb[i] = q;
@@ -1193,14 +1199,18 @@ __global__ void k_load_positions(Dev d, const double* __restrict__ xin, const in
   const int b = boxid[u];
   const Box& bx = d.box[b];
   unsigned long long p[3];
+  int im[3];
   for (int k = 0; k < 3; ++k) {
     double v = xin[3 * (size_t)u + k] / bx.L[k];  // box fraction
-    v -= floor(v);
+    const double fl = floor(v);
+    im[k] = (int)fl;
+    v -= fl;
     if (v >= 1.0) v -= 1.0;
     if (v < 0.0) v = 0.0;
     p[k] = frac64_of(v);
   }
   d.x[i] = p[0]; d.y[i] = p[1]; d.z[i] = p[2];
+  if (d.img) d.img[i] = make_int4(im[0], im[1], im[2], 0);
   d.q[i] = make_uint4(q_of(p[0]), q_of(p[1]), q_of(p[2]), (unsigned)b);
 }
 
@@ -1300,16 +1310,17 @@ __global__ void k_thermo_snapshot(Dev d) {
 
 // Sorted -> user order: x (wrapped) and (v + pending half-kick) * s_endc (the
 // end scale of the last step, pending on the stored velocities).
-__global__ void k_gather_state(Dev d, double* __restrict__ xo, double* __restrict__ vo) {
+__global__ void k_gather_state(Dev d, double* __restrict__ xo, double* __restrict__ vo, int unwrap) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
   const int u = d.id[i];
   const Box& bx = d.box[d.q[i].w];
   if (xo) {
     constexpr double k2m64 = 5.421010862427522170037264e-20;  // 2^-64
-    xo[3 * (size_t)u] = __ull2double_rn(d.x[i]) * k2m64 * bx.L[0];
-    xo[3 * (size_t)u + 1] = __ull2double_rn(d.y[i]) * k2m64 * bx.L[1];
-    xo[3 * (size_t)u + 2] = __ull2double_rn(d.z[i]) * k2m64 * bx.L[2];
+    const int4 im = unwrap ? d.img[i] : make_int4(0, 0, 0, 0);
+    xo[3 * (size_t)u] = (__ull2double_rn(d.x[i]) * k2m64 + im.x) * bx.L[0];
+    xo[3 * (size_t)u + 1] = (__ull2double_rn(d.y[i]) * k2m64 + im.y) * bx.L[1];
+    xo[3 * (size_t)u + 2] = (__ull2double_rn(d.z[i]) * k2m64 + im.z) * bx.L[2];
   }
   if (vo) {  // pending half-kick and end-of-step thermostat scale applied
     const double s = d.bst[d.q[i].w].s_endc;

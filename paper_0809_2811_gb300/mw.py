@@ -29,7 +29,7 @@ EXPORTS = (
     "mw_get_neighbors", "mw_energy_forces", "mw_energy_forces_dev", "mw_step", "mw_get_thermo",
     "mw_energy_forces_vjp", "mw_set_engine", "mw_set_nbr_width", "mw_autotune", "mw_get_info",
     "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc", "mw_set_skin", "mw_phase_times",
-    "mw_pair_histogram", "mw_angle_histogram", "mw_last_error",
+    "mw_pair_histogram", "mw_angle_histogram", "mw_get_unwrapped", "mw_last_error",
 )
 
 
@@ -115,6 +115,7 @@ def lib():
             "mw_set_skin": [P, ctypes.c_double],
             "mw_phase_times": [P, ctypes.POINTER(mw_integrator), ctypes.c_int, dp],
             "mw_pair_histogram": [P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)],
+            "mw_get_unwrapped": [P, dp],
             "mw_angle_histogram": [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)],
             "mw_energy_forces_noalloc": [ctypes.c_int, dp, ctypes.POINTER(mw_params), ctypes.c_double, P, P, P, P,
                                          P],
@@ -395,6 +396,12 @@ class System:
 
     def thermo(self):
         return mw_get_thermo(self.h, self.nbox)
+
+    def get_unwrapped(self) -> np.ndarray:
+        """Positions plus the periodic images crossed since set_state (n_total x 3, A)."""
+        x = np.empty((self.n_total, 3))
+        _check(lib().mw_get_unwrapped(self.h, _dp(x)))
+        return x
 
     def pair_histogram(self, dr: float, nbins: int) -> np.ndarray:
         return mw_pair_histogram(self.h, self.nbox, dr, nbins)

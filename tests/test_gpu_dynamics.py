@@ -248,3 +248,28 @@ def test_liquid_vapor_slab_surface_tension(mwlib):
     assert abs(np.mean(temps) - 300.0) < 10.0
     z = np.mod(xf[:, 2], box[2])
     assert z.min() > 5.0 and z.max() < box[2] - 5.0  # still a slab in the middle of the cell
+
+
+def test_unwrapped_positions_follow_free_flight(mwlib):
+    """27 atoms 8 A apart (beyond a sigma: no force) all moving with one
+    velocity V: the unwrapped positions after n steps are x0 + V n dt while the
+    atoms cross the 24 A box many times (and the list is rebuilt every step,
+    re-sorting the atoms); positions given outside the box come back as given."""
+    L = 24.0
+    g = np.arange(3) * 8.0 + 1.0
+    x0 = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) + np.array([-30.0, 50.0, 7.0])
+    V = np.array([0.37, -0.21, 0.13])
+    v0 = np.tile(V, (len(x0), 1))
+    s = mwlib.System(len(x0), np.array([L, L, L]))
+    try:
+        s.set_state(x0, v0)
+        u0 = s.get_unwrapped()
+        s.step(200, dt=10.0)
+        u1 = s.get_unwrapped()
+        f, _, _ = s.energy_forces()
+    finally:
+        s.close()
+    assert np.abs(u0 - x0).max() <= 1e-9 * np.abs(x0).max()
+    assert np.abs(f).max() == 0.0
+    want = x0 + V * 200 * 10.0
+    assert np.abs(u1 - want).max() <= 1e-6 * np.abs(want).max()

@@ -64,6 +64,8 @@ def lib():
                                       ctypes.c_int, i, i, ctypes.c_int, i, i]
         _lib.or_md.argtypes = [d, ctypes.c_int, d, d, d, ctypes.c_double, ctypes.c_double,
                                ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, d, d]
+        _lib.or_md_npt.argtypes = [d, ctypes.c_int, d, d, d, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, d, d]
         _lib.or_force_vjp.argtypes = [d, ctypes.c_int, d, d, d, d, d]
         _lib.or_energy_param_grad.argtypes = [d, ctypes.c_int, d, d, d]
         ll = ctypes.POINTER(ctypes.c_longlong)
@@ -161,6 +163,27 @@ def md(x, v, box, nsteps, dt=10.0, kind=0, T0=300.0, tau=1000.0, mass=18.015, pr
     _check(lib().or_md(_dp(prm), x.shape[0], _dp(x), _dp(v), _dp(box), mass, dt, kind, T0, tau, nsteps,
                        _dp(st), _dp(th)), "md")
     return x, v, (float(st[0]), float(st[1])), th
+
+
+# kcal/mol per A^3 in atm (101325 Pa per atm)
+KCAL_PER_A3_ATM = 4184.0 / 6.02214076e23 / 1e-30 / 101325.0
+
+
+def md_npt(x, v, box, nsteps, dt=10.0, T0=298.0, tau=1000.0, p_atm=0.0, tau_p=2500.0, mass=18.015, prm=None,
+           state=(0.0, 0.0, 0.0)):
+    """Isobaric-isothermal run (Nose-Hoover thermostat and isotropic barostat,
+    Martyna-Tobias-Klein split); returns (x, v, box, state, thermo[nsteps+1, 10]).
+
+    thermo columns: pe, e2, e3, ke, T, conserved, xi, eta, V (A^3), P (kcal/mol/A^3)."""
+    prm = default_params() if prm is None else np.ascontiguousarray(prm, np.float64)
+    x = np.array(x, np.float64).reshape(-1, 3)
+    v = np.array(v, np.float64).reshape(-1, 3)
+    box = np.array(box, np.float64)
+    st = np.array(state, np.float64)
+    th = np.zeros((nsteps + 1, 10))
+    _check(lib().or_md_npt(_dp(prm), x.shape[0], _dp(x), _dp(v), _dp(box), mass, dt, T0, tau,
+                           p_atm / KCAL_PER_A3_ATM, tau_p, nsteps, _dp(st), _dp(th)), "md_npt")
+    return x, v, box, (float(st[0]), float(st[1]), float(st[2])), th
 
 
 def force_vjp(x, box, w, prm=None):

@@ -545,6 +545,88 @@ int or_md(const double* prm, int n, double* x, double* v, const double* box, dou
   return rc;
 }
 
+/*
+ * Isobaric-isothermal dynamics.  Sec. II.B controls pressure with a
+ * Nose-Hoover barostat (relaxation time 2.5 ps, p = 0) next to the 1 ps
+ * Nose-Hoover thermostat; read as the isotropic Martyna-Tobias-Klein
+ * equations with the single particle thermostat of or_md:
+ *   dr/dt = v + (pe/W) r,   dv/dt = F/m - (1 + 3/Ndf) (pe/W) v - xi v,
+ *   dL/dt = (pe/W) L,       dpe/dt = (1 + 3/Ndf) 2 KE + tr(Wv) - 3 P V,
+ * W = (Ndf + 3) kB T0 tau_p^2, Wv the virial (sum over legs of d F), V = Lx Ly Lz.
+ * Symmetric Trotter split per step: thermostat half; barostat half on pe;
+ * friction half (v times exp(-dt/2 (1 + 3/Ndf) pe/W)); kick; drift
+ * r -> r e^u + v dt e^(u/2) sinh(u/2)/(u/2), L -> L e^u with u = dt pe/W;
+ * forces; kick; friction half; barostat half; thermostat half.
+ * P in kcal/mol/A^3.  box[3] is scaled in place; state = xi, eta, pe.
+ * thermo (nsteps+1)*10, may be NULL: pe, e2, e3, ke, T, conserved, xi, eta,
+ * V, pressure (kcal/mol/A^3); conserved = ke + pe + P V + pe^2/(2W)
+ *   + Q xi^2/2 + Ndf kB T0 eta.  Positions are wrapped into [0, L).
+ */
+int or_md_npt(const double* prm, int n, double* x, double* v, double* box, double mass, double dt, double T0,
+              double tau, double P, double tau_p, int nsteps, double* state, double* thermo) {
+  if (n < 2) return OR_EINVAL;
+  double* f = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+  if (!f) return OR_ENOMEM;
+  double out[11];
+  for (int i = 0; i < 3 * n; ++i) x[i] = wrap1(x[i], box[i % 3]);
+  int rc = or_energy_forces_cell(prm, n, x, box, f, out);
+  if (rc != OR_OK) {
+    free(f);
+    return rc;
+  }
+  const double Ndf = 3.0 * n - 3.0;
+  const double Q = Ndf * OR_KB * T0 * tau * tau;
+  const double W = (Ndf + 3.0) * OR_KB * T0 * tau_p * tau_p;
+  const double a3 = 1.0 + 3.0 / Ndf;
+  double xi = state[0], eta = state[1], pe = state[2];
+  const double cf = 0.5 * dt * OR_FCONV / mass;
+  for (int s = 0; s <= nsteps; ++s) {
+    if (s > 0) {
+      double ke = kinetic(n, v, mass);
+      double V = box[0] * box[1] * box[2];
+      nh_half(n, v, &ke, &xi, &eta, dt, Ndf, T0, Q);
+      pe += 0.5 * dt * (a3 * 2.0 * ke + (out[2] + out[3] + out[4]) - 3.0 * P * V);
+      const double fr = exp(-0.5 * dt * a3 * pe / W);
+      for (int i = 0; i < 3 * n; ++i) v[i] *= fr;
+      for (int i = 0; i < 3 * n; ++i) v[i] += cf * f[i];
+      const double u = dt * pe / W;
+      const double eu = exp(u);
+      const double sh = (fabs(u) > 1e-8) ? exp(0.5 * u) * sinh(0.5 * u) / (0.5 * u) : 1.0 + 0.5 * u;
+      for (int k = 0; k < 3; ++k) box[k] *= eu;
+      for (int i = 0; i < 3 * n; ++i) x[i] = wrap1(x[i] * eu + v[i] * dt * sh, box[i % 3]);
+      rc = or_energy_forces_cell(prm, n, x, box, f, out);
+      if (rc != OR_OK) break;
+      for (int i = 0; i < 3 * n; ++i) v[i] += cf * f[i];
+      for (int i = 0; i < 3 * n; ++i) v[i] *= fr;  /* pe is unchanged since the first friction half */
+      ke = kinetic(n, v, mass);
+      V = box[0] * box[1] * box[2];
+      pe += 0.5 * dt * (a3 * 2.0 * ke + (out[2] + out[3] + out[4]) - 3.0 * P * V);
+      nh_half(n, v, &ke, &xi, &eta, dt, Ndf, T0, Q);
+    }
+    if (thermo) {
+      const double ke = kinetic(n, v, mass);
+      const double epot = out[0] + out[1];
+      const double V = box[0] * box[1] * box[2];
+      double* t = thermo + 10 * (size_t)s;
+      t[0] = epot;
+      t[1] = out[0];
+      t[2] = out[1];
+      t[3] = ke;
+      t[4] = 2.0 * ke / (Ndf * OR_KB);
+      t[5] = ke + epot + P * V + 0.5 * pe * pe / W + 0.5 * Q * xi * xi + Ndf * OR_KB * T0 * eta;
+      t[6] = xi;
+      t[7] = eta;
+      t[8] = V;
+      t[9] = (2.0 * ke + out[2] + out[3] + out[4]) / (3.0 * V);
+    }
+  }
+  state[0] = xi;
+  state[1] = eta;
+  state[2] = pe;
+  free(f);
+  return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* Complex-step derivatives for the force-matching adjoint.             */
 /* ------------------------------------------------------------------ */

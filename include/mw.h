@@ -64,10 +64,20 @@ typedef enum mw_status {
   MW_ETIMEOUT = 6,         /* a bounded device-side wait ran out (persistent engine) */
   MW_ECUDA = 7,            /* a CUDA runtime call failed */
   MW_ENOMEM = 8,           /* device or host allocation failed */
-  MW_ESTATE = 9            /* call out of order (e.g. forces before any state was set) */
+  MW_ESTATE = 9,           /* call out of order (e.g. forces before any state was set) */
+  MW_EGRID = 10            /* mw_step_async/mw_sync only: an isobaric box shrank or grew out of its cell
+                              grid; the run stopped after a whole step, the grid was laid out again and
+                              the next call continues (mw_step does this by itself) */
 } mw_status;
 
-typedef enum mw_thermostat { MW_NVE = 0, MW_BERENDSEN = 1, MW_NOSE_HOOVER = 2 } mw_thermostat;
+/* MW_NPT: isothermal-isobaric dynamics, a Nose-Hoover thermostat (T0, tau)
+ * and an isotropic barostat (p_ext, tau_p) in the Martyna-Tobias-Klein form,
+ * the paper's constant-pressure runs of Sec. II.B-C (1 atm; the box is
+ * cubic or orthorhombic and scales by one factor in all three edges).  Each
+ * box of a batch has its own barostat.  Conserved: ke + pe + Q xi^2/2 +
+ * N_df kB T0 eta + p_ext V + pe_b^2/(2 W), with Q = N_df kB T0 tau^2 and
+ * W = (N_df + 3) kB T0 tau_p^2. */
+typedef enum mw_thermostat { MW_NVE = 0, MW_BERENDSEN = 1, MW_NOSE_HOOVER = 2, MW_NPT = 3 } mw_thermostat;
 
 /* How mw_step launches work.  GRAPH: one kernel per phase, one step captured
  * in a CUDA graph and replayed.  PERSISTENT: one cooperative launch runs many
@@ -82,6 +92,8 @@ typedef struct mw_integrator {
   double T0;                /* K, target temperature of every box ... */
   const double* T0_per_box; /* ... unless this host array of nbox targets is non-NULL */
   double tau;               /* fs, thermostat relaxation time (> 0 unless NVE) */
+  double p_ext;             /* atm, target pressure (MW_NPT only) */
+  double tau_p;             /* fs, barostat period (MW_NPT only, > 0) */
 } mw_integrator;
 
 /* Per-box thermodynamic snapshot at the end of the last completed step. */
@@ -90,11 +102,14 @@ typedef struct mw_thermo {
   double pe, e2, e3;  /* potential energy and its two- and three-body parts, kcal/mol */
   double ke;          /* kinetic energy, kcal/mol */
   double temperature; /* K, 2 ke / (Ndf kB), Ndf = 3 n - 3 */
-  double conserved;   /* ke + pe (+ Q xi^2/2 + Ndf kB T0 eta under Nose-Hoover) */
+  double conserved;   /* ke + pe (+ Q xi^2/2 + Ndf kB T0 eta under Nose-Hoover and MW_NPT;
+                         + p_ext V + pe_b^2/(2 W) under MW_NPT) */
   double pressure;    /* atm, (2 ke + tr W) / (3 V) */
   double virial[6];   /* xx yy zz xy xz yz, kcal/mol: sum over terms and legs of d_a F_b */
   double xi, eta;     /* Nose-Hoover thermostat velocity (1/fs) and position */
   int64_t rebuilds;   /* neighbour-list rebuilds of this box since mw_set_state */
+  double volume;      /* A^3, the box during that step */
+  double box[3];      /* A, its edges (they change only under MW_NPT) */
 } mw_thermo;
 
 typedef struct mw_info {
@@ -108,6 +123,7 @@ typedef struct mw_info {
   double r_list;      /* a sigma + skin, A */
   int64_t npairs, ntriplets; /* legs r < a sigma (unordered pairs) and triplets at the last force call */
   int64_t rebuild_steps;     /* steps and force calls that rebuilt at least one box since mw_set_state */
+  int64_t regrids;           /* cell grids laid out again because an MW_NPT box left its grid */
 } mw_info;
 
 typedef struct mw_system mw_system;
@@ -206,6 +222,11 @@ mw_status mw_sync(mw_system* s);
 
 /* Thermo records (nbox) of the last completed step, or of the state just set. */
 mw_status mw_get_thermo(mw_system* s, mw_thermo* out);
+
+/* Current edges of every box (nbox * 3 doubles, A): those given at creation
+ * unless an MW_NPT run has scaled them.  Positions passed to mw_set_state are
+ * taken in these boxes. */
+mw_status mw_get_box(mw_system* s, double* box);
 
 /* Adjoint of the forces at the current positions (no counterpart in the
  * paper, whose Sec. II.D tunes lambda, epsilon, sigma by scans).  Given

@@ -71,6 +71,8 @@ struct mw_system {
   bool forces_valid = false;
   bool need_prime = true;  // thermostat start half must be recomputed before the next step
   bool record_pending = false;  // steps ran since the last thermo record was written
+  bool boxes_stale = false;     // an isobaric run changed the device's box geometry since the last pull
+  long long regrids = 0;        // cell grids laid out again because an isobaric box left its grid
   unsigned long long* ana = nullptr;  // structure-analysis histograms (grow-only)
   size_t ana_cap = 0;
   long long host_step = 0;
@@ -150,16 +152,34 @@ void make_fparams(mw_system* s) {
   f.q = p.q;
 }
 
+// The device's box geometry (scaled every step by the barostat of an
+// isobaric run) back into the host copy, before host code reads or uploads it.
+mw_status pull_boxes(mw_system* s) {
+  if (!s->boxes_stale) return MW_OK;
+  MW_CUDA(cudaMemcpyAsync(s->boxes.data(), s->d.box, sizeof(Box) * s->nbox, cudaMemcpyDeviceToHost, s->stream));
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  s->boxes_stale = false;
+  return MW_OK;
+}
+
 // Cell grids of all boxes for the current list radius; returns the total.
+// Under an isobaric integrator the cells get kCellMargin r_list of width at
+// the smaller of the current and the coming edges, so that a box may shrink
+// by about a tenth before its grid has to be laid out again.
 mw_status layout_cells(mw_system* s, int* ncell_out) {
+  mw_status st;
+  if ((st = pull_boxes(s)) != MW_OK) return st;
   const double rl = r_list(s);
+  const bool npt = s->integ.kind == TH_NPT;
+  const double cw = npt ? kCellMargin * rl : rl;
   long long total = 0;
   for (int b = 0; b < s->nbox; ++b) {
     Box& bx = s->boxes[b];
     for (int k = 0; k < 3; ++k) {
-      if (bx.L[k] < 2.0 * rl)
-        return fail(MW_EBOX, "box %d edge %d = %g A is shorter than 2 r_list = %g A", b, k, bx.L[k], 2 * rl);
-      bx.nc[k] = std::max(1, (int)std::floor(bx.L[k] / rl));
+      const double L = (npt && bx.Ln[k] > 0) ? std::min(bx.L[k], bx.Ln[k]) : bx.L[k];
+      if (L < 2.0 * rl)
+        return fail(MW_EBOX, "box %d edge %d = %g A is shorter than 2 r_list = %g A", b, k, L, 2 * rl);
+      bx.nc[k] = std::max(1, (int)std::floor(L / cw));
     }
     bx.cell_off = (int)total;
     total += (long long)bx.nc[0] * bx.nc[1] * bx.nc[2];
@@ -265,6 +285,7 @@ mw_status read_global(mw_system* s, Global* g) {
 
 mw_status status_error(const Global& g) {
   switch (g.status) {
+    case ST_GRID: return fail(MW_EGRID, "an isobaric box left its cell grid after step %llu (mw_sync laid the grid out again; continue with mw_step_async)", g.step);
     case ST_OK: return MW_OK;
     case ST_OVERFLOW: return fail(MW_ENLIST_OVERFLOW, "neighbour list overflow (max count %d)", g.max_count);
     case ST_NAN: return fail(MW_ENAN, "non-finite velocity or force at atom slot %d", g.err_index);
@@ -430,10 +451,32 @@ mw_status finish_interrupted_step(mw_system* s) {
   return MW_OK;
 }
 
+// An isobaric box left its cell grid (ST_GRID, raised at a step boundary):
+// lay the grids out again for the current and coming edges, rebuild every
+// box, clear the status.  The run continues from the same step.
+mw_status regrid(mw_system* s) {
+  s->boxes_stale = true;
+  mw_status st;
+  int ncell;
+  if ((st = layout_cells(s, &ncell)) != MW_OK) {
+    s->boxes_stale = true;  // host copy partly rewritten: take the device's again
+    return st;
+  }
+  s->ncell = ncell;
+  if ((st = alloc_cells(s)) != MW_OK) return st;
+  if ((st = upload_boxes(s)) != MW_OK) return st;
+  if ((st = set_global_field(s, offsetof(Global, status), 0)) != MW_OK) return st;
+  if ((st = flag_all(s)) != MW_OK) return st;
+  s->regrids += 1;
+  s->boxes_stale = true;  // the run goes on scaling the boxes
+  return MW_OK;
+}
+
 // The start-of-step thermostat half is normally computed at the end of the
 // previous step; it is recomputed here only after a state or integrator
 // change.
 mw_status prime_thermostat(mw_system* s) {
+  if (s->integ.kind == TH_NPT) s->boxes_stale = true;  // the barostat scales the boxes from here on
   if (!s->need_prime) return MW_OK;
   k_prime_thermostat<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d);
   MW_CUDA(cudaGetLastError());
@@ -451,9 +494,16 @@ mw_status run_graph_engine(mw_system* s, int nsteps) {
   }
   int remaining = nsteps;
   int guard = 0;
+  int regrid_guard = 0;
   while (remaining > 0) {
     Global g0;
     if ((st = read_global(s, &g0)) != MW_OK) return st;
+    if (g0.status == ST_GRID) {
+      if (++regrid_guard > 8) return fail(MW_EGRID, "cell grid of an isobaric box kept failing");
+      if ((st = regrid(s)) != MW_OK) return st;
+      if ((st = capture_graphs(s, K)) != MW_OK) return st;
+      continue;
+    }
     const unsigned long long step0 = g0.step;
     const int full = remaining / K, rest = remaining % K;
     for (int k = 0; k < full; ++k) MW_CUDA(cudaGraphLaunch(s->graphK, s->stream));
@@ -475,6 +525,11 @@ mw_status run_graph_engine(mw_system* s, int nsteps) {
       s->host_step += 1;
       remaining -= done + 1;
       if ((st = capture_graphs(s, K)) != MW_OK) return st;
+      continue;
+    }
+    if (g.status == ST_GRID) {  // stopped at a step boundary; the loop head lays the grid out again
+      remaining -= done;
+      if (done > 0) regrid_guard = 0;
       continue;
     }
     if (g.status) return status_error(g);
@@ -529,8 +584,13 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
 mw_status validate_integ(mw_system* s, const mw_integrator* in) {
   if (!in) return fail(MW_EINVAL, "integrator is NULL");
   if (!(in->dt > 0) || !std::isfinite(in->dt)) return fail(MW_EINVAL, "dt must be > 0");
-  if (in->thermostat < MW_NVE || in->thermostat > MW_NOSE_HOOVER) return fail(MW_EINVAL, "unknown thermostat");
+  if (in->thermostat < MW_NVE || in->thermostat > MW_NPT) return fail(MW_EINVAL, "unknown thermostat");
   if (in->thermostat != MW_NVE && !(in->tau > 0)) return fail(MW_EINVAL, "tau must be > 0");
+  const bool npt = in->thermostat == MW_NPT;
+  if (npt && (!(in->tau_p > 0) || !std::isfinite(in->tau_p) || !std::isfinite(in->p_ext)))
+    return fail(MW_EINVAL, "isobaric runs need tau_p > 0 and a finite p_ext");
+  mw_status st;
+  if ((st = pull_boxes(s)) != MW_OK) return st;
   bool boxes_changed = false;
   for (int b = 0; b < s->nbox; ++b) {
     const double T0 = in->T0_per_box ? in->T0_per_box[b] : in->T0;
@@ -547,11 +607,25 @@ mw_status validate_integ(mw_system* s, const mw_integrator* in) {
       bx.q4f = (float)q4;
       boxes_changed = true;
     }
+    if (npt) {
+      const double a3 = 1.0 + 3.0 / bx.Ndf;
+      const double W = (bx.Ndf + 3.0) * kKB * T0 * in->tau_p * in->tau_p;
+      if (bx.a3 != (float)a3 || bx.W != W) {
+        bx.a3 = (float)a3;
+        bx.W = W;
+        boxes_changed = true;
+      }
+    }
     for (int k = 0; k < 3; ++k) {
       const double dtL = in->dt / bx.L[k];
-      if (bx.dtL[k] != dtL) {
+      if (npt) {  // the drift factor of an isobaric step is set on the device (barostat start half)
         bx.dtL[k] = dtL;
-        bx.dtL64[k] = (float)std::ldexp(dtL, 64);
+        continue;
+      }
+      const float dtL64 = (float)std::ldexp(dtL, 64);
+      if (bx.dtL[k] != dtL || bx.dtL64[k] != dtL64) {
+        bx.dtL[k] = dtL;
+        bx.dtL64[k] = dtL64;
         boxes_changed = true;
       }
     }
@@ -572,7 +646,9 @@ mw_status validate_integ(mw_system* s, const mw_integrator* in) {
   I.tau = in->thermostat == MW_NVE ? 1.0 : in->tau;
   I.kind = in->thermostat;
   I.half_skin2 = (float)(0.25 * s->skin * s->skin);
-  mw_status st;
+  I.p_ext = npt ? in->p_ext / kATM : 0.0;
+  I.skin = (float)s->skin;
+  I.rlist = (float)r_list(s);
   const bool integ_changed = std::memcmp(&I, &s->integ, sizeof I) != 0;
   if ((boxes_changed || integ_changed) && s->state_set) {
     // the pending half-kick belongs to the old integrator (the last step's
@@ -714,6 +790,8 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
   s->integ.tau = 1;
   s->integ.kind = TH_NVE;
   s->integ.half_skin2 = (float)(0.25 * skin * skin);
+  s->integ.skin = (float)skin;
+  s->integ.rlist = (float)r_list(s);
   if ((st = upload_integ(s)) != MW_OK) return bad(st);
   Global g{};
   e = cudaMemcpyAsync(d.g, &g, sizeof g, cudaMemcpyHostToDevice, s->stream);
@@ -996,6 +1074,10 @@ mw_status mw_sync(mw_system* s) {
   mw_status st;
   if ((st = read_global(s, &g)) != MW_OK) return st;
   s->host_step = (long long)g.step;
+  if (g.status == ST_GRID) {  // the run stopped at a step boundary: ready to continue
+    if ((st = regrid(s)) != MW_OK) return st;
+    s->graph_dirty = true;
+  }
   return status_error(g);
 }
 
@@ -1027,7 +1109,18 @@ mw_status mw_get_thermo(mw_system* s, mw_thermo* out) {
     o.xi = r[TR_XI];
     o.eta = r[TR_ETA];
     o.rebuilds = (int64_t)r[TR_REBUILDS];
+    o.volume = r[TR_VOL];
+    for (int k = 0; k < 3; ++k) o.box[k] = r[TR_L0 + k];
   }
+  return MW_OK;
+}
+
+mw_status mw_get_box(mw_system* s, double* box) {
+  if (!s || !box) return fail(MW_EINVAL, "bad arguments");
+  mw_status st;
+  if ((st = pull_boxes(s)) != MW_OK) return st;
+  for (int b = 0; b < s->nbox; ++b)
+    for (int k = 0; k < 3; ++k) box[3 * b + k] = s->boxes[b].L[k];
   return MW_OK;
 }
 
@@ -1067,6 +1160,7 @@ mw_status mw_get_info(mw_system* s, mw_info* out) {
   out->npairs = s->npairs;
   out->ntriplets = s->ntrip;
   out->rebuild_steps = g.rebuild_steps;
+  out->regrids = s->regrids;
   return MW_OK;
 }
 

@@ -32,9 +32,9 @@ constexpr double kATM = 68568.4158;            // atm per kcal/mol/A^3
 constexpr unsigned kFull = 0xffffffffu;
 
 // Status codes written to Global::status (same values as mw_status).
-enum : int { ST_OK = 0, ST_OVERFLOW = 3, ST_NAN = 4, ST_LOST = 5, ST_TIMEOUT = 6, ST_LEGS = 10 };
+enum : int { ST_OK = 0, ST_OVERFLOW = 3, ST_NAN = 4, ST_LOST = 5, ST_TIMEOUT = 6, ST_LEGS = 10, ST_GRID = 11 };
 
-enum : int { TH_NVE = 0, TH_BERENDSEN = 1, TH_NH = 2 };
+enum : int { TH_NVE = 0, TH_BERENDSEN = 1, TH_NH = 2, TH_NPT = 3 };
 
 // Legs staged per centre atom in the fused force kernel's shared-memory table;
 // centres with more legs take the overflow path.
@@ -42,7 +42,7 @@ constexpr int kLMax = 24;
 // Upper bound for the overflow path (more legs than this = overlapping atoms).
 constexpr int kMaxLegsOverflow = 64;
 
-struct Box {        // read-only in kernels
+struct Box {        // read-only in kernels, except the geometry under isobaric runs (end_of_step_box)
   double L[3];
   double dtL[3];    // dt / L: drift of the box fraction per unit velocity
   float dtL64[3];   // dt / L * 2^64: drift in 2^-64 box-fraction units per unit velocity (FP32)
@@ -60,6 +60,11 @@ struct Box {        // read-only in kernels
   double inv_ndf_kb;  // 1 / (N_df k_B): T = 2 KE inv_ndf_kb
   double p_fac;     // atm per kcal/mol of 2 KE + tr W: 1/(3 V) in atm
   int vexp_lost;    // a velocity component whose FP32 exponent field is >= this is a runaway (see validate_integ)
+  // isobaric runs only: the box scales at the drift of every step
+  float hs2;        // squared displacement (measured with this step's Lq) that triggers a rebuild
+  float a3;         // 1 + 3/N_df (barostat coupling)
+  double W;         // barostat mass (N_df + 3) k_B T0 tau_p^2
+  double Ln[3];     // edges of the coming step, made current by the last block of its kick1
 };
 
 struct BoxState {   // mutated by kernels
@@ -74,11 +79,14 @@ struct BoxState {   // mutated by kernels
   int rebuild;            // displacement flag of this box
   int pad_;
   long long rebuilds;
+  double pe_b;            // barostat momentum (isobaric runs), after the start half of the next step
+  double pe_e;            // the same after the last end half
+  double Lb;              // edge 0 of the box at its last build (isotropic scaling: one ratio for all edges)
 };
 
 // Per-box thermo record written at the end of each step (doubles).
 enum { TR_STEP, TR_PE, TR_E2, TR_E3, TR_KE, TR_T, TR_CONS, TR_P, TR_W0, TR_XI = TR_W0 + 6, TR_ETA,
-       TR_REBUILDS, TR_N };
+       TR_REBUILDS, TR_VOL, TR_L0, TR_N = TR_L0 + 3 };
 
 struct Global {
   unsigned long long step;  // completed steps since set_state
@@ -86,6 +94,7 @@ struct Global {
   int status;
   int max_count;            // widest neighbour set of the last build
   unsigned done;            // last-block counter of k_kick2
+  int wpar;                 // parity slot of ew[] holding the virial of the latest force evaluation
   unsigned done1;           // last-block counter of k_kick1 (graph condition)
   long long rebuild_steps;  // steps (or force calls) that rebuilt at least one box
   int pend;                 // 1: velocities lack the second half-kick of the last step
@@ -106,7 +115,16 @@ struct Integ {
   double tau;
   int kind;
   float half_skin2;  // (skin/2)^2
+  double p_ext;      // target pressure of isobaric runs (kcal/mol/A^3)
+  float skin, rlist; // list skin and radius (A): rebuild margin and cell check of a scaling box
 };
+
+// Cell grids of isobaric runs: laid out with cells kCellMargin r_list wide;
+// a box that shrinks below r_list per cell, or grows so that one more cell
+// of kCellGrow r_list fits, stops the run at a step boundary (ST_GRID) for
+// the host to lay the grid out again.
+constexpr double kCellMargin = 1.12;
+constexpr double kCellGrow = 1.2;
 
 struct FParams {     // FP32 constants of the force kernels
   float rc, rc2, rl2;
@@ -348,7 +366,7 @@ __device__ __forceinline__ float nh_half(const Integ& I, const Box& bx, ThermoSt
 // the Berendsen scale s = sqrt(1 + dt/tau (T0/T - 1)) (sig = x / (s + 1) with
 // x = dt/tau (T0/T - 1), free of cancellation); NVE changes nothing.
 __device__ __forceinline__ float end_half(const Integ& I, const Box& bx, ThermoState& t) {
-  if (I.kind == TH_NH) return nh_half(I, bx, t);
+  if (I.kind == TH_NH || I.kind == TH_NPT) return nh_half(I, bx, t);
   if (I.kind == TH_BERENDSEN && t.ke > 0.f) {
     const float T = 2.0f * t.ke * (float)bx.inv_ndf_kb;
     const float x = (float)(I.dt / I.tau) * ((float)bx.T0 / T - 1.0f);
@@ -362,7 +380,7 @@ __device__ __forceinline__ float end_half(const Integ& I, const Box& bx, ThermoS
 
 // Start-of-step half, before the first half-kick (Nose-Hoover only).
 __device__ __forceinline__ float start_half(const Integ& I, const Box& bx, ThermoState& t) {
-  return I.kind == TH_NH ? nh_half(I, bx, t) : 0.f;
+  return (I.kind == TH_NH || I.kind == TH_NPT) ? nh_half(I, bx, t) : 0.f;
 }
 
 __device__ __forceinline__ ThermoState thermo_in(const Box& bx, float4 th, double ke) {
@@ -386,6 +404,7 @@ __device__ void write_record(const Dev& d, const Integ& I, int b, int pp, unsign
   const double e2 = st->ew[pp][0], e3 = st->ew[pp][1];
   const double ke = st->ke_last;
   const double xi = (double)st->th_e.x + (double)st->th_e.y, eta = (double)st->th_e.z + (double)st->th_e.w;
+  const double V = bx.volume;  // the box of the completed step (the next one is made current in its kick1)
   r[TR_STEP] = (double)step_done;
   r[TR_PE] = e2 + e3;
   r[TR_E2] = e2;
@@ -393,13 +412,83 @@ __device__ void write_record(const Dev& d, const Integ& I, int b, int pp, unsign
   r[TR_KE] = ke;
   r[TR_T] = 2.0 * ke * bx.inv_ndf_kb;
   double cons = ke + e2 + e3;
-  if (I.kind == TH_NH) cons += 0.5 * bx.Q * xi * xi + bx.ndfkT0 * eta;
+  if (I.kind == TH_NH || I.kind == TH_NPT) cons += 0.5 * bx.Q * xi * xi + bx.ndfkT0 * eta;
+  if (I.kind == TH_NPT) cons += I.p_ext * V + 0.5 * st->pe_e * st->pe_e / bx.W;
   r[TR_CONS] = cons;
-  r[TR_P] = (2.0 * ke + st->ew[pp][2] + st->ew[pp][3] + st->ew[pp][4]) * bx.p_fac;
+  r[TR_P] = (2.0 * ke + st->ew[pp][2] + st->ew[pp][3] + st->ew[pp][4]) / (3.0 * V) * kATM;
   for (int k = 0; k < 6; ++k) r[TR_W0 + k] = st->ew[pp][2 + k];
   r[TR_XI] = xi;
   r[TR_ETA] = eta;
   r[TR_REBUILDS] = (double)st->rebuilds;
+  r[TR_VOL] = V;
+  for (int k = 0; k < 3; ++k) r[TR_L0 + k] = bx.L[k];
+}
+
+// Isotropic barostat (Sec. II.B, read as the Martyna-Tobias-Klein form):
+// half step on its momentum, pe += dt/2 [(1 + 3/N_df) 2 KE + tr(W) - 3 P V],
+// and the friction on the velocities, v *= exp(-dt/2 (1 + 3/N_df) pe/W),
+// returned as s - 1 (FP32).  pe and the volume stay FP64.  The geometry is
+// read with L2 loads (__ldcg): in the persistent engine another block wrote
+// it earlier in the same launch.
+__device__ __forceinline__ void baro_half(const Integ& I, const Box& bx, double ke, double trw, double& pe) {
+  pe += 0.5 * I.dt * (bx.a3 * 2.0 * ke + trw - 3.0 * I.p_ext * __ldcg(&bx.volume));
+}
+__device__ __forceinline__ float baro_friction(const Integ& I, const Box& bx, double pe) {
+  return expm1f((float)(-0.5 * I.dt * bx.a3 * pe / bx.W));
+}
+
+// The box of the coming step: every edge scaled by e^u, u = dt pe/W, during
+// its drift.  A box fraction then advances by (v dt / L) (1 - e^-u)/u (the
+// drift r -> r e^u + v dt e^(u/2) sinh(u/2)/(u/2) divided by the new edge),
+// which the kick kernel's drift factor absorbs; the new edges (Ln) become
+// current after that drift, in time for the list build and the force.
+// Rebuild margin: a pair outside the list (r >= r_list at the build) is at
+// least c r_list - 2 d apart, c = L/L_build, d the largest displacement
+// since the build, so the list holds while 2 d <= r_list - r_c -
+// r_list max(0, 1 - c); the displacement is measured with the current
+// edges, e^-u of the new ones.  A margin below skin/2 rebuilds at once.
+__device__ void npt_geometry(const Dev& d, const Integ& I, int b, double pe) {
+  Box& bx = const_cast<Box*>(d.box)[b];
+  BoxState* st = d.bst + b;
+  const float u = (float)(I.dt * pe / bx.W);
+  const float eu = expm1f(u);
+  const float fdr = fabsf(u) > 1e-3f ? -expm1f(-u) / u : fmaf(u, fmaf(u, 1.0f / 6.0f, -0.5f), 1.0f);
+  const float dt64 = (float)(I.dt * 18446744073709551616.0);  // dt 2^64
+  bool grid = false;
+  for (int k = 0; k < 3; ++k) {
+    const double L = __ldcg(&bx.L[k]);
+    const double Ln = fma(L, (double)eu, L);
+    bx.dtL64[k] = dt64 / (float)L * fdr;
+    bx.Ln[k] = Ln;
+    const int nc = bx.nc[k];
+    if (Ln < 2.0 * I.rlist || (nc >= 4 && Ln < nc * (double)I.rlist) || Ln >= (nc + 1) * kCellGrow * I.rlist)
+      grid = true;
+  }
+  if (grid) set_status(d.g, ST_GRID);
+  const float c = (float)(bx.Ln[0] / __ldcg(&st->Lb));
+  const float m = I.skin - I.rlist * fmaxf(0.0f, 1.0f - c);
+  if (m < 0.5f * I.skin) {
+    st->rebuild = 1;
+    d.g->any_rebuild = 1;
+  }
+  const float h = 0.5f * fmaxf(m, 0.0f) / (1.0f + eu);
+  bx.hs2 = h * h;
+}
+
+// The edges of the coming step made current (the last block of kick1, once
+// every block has drifted with the old ones).
+__device__ void npt_commit_box(const Dev& d, int b) {
+  Box& bx = const_cast<Box*>(d.box)[b];
+  double vol = 1.0;
+  for (int k = 0; k < 3; ++k) {
+    const double Ln = __ldcg(&bx.Ln[k]);
+    bx.L[k] = Ln;
+    bx.Lq[k] = (float)(Ln * 2.3283064365386963e-10);  // 2^-32
+    bx.qs[k] = 4294967296.0 / Ln;
+    vol *= Ln;
+  }
+  bx.volume = vol;
+  bx.p_fac = kATM / (3.0 * vol);
 }
 
 // Thermostat at the end of the step of parity par, for box b (one thread per
@@ -409,11 +498,38 @@ __device__ void write_record(const Dev& d, const Integ& I, int b, int pp, unsign
 __device__ void end_of_step_box(const Dev& d, const Integ& I, int b, int par) {
   BoxState* st = d.bst + b;
   const Box& bx = d.box[b];
-  const double ke = __ldcg(&st->ke_acc[par]);
-  ThermoState t = thermo_in(bx, __ldcg(&st->th), ke);
+  const double ke0 = __ldcg(&st->ke_acc[par]);
+  if (I.kind == TH_NPT) {
+    // end of this step: friction, barostat half, thermostat half; start of
+    // the next: thermostat half, barostat half, friction; then the new box
+    const double trw = __ldcg(&st->ew[par][2]) + __ldcg(&st->ew[par][3]) + __ldcg(&st->ew[par][4]);
+    double pe = __ldcg(&st->pe_b);
+    const float f1 = baro_friction(I, bx, pe);
+    double ke = fma(ke0, (double)(f1 * (2.0f + f1)), ke0);
+    baro_half(I, bx, ke, trw, pe);
+    ThermoState t = thermo_in(bx, __ldcg(&st->th), ke);
+    const float se = end_half(I, bx, t);
+    ke = fma(ke, (double)(se * (2.0f + se)), ke);
+    st->th_e = make_float4(t.xh, t.xl, t.eh, t.el);
+    st->ke_last = ke;
+    st->pe_e = pe;
+    const float e1 = fmaf(f1, se, f1 + se);
+    st->s_endc = 1.0 + (double)e1;
+    const float ss = start_half(I, bx, t);
+    ke = fma(ke, (double)(ss * (2.0f + ss)), ke);
+    st->th = make_float4(t.xh, t.xl, t.eh, t.el);
+    baro_half(I, bx, ke, trw, pe);
+    const float f2 = baro_friction(I, bx, pe);
+    const float e2 = fmaf(ss, f2, ss + f2);
+    st->sig = fmaf(e1, e2, e1 + e2);
+    st->pe_b = pe;
+    npt_geometry(d, I, b, pe);
+    return;
+  }
+  ThermoState t = thermo_in(bx, __ldcg(&st->th), ke0);
   const float se = end_half(I, bx, t);
   st->th_e = make_float4(t.xh, t.xl, t.eh, t.el);
-  st->ke_last = fma(ke, (double)(se * (2.0f + se)), ke);
+  st->ke_last = fma(ke0, (double)(se * (2.0f + se)), ke0);
   st->s_endc = 1.0 + (double)se;
   const float ss = start_half(I, bx, t);
   st->th = make_float4(t.xh, t.xl, t.eh, t.el);
@@ -432,7 +548,19 @@ __global__ void k_prime_thermostat(Dev d) {
   const float se = (float)(st->s_endc - 1.0);
   const float ss = start_half(I, bx, t);
   st->th = make_float4(t.xh, t.xl, t.eh, t.el);
-  st->sig = fmaf(se, ss, se + ss);
+  float e2 = ss;
+  if (I.kind == TH_NPT) {  // barostat half and friction with the latest virial
+    const int wp = d.g->wpar;
+    const double trw = st->ew[wp][2] + st->ew[wp][3] + st->ew[wp][4];
+    const double ke = fma(st->ke_last, (double)(ss * (2.0f + ss)), st->ke_last);
+    double pe = st->pe_e;
+    baro_half(I, bx, ke, trw, pe);
+    const float f2 = baro_friction(I, bx, pe);
+    e2 = fmaf(ss, f2, ss + f2);
+    st->pe_b = pe;
+    npt_geometry(d, I, b, pe);
+  }
+  st->sig = fmaf(se, e2, se + e2);
 }
 
 // Uniform early exit of a block on a device error status (one read, shared),
@@ -519,7 +647,7 @@ __device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, 
   // displacement since the last build: sum the three components of the atom
   const int base = lane - c;
   const float d1 = __shfl_sync(kFull, dd, min(base + 1, 31)), d2 = __shfl_sync(kFull, dd, min(base + 2, 31));
-  if (act && c == 0 && dd + d1 + d2 > I.half_skin2) {
+  if (act && c == 0 && dd + d1 + d2 > (I.kind == TH_NPT ? d.box[b].hs2 : I.half_skin2)) {
     d.bst[b].rebuild = 1;
     d.g->any_rebuild = 1;
   }
@@ -993,7 +1121,10 @@ __global__ void __launch_bounds__(kFThreads, 8) k_force(Dev d, FParams P) {
   const int par = (int)(d.g->step & 1ull);
   if (blockIdx.x == 0) {  // the rebuild (if any) is consumed
     for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
-    if (threadIdx.x == 0) d.g->any_rebuild = 0;
+    if (threadIdx.x == 0) {
+      d.g->any_rebuild = 0;
+      d.g->wpar = par;
+    }
   }
   force_block<kCount>(d, P, T, blockIdx.x, par);
 }
@@ -1015,7 +1146,7 @@ __global__ void __launch_bounds__(kKThreads) k_kick1(Dev d, cudaGraphConditional
   const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (blockIdx.x == 0 && threadIdx.x == 0) d.g->n_over = 0;
   if (w * kKAtoms < d.N) kick1_lane(d, I, w, par, pend);
-  if constexpr (kCond) {
+  if (kCond || I.kind == TH_NPT) {  // block-uniform
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {  // one fence per block after the barrier orders the block's writes
@@ -1023,10 +1154,14 @@ __global__ void __launch_bounds__(kKThreads) k_kick1(Dev d, cudaGraphConditional
       last = (atomicAdd(&d.g->done1, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {
       __threadfence();
-      d.g->done1 = 0u;
-      cudaGraphSetConditional(rebuild_cond, *(volatile int*)&d.g->any_rebuild ? 1u : 0u);
+      if (I.kind == TH_NPT)
+        for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) npt_commit_box(d, b);
+      if (threadIdx.x == 0) {
+        d.g->done1 = 0u;
+        if constexpr (kCond) cudaGraphSetConditional(rebuild_cond, *(volatile int*)&d.g->any_rebuild ? 1u : 0u);
+      }
     }
   }
 }
@@ -1134,7 +1269,10 @@ __global__ void k_copyback(Dev d) {
   if (!d.g->any_rebuild || d.g->status) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) d.g->rebuild_steps += 1;
-  if (i < d.nbox && box_flagged(d, i)) d.bst[i].rebuilds += 1;
+  if (i < d.nbox && box_flagged(d, i)) {
+    d.bst[i].rebuilds += 1;
+    d.bst[i].Lb = d.box[i].L[0];
+  }
   if (i < d.N) copyback_item(d, i);
 }
 
@@ -1299,13 +1437,16 @@ __global__ void k_thermo_snapshot(Dev d) {
   t[TR_T] = 2.0 * ke * bx.inv_ndf_kb;
   double cons = ke + e2 + e3;
   const double xi = (double)st->th_e.x + (double)st->th_e.y, eta = (double)st->th_e.z + (double)st->th_e.w;
-  if (I.kind == TH_NH) cons += 0.5 * bx.Q * xi * xi + bx.ndfkT0 * eta;
+  if (I.kind == TH_NH || I.kind == TH_NPT) cons += 0.5 * bx.Q * xi * xi + bx.ndfkT0 * eta;
+  if (I.kind == TH_NPT) cons += I.p_ext * bx.volume + 0.5 * st->pe_e * st->pe_e / bx.W;
   t[TR_CONS] = cons;
-  t[TR_P] = (2.0 * ke + st->ew[par][2] + st->ew[par][3] + st->ew[par][4]) * bx.p_fac;
+  t[TR_P] = (2.0 * ke + st->ew[par][2] + st->ew[par][3] + st->ew[par][4]) / (3.0 * bx.volume) * kATM;
   for (int k = 0; k < 6; ++k) t[TR_W0 + k] = st->ew[par][2 + k];
   t[TR_XI] = xi;
   t[TR_ETA] = eta;
   t[TR_REBUILDS] = (double)st->rebuilds;
+  t[TR_VOL] = bx.volume;
+  for (int k = 0; k < 3; ++k) t[TR_L0 + k] = bx.L[k];
 }
 
 // Sorted -> user order: x (wrapped) and (v + pending half-kick) * s_endc (the

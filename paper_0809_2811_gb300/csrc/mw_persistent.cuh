@@ -182,7 +182,14 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     const int pend = *(volatile int*)&g->pend;  // stable: written only at the end of the kick2 phase
     if (tid == 0) g->n_over = 0;
     for (int w = gw; w * kKAtoms < d.N; w += nwarps) kick1_lane(d, I, w, par, pend);
-    if (grid_barrier(g, gen)) return;
+    if (I.kind == TH_NPT) {  // the new edges once every block has drifted with the old
+      if (grid_barrier_last(g, gen, [&] {
+            for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) npt_commit_box(d, b);
+          }))
+        return;
+    } else if (grid_barrier(g, gen)) {
+      return;
+    }
     // a2 + a3: cell binning and neighbour list, when due (flag is stable until kick2)
     if (*(volatile int*)&g->any_rebuild) {
       if (tid == 0) g->max_count = 0;
@@ -196,11 +203,15 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
       if (grid_barrier(g, gen)) return;
       for (int i = tid; i < d.N; i += nth) copyback_item(d, i);
       for (int c = gw; c < d.ncell; c += nwarps) neigh_cell_warp(d, d.tq, c, P.rl2);
-      if (tid < d.nbox && box_flagged(d, tid)) d.bst[tid].rebuilds += 1;
+      if (tid < d.nbox && box_flagged(d, tid)) {
+        d.bst[tid].rebuilds += 1;
+        d.bst[tid].Lb = d.box[tid].L[0];
+      }
       if (tid == 0) g->rebuild_steps += 1;
       if (grid_barrier(g, gen)) return;
     }
     // a4 - a6: fused two- + three-body force, energy, virial
+    if (tid == 0) g->wpar = par;
     for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) force_block<kCount>(d, P, T, blk, par);
     if (grid_barrier(g, gen)) return;
     // a7 second half: kinetic energy of v + a per box; the rebuild (if any) is consumed

@@ -16,10 +16,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmw.so")
 
-MW_OK, MW_EINVAL, MW_EBOX, MW_ENLIST_OVERFLOW, MW_ENAN, MW_ELOST, MW_ETIMEOUT, MW_ECUDA, MW_ENOMEM, MW_ESTATE = range(10)
+(MW_OK, MW_EINVAL, MW_EBOX, MW_ENLIST_OVERFLOW, MW_ENAN, MW_ELOST, MW_ETIMEOUT, MW_ECUDA, MW_ENOMEM, MW_ESTATE,
+ MW_EGRID) = range(11)
 STATUS_NAMES = {0: "MW_OK", 1: "MW_EINVAL", 2: "MW_EBOX", 3: "MW_ENLIST_OVERFLOW", 4: "MW_ENAN", 5: "MW_ELOST",
-                6: "MW_ETIMEOUT", 7: "MW_ECUDA", 8: "MW_ENOMEM", 9: "MW_ESTATE"}
-MW_NVE, MW_BERENDSEN, MW_NOSE_HOOVER = 0, 1, 2
+                6: "MW_ETIMEOUT", 7: "MW_ECUDA", 8: "MW_ENOMEM", 9: "MW_ESTATE", 10: "MW_EGRID"}
+MW_NVE, MW_BERENDSEN, MW_NOSE_HOOVER, MW_NPT = 0, 1, 2, 3
 MW_ENGINE_AUTO, MW_ENGINE_GRAPH, MW_ENGINE_PERSISTENT = 0, 1, 2
 
 # every symbol include/mw.h declares
@@ -29,7 +30,7 @@ EXPORTS = (
     "mw_get_neighbors", "mw_energy_forces", "mw_energy_forces_dev", "mw_step", "mw_get_thermo",
     "mw_energy_forces_vjp", "mw_set_engine", "mw_set_nbr_width", "mw_autotune", "mw_get_info",
     "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc", "mw_set_skin", "mw_phase_times",
-    "mw_pair_histogram", "mw_angle_histogram", "mw_get_unwrapped", "mw_last_error",
+    "mw_pair_histogram", "mw_angle_histogram", "mw_get_unwrapped", "mw_get_box", "mw_last_error",
 )
 
 
@@ -42,7 +43,8 @@ class mw_params(ctypes.Structure):
 
 class mw_integrator(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("thermostat", ctypes.c_int), ("T0", ctypes.c_double),
-                ("T0_per_box", ctypes.POINTER(ctypes.c_double)), ("tau", ctypes.c_double)]
+                ("T0_per_box", ctypes.POINTER(ctypes.c_double)), ("tau", ctypes.c_double),
+                ("p_ext", ctypes.c_double), ("tau_p", ctypes.c_double)]
 
 
 class mw_thermo(ctypes.Structure):
@@ -50,11 +52,12 @@ class mw_thermo(ctypes.Structure):
                 ("e3", ctypes.c_double), ("ke", ctypes.c_double), ("temperature", ctypes.c_double),
                 ("conserved", ctypes.c_double), ("pressure", ctypes.c_double),
                 ("virial", ctypes.c_double * 6), ("xi", ctypes.c_double), ("eta", ctypes.c_double),
-                ("rebuilds", ctypes.c_int64)]
+                ("rebuilds", ctypes.c_int64), ("volume", ctypes.c_double), ("box", ctypes.c_double * 3)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "virial"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("virial", "box")}
         d["virial"] = list(self.virial)
+        d["box"] = list(self.box)
         return d
 
 
@@ -63,7 +66,7 @@ class mw_info(ctypes.Structure):
                 ("max_count", ctypes.c_int), ("ncell_total", ctypes.c_int), ("engine", ctypes.c_int),
                 ("persistent_blocks", ctypes.c_int), ("persistent_threads", ctypes.c_int),
                 ("r_list", ctypes.c_double), ("npairs", ctypes.c_int64), ("ntriplets", ctypes.c_int64),
-                ("rebuild_steps", ctypes.c_int64)]
+                ("rebuild_steps", ctypes.c_int64), ("regrids", ctypes.c_int64)]
 
 
 class MWError(RuntimeError):
@@ -116,6 +119,7 @@ def lib():
             "mw_phase_times": [P, ctypes.POINTER(mw_integrator), ctypes.c_int, dp],
             "mw_pair_histogram": [P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)],
             "mw_get_unwrapped": [P, dp],
+            "mw_get_box": [P, dp],
             "mw_angle_histogram": [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)],
             "mw_energy_forces_noalloc": [ctypes.c_int, dp, ctypes.POINTER(mw_params), ctypes.c_double, P, P, P, P,
                                          P],
@@ -233,12 +237,16 @@ def mw_energy_forces_dev(h: int, x_dev=None, f_dev=None, energy_dev=None, virial
     _check(lib().mw_energy_forces_dev(h, _ptr(x_dev), _ptr(f_dev), _ptr(energy_dev), _ptr(virial_dev)))
 
 
-def make_integrator(dt=10.0, thermostat=MW_NVE, T0=300.0, tau=1000.0, T0_per_box=None):
+def make_integrator(dt=10.0, thermostat=MW_NVE, T0=300.0, tau=1000.0, T0_per_box=None, p_ext=1.0,
+                    tau_p=5000.0):
+    """tau, tau_p in fs; p_ext in atm (MW_NPT only)."""
     it = mw_integrator()
     it.dt = dt
     it.thermostat = thermostat
     it.T0 = T0
     it.tau = tau
+    it.p_ext = p_ext
+    it.tau_p = tau_p
     if T0_per_box is not None:
         arr = np.ascontiguousarray(T0_per_box, np.float64)
         it._keep = arr
@@ -390,9 +398,16 @@ class System:
     def neighbors(self, width: int = 128):
         return mw_get_neighbors(self.h, self.n_total, width)
 
-    def step(self, nsteps: int, dt=10.0, thermostat=MW_NVE, T0=300.0, tau=1000.0, T0_per_box=None):
-        it = make_integrator(dt, thermostat, T0, tau, T0_per_box)
+    def step(self, nsteps: int, dt=10.0, thermostat=MW_NVE, T0=300.0, tau=1000.0, T0_per_box=None, p_ext=1.0,
+             tau_p=5000.0):
+        it = make_integrator(dt, thermostat, T0, tau, T0_per_box, p_ext, tau_p)
         return mw_step(self.h, it, nsteps, self.nbox)
+
+    def box(self) -> np.ndarray:
+        """Current edges of every box (nbox x 3, A); they change under MW_NPT."""
+        b = np.empty((self.nbox, 3))
+        _check(lib().mw_get_box(self.h, _dp(b)))
+        return b
 
     def thermo(self):
         return mw_get_thermo(self.h, self.nbox)

@@ -35,9 +35,37 @@ def test_params_default_is_the_papers():
 def test_struct_sizes_match_header_layout():
     # sizes the C compiler gives these structs on LP64
     assert ctypes.sizeof(mw.mw_params) == 72
-    assert ctypes.sizeof(mw.mw_integrator) == 40
-    assert ctypes.sizeof(mw.mw_thermo) == 136
-    assert ctypes.sizeof(mw.mw_info) == 64
+    assert ctypes.sizeof(mw.mw_integrator) == 56
+    assert ctypes.sizeof(mw.mw_thermo) == 168
+    assert ctypes.sizeof(mw.mw_info) == 72
+
+
+def test_struct_layout_matches_the_c_compiler(tmp_path):
+    """Every field offset of the ctypes mirrors equals the C compiler's for include/mw.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    structs = [mw.mw_params, mw.mw_integrator, mw.mw_thermo, mw.mw_info]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mw.h"', "int main(void) {"]
+    expect = []
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        expect.append(ctypes.sizeof(st))
+        for f, _ in st._fields_:
+            cf = "lambda" if f == "lambda_" else f
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {cf}));')
+            expect.append(getattr(st, f).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
 
 
 def test_oracle_and_library_share_no_code():

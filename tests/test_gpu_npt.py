@@ -1,0 +1,228 @@
+"""Isobaric-isothermal dynamics (MW_NPT) vs the oracle's, through the C ABI.
+
+Sec. II.B runs constant-pressure simulations with a Nose-Hoover thermostat
+and barostat (relaxation times 1 and 2.5 ps, p = 0).  The oracle integrates
+the same Martyna-Tobias-Klein equations (isotropic box, symmetric Trotter
+split) in FP64; the library keeps the thermostat and the barostat friction in
+FP32 and the barostat momentum and the box edges in FP64, and its FP32 forces
+make the chaotic trajectories separate slowly, so short runs are compared
+state by state and longer ones on conserved and averaged quantities.
+"""
+import numpy as np
+import pytest
+
+from paper_0809_2811_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+ENGINES = {"graph": 1, "persistent": 2}
+# grams per mole of water over Avogadro's number, in g per A^3 -> g/cm^3
+G_PER_MOL_A3 = 18.015 / 6.02214076e23 * 1e24
+R_KCAL = 1.987204259e-3  # kcal/mol/K
+
+
+def _min_image(d, box):
+    return d - box * np.rint(d / box)
+
+
+def _gpu_npt(mwlib, x, v, box, nsteps, engine=None, **kw):
+    s = mwlib.System(len(x), box)
+    try:
+        if engine is not None:
+            s.set_engine(engine)
+        s.set_state(x, v)
+        th = s.step(nsteps, thermostat=mwlib.MW_NPT, **kw)[0]
+        xg, vg = s.get_state()
+        bg = s.box()[0]
+        info = s.info()
+    finally:
+        s.close()
+    return th, xg, vg, bg, info
+
+
+def _compare(th, xg, vg, bg, xo, vo, bo, st, tho, nsteps, pos_tol=5e-5, vel_tol=5e-7):
+    """Bounds about ten times the differences measured on GB300 (20-30 steps:
+    edges 3e-9, positions 2e-6 A (1.4e-5 A through a regrid), velocities
+    4e-8 A/fs, energies 1e-7, thermostat 5e-7, pressure 0.02 atm)."""
+    # edges: one factor per step from the FP64 barostat momentum and an FP32 exp
+    assert np.allclose(bg, bo, rtol=5e-8, atol=0)
+    assert th["box"] == pytest.approx(list(bg), rel=1e-15)
+    assert th["volume"] == pytest.approx(tho[8], rel=1.5e-7)
+    assert np.abs(_min_image(xg - xo, bo)).max() < pos_tol
+    assert np.abs(vg - vo).max() < vel_tol
+    assert th["pe"] == pytest.approx(tho[0], rel=1e-6)
+    assert th["ke"] == pytest.approx(tho[3], rel=3e-6)
+    assert th["conserved"] == pytest.approx(tho[5], rel=1e-6)
+    assert th["xi"] == pytest.approx(st[0], rel=5e-6, abs=1e-12)
+    assert th["eta"] == pytest.approx(st[1], rel=5e-6, abs=1e-12)
+    assert th["pressure"] == pytest.approx(tho[9] * 68568.4158, abs=0.2)
+    assert th["step"] == nsteps
+
+
+@pytest.mark.parametrize("engine", sorted(ENGINES))
+def test_npt_short_trajectory_matches_oracle(mwlib, orc, engine):
+    """20 steps from the jittered 512-atom start (about -12000 atm: the box
+    shrinks by 3.6% in edge), p = 1 atm, tau_p = 2 ps."""
+    x, v, box = I.nve512()
+    x = I.snap_to_grid(x, box)
+    kw = dict(dt=10.0, T0=250.0, tau=200.0, p_ext=1.0, tau_p=2000.0)
+    th, xg, vg, bg, _ = _gpu_npt(mwlib, x, v, box, 20, ENGINES[engine], **kw)
+    xo, vo, bo, st, tho = orc.md_npt(x, v, box, 20, dt=10.0, T0=250.0, tau=200.0, p_atm=1.0, tau_p=2000.0)
+    assert bo[0] < 0.97 * box[0]
+    _compare(th, xg, vg, bg, xo, vo, bo, st, tho[-1], 20)
+
+
+@pytest.mark.parametrize("engine", sorted(ENGINES))
+def test_npt_box_leaves_its_cell_grid_and_the_run_continues(mwlib, orc, engine):
+    """A liquid started at 0.80 g/cm^3 under p = 0 collapses (edge 26.75 ->
+    22.8 A within 80 fs at tau_p = 0.5 ps): its 5-cell grid no longer holds
+    r_list per cell, the run stops at a step boundary, the grid is laid out
+    again (4 cells) and the run goes on; the trajectory still follows the
+    oracle's."""
+    x, box = I.jittered_box(512, 0.80, 0.25, 901)
+    x = I.snap_to_grid(x, box)
+    v = I.maxwell_velocities(512, 250.0, seed=902)
+    th, xg, vg, bg, info = _gpu_npt(mwlib, x, v, box, 30, ENGINES[engine], dt=10.0, T0=250.0, tau=200.0,
+                                    p_ext=0.0, tau_p=500.0)
+    xo, vo, bo, st, tho = orc.md_npt(x, v, box, 30, dt=10.0, T0=250.0, tau=200.0, p_atm=0.0, tau_p=500.0)
+    assert info["regrids"] >= 1
+    assert info["ncell_total"] == 4 ** 3
+    _compare(th, xg, vg, bg, xo, vo, bo, st, tho[-1], 30, pos_tol=1.5e-4, vel_tol=2e-6)
+
+
+@pytest.mark.parametrize("engine", sorted(ENGINES))
+def test_npt_batch_has_one_barostat_per_box(mwlib, orc, engine):
+    n = [216, 343, 290]
+    rho = [0.95, 1.0, 1.08]
+    T = [230.0, 260.0, 300.0]
+    xs, vs, boxes = [], [], []
+    for k in range(3):
+        x, b = I.jittered_box(n[k], rho[k], 0.2, 950 + k)
+        xs.append(I.snap_to_grid(x, b))
+        vs.append(I.maxwell_velocities(n[k], T[k], seed=960 + k))
+        boxes.append(b)
+    s = mwlib.System(n, np.array(boxes))
+    try:
+        s.set_engine(ENGINES[engine])
+        s.set_state(np.concatenate(xs), np.concatenate(vs))
+        th = s.step(15, dt=10.0, thermostat=mwlib.MW_NPT, T0_per_box=T, tau=300.0, p_ext=1.0, tau_p=1500.0)
+        bg = s.box()
+        xg, vg = s.get_state()
+    finally:
+        s.close()
+    off = 0
+    for k in range(3):
+        xo, vo, bo, st, tho = orc.md_npt(xs[k], vs[k], boxes[k], 15, dt=10.0, T0=T[k], tau=300.0, p_atm=1.0,
+                                         tau_p=1500.0)
+        sl = slice(off, off + n[k])
+        _compare(th[k], xg[sl], vg[sl], bg[k], xo, vo, bo, st, tho[-1], 15)
+        off += n[k]
+
+
+def test_npt_conserved_quantity_error_is_second_order_in_dt(mwlib):
+    """20 ps of NPT (p = 0, tau = 1 ps, tau_p = 2.5 ps as in Sec. II.B) from a
+    512-atom liquid held 5 ps at 298 K by Nose-Hoover: the extended energy
+    follows the volume oscillation set off by the ~700 atm start with an
+    excursion of the integrator's own O(dt^2) size (the oracle's FP64 run of
+    the same protocol moves by 2.1 kcal/mol = 4e-4 |E| at dt = 10 fs), and
+    halving dt cuts it about fourfold.  A precision leak in the FP32
+    thermostat, friction or drift factors would not shrink with dt."""
+    x, v, box = I.nve512()
+    x = I.snap_to_grid(x, box)
+    s = mwlib.System(512, box)
+    try:
+        s.set_state(x, v)
+        s.step(500, dt=10.0, thermostat=mwlib.MW_NOSE_HOOVER, T0=298.0, tau=1000.0)
+        x1, v1 = s.get_state()
+    finally:
+        s.close()
+    dev = {}
+    for dt in (10.0, 5.0):
+        kw = dict(dt=dt, thermostat=mwlib.MW_NPT, T0=298.0, tau=1000.0, p_ext=0.0, tau_p=2500.0)
+        per = int(round(500.0 / dt))
+        s = mwlib.System(512, box)
+        try:
+            s.set_state(x1, v1)
+            c = [s.step(1, **kw)[0]["conserved"]]
+            for _ in range(40):
+                c.append(s.step(per, **kw)[0]["conserved"])
+        finally:
+            s.close()
+        c = np.array(c)
+        dev[dt] = np.abs(c - c[0]).max() / abs(c[0])
+    assert dev[10.0] < 1.5e-3
+    assert dev[5.0] < 0.45 * dev[10.0]
+
+
+def test_npt_then_nvt_keeps_the_scaled_box(mwlib):
+    """After an isobaric run the box stays where the barostat left it: the
+    thermo record, mw_get_box and the positions agree, and a following
+    Nose-Hoover run keeps it fixed."""
+    x, v, box = I.nve512()
+    s = mwlib.System(512, box)
+    try:
+        s.set_state(x, v)
+        th = s.step(100, dt=10.0, thermostat=mwlib.MW_NPT, T0=298.0, tau=1000.0, p_ext=0.0, tau_p=1000.0)[0]
+        b1 = s.box()[0]
+        assert th["box"] == list(b1)
+        assert abs(b1[0] / box[0] - 1) > 1e-3
+        assert b1[0] == b1[1] == b1[2]
+        assert th["volume"] == pytest.approx(b1.prod(), rel=1e-14)
+        xg, _ = s.get_state()
+        assert (xg >= 0).all() and (xg < b1).all()
+        th2 = s.step(50, dt=10.0, thermostat=mwlib.MW_NOSE_HOOVER, T0=298.0, tau=1000.0)[0]
+        assert list(s.box()[0]) == list(b1)
+        assert th2["volume"] == th["volume"]
+        assert th2["step"] == 150
+    finally:
+        s.close()
+
+
+def test_npt_autotune_restores_the_box(mwlib, tmp_path, monkeypatch):
+    monkeypatch.setenv("MW_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    x, box = I.jittered_box(2048, 1.0, 0.1, 17)
+    v = I.maxwell_velocities(2048, 260.0, seed=18)
+    s = mwlib.System(2048, box)
+    try:
+        s.set_state(x, v)
+        it = mwlib.make_integrator(10.0, mwlib.MW_NPT, 260.0, 500.0, p_ext=0.0, tau_p=1000.0)
+        mwlib.mw_step(s.h, it, 20, 1)
+        b0 = s.box()[0].copy()
+        t0 = s.thermo()[0]
+        assert mwlib.mw_autotune(s.h, it, 20) in (1, 2)
+        assert list(s.box()[0]) == list(b0)
+        t1 = s.thermo()[0]
+        assert t1["step"] == t0["step"]
+        assert t1["volume"] == pytest.approx(t0["volume"], rel=1e-15)
+        th = mwlib.mw_step(s.h, it, 20, 1)[0]
+        assert th["step"] == 40
+    finally:
+        s.close()
+
+
+def test_npt_density_and_vaporization_enthalpy_298K(mwlib):
+    """Table 1 at 298 K and Sec. II.B's protocol (4096 particles, p = 0, NH
+    thermostat and barostat, 1 and 2.5 ps): density 0.997 g/cm^3, enthalpy of
+    vaporization 10.65 kcal/mol (H_gas = 2.5 RT, H_liq = <E + pV> per mol).
+    Melted from a jittered lattice, equilibrated 30 ps, averaged over 100 ps
+    (the standard error of either mean is far inside the bands)."""
+    x, box = I.jittered_box(4096, 0.997, 0.1, 4242)
+    v = I.maxwell_velocities(4096, 400.0, seed=4243)
+    s = mwlib.System(4096, box)
+    kw = dict(dt=10.0, thermostat=mwlib.MW_NPT, T0=298.0, tau=1000.0, p_ext=0.0, tau_p=2500.0)
+    try:
+        s.set_state(x, v)
+        s.step(1000, dt=5.0, thermostat=mwlib.MW_BERENDSEN, T0=400.0, tau=200.0)
+        s.step(1000, dt=10.0, thermostat=mwlib.MW_NOSE_HOOVER, T0=298.0, tau=1000.0)
+        s.step(3000, **kw)
+        vol, h = [], []
+        for _ in range(200):
+            t = s.step(50, **kw)[0]
+            vol.append(t["volume"])
+            h.append(t["pe"] + t["ke"])
+    finally:
+        s.close()
+    rho = 4096 * G_PER_MOL_A3 / np.mean(vol)
+    dh = 2.5 * R_KCAL * 298.0 - np.mean(h) / 4096
+    assert rho == pytest.approx(0.997, abs=0.004)
+    assert dh == pytest.approx(10.65, abs=0.15)

@@ -12,6 +12,10 @@ Function map (section of the paper each follows):
   energy_forces_cell           same, cell-list owner loop
   neighbors                    neighbour sets {j : |d_ij| < r_list}
   md                           Sec. II.B velocity-Verlet run (thermostat reading)
+  md_npt                       Sec. II.B isobaric-isothermal run (barostat reading)
+  energy_forces_species        Sec. II.A equations with a parameter vector per
+                               species triple (mW with solutes, Sec. IV)
+  md_species                   md with that potential
   force_vjp                    force-matching adjoint (no counterpart in the paper)
   energy_param_grad            dE/d(lambda, epsilon, sigma)
 """
@@ -67,6 +71,10 @@ def lib():
         _lib.or_md_npt.argtypes = [d, ctypes.c_int, d, d, d, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, d, d]
         _lib.or_force_vjp.argtypes = [d, ctypes.c_int, d, d, d, d, d]
+        _lib.or_species_table_check.argtypes = [d, ctypes.c_int]
+        _lib.or_energy_forces_species.argtypes = [d, ctypes.c_int, i, ctypes.c_int, d, d, d, d]
+        _lib.or_md_species.argtypes = [d, ctypes.c_int, i, ctypes.c_int, d, d, d, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, d, d]
         _lib.or_energy_param_grad.argtypes = [d, ctypes.c_int, d, d, d]
         ll = ctypes.POINTER(ctypes.c_longlong)
         _lib.or_pair_histogram.argtypes = [ctypes.c_int, d, d, ctypes.c_double, ctypes.c_int, ctypes.c_double, ll, ll]
@@ -236,3 +244,49 @@ def angle_histogram(x, box, nc=8, nbins=180, tol_deg=1e-3, rel=1e-5):
     _check(lib().or_angle_histogram(len(x), _dp(x), _dp(box), int(nc), int(nbins), float(tol_deg), float(rel),
                                     _llp(h), _llp(a), _llp(t)), "or_angle_histogram")
     return h, a, int(t[0])
+
+
+def species_table(nt, entry):
+    """nt^3 parameter vectors from entry(a, b, c) -> parameter vector (or dict of overrides)."""
+    t = np.zeros((nt, nt, nt, 10))
+    for a in range(nt):
+        for b in range(nt):
+            for c in range(nt):
+                e = entry(a, b, c)
+                t[a, b, c] = params(**e) if isinstance(e, dict) else np.asarray(e, np.float64)
+    return t
+
+
+def species_table_ok(table) -> bool:
+    t = np.ascontiguousarray(table, np.float64)
+    return lib().or_species_table_check(_dp(t), t.shape[0]) == 0
+
+
+def energy_forces_species(x, box, types, table):
+    """Several species (brute force): same dict as energy_forces."""
+    t = np.ascontiguousarray(table, np.float64)
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    box = np.ascontiguousarray(box, np.float64)
+    ty = np.ascontiguousarray(types, np.int32)
+    n = x.shape[0]
+    f = np.zeros((n, 3))
+    out = np.zeros(11)
+    _check(lib().or_energy_forces_species(_dp(t), t.shape[0], _ip(ty), n, _dp(x), _dp(box), _dp(f), _dp(out)),
+           "energy_forces_species")
+    return {"e2": out[0], "e3": out[1], "energy": out[0] + out[1], "forces": f, "virial": out[2:8].copy(),
+            "npairs": int(out[8]), "ntriplets": int(out[9]), "virial_abs": out[10]}
+
+
+def md_species(x, v, box, types, table, nsteps, dt=10.0, kind=0, T0=300.0, tau=1000.0, mass=18.015,
+               state=(0.0, 0.0)):
+    """md() with the several-species potential; returns (x, v, state, thermo[nsteps+1, 8])."""
+    t = np.ascontiguousarray(table, np.float64)
+    ty = np.ascontiguousarray(types, np.int32)
+    x = np.array(x, np.float64).reshape(-1, 3)
+    v = np.array(v, np.float64).reshape(-1, 3)
+    box = np.ascontiguousarray(box, np.float64)
+    st = np.array(state, np.float64)
+    th = np.zeros((nsteps + 1, 8))
+    _check(lib().or_md_species(_dp(t), t.shape[0], _ip(ty), x.shape[0], _dp(x), _dp(v), _dp(box), mass, dt, kind,
+                               T0, tau, nsteps, _dp(st), _dp(th)), "md_species")
+    return x, v, (float(st[0]), float(st[1])), th

@@ -30,6 +30,15 @@
  *     and the angle histogram behind the adf (for each atom k its n_c
  *     nearest neighbours, the angles theta_ikj at k over every ordered pair
  *     i != j of them).  Both by brute force over all pairs.
+ *   - Several species (the paper's mW with solutes of their own lambda,
+ *     epsilon, sigma, Sec. IV, and the SW family of Fig. 2): the same two
+ *     equations with a parameter vector per ordered species triple, in the
+ *     usual layout of multi-species SW tables: the pair (i, j) takes the
+ *     entry (ti, tj, tj); the three-body term of centre i with legs j, k
+ *     takes lambda, epsilon and cos theta0 from (ti, tj, tk), and each leg's
+ *     exponential factor (gamma, sigma, a) from that leg's pair entry.  The
+ *     paper prints no mixing rule; this is the reading.  Brute force over
+ *     all pairs.
  *   - Force-matching adjoint (no counterpart in the paper, whose Sec. II.D
  *     tunes lam, eps, sig by scans): the derivative of the forces along a
  *     direction, taken by the complex-step method (Squire & Trapp, SIAM Rev.
@@ -456,6 +465,158 @@ int or_neighbors(int n, const double* x, const double* box, double rlist, double
 }
 
 /* ------------------------------------------------------------------ */
+/* Several species.                                                     */
+/* ------------------------------------------------------------------ */
+
+/* Entry (a, b, c) of a table of nt^3 parameter vectors. */
+static const double* sp_entry(const double* table, int nt, int a, int b, int c) {
+  return table + 10 * (((size_t)a * nt + b) * nt + c);
+}
+
+/* The table's own consistency: the pair term of (a, b) must not depend on
+ * which of the two is taken first, and the three-body term of a centre a
+ * must not depend on the order of its legs b, c. */
+int or_species_table_check(const double* table, int nt) {
+  if (nt < 1) return OR_EINVAL;
+  static const int pair_fields[] = {1, 2, 3, 5, 6, 8, 9};
+  static const int tri_fields[] = {0, 1, 7};
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      const double* ab = sp_entry(table, nt, a, b, b);
+      const double* ba = sp_entry(table, nt, b, a, a);
+      for (int k = 0; k < 7; ++k)
+        if (ab[pair_fields[k]] != ba[pair_fields[k]]) return OR_EINVAL;
+      if (!(ab[2] > 0) || !(ab[3] > 0)) return OR_EINVAL;
+      for (int c = 0; c < nt; ++c) {
+        const double* abc = sp_entry(table, nt, a, b, c);
+        const double* acb = sp_entry(table, nt, a, c, b);
+        for (int k = 0; k < 3; ++k)
+          if (abc[tri_fields[k]] != acb[tri_fields[k]]) return OR_EINVAL;
+      }
+    }
+  return OR_OK;
+}
+
+/* Three-body term of a centre whose legs carry their own exponential
+ * factors: lam eps (cos - c0)^2 exp(gj sj/(rj - aj sj)) exp(gk sk/(rk - ak sk)),
+ * with lam, eps, c0 from pt and (gamma, sigma, a) of each leg from pj, pk;
+ * gradient with respect to the two leg vectors as in tri_grad. */
+static double sp_tri_grad(const double* pt, const double* pj, const double* pk, const double* dj, double rj,
+                          const double* dk, double rk, double* gj, double* gk) {
+  const double lam = pt[0], eps = pt[1], c0 = pt[7];
+  const double sj = pj[2], aj = pj[3], gmj = pj[4];
+  const double sk = pk[2], ak = pk[3], gmk = pk[4];
+  double uj[3], uk[3];
+  for (int d = 0; d < 3; ++d) {
+    uj[d] = dj[d] / rj;
+    uk[d] = dk[d] / rk;
+  }
+  const double c = uj[0] * uk[0] + uj[1] * uk[1] + uj[2] * uk[2];
+  const double D = c - c0;
+  const double xj = rj - aj * sj, xk = rk - ak * sk;
+  const double pre = lam * eps * exp(gmj * sj / xj) * exp(gmk * sk / xk);
+  const double dlj = -gmj * sj / (xj * xj);
+  const double dlk = -gmk * sk / (xk * xk);
+  for (int d = 0; d < 3; ++d) {
+    const double dcj = (uk[d] - c * uj[d]) / rj;
+    const double dck = (uj[d] - c * uk[d]) / rk;
+    gj[d] = pre * (2.0 * D * dcj + D * D * dlj * uj[d]);
+    gk[d] = pre * (2.0 * D * dck + D * D * dlk * uk[d]);
+  }
+  return pre * D * D;
+}
+
+/*
+ * Energy, forces and virial of a box of several species, by brute force.
+ * table: nt^3 parameter vectors (layout of or_params_default), entry
+ * (a, b, c) at index (a nt + b) nt + c; types[n] in [0, nt).  Outputs as
+ * or_energy_forces_brute (out[8] pairs, out[9] triplets).  Requires every
+ * edge >= 2 max(a sigma).
+ */
+int or_energy_forces_species(const double* table, int nt, const int* types, int n, const double* x,
+                             const double* box, double* f, double* out) {
+  if (n < 0 || or_species_table_check(table, nt) != OR_OK) return OR_EINVAL;
+  double rcmax = 0;
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      const double* e = sp_entry(table, nt, a, b, b);
+      if (e[3] * e[2] > rcmax) rcmax = e[3] * e[2];
+    }
+  if (box[0] < 2 * rcmax || box[1] < 2 * rcmax || box[2] < 2 * rcmax) return OR_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (types[i] < 0 || types[i] >= nt) return OR_EINVAL;
+  double E2 = 0, E3 = 0, W[7] = {0, 0, 0, 0, 0, 0, 0};
+  double npair = 0, ntrip = 0;
+  if (f) memset(f, 0, sizeof(double) * 3 * (size_t)n);
+  int cap = 64;
+  or_leg* legs = (or_leg*)malloc(sizeof(or_leg) * (size_t)cap);
+  if (!legs) return OR_ENOMEM;
+  for (int i = 0; i < n; ++i) {
+    const int ti = types[i];
+    int nl = 0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      const double* pij = sp_entry(table, nt, ti, types[j], types[j]);
+      double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+      min_image(box, d);
+      const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      if (!(r < pij[3] * pij[2])) continue;
+      if (nl == cap) {
+        cap *= 2;
+        or_leg* nlg = (or_leg*)realloc(legs, sizeof(or_leg) * (size_t)cap);
+        if (!nlg) {
+          free(legs);
+          return OR_ENOMEM;
+        }
+        legs = nlg;
+      }
+      legs[nl].j = j;
+      legs[nl].r = r;
+      for (int k = 0; k < 3; ++k) legs[nl].d[k] = d[k];
+      ++nl;
+      if (j > i) { /* pair term once per unordered pair */
+        E2 += or_phi2(pij, r);
+        const double dp = or_dphi2(pij, r);
+        double Fj[3];
+        for (int k = 0; k < 3; ++k) Fj[k] = -dp * d[k] / r;
+        if (f)
+          for (int k = 0; k < 3; ++k) {
+            f[3 * j + k] += Fj[k];
+            f[3 * i + k] -= Fj[k];
+          }
+        add_virial(W, d, Fj);
+        npair += 1;
+      }
+    }
+    for (int a = 0; a < nl; ++a)
+      for (int b = a + 1; b < nl; ++b) {
+        const int tj = types[legs[a].j], tk = types[legs[b].j];
+        double gj[3], gk[3];
+        E3 += sp_tri_grad(sp_entry(table, nt, ti, tj, tk), sp_entry(table, nt, ti, tj, tj),
+                          sp_entry(table, nt, ti, tk, tk), legs[a].d, legs[a].r, legs[b].d, legs[b].r, gj, gk);
+        double Fj[3] = {-gj[0], -gj[1], -gj[2]}, Fk[3] = {-gk[0], -gk[1], -gk[2]};
+        if (f)
+          for (int d = 0; d < 3; ++d) {
+            f[3 * legs[a].j + d] += Fj[d];
+            f[3 * legs[b].j + d] += Fk[d];
+            f[3 * i + d] -= Fj[d] + Fk[d];
+          }
+        add_virial(W, legs[a].d, Fj);
+        add_virial(W, legs[b].d, Fk);
+        ntrip += 1;
+      }
+  }
+  free(legs);
+  out[0] = E2;
+  out[1] = E3;
+  for (int k = 0; k < 6; ++k) out[2 + k] = W[k];
+  out[8] = npair;
+  out[9] = ntrip;
+  out[10] = W[6];
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* Dynamics: velocity Verlet with an optional thermostat (Sec. II.B).   */
 /* ------------------------------------------------------------------ */
 
@@ -490,14 +651,43 @@ static void nh_half(int n, double* v, double* ke, double* xi, double* eta, doubl
  * conserved = ke + pe (+ Q xi^2 / 2 + Ndf kB T0 eta under Nose-Hoover).
  * Positions are wrapped into [0, L).  Ndf = 3n - 3.
  */
+typedef struct {
+  const double* prm; /* one species: parameter vector */
+  const double* table; /* several species: nt^3 vectors, or NULL */
+  int nt;
+  const int* types;
+} md_pot;
+
+static int md_forces(const md_pot* pot, int n, const double* x, const double* box, double* f, double* out) {
+  if (pot->table) return or_energy_forces_species(pot->table, pot->nt, pot->types, n, x, box, f, out);
+  return or_energy_forces_cell(pot->prm, n, x, box, f, out);
+}
+
+static int md_run(const md_pot* pot, int n, double* x, double* v, const double* box, double mass, double dt,
+                  int kind, double T0, double tau, int nsteps, double* state, double* thermo);
+
 int or_md(const double* prm, int n, double* x, double* v, const double* box, double mass, double dt,
           int kind, double T0, double tau, int nsteps, double* state, double* thermo) {
+  const md_pot pot = {prm, NULL, 0, NULL};
+  return md_run(&pot, n, x, v, box, mass, dt, kind, T0, tau, nsteps, state, thermo);
+}
+
+/* or_md with the several-species potential of or_energy_forces_species. */
+int or_md_species(const double* table, int nt, const int* types, int n, double* x, double* v, const double* box,
+                  double mass, double dt, int kind, double T0, double tau, int nsteps, double* state,
+                  double* thermo) {
+  const md_pot pot = {NULL, table, nt, types};
+  return md_run(&pot, n, x, v, box, mass, dt, kind, T0, tau, nsteps, state, thermo);
+}
+
+static int md_run(const md_pot* pot, int n, double* x, double* v, const double* box, double mass, double dt,
+                  int kind, double T0, double tau, int nsteps, double* state, double* thermo) {
   if (n < 2 || kind < 0 || kind > 2) return OR_EINVAL;
   double* f = (double*)malloc(sizeof(double) * 3 * (size_t)n);
   if (!f) return OR_ENOMEM;
   double out[11];
   for (int i = 0; i < 3 * n; ++i) x[i] = wrap1(x[i], box[i % 3]);
-  int rc = or_energy_forces_cell(prm, n, x, box, f, out);
+  int rc = md_forces(pot, n, x, box, f, out);
   if (rc != OR_OK) {
     free(f);
     return rc;
@@ -512,7 +702,7 @@ int or_md(const double* prm, int n, double* x, double* v, const double* box, dou
       if (kind == 2) nh_half(n, v, &ke, &xi, &eta, dt, Ndf, T0, Q);
       for (int i = 0; i < 3 * n; ++i) v[i] += cf * f[i];
       for (int i = 0; i < 3 * n; ++i) x[i] = wrap1(x[i] + dt * v[i], box[i % 3]);
-      rc = or_energy_forces_cell(prm, n, x, box, f, out);
+      rc = md_forces(pot, n, x, box, f, out);
       if (rc != OR_OK) break;
       for (int i = 0; i < 3 * n; ++i) v[i] += cf * f[i];
       ke = kinetic(n, v, mass);

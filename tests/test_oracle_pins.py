@@ -464,3 +464,165 @@ def test_npt_conserved_quantity_is_second_order(orc):
         assert th[-1, 8] != th[0, 8]  # the box did move
     assert dev[0] < 5e-4
     assert 3.0 < dev[0] / dev[1] < 5.0
+
+
+# ---------------------------------------------------------------------------
+# Several species (Sec. IV's mW with solutes of other lambda, epsilon, sigma,
+# and the SW family of Fig. 2): a parameter vector per species triple.  Pinned
+# by reduction to the one-species oracle, by the entries a few isolated atoms
+# select, and by derivatives.
+
+def _mixed_table(orc, seed=0, nt=2):
+    """A table with every species pair and triplet different, symmetric in
+    the pair and in the two legs (the table rule the oracle checks)."""
+    rng = np.random.default_rng(seed)
+    p0 = orc.default_params()
+    pair = {}
+    for a in range(nt):
+        for b in range(a, nt):
+            q = p0.copy()
+            q[1] *= rng.uniform(0.7, 1.3)   # epsilon
+            q[2] *= rng.uniform(0.9, 1.1)   # sigma
+            q[3] *= rng.uniform(0.95, 1.05)  # a
+            q[4] *= rng.uniform(0.8, 1.2)   # gamma
+            q[5] *= rng.uniform(0.9, 1.1)   # A
+            q[6] *= rng.uniform(0.9, 1.1)   # B
+            pair[(a, b)] = pair[(b, a)] = q
+    tri = {}
+    for a in range(nt):
+        for b in range(nt):
+            for c in range(b, nt):
+                tri[(a, b, c)] = tri[(a, c, b)] = (rng.uniform(10, 30), rng.uniform(4, 8), rng.uniform(-0.5, -0.2))
+
+    def entry(a, b, c):
+        e = pair[(a, b)].copy() if b == c else p0.copy()
+        if b != c:  # (gamma, sigma, a) of a mixed entry are never read; lambda, epsilon, cos theta0 are
+            e[1:7] = pair[(a, b)][1:7]
+        if b == c:
+            e[0] = tri[(a, b, c)][0]
+            # the pair term reads epsilon from (a, b, b): the triplet (a, b, b) shares it
+            e[7] = tri[(a, b, c)][2]
+        else:
+            e[0], e[1], e[7] = tri[(a, b, c)]
+        return e
+    return orc.species_table(nt, entry)
+
+
+def test_species_one_type_is_the_one_species_oracle(orc):
+    x, box = _jittered(seed=31, n=300)
+    p = orc.default_params()
+    r1 = orc.energy_forces_species(x, box, np.zeros(len(x), int), orc.species_table(1, lambda a, b, c: p))
+    r0 = orc.energy_forces(x, box)
+    assert r1["e2"] == pytest.approx(r0["e2"], rel=1e-13)
+    assert r1["e3"] == pytest.approx(r0["e3"], rel=1e-13)
+    assert np.abs(r1["forces"] - r0["forces"]).max() < 1e-11
+    assert np.allclose(r1["virial"], r0["virial"], rtol=1e-12, atol=1e-9)
+    assert (r1["npairs"], r1["ntriplets"]) == (r0["npairs"], r0["ntriplets"])
+
+
+def test_species_labels_of_identical_species_do_not_matter(orc):
+    x, box = _jittered(seed=32, n=250)
+    p = orc.default_params()
+    ty = np.random.default_rng(3).integers(0, 3, len(x))
+    r3 = orc.energy_forces_species(x, box, ty, orc.species_table(3, lambda a, b, c: p))
+    r0 = orc.energy_forces(x, box)
+    assert r3["energy"] == pytest.approx(r0["energy"], rel=1e-13)
+    assert np.abs(r3["forces"] - r0["forces"]).max() < 1e-11
+
+
+def test_species_pair_term_takes_the_pair_entry(orc):
+    """Two atoms of species 0 and 1: the energy is phi2 of entry (0, 1, 1)
+    (= entry (1, 0, 0)), the one-species oracle's pair term with those
+    parameters, and the force is its derivative."""
+    t = _mixed_table(orc, seed=4)
+    box = np.array([30.0, 30.0, 30.0])
+    for r in (2.6, 3.1, 3.9):
+        x = np.array([[5.0, 5.0, 5.0], [5.0 + r * 0.6, 5.0 + r * 0.8, 5.0]])
+        res = orc.energy_forces_species(x, box, [0, 1], t)
+        pe = t[0, 1, 1]
+        assert res["e3"] == 0.0
+        assert res["e2"] == pytest.approx(orc.phi2(r, pe)[0], rel=1e-14)
+        assert res["forces"][1] == pytest.approx(-orc.dphi2(r, pe)[0] * np.array([0.6, 0.8, 0.0]), rel=1e-12)
+        assert orc.energy_forces_species(x, box, [1, 0], t)["e2"] == pytest.approx(res["e2"], rel=1e-14)
+
+
+def test_species_triplet_takes_the_centre_legs_entry(orc):
+    """Centre of species 0 with legs to species 1 and 2 that are out of each
+    other's range: the only triplet is (0; 1, 2), and with all leg parameters
+    equal its energy is the one-species oracle's with lambda, epsilon and
+    cos theta0 of entry (0, 1, 2)."""
+    p0 = orc.default_params()
+    lam = {(0, 1, 2): 17.0, (0, 2, 1): 17.0}
+    eps3 = {(0, 1, 2): 5.5, (0, 2, 1): 5.5}
+    c0 = {(0, 1, 2): -0.25, (0, 2, 1): -0.25}
+
+    def entry(a, b, c):
+        e = p0.copy()
+        if (a, b, c) in lam:
+            e[0], e[1], e[7] = lam[(a, b, c)], eps3[(a, b, c)], c0[(a, b, c)]
+        return e
+    t = orc.species_table(3, entry)
+    box = np.array([30.0, 30.0, 30.0])
+    ang = math.radians(150.0)
+    r1, r2 = 3.0, 3.6
+    x = np.array([[10.0, 10.0, 10.0], [10.0 + r1, 10.0, 10.0],
+                  [10.0 + r2 * math.cos(ang), 10.0 + r2 * math.sin(ang), 10.0]])
+    res = orc.energy_forces_species(x, box, [0, 1, 2], t)
+    assert res["ntriplets"] == 1
+    pt = p0.copy()
+    pt[0], pt[1], pt[7] = 17.0, 5.5, -0.25
+    assert res["e3"] == pytest.approx(orc.phi3(r1, r2, math.cos(ang), pt), rel=1e-13)
+    assert res["e3"] != pytest.approx(orc.phi3(r1, r2, math.cos(ang), p0), rel=1e-3)
+    # the same atoms with the centre of another species take that centre's entries
+    res2 = orc.energy_forces_species(x, box, [1, 0, 2], t)
+    assert res2["e3"] == pytest.approx(orc.phi3(r1, r2, math.cos(ang), p0), rel=1e-13)
+
+
+def test_species_forces_and_virial_are_derivatives(orc):
+    """A two-species mixture with every pair and triplet entry different:
+    F = -grad E (central differences) and tr W = -dE/d(ln s) under a uniform
+    scaling of positions and box."""
+    t = _mixed_table(orc, seed=7)
+    x, box = _jittered(seed=33, n=160)
+    ty = np.random.default_rng(8).integers(0, 2, len(x))
+    r = orc.energy_forces_species(x, box, ty, t)
+    assert r["e3"] > 0 and r["ntriplets"] > 0
+    h = 1e-5
+    rng = np.random.default_rng(9)
+    for i in rng.choice(len(x), 8, replace=False):
+        for k in range(3):
+            xp = x.copy()
+            xp[i, k] += h
+            xm = x.copy()
+            xm[i, k] -= h
+            fd = -(orc.energy_forces_species(xp, box, ty, t)["energy"]
+                   - orc.energy_forces_species(xm, box, ty, t)["energy"]) / (2 * h)
+            assert r["forces"][i, k] == pytest.approx(fd, rel=1e-6, abs=1e-6)
+    hs = 1e-6
+    ep = orc.energy_forces_species(x * (1 + hs), box * (1 + hs), ty, t)["energy"]
+    em = orc.energy_forces_species(x * (1 - hs), box * (1 - hs), ty, t)["energy"]
+    assert sum(r["virial"][:3]) == pytest.approx(-(ep - em) / (2 * hs), rel=1e-6)
+
+
+def test_species_table_rule_is_checked(orc):
+    t = _mixed_table(orc, seed=10)
+    assert orc.species_table_ok(t)
+    bad = t.copy()
+    bad[0, 1, 1, 1] *= 1.01  # pair (0, 1) no longer equals pair (1, 0)
+    assert not orc.species_table_ok(bad)
+    bad = t.copy()
+    bad[1, 0, 1, 0] += 1.0  # lambda of (1; 0, 1) differs from (1; 1, 0)
+    assert not orc.species_table_ok(bad)
+    with pytest.raises(RuntimeError):
+        orc.energy_forces_species(*_jittered(seed=34, n=50), np.zeros(50, int), bad)
+
+
+def test_species_dynamics_with_one_type_is_the_one_species_run(orc):
+    x, v, box = I.nve512()
+    p = orc.default_params()
+    t = orc.species_table(2, lambda a, b, c: p)
+    ty = np.arange(512) % 2
+    xa, va, sa, tha = orc.md_species(x, v, box, ty, t, 20, dt=10.0, kind=2, T0=298.0, tau=1000.0)
+    xb, vb, sb, thb = orc.md(x, v, box, 20, dt=10.0, kind=2, T0=298.0, tau=1000.0)
+    assert np.abs(xa - xb).max() < 1e-9 and np.abs(va - vb).max() < 1e-12
+    assert tha[-1, 5] == pytest.approx(thb[-1, 5], rel=1e-12)

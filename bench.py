@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--prep-steps", type=int, default=3000)
     ap.add_argument("--workload", default="ice_liquid_32k",
                     choices=["ice_liquid_32k", "nve512", "batch256", "slab1m", "fm4096x64", "structure_32k", "slab_gamma",
-                             "diffusion_4096", "npt_density_scan"])
+                             "diffusion_4096", "npt_density_scan", "solute_32k"])
     ap.add_argument("--drift-steps", type=int, default=0,
                     help="after timing, run this many NVE steps and report the energy drift per ns")
     return ap.parse_args()
@@ -455,6 +455,20 @@ def run_other(args, world, rank, local, pg):
         integ = mw.make_integrator(10.0, mw.MW_NVE)
         natoms = 512
         cfg = {"workload": "512-atom SC-jitter NVE, 1.000 g/cm^3, 298 K start, dt 10 fs", "atoms": 512}
+        flush_use = flush
+    elif args.workload == "solute_32k":
+        n = 32768
+        x, box = I.jittered_box(n, 1.0, 0.1, I.BASE_SEED + 5)
+        ty = I.species_draw(n, 2, I.BASE_SEED + 55, [0.9, 0.1])
+        v = I.maxwell_velocities(n, 400.0, seed=I.BASE_SEED + 56)
+        sysm = mw.System(n, box, stream=sp)
+        sysm.set_species(I.species_table_solute(), ty)
+        sysm.set_state(x, v)
+        sysm.step(1000, dt=5.0, thermostat=mw.MW_BERENDSEN, T0=400.0, tau=200.0)
+        integ = mw.make_integrator(10.0, mw.MW_NOSE_HOOVER, 298.0, TAU)
+        natoms = n
+        cfg = {"workload": "32768 atoms, mW + 10% two-body-only solute (two species), 1.0 g/cm^3, NH 298 K, "
+                           "dt 10 fs", "atoms": n, "species": 2}
         flush_use = flush
     elif args.workload == "batch256":
         n, boxes, x, v, T = I.batch_boxes(256, I.BASE_SEED + 3)

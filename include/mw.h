@@ -173,6 +173,24 @@ mw_status mw_get_unwrapped(mw_system* s, double* x);
  * its radius a sigma + skin follows sigma). */
 mw_status mw_set_params(mw_system* s, const mw_params* prm);
 
+/* Several species (Sec. IV: mW with solutes of their own lambda, epsilon,
+ * sigma; the SW family of Fig. 2 mixed).  table: nt^3 parameter sets, entry
+ * (a, b, c) at index (a nt + b) nt + c; types: n_total species in [0, nt),
+ * caller's atom order (host array, copied).  The pair term of atoms of
+ * species a and b uses entry (a, b, b), which must equal (b, a, a) in
+ * epsilon, sigma, a, A, B, p and q.  The three-body term of a centre of
+ * species a with legs to species b and c uses lambda, epsilon and
+ * cos_theta0 of entry (a, b, c), which must equal (a, c, b), and for each
+ * leg the gamma, sigma and a of that leg's pair entry.  1 <= nt <=
+ * MW_MAX_SPECIES; nt = 1 is mw_set_params(table[0]) (types unused).  The
+ * list radius becomes the largest a sigma + skin.  One mass for all atoms.
+ * While nt > 1, forces come from a kernel that walks every leg pair of each
+ * centre (slower than the one-species kernel); mw_step uses the graph engine
+ * and mw_energy_forces_vjp returns MW_EINVAL.  Calling mw_set_params returns
+ * to one species. */
+#define MW_MAX_SPECIES 8
+mw_status mw_set_species(mw_system* s, int nt, const mw_params* table, const int* types);
+
 /* Forces a cell binning + neighbour-list rebuild now; *max_count_out (may be
  * NULL) receives the widest neighbour set.  Grows the list if needed. */
 mw_status mw_build_neighbors(mw_system* s, int* max_count_out);

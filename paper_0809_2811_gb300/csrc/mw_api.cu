@@ -20,6 +20,9 @@
 #include "mw_persistent.cuh"
 #include "mw_adjoint.cuh"
 #include "mw_structure.cuh"
+#include "mw_species.cuh"
+
+static_assert(MW_MAX_SPECIES == mw::kMaxSpecies, "species limit of the header and the kernels");
 
 using namespace mw;
 
@@ -72,6 +75,13 @@ struct mw_system {
   bool need_prime = true;  // thermostat start half must be recomputed before the next step
   bool record_pending = false;  // steps ran since the last thermo record was written
   bool boxes_stale = false;     // an isobaric run changed the device's box geometry since the last pull
+  // several species (nsp > 1): the caller's table and the largest pair cutoff
+  int nsp = 1;
+  std::vector<mw_params> sp_table;
+  double sp_rc_max = 0;
+  int *typ_buf = nullptr, *ttyp_buf = nullptr, *utyp_buf = nullptr;
+  SpPair* sp_pair_buf = nullptr;
+  float2* sp_tri_buf = nullptr;
   long long regrids = 0;        // cell grids laid out again because an isobaric box left its grid
   unsigned long long* ana = nullptr;  // structure-analysis histograms (grow-only)
   size_t ana_cap = 0;
@@ -119,7 +129,9 @@ void dfree(mw_system* s, void* p) {
   cudaFree(p);
 }
 
-double r_list(const mw_system* s) { return s->prm.a * s->prm.sigma + s->skin; }
+// Largest interaction range: a sigma, or the widest pair's under several species.
+double cutoff(const mw_system* s) { return s->nsp > 1 ? s->sp_rc_max : s->prm.a * s->prm.sigma; }
+double r_list(const mw_system* s) { return cutoff(s) + s->skin; }
 
 mw_status check_params(const mw_params* p) {
   if (!p) return fail(MW_EINVAL, "params is NULL");
@@ -134,7 +146,7 @@ mw_status check_params(const mw_params* p) {
 
 void make_fparams(mw_system* s) {
   const mw_params& p = s->prm;
-  const double rc = p.a * p.sigma, rl = rc + s->skin;
+  const double rc = p.a * p.sigma, rl = r_list(s);  // r_list: the widest pair under several species
   const double l2e = 1.4426950408889634;
   FParams& f = s->fp;
   f.rc = (float)rc;
@@ -310,6 +322,13 @@ void launch_rebuild(mw_system* s) {
 
 void launch_force(mw_system* s) {
   const Dev& d = s->d;
+  if (s->nsp > 1) {
+    if (s->count_terms)
+      k_force_species<true><<<div_up(s->N, kSpThreads), kSpThreads, 0, s->stream>>>(d);
+    else
+      k_force_species<false><<<div_up(s->N, kSpThreads), kSpThreads, 0, s->stream>>>(d);
+    return;
+  }
   const int gb = div_up(s->N, kFAtoms);
   if (s->count_terms)
     k_force<true><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
@@ -569,6 +588,7 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   MW_CUDA(cudaMemcpyAsync(s->d.g, &g, sizeof(Global), cudaMemcpyHostToDevice, s->stream));
   const int gb = div_up(s->N, kThreads);
   k_load_positions<<<gb, kThreads, 0, s->stream>>>(s->d, xd, s->boxid, 1);
+  if (s->nsp > 1) k_gather_types<<<gb, kThreads, 0, s->stream>>>(s->d);
   k_load_velocities<<<gb, kThreads, 0, s->stream>>>(s->d, vd);
   k_ke_init<<<gb, kThreads, 0, s->stream>>>(s->d);
   MW_CUDA(cudaMemsetAsync(s->d.f, 0, sizeof(float4) * s->N, s->stream));
@@ -895,13 +915,18 @@ mw_status mw_set_params(mw_system* s, const mw_params* prm) {
   if ((st = check_params(prm)) != MW_OK) return st;
   if ((st = flush_pending(s)) != MW_OK) return st;  // the pending half-kick belongs to the old potential
   const mw_params old = s->prm;
+  const int old_nsp = s->nsp;
   s->prm = *prm;
+  s->nsp = 1;  // one species again
   int ncell;
   if ((st = layout_cells(s, &ncell)) != MW_OK) {
     s->prm = old;
+    s->nsp = old_nsp;
     layout_cells(s, &ncell);
     return st;
   }
+  s->d.nsp = 1;
+  s->d.typ = nullptr;
   make_fparams(s);
   s->ncell = ncell;
   if ((st = alloc_cells(s)) != MW_OK) return st;
@@ -909,6 +934,108 @@ mw_status mw_set_params(mw_system* s, const mw_params* prm) {
   s->graph_dirty = true;
   s->forces_valid = false;
   if (s->state_set) {
+    if ((st = flag_all(s)) != MW_OK) return st;
+  }
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  return MW_OK;
+}
+
+mw_status mw_set_species(mw_system* s, int nt, const mw_params* table, const int* types) {
+  if (!s) return fail(MW_EINVAL, "system is NULL");
+  if (nt < 1 || nt > MW_MAX_SPECIES) return fail(MW_EINVAL, "need 1 <= nt <= %d species", MW_MAX_SPECIES);
+  if (!table) return fail(MW_EINVAL, "table is NULL");
+  if (nt == 1) return mw_set_params(s, &table[0]);
+  if (!types) return fail(MW_EINVAL, "types is NULL");
+  mw_status st;
+  const size_t ne = (size_t)nt * nt * nt;
+  auto E = [&](int a, int b, int c) -> const mw_params& { return table[((size_t)a * nt + b) * nt + c]; };
+  for (size_t k = 0; k < ne; ++k)
+    if ((st = check_params(&table[k])) != MW_OK) return st;
+  double rcmax = 0;
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      const mw_params& ab = E(a, b, b);
+      const mw_params& ba = E(b, a, a);
+      if (ab.epsilon != ba.epsilon || ab.sigma != ba.sigma || ab.a != ba.a || ab.A != ba.A || ab.B != ba.B ||
+          ab.p != ba.p || ab.q != ba.q)
+        return fail(MW_EINVAL, "pair entries (%d,%d,%d) and (%d,%d,%d) differ in a two-body parameter", a, b, b,
+                    b, a, a);
+      rcmax = std::max(rcmax, ab.a * ab.sigma);
+      for (int c = 0; c < nt; ++c) {
+        const mw_params& abc = E(a, b, c);
+        const mw_params& acb = E(a, c, b);
+        if (abc.lambda != acb.lambda || abc.epsilon != acb.epsilon || abc.cos_theta0 != acb.cos_theta0)
+          return fail(MW_EINVAL, "entries (%d,%d,%d) and (%d,%d,%d) differ in lambda, epsilon or cos_theta0", a,
+                      b, c, a, c, b);
+      }
+    }
+  for (int i = 0; i < s->N; ++i)
+    if (types[i] < 0 || types[i] >= nt) return fail(MW_EINVAL, "types[%d] = %d is outside [0, %d)", i, types[i], nt);
+  // FP32 constants of every pair and triplet
+  const double l2e = 1.4426950408889634;
+  std::vector<SpPair> pairs((size_t)nt * nt);
+  std::vector<float2> tri(ne);
+  for (int a = 0; a < nt; ++a)
+    for (int b = 0; b < nt; ++b) {
+      const mw_params& p = E(a, b, b);
+      SpPair& q = pairs[(size_t)a * nt + b];
+      const double rc = p.a * p.sigma;
+      q.rc = (float)rc;
+      q.rc2 = (float)(rc * rc);
+      q.sig = (float)p.sigma;
+      q.sig_l2e = (float)(p.sigma * l2e);
+      q.gsig = (float)(p.gamma * p.sigma);
+      q.gsig_l2e = (float)(p.gamma * p.sigma * l2e);
+      q.Aeps = (float)(p.A * p.epsilon);
+      q.B = (float)p.B;
+      q.p = p.p;
+      q.q = p.q;
+      for (int c = 0; c < nt; ++c) {
+        const mw_params& t = E(a, b, c);
+        tri[((size_t)a * nt + b) * nt + c] = make_float2((float)(t.lambda * t.epsilon), (float)t.cos_theta0);
+      }
+    }
+  if ((st = flush_pending(s)) != MW_OK) return st;  // the pending half-kick belongs to the old potential
+  if (!s->typ_buf) {
+    if ((st = dalloc(s, &s->typ_buf, s->N)) != MW_OK || (st = dalloc(s, &s->ttyp_buf, s->N)) != MW_OK ||
+        (st = dalloc(s, &s->utyp_buf, s->N)) != MW_OK ||
+        (st = dalloc(s, &s->sp_pair_buf, (size_t)kMaxSpecies * kMaxSpecies)) != MW_OK ||
+        (st = dalloc(s, &s->sp_tri_buf, (size_t)kMaxSpecies * kMaxSpecies * kMaxSpecies)) != MW_OK)
+      return st;
+  }
+  MW_CUDA(cudaMemcpyAsync(s->sp_pair_buf, pairs.data(), sizeof(SpPair) * pairs.size(), cudaMemcpyHostToDevice,
+                          s->stream));
+  MW_CUDA(cudaMemcpyAsync(s->sp_tri_buf, tri.data(), sizeof(float2) * tri.size(), cudaMemcpyHostToDevice, s->stream));
+  MW_CUDA(cudaMemcpyAsync(s->utyp_buf, types, sizeof(int) * s->N, cudaMemcpyHostToDevice, s->stream));
+  const int old_nsp = s->nsp;
+  const double old_rc = s->sp_rc_max;
+  s->nsp = nt;
+  s->sp_rc_max = rcmax;
+  int ncell;
+  if ((st = layout_cells(s, &ncell)) != MW_OK) {
+    s->nsp = old_nsp;
+    s->sp_rc_max = old_rc;
+    layout_cells(s, &ncell);
+    return st;
+  }
+  s->sp_table.assign(table, table + ne);
+  s->d.nsp = nt;
+  s->d.typ = s->typ_buf;
+  s->d.ttyp = s->ttyp_buf;
+  s->d.utyp = s->utyp_buf;
+  s->d.sp_pair = s->sp_pair_buf;
+  s->d.sp_tri = s->sp_tri_buf;
+  make_fparams(s);
+  s->ncell = ncell;
+  if ((st = alloc_cells(s)) != MW_OK) return st;
+  if ((st = upload_boxes(s)) != MW_OK) return st;
+  const int w = initial_width(s);
+  if (w > s->W && (st = alloc_nbr(s, w)) != MW_OK) return st;
+  s->graph_dirty = true;
+  s->forces_valid = false;
+  if (s->state_set) {
+    k_gather_types<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d);
+    MW_CUDA(cudaGetLastError());
     if ((st = flag_all(s)) != MW_OK) return st;
   }
   MW_CUDA(cudaStreamSynchronize(s->stream));

@@ -133,6 +133,15 @@ struct FParams {     // FP32 constants of the force kernels
   int p, q;
 };
 
+// Several species: FP32 constants of the pair (a, b), from the parameter
+// set of entry (a, b, b); the three-body leg factor of a leg from a centre
+// of species a to one of species b uses the same set's gamma, sigma, a.
+constexpr int kMaxSpecies = 8;
+struct SpPair {
+  float rc, rc2, sig, sig_l2e, gsig, gsig_l2e, Aeps, B;
+  int p, q;
+};
+
 struct Dev {
   int N, W, ncell, nbox;
   // master state: positions as 64-bit box fractions (s 2^64, wrapping), velocities
@@ -159,6 +168,13 @@ struct Dev {
   const Integ* integ;
   double* stage;      // n*3 doubles staging (user order)
   double* stage2;
+  // several species (null / 1 for one species): species of each sorted atom
+  // and its staging copy, the caller-order species, and the tables
+  int *typ, *ttyp;
+  const int* utyp;
+  const SpPair* sp_pair;  // nsp^2, (a, b) at a nsp + b
+  const float2* sp_tri;   // nsp^3: (lambda epsilon, cos theta0) of (centre a; legs b, c)
+  int nsp;
 };
 
 // ---------------------------------------------------------------------------
@@ -1183,6 +1199,7 @@ __device__ __forceinline__ void scatter_item(const Dev& d, int i) {
   d.tid[p] = d.id[i];
   d.tq[p] = d.q[i];
   d.timg[p] = d.img[i];
+  if (d.typ) d.ttyp[p] = d.typ[i];
 }
 
 // a2: staging arrays back to the state arrays; build positions recorded.
@@ -1192,6 +1209,7 @@ __device__ __forceinline__ void copyback_item(const Dev& d, int i) {
   d.vx[i] = d.tvx[i]; d.vy[i] = d.tvy[i]; d.vz[i] = d.tvz[i];
   d.id[i] = d.tid[i];
   d.img[i] = d.timg[i];
+  if (d.typ) d.typ[i] = d.ttyp[i];
   const uint4 q = d.tq[i];
   d.q[i] = q;
   d.qb[i] = q;

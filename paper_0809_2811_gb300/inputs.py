@@ -18,6 +18,14 @@ Recipes (workloads of the paper's kind; there is no dataset to stand in for):
     T uniform in [200, 320] K, jittered simple-cubic start of
     n = ceil(N^(1/3)) sites per edge with N sites picked by a seeded
     permutation.
+  * several species: parameter tables (nt, nt, nt, 10), entry (a, b, c) the
+    set of centre a with legs to b and c, last axis (lambda, epsilon, sigma,
+    a, gamma, A, B, cos theta0, p, q).  Three recipes: every pair and triplet
+    different (seeded factors around the paper's mW values, the pair set
+    shared by (a, b, b) and (b, a, a), the triplet set by (a, b, c) and
+    (a, c, b)); mW with a solute that has two-body terms only; the SW family
+    of Fig. 2 (lambda 20, 21, 23.15, 26.2) mixed by geometric means.
+    Species are assigned to atoms by a seeded draw.
 """
 from __future__ import annotations
 
@@ -192,3 +200,87 @@ def liquid_vapor_slab(n: int = 1024, lxy: float = 30.0, lz: float = 100.0, rho: 
     z0 = 0.5 * (lz - t)
     x = lattice_fill(n, [0.0, 0.0, z0], [lxy, lxy, z0 + t], rho, jitter, seed)
     return x, np.array([lxy, lxy, lz])
+
+
+# ---------------------------------------------------------------------------
+# Several species.
+
+# The paper's mW set (Sec. II.A and II.D) in table layout: lambda, epsilon,
+# sigma, a, gamma, A, B, cos theta0, p, q.
+MW_SET = np.array([23.15, 6.189, 2.3925, 1.8, 1.2, 7.049556277, 0.6022245584, -1.0 / 3.0, 4.0, 0.0])
+
+
+def species_table_mixed(nt: int, seed: int = 0) -> np.ndarray:
+    """Every pair and triplet set different: seeded factors on epsilon, sigma,
+    a, gamma, A, B of each unordered pair and on lambda, epsilon, cos theta0
+    of each centre and unordered leg pair."""
+    rng = np.random.default_rng(seed)
+    pair = {}
+    for a in range(nt):
+        for b in range(a, nt):
+            q = MW_SET.copy()
+            q[1] *= rng.uniform(0.7, 1.3)
+            q[2] *= rng.uniform(0.9, 1.1)
+            q[3] *= rng.uniform(0.95, 1.05)
+            q[4] *= rng.uniform(0.8, 1.2)
+            q[5] *= rng.uniform(0.9, 1.1)
+            q[6] *= rng.uniform(0.9, 1.1)
+            pair[(a, b)] = pair[(b, a)] = q
+    t = np.zeros((nt, nt, nt, 10))
+    for a in range(nt):
+        for b in range(nt):
+            for c in range(b, nt):
+                lam = MW_SET[0] * rng.uniform(0.6, 1.3)
+                c0 = rng.uniform(-0.5, -0.2)
+                eps = pair[(a, b)][1] if b == c else MW_SET[1] * rng.uniform(0.7, 1.3)
+                for bb, cc in ((b, c), (c, b)):
+                    e = pair[(a, bb)].copy()
+                    e[0], e[1], e[7] = lam, eps, c0
+                    t[a, bb, cc] = e
+    return t
+
+
+def species_table_solute(eps_ss: float = 0.34, sig_ss: float = 3.4, eps_ws: float = 0.25,
+                         sig_ws: float = 2.9) -> np.ndarray:
+    """Species 0 = mW, species 1 = a solute with two-body terms only (lambda
+    = 0 in every triplet that holds it): a hydrophobic particle of the kind
+    Sec. IV discusses.  Sizes in A, energies in kcal/mol."""
+    t = np.zeros((2, 2, 2, 10))
+    for a in range(2):
+        for b in range(2):
+            for c in range(2):
+                e = MW_SET.copy()
+                if (a, b) == (1, 1):
+                    e[1], e[2] = eps_ss, sig_ss
+                elif a != b:
+                    e[1], e[2] = eps_ws, sig_ws
+                if a == 1 or b == 1 or c == 1:
+                    e[0] = 0.0
+                    if b != c:
+                        e[1] = MW_SET[1]
+                t[a, b, c] = e
+    # the (a, b, b) sets carry the pair's epsilon, sigma; mixed triplets use
+    # lambda = 0, so their epsilon is immaterial but kept symmetric
+    return t
+
+
+def species_table_sw_family() -> np.ndarray:
+    """Fig. 2's tetrahedral family as four species: lambda = 20 (Ge), 21 (Si),
+    23.15 (water), 26.2 (C), all in the mW energy and length scales; a pair
+    or triplet takes the geometric mean of the lambdas involved."""
+    lams = [20.0, 21.0, 23.15, 26.2]
+    nt = len(lams)
+    t = np.zeros((nt, nt, nt, 10))
+    for a in range(nt):
+        for b in range(nt):
+            for c in range(nt):
+                e = MW_SET.copy()
+                e[0] = (lams[a] * lams[min(b, c)] * lams[max(b, c)]) ** (1.0 / 3.0)  # same for (a, c, b)
+                t[a, b, c] = e
+    return t
+
+
+def species_draw(n: int, nt: int, seed: int = 0, weights=None) -> np.ndarray:
+    """Seeded species of n atoms (int32), drawn with the given weights."""
+    rng = np.random.default_rng(seed)
+    return rng.choice(nt, size=n, p=weights).astype(np.int32)

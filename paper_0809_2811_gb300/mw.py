@@ -30,7 +30,7 @@ EXPORTS = (
     "mw_get_neighbors", "mw_energy_forces", "mw_energy_forces_dev", "mw_step", "mw_get_thermo",
     "mw_energy_forces_vjp", "mw_set_engine", "mw_set_nbr_width", "mw_autotune", "mw_get_info",
     "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc", "mw_set_skin", "mw_phase_times",
-    "mw_pair_histogram", "mw_angle_histogram", "mw_get_unwrapped", "mw_get_box", "mw_last_error",
+    "mw_pair_histogram", "mw_angle_histogram", "mw_get_unwrapped", "mw_get_box", "mw_set_species", "mw_last_error",
 )
 
 
@@ -120,6 +120,7 @@ def lib():
             "mw_pair_histogram": [P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)],
             "mw_get_unwrapped": [P, dp],
             "mw_get_box": [P, dp],
+            "mw_set_species": [P, ctypes.c_int, ctypes.POINTER(mw_params), ip],
             "mw_angle_histogram": [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)],
             "mw_energy_forces_noalloc": [ctypes.c_int, dp, ctypes.POINTER(mw_params), ctypes.c_double, P, P, P, P,
                                          P],
@@ -235,6 +236,37 @@ def mw_energy_forces(h: int, n_total: int, nbox: int):
 
 def mw_energy_forces_dev(h: int, x_dev=None, f_dev=None, energy_dev=None, virial_dev=None):
     _check(lib().mw_energy_forces_dev(h, _ptr(x_dev), _ptr(f_dev), _ptr(energy_dev), _ptr(virial_dev)))
+
+
+MW_MAX_SPECIES = 8
+PARAM_FIELDS = ("lambda_", "epsilon", "sigma", "a", "gamma", "A", "B", "cos_theta0", "p", "q")
+
+
+def species_params(table) -> "ctypes.Array":
+    """nt^3 mw_params from an (nt, nt, nt, 10) array whose last axis is
+    (lambda, epsilon, sigma, a, gamma, A, B, cos_theta0, p, q), or from a
+    flat sequence of mw_params in (a nt + b) nt + c order."""
+    if isinstance(table, np.ndarray):
+        t = np.asarray(table, np.float64)
+        nt = t.shape[0]
+        assert t.shape == (nt, nt, nt, 10), t.shape
+        arr = (mw_params * (nt ** 3))()
+        for k, row in enumerate(t.reshape(-1, 10)):
+            for f, v in zip(PARAM_FIELDS, row):
+                setattr(arr[k], f, int(v) if f in ("p", "q") else float(v))
+        return arr
+    arr = (mw_params * len(table))()
+    for k, e in enumerate(table):
+        arr[k] = e
+    return arr
+
+
+def mw_set_species(h: int, table, types):
+    arr = species_params(table)
+    nt = int(round(len(arr) ** (1.0 / 3.0)))
+    ty = np.ascontiguousarray(types, np.int32) if types is not None else None
+    _check(lib().mw_set_species(h, nt, arr, ty.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if ty is not None
+                                else None))
 
 
 def make_integrator(dt=10.0, thermostat=MW_NVE, T0=300.0, tau=1000.0, T0_per_box=None, p_ext=1.0,
@@ -402,6 +434,10 @@ class System:
              tau_p=5000.0):
         it = make_integrator(dt, thermostat, T0, tau, T0_per_box, p_ext, tau_p)
         return mw_step(self.h, it, nsteps, self.nbox)
+
+    def set_species(self, table, types):
+        """Several species: table (nt, nt, nt, 10) or nt^3 mw_params, types per atom (caller's order)."""
+        mw_set_species(self.h, table, types)
 
     def box(self) -> np.ndarray:
         """Current edges of every box (nbox x 3, A); they change under MW_NPT."""

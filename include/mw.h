@@ -124,6 +124,8 @@ typedef struct mw_info {
   int64_t npairs, ntriplets; /* legs r < a sigma (unordered pairs) and triplets at the last force call */
   int64_t rebuild_steps;     /* steps and force calls that rebuilt at least one box since mw_set_state */
   int64_t regrids;           /* cell grids laid out again because an MW_NPT box left its grid */
+  int species;               /* species of the potential (1 unless mw_set_species set more) */
+  int species_moments;       /* 1: the species table factors into leg weights and the moment kernel runs */
 } mw_info;
 
 typedef struct mw_system mw_system;
@@ -184,10 +186,13 @@ mw_status mw_set_params(mw_system* s, const mw_params* prm);
  * leg the gamma, sigma and a of that leg's pair entry.  1 <= nt <=
  * MW_MAX_SPECIES; nt = 1 is mw_set_params(table[0]) (types unused).  The
  * list radius becomes the largest a sigma + skin.  One mass for all atoms.
- * While nt > 1, forces come from a kernel that walks every leg pair of each
- * centre (slower than the one-species kernel); mw_step uses the graph engine
- * and mw_energy_forces_vjp returns MW_EINVAL.  Calling mw_set_params returns
- * to one species. */
+ * When lambda epsilon of every (a, b, c) is h_ab h_ac (h_ab = sqrt(lambda
+ * epsilon) of (a, b, b), to 1e-9 relative: geometric-mean mixing, a solute
+ * with lambda = 0) and cos_theta0 depends on the centre's species alone, the
+ * one-species moment kernel runs with per-leg constants; otherwise a kernel
+ * that walks every leg pair of each centre (several times slower).  While
+ * nt > 1, mw_step uses the graph engine and mw_energy_forces_vjp returns
+ * MW_EINVAL.  Calling mw_set_params returns to one species. */
 #define MW_MAX_SPECIES 8
 mw_status mw_set_species(mw_system* s, int nt, const mw_params* table, const int* types);
 

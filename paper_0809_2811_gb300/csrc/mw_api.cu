@@ -77,6 +77,7 @@ struct mw_system {
   bool boxes_stale = false;     // an isobaric run changed the device's box geometry since the last pull
   // several species (nsp > 1): the caller's table and the largest pair cutoff
   int nsp = 1;
+  bool sp_moment = false;  // the table factors into leg weights: moment kernel (k_force_sp)
   std::vector<mw_params> sp_table;
   double sp_rc_max = 0;
   int *typ_buf = nullptr, *ttyp_buf = nullptr, *utyp_buf = nullptr;
@@ -146,7 +147,7 @@ mw_status check_params(const mw_params* p) {
 
 void make_fparams(mw_system* s) {
   const mw_params& p = s->prm;
-  const double rc = p.a * p.sigma, rl = r_list(s);  // r_list: the widest pair under several species
+  const double rc = cutoff(s), rl = r_list(s);  // the widest pair under several species
   const double l2e = 1.4426950408889634;
   FParams& f = s->fp;
   f.rc = (float)rc;
@@ -322,6 +323,14 @@ void launch_rebuild(mw_system* s) {
 
 void launch_force(mw_system* s) {
   const Dev& d = s->d;
+  if (s->nsp > 1 && s->sp_moment) {
+    const int gb = div_up(s->N, kFAtoms);
+    if (s->count_terms)
+      k_force_sp<true><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
+    else
+      k_force_sp<false><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
+    return;
+  }
   if (s->nsp > 1) {
     if (s->count_terms)
       k_force_species<true><<<div_up(s->N, kSpThreads), kSpThreads, 0, s->stream>>>(d);
@@ -990,11 +999,24 @@ mw_status mw_set_species(mw_system* s, int nt, const mw_params* table, const int
       q.B = (float)p.B;
       q.p = p.p;
       q.q = p.q;
+      q.h = (float)std::sqrt(std::max(0.0, E(a, b, b).lambda * E(a, b, b).epsilon));
+      q.c0 = (float)E(a, 0, 0).cos_theta0;
       for (int c = 0; c < nt; ++c) {
         const mw_params& t = E(a, b, c);
         tri[((size_t)a * nt + b) * nt + c] = make_float2((float)(t.lambda * t.epsilon), (float)t.cos_theta0);
       }
     }
+  // moment kernel when lambda epsilon of (a; b, c) = h_ab h_ac (to 1e-9) and
+  // cos theta0 is the centre's
+  bool moment = true;
+  for (int a = 0; a < nt && moment; ++a)
+    for (int b = 0; b < nt && moment; ++b)
+      for (int c = 0; c < nt && moment; ++c) {
+        const mw_params& t = E(a, b, c);
+        const double le = t.lambda * t.epsilon;
+        const double hh = std::sqrt(E(a, b, b).lambda * E(a, b, b).epsilon * E(a, c, c).lambda * E(a, c, c).epsilon);
+        if (t.cos_theta0 != E(a, 0, 0).cos_theta0 || std::fabs(le - hh) > 1e-9 * std::max(le, hh)) moment = false;
+      }
   if ((st = flush_pending(s)) != MW_OK) return st;  // the pending half-kick belongs to the old potential
   if (!s->typ_buf) {
     if ((st = dalloc(s, &s->typ_buf, s->N)) != MW_OK || (st = dalloc(s, &s->ttyp_buf, s->N)) != MW_OK ||
@@ -1019,6 +1041,7 @@ mw_status mw_set_species(mw_system* s, int nt, const mw_params* table, const int
     return st;
   }
   s->sp_table.assign(table, table + ne);
+  s->sp_moment = moment;
   s->d.nsp = nt;
   s->d.typ = s->typ_buf;
   s->d.ttyp = s->ttyp_buf;
@@ -1288,6 +1311,8 @@ mw_status mw_get_info(mw_system* s, mw_info* out) {
   out->ntriplets = s->ntrip;
   out->rebuild_steps = g.rebuild_steps;
   out->regrids = s->regrids;
+  out->species = s->nsp;
+  out->species_moments = (s->nsp > 1 && s->sp_moment) ? 1 : 0;
   return MW_OK;
 }
 

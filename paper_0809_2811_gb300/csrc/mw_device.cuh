@@ -137,9 +137,13 @@ struct FParams {     // FP32 constants of the force kernels
 // set of entry (a, b, b); the three-body leg factor of a leg from a centre
 // of species a to one of species b uses the same set's gamma, sigma, a.
 constexpr int kMaxSpecies = 8;
+// h and c0 serve the moment kernel, for tables whose lambda epsilon of
+// (centre a; legs b, c) is h_ab h_ac and whose cos theta0 depends on the
+// centre alone: h = sqrt(lambda epsilon) of (a, b, b), c0 = cos theta0 of a.
 struct SpPair {
   float rc, rc2, sig, sig_l2e, gsig, gsig_l2e, Aeps, B;
   int p, q;
+  float h, c0;
 };
 
 struct Dev {
@@ -811,10 +815,16 @@ constexpr int kWAtoms = 32 / kG;         // centres per warp
 constexpr int kLPad = kLMax + 1;         // row pitch (float4): shifts rows by 4 banks
 constexpr int kPre = 8;                  // neighbour slots per lane fetched ahead in the leg phase
 
-struct LegTable {
-  float4 ue[kFAtoms * kLPad];   // ux, uy, uz, ee
-  float4 aux[kFAtoms * kLPad];  // tr, nde, r, j (int bits)
+template <int kPad>
+struct LegTableT {
+  float4 ue[kFAtoms * kPad];   // ux, uy, uz, ee
+  float4 aux[kFAtoms * kPad];  // tr, nde, r, j (int bits)
 };
+using LegTable = LegTableT<kLPad>;
+// Several species: a solute's larger cutoff gives its centres more legs, so
+// the species instantiation stages up to 48 (row pitch 49 float4, 4 banks).
+constexpr int kLMaxSp = 48;
+using LegTableSp = LegTableT<kLMaxSp + 1>;
 
 // Whole owner contribution (pair terms and three-body terms) of a centre with
 // more than kLMax legs (rare): legs in local memory, every unordered leg pair
@@ -917,10 +927,22 @@ __device__ __noinline__ void force_overflow_item(const Dev& d, const FParams& P,
   for (int k = 0; k < 6; ++k) atomicAdd(p + 2 + k, (double)w[k]);
 }
 
-// One block of kFAtoms centres (atoms blk*kFAtoms ...); every thread of the
-// block calls it.
 template <bool kCount>
-__device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk, int par) {
+__device__ __noinline__ int species_item(const Dev& d, const SpPair* sp, const float2* st, int nsp, int i,
+                                         float (&acc)[8]);
+
+// One block of kFAtoms centres (atoms blk*kFAtoms ...); every thread of the
+// block calls it.  kSp: several species whose three-body strengths factor
+// into leg weights (SpPair::h) and whose cos theta0 is the centre's
+// (SpPair::c0); sps is the nsp^2 pair table in shared memory.  Every leg
+// then carries its own pair constants and weight and the moments stay exact;
+// P.rc is the widest pair cutoff (the leg test of phase A), and a leg
+// beyond its own pair's cutoff is dropped in phase B.
+template <bool kCount, bool kSp = false>
+__device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLMaxSp : kLMax) + 1>& T, int blk,
+                            int par, const SpPair* sps = nullptr, int nsp = 1) {
+  constexpr int kLM = kSp ? kLMaxSp : kLMax;  // legs staged per centre
+  constexpr int kLP = kLM + 1;                // row pitch
   const int lane = threadIdx.x & 31;
   const int g = threadIdx.x & (kG - 1);
   const int a = threadIdx.x / kG;
@@ -931,6 +953,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
   uint4 qi = make_uint4(0u, 0u, 0u, 0u);
   int cnt = 0, b = -1;
   float L0 = 0.f, L1 = 0.f, L2 = 0.f;
+  const SpPair* spi = nullptr;  // the centre's row of the pair table (kSp)
   if (valid) {
     qi = d.q[i];
     b = (int)qi.w;
@@ -939,6 +962,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
     L0 = bx.Lq[0];
     L1 = bx.Lq[1];
     L2 = bx.Lq[2];
+    if constexpr (kSp) spi = sps + d.typ[i] * nsp;
   }
   // ---- leg phase A: row entries and candidate positions are fetched for
   // kPre slots per lane before any is used (two memory latencies per batch
@@ -949,7 +973,8 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
   const unsigned gsh = lane & ~(kG - 1);
   const int* row = d.nbr + (size_t)(valid ? i : 0) * d.W;
   int nl = 0;
-  auto test_slot = [&](int j, uint32_t jx, uint32_t jy, uint32_t jz, bool have) {
+  // (kSp: the partner's species rides in the record's x slot until phase B)
+  auto test_slot = [&](int j, uint32_t jx, uint32_t jy, uint32_t jz, int tj, bool have) {
     bool hit = false;
     float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
     if (have) {
@@ -957,13 +982,16 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
       dy = fix_diff(qi.y, jy, L1);
       dz = fix_diff(qi.z, jz, L2);
       r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      hit = r2 < P.rc2;
+      if constexpr (kSp)
+        hit = r2 < spi[tj].rc2;
+      else
+        hit = r2 < P.rc2;
     }
     const unsigned m = (__ballot_sync(kFull, hit) >> gsh) & ((1u << kG) - 1u);
     const int pos = nl + __popc(m & ((1u << g) - 1u));
-    if (hit && pos < kLMax) {
-      T.ue[a * kLPad + pos] = make_float4(dx, dy, dz, r2);
-      T.aux[a * kLPad + pos] = make_float4(0.f, 0.f, 0.f, __int_as_float(j));
+    if (hit && pos < kLM) {
+      T.ue[a * kLP + pos] = make_float4(dx, dy, dz, r2);
+      T.aux[a * kLP + pos] = make_float4(__int_as_float(tj), 0.f, 0.f, __int_as_float(j));
     }
     nl += __popc(m);
   };
@@ -973,6 +1001,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
   for (int t0 = 0; t0 < iters; t0 += kPre) {  // warp-uniform
     int jr[kPre];
     uint32_t qx[kPre], qy[kPre], qz[kPre];
+    int tj[kPre];
 #pragma unroll
     for (int t = 0; t < kPre; ++t) {
       const int s = g + kG * (t0 + t);
@@ -985,54 +1014,89 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
       qx[t] = qj.x;
       qy[t] = qj.y;
       qz[t] = qj.z;
+      tj[t] = 0;
+      if constexpr (kSp)
+        if (jr[t] >= 0) tj[t] = d.typ[jr[t]];
     }
 #pragma unroll
     for (int t = 0; t < kPre; ++t)
-      if (t0 + t < iters) test_slot(jr[t], qx[t], qy[t], qz[t], jr[t] >= 0);
+      if (t0 + t < iters) test_slot(jr[t], qx[t], qy[t], qz[t], tj[t], jr[t] >= 0);
   }
   __syncwarp();
   // ---- leg phase B: leg terms for the compacted legs only, spread over the
   // group's lanes: pair term (owner computes), the leg's table entry and its
   // share of the centre's moments S0, s, M.
-  const int nstage = (nl <= kLMax) ? nl : 0;  // larger centres: force_overflow_item does everything
+  const int nstage = (nl <= kLM) ? nl : 0;  // larger centres: force_overflow_item does everything
   float m0 = 0.f, msx = 0.f, msy = 0.f, msz = 0.f;                            // S0, s
   float mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;     // M
+  int nvalid = 0;  // legs inside their own pair's cutoff (kSp counting)
   for (int l = g; l < nstage; l += kG) {
-    float4* ue_p = T.ue + a * kLPad + l;
-    float4* ax_p = T.aux + a * kLPad + l;
+    float4* ue_p = T.ue + a * kLP + l;
+    float4* ax_p = T.aux + a * kLP + l;
     const float4 rec = *ue_p;
+    // the leg's constants: the one species', or its pair's (kSp)
+    float p_rc = P.rc, p_sig = P.sig, p_sig_l2e = P.sig_l2e, p_gsig = P.gsig, p_gsig_l2e = P.gsig_l2e;
+    float p_Aeps = P.Aeps, p_B = P.B, p_h = P.sle;
+    int p_p = P.p, p_q = P.q;
+    if constexpr (kSp) {
+      const SpPair& pp = spi[__float_as_int(ax_p->x)];
+      p_rc = pp.rc;
+      p_sig = pp.sig;
+      p_sig_l2e = pp.sig_l2e;
+      p_gsig = pp.gsig;
+      p_gsig_l2e = pp.gsig_l2e;
+      p_Aeps = pp.Aeps;
+      p_B = pp.B;
+      p_h = pp.h;
+      p_p = pp.p;
+      p_q = pp.q;
+    }
     const float r2 = rec.w;
     const float invr = rsqrtf(r2);
     const float r = r2 * invr;
-    if (!(r < P.rc)) {  // FP32 rounding put it on the cutoff: contributes nothing
+    if (!(r < p_rc)) {  // FP32 rounding put it on the cutoff (or past its pair's): contributes nothing
       *ue_p = make_float4(0.f, 0.f, 0.f, 0.f);
       continue;
     }
+    if constexpr (kSp && kCount) ++nvalid;
     const float ux = rec.x * invr, uy = rec.y * invr, uz = rec.z * invr;
-    const float tinv = __fdividef(1.0f, r - P.rc);  // 1/(r - a sig) < 0
-    const float e2 = exp2f(P.sig_l2e * tinv);
-    const float ee = P.sle * exp2f(P.gsig_l2e * tinv);
-    const float sr = P.sig * invr;
+    const float tinv = __fdividef(1.0f, r - p_rc);  // 1/(r - a sig) < 0
+    const float e2 = exp2f(p_sig_l2e * tinv);
+    const float ee = p_h * exp2f(p_gsig_l2e * tinv);
+    const float sr = p_sig * invr;
     float srp, srq;
-    if (P.p == 4 && P.q == 0) {  // the SW / mW exponents
+    if (p_p == 4 && p_q == 0) {  // the SW / mW exponents
       const float sr2 = sr * sr;
       srp = sr2 * sr2;
       srq = 1.0f;
     } else {
-      srp = powi(sr, P.p);
-      srq = powi(sr, P.q);
+      srp = powi(sr, p_p);
+      srq = powi(sr, p_q);
     }
-    const float brk = fmaf(P.B, srp, -srq);
-    const float ae2 = P.Aeps * e2;
+    const float brk = fmaf(p_B, srp, -srq);
+    const float ae2 = p_Aeps * e2;
     const float phi = ae2 * brk;
-    const float dphi = ae2 * (fmaf((float)(-P.p) * P.B, srp, (float)P.q * srq) * invr - brk * P.sig * tinv * tinv);
+    const float dphi = ae2 * (fmaf((float)(-p_p) * p_B, srp, (float)p_q * srq) * invr - brk * p_sig * tinv * tinv);
     acc[0] = fmaf(0.5f, phi, acc[0]);
     fx = fmaf(dphi, ux, fx);
     fy = fmaf(dphi, uy, fy);
     fz = fmaf(dphi, uz, fz);
+    if constexpr (kSp) {
+      if (p_h == 0.f) {  // no three-body weight (a lambda = 0 pair): its pair virial here, no phase C
+        const float wv = -0.5f * dphi * r;
+        acc[2] = fmaf(wv * ux, ux, acc[2]);
+        acc[3] = fmaf(wv * uy, uy, acc[3]);
+        acc[4] = fmaf(wv * uz, uz, acc[4]);
+        acc[5] = fmaf(wv * ux, uy, acc[5]);
+        acc[6] = fmaf(wv * ux, uz, acc[6]);
+        acc[7] = fmaf(wv * uy, uz, acc[7]);
+        *ue_p = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+    }
     *ue_p = make_float4(ux, uy, uz, ee);
     // (-1/2 dphi: the pair term's share of the virial, taken in phase C), nde, r, j
-    *ax_p = make_float4(-0.5f * dphi, P.gsig * tinv * tinv, r, ax_p->w);
+    *ax_p = make_float4(-0.5f * dphi, p_gsig * tinv * tinv, r, ax_p->w);
     const float ex = ee * ux, ey = ee * uy, ez = ee * uz;
     m0 += ee;
     msx += ex;
@@ -1061,12 +1125,12 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
   }
   __syncwarp();  // the group's table entries are complete
   // ---- leg phase C: three-body force on each leg partner from the moments
-  const float c0 = P.c0;
+  const float c0 = (kSp && valid) ? spi[0].c0 : P.c0;
   const float s0c = c0 * c0 * m0;
   const float oc0 = 1.0f - c0;  // D_jj with c_jj = |u_j|^2 = 1
   for (int l = g; l < nstage; l += kG) {
-    const float4 uj = T.ue[a * kLPad + l];
-    const float4 xj = T.aux[a * kLPad + l];
+    const float4 uj = T.ue[a * kLP + l];
+    const float4 xj = T.aux[a * kLP + l];
     const float ee = uj.w;
     if (ee == 0.f) continue;  // leg dropped in phase B
     const float mx = fmaf(mxx, uj.x, fmaf(mxy, uj.y, mxz * uj.z));  // M u_j
@@ -1113,11 +1177,23 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTable& T, int blk
   }
   if (valid && g == 0) {
     red_add_v4(d.f + i, fx, fy, fz);
-    if (nl > kLMax) force_overflow_item<kCount>(d, P, i, par);  // rare: more legs than the table holds
+    if (nl > kLM) {  // rare: more legs than the table holds
+      if constexpr (kSp)
+        species_item<kCount>(d, sps, d.sp_tri, nsp, i, acc);
+      else
+        force_overflow_item<kCount>(d, P, i, par);
+    }
   }
   if (kCount) {  // legs and table-path triplets, one atomic per warp
-    unsigned long long legs = (valid && g == 0) ? (unsigned long long)nl : 0ull;
-    unsigned long long tri = (valid && g == 0 && nl <= kLMax) ? (unsigned long long)(nl * (nl - 1) / 2) : 0ull;
+    int nleg = nl;
+    if constexpr (kSp) {  // legs inside their own pair's cutoff, summed over the group
+#pragma unroll
+      for (int o = 1; o < kG; o <<= 1) nvalid += __shfl_xor_sync(kFull, nvalid, o);
+      nleg = nvalid;
+    }
+    unsigned long long legs = (valid && g == 0 && (!kSp || nl <= kLM)) ? (unsigned long long)nleg : 0ull;
+    unsigned long long tri =
+        (valid && g == 0 && nl <= kLM) ? (unsigned long long)(nleg * (nleg - 1) / 2) : 0ull;
     for (int o = 16; o > 0; o >>= 1) {
       legs += __shfl_down_sync(kFull, legs, o);
       tri += __shfl_down_sync(kFull, tri, o);

@@ -5,10 +5,13 @@
 // of (ti, tj, tj); the three-body term of centre i with legs j, k takes
 // lambda epsilon and cos theta0 of (ti, tj, tk) and each leg's exponential
 // factor from that leg's pair set.  lambda epsilon then varies per leg pair,
-// so the per-centre moment form of k_force does not apply: each centre
-// walks its leg pairs directly (one thread per centre, legs in local
-// memory), with the same pair-term ownership, scatter of the leg forces and
-// per-box FP64 reductions as the one-species kernels.
+// so the per-centre moment form of k_force applies only when it factors into
+// leg weights, lambda epsilon of (a; b, c) = h_ab h_ac with cos theta0 set by
+// the centre (geometric-mean mixing; a solute with lambda = 0): k_force_sp.
+// Other tables take k_force_species, where each centre walks its leg pairs
+// directly (one thread per centre, legs in local memory), with the same
+// pair-term ownership, scatter of the leg forces and per-box FP64
+// reductions as the one-species kernels.
 #pragma once
 
 #include "mw_device.cuh"
@@ -150,6 +153,29 @@ __global__ void __launch_bounds__(kSpThreads) k_force_species(Dev d) {
   int b = -1;
   if (i < d.N) b = species_item<kCount>(d, sp, st, nsp, i, acc);
   box_accumulate<8>(acc, b, [&](int bb) { return &d.bst[bb].ew[par][0]; });
+}
+
+// Force phase for tables whose three-body strengths factor into leg weights
+// (lambda epsilon of (a; b, c) = h_ab h_ac, cos theta0 of the centre): the
+// one-species moment kernel with per-leg constants (force_block<., true>).
+// P.rc is the widest pair cutoff.  Block 0 consumes the rebuild flags.
+template <bool kCount>
+__global__ void __launch_bounds__(kFThreads, 4) k_force_sp(Dev d, FParams P) {
+  if (block_stop(d)) return;
+  __shared__ LegTableSp T;
+  __shared__ SpPair sp[kMaxSpecies * kMaxSpecies];
+  const int nsp = d.nsp;
+  for (int k = threadIdx.x; k < nsp * nsp; k += blockDim.x) sp[k] = d.sp_pair[k];
+  const int par = (int)(d.g->step & 1ull);
+  if (blockIdx.x == 0) {
+    for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
+    if (threadIdx.x == 0) {
+      d.g->any_rebuild = 0;
+      d.g->wpar = par;
+    }
+  }
+  __syncthreads();
+  force_block<kCount, true>(d, P, T, blockIdx.x, par, sp, nsp);
 }
 
 // Sorted species from the caller-order ones (after a new state or a new

@@ -66,7 +66,8 @@ class mw_info(ctypes.Structure):
                 ("max_count", ctypes.c_int), ("ncell_total", ctypes.c_int), ("engine", ctypes.c_int),
                 ("persistent_blocks", ctypes.c_int), ("persistent_threads", ctypes.c_int),
                 ("r_list", ctypes.c_double), ("npairs", ctypes.c_int64), ("ntriplets", ctypes.c_int64),
-                ("rebuild_steps", ctypes.c_int64), ("regrids", ctypes.c_int64)]
+                ("rebuild_steps", ctypes.c_int64), ("regrids", ctypes.c_int64), ("species", ctypes.c_int),
+                ("species_moments", ctypes.c_int)]
 
 
 class MWError(RuntimeError):

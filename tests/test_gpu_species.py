@@ -49,10 +49,51 @@ def test_species_energy_forces_match_oracle(mwlib, orc, case):
         ref = _check(s, orc, x, box, ty, table)
         assert ref["ntriplets"] > 0
         rc = max(table[a, b, b, 3] * table[a, b, b, 2] for a in range(len(table)) for b in range(len(table)))
-        assert s.info()["r_list"] == pytest.approx(rc + 1.0, rel=1e-12)
+        info = s.info()
+        assert info["r_list"] == pytest.approx(rc + 1.0, rel=1e-12)
+        assert info["species"] == len(table)
+        # geometric-mean family and the lambda = 0 solute factor into leg weights
+        assert info["species_moments"] == (1 if case in ("mw_solute_1200", "sw_family_1331") else 0)
         check_neighbors(s, orc, x, box)
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("table", ["sw_family", "mixed3"])
+def test_species_dense_box_more_legs_than_staged(mwlib, orc, table):
+    """Dense boxes: the Fig. 2 family at 4.5 g/cm^3 has 50 legs per centre on
+    average (at most 56), so the moment kernel, which stages 48, hands most
+    centres to the per-centre walker; the every-entry-different table at 3.5
+    has 45 on average and at most 60 (the walker holds 64)."""
+    x, box = I.jittered_box(512, 4.5 if table == "sw_family" else 3.5, 0.1, 104)
+    x = I.snap_to_grid(x, box)
+    t = I.species_table_sw_family() if table == "sw_family" else I.species_table_mixed(3, 17)
+    ty = I.species_draw(512, len(t), 18)
+    s = mwlib.System(512, box)
+    try:
+        s.set_species(t, ty)
+        s.set_state(x)
+        _check(s, orc, x, box, ty, t)
+    finally:
+        s.close()
+
+
+def test_species_count_terms_match_oracle(mwlib, orc):
+    for t in (I.species_table_solute(), I.species_table_mixed(2, 5)):
+        x, box = I.jittered_box(1000, 1.0, 0.3, 205)
+        x = I.snap_to_grid(x, box)
+        ty = I.species_draw(1000, 2, 19, [0.8, 0.2])
+        s = mwlib.System(1000, box)
+        try:
+            s.set_species(t, ty)
+            mwlib.mw_set_count_terms(s.h, True)
+            s.set_state(x)
+            s.energy_forces()
+            info = s.info()
+        finally:
+            s.close()
+        ref = orc.energy_forces_species(x, box, ty, t)
+        assert (info["npairs"], info["ntriplets"]) == (ref["npairs"], ref["ntriplets"])
 
 
 def test_species_set_before_or_after_state_and_back_to_one(mwlib, orc):
@@ -98,14 +139,16 @@ def test_species_batch_of_uneven_boxes(mwlib, orc):
         s.close()
 
 
+@pytest.mark.parametrize("table_kind", ["mixed", "solute"])
 @pytest.mark.parametrize("kind", [0, 2])
-def test_species_dynamics_match_oracle(mwlib, orc, kind):
-    """20 steps of a two-species mixture (every set different) from the
-    512-atom start: same tolerances as the one-species trajectory test."""
+def test_species_dynamics_match_oracle(mwlib, orc, kind, table_kind):
+    """20 steps of a two-species mixture from the 512-atom start (every set
+    different: the leg-pair walker; mW with a solute: the moment kernel):
+    same tolerances as the one-species trajectory test."""
     x, v, box = I.nve512()
     x = I.snap_to_grid(x, box)
-    ty = I.species_draw(512, 2, 15)
-    table = I.species_table_mixed(2, 16)
+    ty = I.species_draw(512, 2, 15, None if table_kind == "mixed" else [0.85, 0.15])
+    table = I.species_table_mixed(2, 16) if table_kind == "mixed" else I.species_table_solute()
     s = mwlib.System(512, box)
     try:
         s.set_species(table, ty)

@@ -311,6 +311,26 @@ mw_status status_error(const Global& g) {
 
 // Kernel sequences ----------------------------------------------------------
 
+// The kick kernels: the isobaric instantiations under MW_NPT.
+void launch_kick1(mw_system* s, bool cond, cudaGraphConditionalHandle h) {
+  const int kb = kick_blocks(s->N, kKThreads);
+  const bool npt = s->integ.kind == TH_NPT;
+  if (cond)
+    npt ? k_kick1<true, true><<<kb, kKThreads, 0, s->stream>>>(s->d, h)
+        : k_kick1<true, false><<<kb, kKThreads, 0, s->stream>>>(s->d, h);
+  else
+    npt ? k_kick1<false, true><<<kb, kKThreads, 0, s->stream>>>(s->d, 0ull)
+        : k_kick1<false, false><<<kb, kKThreads, 0, s->stream>>>(s->d, 0ull);
+}
+
+void launch_kick2(mw_system* s) {
+  const int kb = kick_blocks(s->N, kKThreads);
+  if (s->integ.kind == TH_NPT)
+    k_kick2<true><<<kb, kKThreads, 0, s->stream>>>(s->d);
+  else
+    k_kick2<false><<<kb, kKThreads, 0, s->stream>>>(s->d);
+}
+
 void launch_rebuild(mw_system* s) {
   const Dev& d = s->d;
   const int gb = div_up(s->N, kThreads);
@@ -354,10 +374,10 @@ mw_status capture_step(mw_system* s) {
     // Same kernels without the IF node (the rebuild kernels return at once
     // when no box needs a rebuild): profilers that skip conditional graphs
     // still see every kernel of the step.
-    k_kick1<false><<<kick_blocks(s->N, kKThreads), kKThreads, 0, s->stream>>>(d, 0ull);
+    launch_kick1(s, false, 0ull);
     launch_rebuild(s);
     launch_force(s);
-    k_kick2<<<kick_blocks(s->N, kKThreads), kKThreads, 0, s->stream>>>(d);
+    launch_kick2(s);
     MW_CUDA(cudaGetLastError());
     return MW_OK;
   }
@@ -368,7 +388,7 @@ mw_status capture_step(mw_system* s) {
   MW_CUDA(cudaStreamGetCaptureInfo(s->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphConditionalHandle h;
   MW_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-  k_kick1<true><<<kick_blocks(s->N, kKThreads), kKThreads, 0, s->stream>>>(d, h);
+  launch_kick1(s, true, h);
   MW_CUDA(cudaGetLastError());
   MW_CUDA(cudaStreamGetCaptureInfo(s->stream, &cs, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphNodeParams p = {};
@@ -388,7 +408,7 @@ mw_status capture_step(mw_system* s) {
   MW_CUDA(cudaGetLastError());
   MW_CUDA(cudaStreamEndCapture(s->cap_stream, &body));
   launch_force(s);
-  k_kick2<<<kick_blocks(s->N, kKThreads), kKThreads, 0, s->stream>>>(d);
+  launch_kick2(s);
   MW_CUDA(cudaGetLastError());
   return MW_OK;
 }
@@ -474,7 +494,7 @@ mw_status finish_interrupted_step(mw_system* s) {
   const int gb = div_up(s->N, kThreads);
   launch_rebuild(s);
   launch_force(s);
-  k_kick2<<<kick_blocks(s->N, kKThreads), kKThreads, 0, s->stream>>>(s->d);
+  launch_kick2(s);
   MW_CUDA(cudaGetLastError());
   return MW_OK;
 }
@@ -686,6 +706,7 @@ mw_status validate_integ(mw_system* s, const mw_integrator* in) {
   }
   if (boxes_changed && (st = upload_boxes(s)) != MW_OK) return st;
   if (integ_changed) {
+    if ((I.kind == TH_NPT) != (s->integ.kind == TH_NPT)) s->graph_dirty = true;  // other kick kernels
     s->integ = I;
     if ((st = upload_integ(s)) != MW_OK) return st;
   }

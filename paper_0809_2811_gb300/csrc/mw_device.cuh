@@ -385,8 +385,10 @@ __device__ __forceinline__ float nh_half(const Integ& I, const Box& bx, ThermoSt
 // End-of-step half, after the second half-kick: Nose-Hoover half step, or
 // the Berendsen scale s = sqrt(1 + dt/tau (T0/T - 1)) (sig = x / (s + 1) with
 // x = dt/tau (T0/T - 1), free of cancellation); NVE changes nothing.
+// (kNpt: the isobaric instantiation, whose thermostat is always Nose-Hoover)
+template <bool kNpt = false>
 __device__ __forceinline__ float end_half(const Integ& I, const Box& bx, ThermoState& t) {
-  if (I.kind == TH_NH || I.kind == TH_NPT) return nh_half(I, bx, t);
+  if (kNpt || I.kind == TH_NH) return nh_half(I, bx, t);
   if (I.kind == TH_BERENDSEN && t.ke > 0.f) {
     const float T = 2.0f * t.ke * (float)bx.inv_ndf_kb;
     const float x = (float)(I.dt / I.tau) * ((float)bx.T0 / T - 1.0f);
@@ -399,8 +401,9 @@ __device__ __forceinline__ float end_half(const Integ& I, const Box& bx, ThermoS
 }
 
 // Start-of-step half, before the first half-kick (Nose-Hoover only).
+template <bool kNpt = false>
 __device__ __forceinline__ float start_half(const Integ& I, const Box& bx, ThermoState& t) {
-  return (I.kind == TH_NH || I.kind == TH_NPT) ? nh_half(I, bx, t) : 0.f;
+  return (kNpt || I.kind == TH_NH) ? nh_half(I, bx, t) : 0.f;
 }
 
 __device__ __forceinline__ ThermoState thermo_in(const Box& bx, float4 th, double ke) {
@@ -511,49 +514,59 @@ __device__ void npt_commit_box(const Dev& d, int b) {
   bx.p_fac = kATM / (3.0 * vol);
 }
 
+// Isobaric end-of-step tail (kNpt instantiations only, so that the FP64
+// barostat arithmetic does not raise the register count of the others).
+__device__ void end_of_step_box_npt(const Dev& d, const Integ& I, int b, int par) {
+  BoxState* st = d.bst + b;
+  const Box& bx = d.box[b];
+  const double ke0 = __ldcg(&st->ke_acc[par]);
+  // end of this step: friction, barostat half, thermostat half; start of
+  // the next: thermostat half, barostat half, friction; then the new box
+  const double trw = __ldcg(&st->ew[par][2]) + __ldcg(&st->ew[par][3]) + __ldcg(&st->ew[par][4]);
+  double pe = __ldcg(&st->pe_b);
+  const float f1 = baro_friction(I, bx, pe);
+  double ke = fma(ke0, (double)(f1 * (2.0f + f1)), ke0);
+  baro_half(I, bx, ke, trw, pe);
+  ThermoState t = thermo_in(bx, __ldcg(&st->th), ke);
+  const float se = end_half<true>(I, bx, t);
+  ke = fma(ke, (double)(se * (2.0f + se)), ke);
+  st->th_e = make_float4(t.xh, t.xl, t.eh, t.el);
+  st->ke_last = ke;
+  st->pe_e = pe;
+  const float e1 = fmaf(f1, se, f1 + se);
+  st->s_endc = 1.0 + (double)e1;
+  const float ss = start_half<true>(I, bx, t);
+  ke = fma(ke, (double)(ss * (2.0f + ss)), ke);
+  st->th = make_float4(t.xh, t.xl, t.eh, t.el);
+  baro_half(I, bx, ke, trw, pe);
+  const float f2 = baro_friction(I, bx, pe);
+  const float e2 = fmaf(ss, f2, ss + f2);
+  st->sig = fmaf(e1, e2, e1 + e2);
+  st->pe_b = pe;
+  npt_geometry(d, I, b, pe);
+}
+
 // Thermostat at the end of the step of parity par, for box b (one thread per
 // box, after the step's kinetic-energy sum is complete): the end half of this
 // step, then the start half of the next one; stores the state after each half
 // and the combined scale S - 1 the next kick1 applies.
+template <bool kNpt>
 __device__ void end_of_step_box(const Dev& d, const Integ& I, int b, int par) {
-  BoxState* st = d.bst + b;
-  const Box& bx = d.box[b];
-  const double ke0 = __ldcg(&st->ke_acc[par]);
-  if (I.kind == TH_NPT) {
-    // end of this step: friction, barostat half, thermostat half; start of
-    // the next: thermostat half, barostat half, friction; then the new box
-    const double trw = __ldcg(&st->ew[par][2]) + __ldcg(&st->ew[par][3]) + __ldcg(&st->ew[par][4]);
-    double pe = __ldcg(&st->pe_b);
-    const float f1 = baro_friction(I, bx, pe);
-    double ke = fma(ke0, (double)(f1 * (2.0f + f1)), ke0);
-    baro_half(I, bx, ke, trw, pe);
-    ThermoState t = thermo_in(bx, __ldcg(&st->th), ke);
+  if constexpr (kNpt) {
+    end_of_step_box_npt(d, I, b, par);
+  } else {
+    BoxState* st = d.bst + b;
+    const Box& bx = d.box[b];
+    const double ke0 = __ldcg(&st->ke_acc[par]);
+    ThermoState t = thermo_in(bx, __ldcg(&st->th), ke0);
     const float se = end_half(I, bx, t);
-    ke = fma(ke, (double)(se * (2.0f + se)), ke);
     st->th_e = make_float4(t.xh, t.xl, t.eh, t.el);
-    st->ke_last = ke;
-    st->pe_e = pe;
-    const float e1 = fmaf(f1, se, f1 + se);
-    st->s_endc = 1.0 + (double)e1;
+    st->ke_last = fma(ke0, (double)(se * (2.0f + se)), ke0);
+    st->s_endc = 1.0 + (double)se;
     const float ss = start_half(I, bx, t);
-    ke = fma(ke, (double)(ss * (2.0f + ss)), ke);
     st->th = make_float4(t.xh, t.xl, t.eh, t.el);
-    baro_half(I, bx, ke, trw, pe);
-    const float f2 = baro_friction(I, bx, pe);
-    const float e2 = fmaf(ss, f2, ss + f2);
-    st->sig = fmaf(e1, e2, e1 + e2);
-    st->pe_b = pe;
-    npt_geometry(d, I, b, pe);
-    return;
+    st->sig = fmaf(se, ss, se + ss);
   }
-  ThermoState t = thermo_in(bx, __ldcg(&st->th), ke0);
-  const float se = end_half(I, bx, t);
-  st->th_e = make_float4(t.xh, t.xl, t.eh, t.el);
-  st->ke_last = fma(ke0, (double)(se * (2.0f + se)), ke0);
-  st->s_endc = 1.0 + (double)se;
-  const float ss = start_half(I, bx, t);
-  st->th = make_float4(t.xh, t.xl, t.eh, t.el);
-  st->sig = fmaf(se, ss, se + ss);
 }
 
 // Start half only, from the state after the last end half (a new state, or a
@@ -566,7 +579,7 @@ __global__ void k_prime_thermostat(Dev d) {
   const Box& bx = d.box[b];
   ThermoState t = thermo_in(bx, st->th_e, st->ke_last);
   const float se = (float)(st->s_endc - 1.0);
-  const float ss = start_half(I, bx, t);
+  const float ss = I.kind == TH_NPT ? start_half<true>(I, bx, t) : start_half(I, bx, t);
   st->th = make_float4(t.xh, t.xl, t.eh, t.el);
   float e2 = ss;
   if (I.kind == TH_NPT) {  // barostat half and friction with the latest virial
@@ -610,6 +623,7 @@ __device__ __forceinline__ bool block_stop(const Dev& d) {
 // FP32 exponent.  Also zeroes f for this step.
 constexpr int kKAtoms = 10;     // atoms per warp in the kick kernels
 constexpr int kKThreads = 512;  // threads per block of k_kick1 / k_kick2 (few blocks: few same-address atomics)
+template <bool kNpt>
 __device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, int par, int pend) {
   const int lane = threadIdx.x & 31;
   const int i = w * kKAtoms + lane / 3;
@@ -667,7 +681,7 @@ __device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, 
   // displacement since the last build: sum the three components of the atom
   const int base = lane - c;
   const float d1 = __shfl_sync(kFull, dd, min(base + 1, 31)), d2 = __shfl_sync(kFull, dd, min(base + 2, 31));
-  if (act && c == 0 && dd + d1 + d2 > (I.kind == TH_NPT ? d.box[b].hs2 : I.half_skin2)) {
+  if (act && c == 0 && dd + d1 + d2 > (kNpt ? d.box[b].hs2 : I.half_skin2)) {
     d.bst[b].rebuild = 1;
     d.g->any_rebuild = 1;
   }
@@ -1229,7 +1243,9 @@ __global__ void __launch_bounds__(kFThreads, 8) k_force(Dev d, FParams P) {
 // sets the condition of the graph's IF node that holds the rebuild kernels
 // (skipped when no box moved more than skin/2).  The other instantiation
 // holds no conditional-node call, so profilers can capture it.
-template <bool kCond>
+// kNpt: the isobaric instantiation (rebuild margin per box, and its last
+// block makes the coming step's edges current).
+template <bool kCond, bool kNpt = false>
 __global__ void __launch_bounds__(kKThreads) k_kick1(Dev d, cudaGraphConditionalHandle rebuild_cond) {
   if (block_stop(d)) return;
   const Integ I = *d.integ;
@@ -1237,8 +1253,8 @@ __global__ void __launch_bounds__(kKThreads) k_kick1(Dev d, cudaGraphConditional
   const int pend = d.g->pend;
   const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (blockIdx.x == 0 && threadIdx.x == 0) d.g->n_over = 0;
-  if (w * kKAtoms < d.N) kick1_lane(d, I, w, par, pend);
-  if (kCond || I.kind == TH_NPT) {  // block-uniform
+  if (w * kKAtoms < d.N) kick1_lane<kNpt>(d, I, w, par, pend);
+  if constexpr (kCond || kNpt) {
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {  // one fence per block after the barrier orders the block's writes
@@ -1248,7 +1264,7 @@ __global__ void __launch_bounds__(kKThreads) k_kick1(Dev d, cudaGraphConditional
     __syncthreads();
     if (last) {
       __threadfence();
-      if (I.kind == TH_NPT)
+      if constexpr (kNpt)
         for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) npt_commit_box(d, b);
       if (threadIdx.x == 0) {
         d.g->done1 = 0u;
@@ -1380,6 +1396,7 @@ __global__ void k_neigh(Dev d, float rl2) {
 // a7 second half: kinetic energy of v + a per box; the last block to finish
 // runs the thermostat halves of every box (FP32, a short serial tail) and
 // advances the step.  The half-kick itself stays pending.
+template <bool kNpt = false>
 __global__ void __launch_bounds__(kKThreads) k_kick2(Dev d) {
   if (block_stop(d)) return;
   const Integ I = *d.integ;
@@ -1399,7 +1416,7 @@ __global__ void __launch_bounds__(kKThreads) k_kick2(Dev d) {
   __syncthreads();
   if (am_last) {
     __threadfence();
-    for (int bb = threadIdx.x; bb < d.nbox; bb += blockDim.x) end_of_step_box(d, I, bb, par);
+    for (int bb = threadIdx.x; bb < d.nbox; bb += blockDim.x) end_of_step_box<kNpt>(d, I, bb, par);
     __syncthreads();
     if (threadIdx.x == 0) {
       d.g->done = 0u;

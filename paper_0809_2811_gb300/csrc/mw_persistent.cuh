@@ -161,7 +161,7 @@ __device__ void scan_chunk_offsets(const Dev& d) {
   __syncthreads();
 }
 
-template <bool kCount>
+template <bool kCount, bool kNpt = false>
 __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, int nsteps) {
   __shared__ LegTable T;
   __shared__ unsigned s_gen;
@@ -181,14 +181,14 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     // a1 + a7 first half, a8 displacement check
     const int pend = *(volatile int*)&g->pend;  // stable: written only at the end of the kick2 phase
     if (tid == 0) g->n_over = 0;
-    for (int w = gw; w * kKAtoms < d.N; w += nwarps) kick1_lane(d, I, w, par, pend);
-    if (I.kind == TH_NPT) {  // the new edges once every block has drifted with the old
+    for (int w = gw; w * kKAtoms < d.N; w += nwarps) kick1_lane<kNpt>(d, I, w, par, pend);
+    if constexpr (kNpt) {  // the new edges once every block has drifted with the old
       if (grid_barrier_last(g, gen, [&] {
             for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) npt_commit_box(d, b);
           }))
         return;
-    } else if (grid_barrier(g, gen)) {
-      return;
+    } else {
+      if (grid_barrier(g, gen)) return;
     }
     // a2 + a3: cell binning and neighbour list, when due (flag is stable until kick2)
     if (*(volatile int*)&g->any_rebuild) {
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     // the last block to arrive runs the thermostat halves of every box (end of
     // this step, start of the next) before releasing the others
     if (grid_barrier_last(g, gen, [&] {
-          for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) end_of_step_box(d, I, b, par);
+          for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) end_of_step_box<kNpt>(d, I, b, par);
           if (threadIdx.x == 0) {
             g->pend = 1;
             g->step = step + 1ull;

@@ -343,19 +343,14 @@ void launch_rebuild(mw_system* s) {
 
 void launch_force(mw_system* s) {
   const Dev& d = s->d;
-  if (s->nsp > 1 && s->sp_moment) {
-    const int gb = div_up(s->N, kFAtoms);
-    if (s->count_terms)
-      k_force_sp<true><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
-    else
-      k_force_sp<false><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
-    return;
-  }
   if (s->nsp > 1) {
-    if (s->count_terms)
-      k_force_species<true><<<div_up(s->N, kSpThreads), kSpThreads, 0, s->stream>>>(d);
+    const int gb = div_up(s->N, kFAtoms);
+    if (s->sp_moment)
+      s->count_terms ? k_force_sp<true, 1><<<gb, kFThreads, 0, s->stream>>>(d, s->fp)
+                     : k_force_sp<false, 1><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
     else
-      k_force_species<false><<<div_up(s->N, kSpThreads), kSpThreads, 0, s->stream>>>(d);
+      s->count_terms ? k_force_sp<true, 2><<<gb, kFThreads, 0, s->stream>>>(d, s->fp)
+                     : k_force_sp<false, 2><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
     return;
   }
   const int gb = div_up(s->N, kFAtoms);
@@ -368,8 +363,6 @@ void launch_force(mw_system* s) {
 // One MD step into the stream being captured: kick1, an IF node holding the
 // rebuild kernels (condition set on the device by kick1), force, kick2.
 mw_status capture_step(mw_system* s) {
-  const Dev& d = s->d;
-  const int gb = div_up(s->N, kThreads);
   if (std::getenv("MW_GRAPH_NO_CONDITIONAL")) {
     // Same kernels without the IF node (the rebuild kernels return at once
     // when no box needs a rebuild): profilers that skip conditional graphs

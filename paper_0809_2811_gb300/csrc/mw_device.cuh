@@ -946,15 +946,19 @@ __device__ __noinline__ int species_item(const Dev& d, const SpPair* sp, const f
                                          float (&acc)[8]);
 
 // One block of kFAtoms centres (atoms blk*kFAtoms ...); every thread of the
-// block calls it.  kSp: several species whose three-body strengths factor
-// into leg weights (SpPair::h) and whose cos theta0 is the centre's
-// (SpPair::c0); sps is the nsp^2 pair table in shared memory.  Every leg
-// then carries its own pair constants and weight and the moments stay exact;
-// P.rc is the widest pair cutoff (the leg test of phase A), and a leg
-// beyond its own pair's cutoff is dropped in phase B.
-template <bool kCount, bool kSp = false>
+// block calls it.  kSp = 0: one species.  kSp = 1: several species whose
+// three-body strengths factor into leg weights (SpPair::h) and whose
+// cos theta0 is the centre's (SpPair::c0); every leg carries its own pair
+// constants and weight and the moments stay exact.  kSp = 2: any table;
+// phase C then walks the leg pairs, each lane its own legs j against every
+// other leg k of the centre (each triplet seen from both legs, each visit
+// giving the force on its own leg), with lambda epsilon and cos theta0 of
+// (centre; j, k) from the shared triplet table stt.  sps is the nsp^2 pair
+// table in shared memory; phase A tests each candidate against its own
+// pair's cutoff.
+template <bool kCount, int kSp = 0>
 __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLMaxSp : kLMax) + 1>& T, int blk,
-                            int par, const SpPair* sps = nullptr, int nsp = 1) {
+                            int par, const SpPair* sps = nullptr, int nsp = 1, const float2* stt = nullptr) {
   constexpr int kLM = kSp ? kLMaxSp : kLMax;  // legs staged per centre
   constexpr int kLP = kLM + 1;                // row pitch
   const int lane = threadIdx.x & 31;
@@ -968,6 +972,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
   int cnt = 0, b = -1;
   float L0 = 0.f, L1 = 0.f, L2 = 0.f;
   const SpPair* spi = nullptr;  // the centre's row of the pair table (kSp)
+  int ti = 0;                   // the centre's species (kSp)
   if (valid) {
     qi = d.q[i];
     b = (int)qi.w;
@@ -976,7 +981,10 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
     L0 = bx.Lq[0];
     L1 = bx.Lq[1];
     L2 = bx.Lq[2];
-    if constexpr (kSp) spi = sps + d.typ[i] * nsp;
+    if constexpr (kSp != 0) {
+      ti = d.typ[i];
+      spi = sps + ti * nsp;
+    }
   }
   // ---- leg phase A: row entries and candidate positions are fetched for
   // kPre slots per lane before any is used (two memory latencies per batch
@@ -1061,7 +1069,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
       p_gsig_l2e = pp.gsig_l2e;
       p_Aeps = pp.Aeps;
       p_B = pp.B;
-      p_h = pp.h;
+      p_h = kSp == 2 ? 1.0f : pp.h;  // kSp = 2: the strengths come per leg pair in phase C
       p_p = pp.p;
       p_q = pp.q;
     }
@@ -1095,7 +1103,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
     fx = fmaf(dphi, ux, fx);
     fy = fmaf(dphi, uy, fy);
     fz = fmaf(dphi, uz, fz);
-    if constexpr (kSp) {
+    if constexpr (kSp == 1) {
       if (p_h == 0.f) {  // no three-body weight (a lambda = 0 pair): its pair virial here, no phase C
         const float wv = -0.5f * dphi * r;
         acc[2] = fmaf(wv * ux, ux, acc[2]);
@@ -1110,7 +1118,10 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
     }
     *ue_p = make_float4(ux, uy, uz, ee);
     // (-1/2 dphi: the pair term's share of the virial, taken in phase C), nde, r, j
-    *ax_p = make_float4(-0.5f * dphi, p_gsig * tinv * tinv, r, ax_p->w);
+    // (kSp = 2: j with the partner's species in bits 28-30)
+    const float jw = kSp == 2 ? __int_as_float(__float_as_int(ax_p->w) | (__float_as_int(ax_p->x) << 28)) : ax_p->w;
+    *ax_p = make_float4(-0.5f * dphi, p_gsig * tinv * tinv, r, jw);
+    if constexpr (kSp == 2) continue;  // no moments
     const float ex = ee * ux, ey = ee * uy, ez = ee * uz;
     m0 += ee;
     msx += ex;
@@ -1138,6 +1149,46 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
     myz += __shfl_xor_sync(kFull, myz, o);
   }
   __syncwarp();  // the group's table entries are complete
+  if constexpr (kSp == 2) {
+    // ---- leg phase C (any table): leg j against every other leg k
+    const float2* stc = stt + ti * nsp * nsp;
+    for (int l = g; l < nstage; l += kG) {
+      const float4 uj = T.ue[a * kLP + l];
+      const float4 xj = T.aux[a * kLP + l];
+      if (uj.w == 0.f) continue;  // leg dropped in phase B
+      const int wj = __float_as_int(xj.w);
+      const float2* stj = stc + (wj >> 28) * nsp;
+      const float r = xj.z;
+      const float tr = __fdividef(2.0f, r);
+      const float nde = xj.y;
+      float gx = 0.f, gy = 0.f, gz = 0.f;  // three-body force on the partner of leg j
+      for (int k = 0; k < nstage; ++k) {
+        const float4 uk = T.ue[a * kLP + k];
+        if (k == l || uk.w == 0.f) continue;
+        const float2 lc = stj[__float_as_int(T.aux[a * kLP + k].w) >> 28];  // (lambda eps, cos theta0)
+        const float c = fmaf(uj.x, uk.x, fmaf(uj.y, uk.y, uj.z * uk.z));
+        const float D = c - lc.y;
+        const float gg = lc.x * uj.w * uk.w * D;
+        acc[1] = fmaf(0.5f * gg, D, acc[1]);  // each triplet is visited from both of its legs
+        const float aj = gg * tr, bj = gg * fmaf(c, tr, D * nde);
+        gx = fmaf(-aj, uk.x, fmaf(bj, uj.x, gx));
+        gy = fmaf(-aj, uk.y, fmaf(bj, uj.y, gy));
+        gz = fmaf(-aj, uk.z, fmaf(bj, uj.z, gz));
+      }
+      red_add_v4(d.f + (wj & 0x0FFFFFFF), gx, gy, gz);
+      fx -= gx;
+      fy -= gy;
+      fz -= gz;
+      const float hx = fmaf(xj.x, uj.x, gx), hy = fmaf(xj.x, uj.y, gy), hz = fmaf(xj.x, uj.z, gz);
+      const float rx = r * uj.x, ry = r * uj.y, rz = r * uj.z;
+      acc[2] = fmaf(rx, hx, acc[2]);
+      acc[3] = fmaf(ry, hy, acc[3]);
+      acc[4] = fmaf(rz, hz, acc[4]);
+      acc[5] = fmaf(rx, hy, acc[5]);
+      acc[6] = fmaf(rx, hz, acc[6]);
+      acc[7] = fmaf(ry, hz, acc[7]);
+    }
+  } else {
   // ---- leg phase C: three-body force on each leg partner from the moments
   const float c0 = (kSp && valid) ? spi[0].c0 : P.c0;
   const float s0c = c0 * c0 * m0;
@@ -1182,6 +1233,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
     acc[6] = fmaf(rx, hz, acc[6]);
     acc[7] = fmaf(ry, hz, acc[7]);
   }
+  }  // phase C
   // ---- force on the centre: pair part + three-body reaction, over the group
 #pragma unroll
   for (int o = 1; o < kG; o <<= 1) {
@@ -1192,7 +1244,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
   if (valid && g == 0) {
     red_add_v4(d.f + i, fx, fy, fz);
     if (nl > kLM) {  // rare: more legs than the table holds
-      if constexpr (kSp)
+      if constexpr (kSp != 0)
         species_item<kCount>(d, sps, d.sp_tri, nsp, i, acc);
       else
         force_overflow_item<kCount>(d, P, i, par);

@@ -8,17 +8,17 @@
 // so the per-centre moment form of k_force applies only when it factors into
 // leg weights, lambda epsilon of (a; b, c) = h_ab h_ac with cos theta0 set by
 // the centre (geometric-mean mixing; a solute with lambda = 0): k_force_sp.
-// Other tables take k_force_species, where each centre walks its leg pairs
-// directly (one thread per centre, legs in local memory), with the same
-// pair-term ownership, scatter of the leg forces and per-box FP64
-// reductions as the one-species kernels.
+// Other tables keep the lane-group structure and walk the leg pairs of each
+// centre in phase C (k_force_sp<., 2>).  Centres with more legs than the
+// group stages go to species_item, one thread walking every leg pair with
+// its legs in local memory, with the same pair-term ownership, scatter of
+// the leg forces and per-box reductions.
 #pragma once
 
 #include "mw_device.cuh"
 
 namespace mw {
 
-constexpr int kSpThreads = 128;
 
 // Owner contribution of centre i: pair terms (half energy, the whole force
 // on the centre, half virial; the partner does the same from its side) and
@@ -129,43 +129,22 @@ __device__ int species_item(const Dev& d, const SpPair* sp, const float2* st, in
   return b;
 }
 
-// Force phase of a box set holding several species (one thread per centre).
-// Block 0 consumes the rebuild flags, as k_force does.
-template <bool kCount>
-__global__ void __launch_bounds__(kSpThreads) k_force_species(Dev d) {
-  if (block_stop(d)) return;
-  __shared__ SpPair sp[kMaxSpecies * kMaxSpecies];
-  __shared__ float2 st[kMaxSpecies * kMaxSpecies * kMaxSpecies];
-  const int nsp = d.nsp;
-  for (int k = threadIdx.x; k < nsp * nsp; k += blockDim.x) sp[k] = d.sp_pair[k];
-  for (int k = threadIdx.x; k < nsp * nsp * nsp; k += blockDim.x) st[k] = d.sp_tri[k];
-  const int par = (int)(d.g->step & 1ull);
-  if (blockIdx.x == 0) {
-    for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
-    if (threadIdx.x == 0) {
-      d.g->any_rebuild = 0;
-      d.g->wpar = par;
-    }
-  }
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // E2, E3, W xx yy zz xy xz yz
-  int b = -1;
-  if (i < d.N) b = species_item<kCount>(d, sp, st, nsp, i, acc);
-  box_accumulate<8>(acc, b, [&](int bb) { return &d.bst[bb].ew[par][0]; });
-}
-
-// Force phase for tables whose three-body strengths factor into leg weights
-// (lambda epsilon of (a; b, c) = h_ab h_ac, cos theta0 of the centre): the
-// one-species moment kernel with per-leg constants (force_block<., true>).
-// P.rc is the widest pair cutoff.  Block 0 consumes the rebuild flags.
-template <bool kCount>
+// Force phase of a box set holding several species: the lane-group kernel
+// with per-leg constants, kMode 1 (tables whose three-body strengths factor
+// into leg weights, lambda epsilon of (a; b, c) = h_ab h_ac with cos theta0
+// of the centre: the moment form) or kMode 2 (any table: leg pairs walked
+// in phase C).  P.rc is the widest pair cutoff.  Block 0 consumes the
+// rebuild flags.
+template <bool kCount, int kMode>
 __global__ void __launch_bounds__(kFThreads, 4) k_force_sp(Dev d, FParams P) {
   if (block_stop(d)) return;
   __shared__ LegTableSp T;
   __shared__ SpPair sp[kMaxSpecies * kMaxSpecies];
+  __shared__ float2 st[kMode == 2 ? kMaxSpecies * kMaxSpecies * kMaxSpecies : 1];
   const int nsp = d.nsp;
   for (int k = threadIdx.x; k < nsp * nsp; k += blockDim.x) sp[k] = d.sp_pair[k];
+  if constexpr (kMode == 2)
+    for (int k = threadIdx.x; k < nsp * nsp * nsp; k += blockDim.x) st[k] = d.sp_tri[k];
   const int par = (int)(d.g->step & 1ull);
   if (blockIdx.x == 0) {
     for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
@@ -175,7 +154,7 @@ __global__ void __launch_bounds__(kFThreads, 4) k_force_sp(Dev d, FParams P) {
     }
   }
   __syncthreads();
-  force_block<kCount, true>(d, P, T, blockIdx.x, par, sp, nsp);
+  force_block<kCount, kMode>(d, P, T, blockIdx.x, par, sp, nsp, st);
 }
 
 // Sorted species from the caller-order ones (after a new state or a new

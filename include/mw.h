@@ -39,6 +39,7 @@
 #ifndef MW_H
 #define MW_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -242,6 +243,23 @@ mw_status mw_step_async(mw_system* s, const mw_integrator* integ, int nsteps);
 /* Waits for the system's stream; returns the device-side status of the work
  * enqueued so far. */
 mw_status mw_sync(mw_system* s);
+
+/* Checkpoint / resume.  A checkpoint is the exact engine state (64-bit box
+ * fractions, FP32-pair velocities, image counters, the forces of the last
+ * evaluation, atom ids and species in the current cell order, every box's
+ * geometry and thermostat / barostat state, the step count, the
+ * integrator), so a run resumed from it continues the saved trajectory as
+ * an uninterrupted run would (to the run-to-run spread of the GPU's
+ * unordered FP32 force sums; a plain mw_set_state restarts the thermostat).
+ * mw_checkpoint_size gives the bytes of the caller-owned buffer that
+ * mw_checkpoint_save fills.  mw_checkpoint_load requires a system with the
+ * same atom counts, boxes and species, the same parameters (and species
+ * table), mass and skin, and a blob from the same library build (structure
+ * sizes are checked); MW_EINVAL otherwise.  The neighbour list is rebuilt
+ * at the next step. */
+mw_status mw_checkpoint_size(mw_system* s, size_t* bytes);
+mw_status mw_checkpoint_save(mw_system* s, void* buf, size_t bytes);
+mw_status mw_checkpoint_load(mw_system* s, const void* buf, size_t bytes);
 
 /* Thermo records (nbox) of the last completed step, or of the state just set. */
 mw_status mw_get_thermo(mw_system* s, mw_thermo* out);

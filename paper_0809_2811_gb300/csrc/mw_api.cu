@@ -851,6 +851,7 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
 #include "mw_adjoint_host.inc"
 #include "mw_autotune.inc"
 #include "mw_structure_host.inc"
+#include "mw_checkpoint_host.inc"
 
 extern "C" {
 

@@ -1486,6 +1486,13 @@ __global__ void k_record(Dev d) {
   for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) write_record(d, I, b, pl, step);
 }
 
+// Thermo record from the energies in parity slot pp (a resumed checkpoint).
+__global__ void k_record_at(Dev d, int pp) {
+  const Integ I = *d.integ;
+  const unsigned long long step = d.g->step;
+  for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) write_record(d, I, b, pp, step);
+}
+
 // ---------------------------------------------------------------------------
 // Setup / IO kernels.
 
@@ -1513,6 +1520,16 @@ __global__ void k_load_positions(Dev d, const double* __restrict__ xin, const in
   d.x[i] = p[0]; d.y[i] = p[1]; d.z[i] = p[2];
   if (d.img) d.img[i] = make_int4(im[0], im[1], im[2], 0);
   d.q[i] = make_uint4(q_of(p[0]), q_of(p[1]), q_of(p[2]), (unsigned)b);
+}
+
+// Fixed-point copies of restored positions (checkpoint resume): q and the
+// build positions qb from the 64-bit fractions, the box from the atom's id.
+__global__ void k_requantize(Dev d, const int* __restrict__ boxid) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.N) return;
+  const uint4 q = make_uint4(q_of(d.x[i]), q_of(d.y[i]), q_of(d.z[i]), (unsigned)boxid[d.id[i]]);
+  d.q[i] = q;
+  d.qb[i] = q;
 }
 
 __global__ void k_load_velocities(Dev d, const double* __restrict__ vin) {

@@ -30,7 +30,8 @@ EXPORTS = (
     "mw_get_neighbors", "mw_energy_forces", "mw_energy_forces_dev", "mw_step", "mw_get_thermo",
     "mw_energy_forces_vjp", "mw_set_engine", "mw_set_nbr_width", "mw_autotune", "mw_get_info",
     "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc", "mw_set_skin", "mw_phase_times",
-    "mw_pair_histogram", "mw_angle_histogram", "mw_get_unwrapped", "mw_get_box", "mw_set_species", "mw_last_error",
+    "mw_pair_histogram", "mw_angle_histogram", "mw_get_unwrapped", "mw_get_box", "mw_set_species",
+    "mw_checkpoint_size", "mw_checkpoint_save", "mw_checkpoint_load", "mw_last_error",
 )
 
 
@@ -121,6 +122,9 @@ def lib():
             "mw_pair_histogram": [P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)],
             "mw_get_unwrapped": [P, dp],
             "mw_get_box": [P, dp],
+            "mw_checkpoint_size": [P, ctypes.POINTER(ctypes.c_size_t)],
+            "mw_checkpoint_save": [P, P, ctypes.c_size_t],
+            "mw_checkpoint_load": [P, P, ctypes.c_size_t],
             "mw_set_species": [P, ctypes.c_int, ctypes.POINTER(mw_params), ip],
             "mw_angle_histogram": [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)],
             "mw_energy_forces_noalloc": [ctypes.c_int, dp, ctypes.POINTER(mw_params), ctypes.c_double, P, P, P, P,
@@ -439,6 +443,19 @@ class System:
     def set_species(self, table, types):
         """Several species: table (nt, nt, nt, 10) or nt^3 mw_params, types per atom (caller's order)."""
         mw_set_species(self.h, table, types)
+
+    def checkpoint(self) -> bytes:
+        """The exact engine state as bytes (mw_checkpoint_save)."""
+        n = ctypes.c_size_t()
+        _check(lib().mw_checkpoint_size(self.h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().mw_checkpoint_save(self.h, buf, n.value))
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        """Continues from a checkpoint taken on a system of the same make (mw_checkpoint_load)."""
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().mw_checkpoint_load(self.h, buf, len(blob)))
 
     def box(self) -> np.ndarray:
         """Current edges of every box (nbox x 3, A); they change under MW_NPT."""

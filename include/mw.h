@@ -261,6 +261,14 @@ mw_status mw_checkpoint_size(mw_system* s, size_t* bytes);
 mw_status mw_checkpoint_save(mw_system* s, void* buf, size_t bytes);
 mw_status mw_checkpoint_load(mw_system* s, const void* buf, size_t bytes);
 
+/* Limit (seconds, 0..60; default 2) of every device-side wait of the
+ * persistent engine (its grid barriers).  A wait that runs out sets
+ * MW_ETIMEOUT and the kernel returns; the state of the interrupted step is
+ * then undefined (set a state again), the context stays usable.  A limit of
+ * 0 makes the first barrier of the next persistent launch give up at once,
+ * which is how the timeout path is tested without a GPU fault. */
+mw_status mw_set_wait_limit(mw_system* s, double seconds);
+
 /* Thermo records (nbox) of the last completed step, or of the state just set. */
 mw_status mw_get_thermo(mw_system* s, mw_thermo* out);
 

@@ -98,6 +98,7 @@ struct mw_system {
   // persistent engine
   int pers_blocks = 0;
   int pers_blocks_limit = 0;  // 0 = as many as can be co-resident
+  unsigned long long wait_ns = kBarrierTimeoutNs;  // limit of each device-side wait
   std::vector<int> cell_box_host;
   std::vector<void*> allocs;
 };
@@ -305,6 +306,7 @@ mw_status status_error(const Global& g) {
     case ST_LOST: return fail(MW_ELOST, "atom slot %d ran away: a velocity component moves it more than a quarter of the shortest box edge per step, or is not finite", g.err_index);
     case ST_TIMEOUT: return fail(MW_ETIMEOUT, "a bounded device-side wait ran out");
     case ST_LEGS: return fail(MW_EINVAL, "more than %d atoms within a*sigma of atom slot %d", kMaxLegsOverflow, g.err_index);
+    case ST_CELLS: return fail(MW_ESTATE, "cell counts left by an interrupted run (set a state again)");
     default: return fail(MW_ECUDA, "device status %d", g.status);
   }
 }
@@ -614,6 +616,9 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   k_load_velocities<<<gb, kThreads, 0, s->stream>>>(s->d, vd);
   k_ke_init<<<gb, kThreads, 0, s->stream>>>(s->d);
   MW_CUDA(cudaMemsetAsync(s->d.f, 0, sizeof(float4) * s->N, s->stream));
+  // cell counts start from zero: a run that stopped on an error may have
+  // binned atoms without the scan that clears them
+  MW_CUDA(cudaMemsetAsync(s->d.cell_cnt, 0, sizeof(int) * s->ncell, s->stream));
   MW_CUDA(cudaGetLastError());
   MW_CUDA(cudaStreamSynchronize(s->stream));
   s->state_set = true;
@@ -1204,7 +1209,10 @@ mw_status mw_step(mw_system* s, const mw_integrator* integ, int nsteps, mw_therm
     if (eng == MW_ENGINE_PERSISTENT && !persistent_available(s)) eng = MW_ENGINE_GRAPH;
     s->engine_used = eng;
     st = eng == MW_ENGINE_PERSISTENT ? run_persistent_engine(s, nsteps) : run_graph_engine(s, nsteps);
-    if (st != MW_OK) return st;
+    if (st != MW_OK) {
+      s->forces_valid = false;  // the state of an interrupted step is not a state to report forces of
+      return st;
+    }
     s->list_built = true;
   }
   if (last) return mw_get_thermo(s, last);
@@ -1286,6 +1294,12 @@ mw_status mw_get_box(mw_system* s, double* box) {
   if ((st = pull_boxes(s)) != MW_OK) return st;
   for (int b = 0; b < s->nbox; ++b)
     for (int k = 0; k < 3; ++k) box[3 * b + k] = s->boxes[b].L[k];
+  return MW_OK;
+}
+
+mw_status mw_set_wait_limit(mw_system* s, double seconds) {
+  if (!s || !(seconds >= 0.0) || !(seconds <= 60.0)) return fail(MW_EINVAL, "wait limit must be in [0, 60] s");
+  s->wait_ns = (unsigned long long)(seconds * 1e9);
   return MW_OK;
 }
 

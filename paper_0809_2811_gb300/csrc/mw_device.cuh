@@ -32,7 +32,8 @@ constexpr double kATM = 68568.4158;            // atm per kcal/mol/A^3
 constexpr unsigned kFull = 0xffffffffu;
 
 // Status codes written to Global::status (same values as mw_status).
-enum : int { ST_OK = 0, ST_OVERFLOW = 3, ST_NAN = 4, ST_LOST = 5, ST_TIMEOUT = 6, ST_LEGS = 10, ST_GRID = 11 };
+enum : int { ST_OK = 0, ST_OVERFLOW = 3, ST_NAN = 4, ST_LOST = 5, ST_TIMEOUT = 6, ST_LEGS = 10, ST_GRID = 11,
+             ST_CELLS = 12 };
 
 enum : int { TH_NVE = 0, TH_BERENDSEN = 1, TH_NH = 2, TH_NPT = 3 };
 
@@ -1338,6 +1339,11 @@ __device__ __forceinline__ void bin_item(const Dev& d, int i) {
 __device__ __forceinline__ void scatter_item(const Dev& d, int i) {
   if (!box_flagged(d, (int)d.q[i].w)) return;
   const int p = d.cell_start[d.cell[i]] + d.rank[i];
+  if ((unsigned)p >= (unsigned)d.N) {  // counts not cleared after an interrupted build: report, write nothing
+    set_status(d.g, ST_CELLS);
+    d.g->err_index = i;
+    return;
+  }
   d.tx[p] = d.x[i]; d.ty[p] = d.y[i]; d.tz[p] = d.z[i];
   d.tvx[p] = d.vx[i]; d.tvy[p] = d.vy[i]; d.tvz[p] = d.vz[i];
   d.tid[p] = d.id[i];

@@ -14,7 +14,7 @@
 namespace mw {
 
 constexpr int kPersThreads = kFThreads;
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // default wait limit, 2 s (mw_set_wait_limit)
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
@@ -27,7 +27,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // rather than atomic contention).  gen is this block's count of barriers
 // passed (all blocks start from the same value).  Returns the status snapshot of the release
 // (identical in every block), or ST_TIMEOUT if this block gave up waiting.
-__device__ int grid_barrier(Global* g, unsigned& gen) {
+__device__ int grid_barrier(Global* g, unsigned& gen, unsigned long long limit_ns) {
   __shared__ int s_status;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -44,12 +44,12 @@ __device__ int grid_barrier(Global* g, unsigned& gen) {
       const unsigned long long t0 = globaltimer_ns();
       bool released = true;
       while (*(volatile unsigned*)&g->bar_gen == gen) {
-        __nanosleep(100);
-        if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+        if (globaltimer_ns() - t0 >= limit_ns) {  // (a limit of 0 gives up at once)
           set_status(g, ST_TIMEOUT);
           released = false;
           break;
         }
+        __nanosleep(100);
       }
       __threadfence();
       st = released ? *(volatile int*)&g->bar_stat[gen & 1u] : ST_TIMEOUT;
@@ -66,7 +66,7 @@ __device__ int grid_barrier(Global* g, unsigned& gen) {
 // block needs next costs no barrier of its own.  Same bounded waits and
 // status snapshot as grid_barrier.
 template <class Fn>
-__device__ int grid_barrier_last(Global* g, unsigned& gen, Fn fn) {
+__device__ int grid_barrier_last(Global* g, unsigned& gen, unsigned long long limit_ns, Fn fn) {
   __shared__ int s_status;
   __shared__ int s_last;
   __syncthreads();
@@ -90,12 +90,12 @@ __device__ int grid_barrier_last(Global* g, unsigned& gen, Fn fn) {
     const unsigned long long t0 = globaltimer_ns();
     bool released = true;
     while (*(volatile unsigned*)&g->bar_gen == gen) {
-      __nanosleep(100);
-      if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+      if (globaltimer_ns() - t0 >= limit_ns) {
         set_status(g, ST_TIMEOUT);
         released = false;
         break;
       }
+      __nanosleep(100);
     }
     __threadfence();
     s_status = released ? *(volatile int*)&g->bar_stat[gen & 1u] : ST_TIMEOUT;
@@ -162,7 +162,7 @@ __device__ void scan_chunk_offsets(const Dev& d) {
 }
 
 template <bool kCount, bool kNpt = false>
-__global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, int nsteps) {
+__global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, int nsteps, unsigned long long wait_ns) {
   __shared__ LegTable T;
   __shared__ unsigned s_gen;
   Global* g = d.g;
@@ -183,24 +183,24 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     if (tid == 0) g->n_over = 0;
     for (int w = gw; w * kKAtoms < d.N; w += nwarps) kick1_lane<kNpt>(d, I, w, par, pend);
     if constexpr (kNpt) {  // the new edges once every block has drifted with the old
-      if (grid_barrier_last(g, gen, [&] {
+      if (grid_barrier_last(g, gen, wait_ns, [&] {
             for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) npt_commit_box(d, b);
           }))
         return;
     } else {
-      if (grid_barrier(g, gen)) return;
+      if (grid_barrier(g, gen, wait_ns)) return;
     }
     // a2 + a3: cell binning and neighbour list, when due (flag is stable until kick2)
     if (*(volatile int*)&g->any_rebuild) {
       if (tid == 0) g->max_count = 0;
       for (int i = tid; i < d.N; i += nth) bin_item(d, i);
-      if (grid_barrier(g, gen)) return;
+      if (grid_barrier(g, gen, wait_ns)) return;
       scan_chunk_local(d);
-      if (grid_barrier(g, gen)) return;
+      if (grid_barrier(g, gen, wait_ns)) return;
       scan_chunk_offsets(d);
-      if (grid_barrier(g, gen)) return;
+      if (grid_barrier(g, gen, wait_ns)) return;
       for (int i = tid; i < d.N; i += nth) scatter_item(d, i);
-      if (grid_barrier(g, gen)) return;
+      if (grid_barrier(g, gen, wait_ns)) return;
       for (int i = tid; i < d.N; i += nth) copyback_item(d, i);
       for (int c = gw; c < d.ncell; c += nwarps) neigh_cell_warp(d, d.tq, c, P.rl2);
       if (tid < d.nbox && box_flagged(d, tid)) {
@@ -208,12 +208,12 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
         d.bst[tid].Lb = d.box[tid].L[0];
       }
       if (tid == 0) g->rebuild_steps += 1;
-      if (grid_barrier(g, gen)) return;
+      if (grid_barrier(g, gen, wait_ns)) return;
     }
     // a4 - a6: fused two- + three-body force, energy, virial
     if (tid == 0) g->wpar = par;
     for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) force_block<kCount>(d, P, T, blk, par);
-    if (grid_barrier(g, gen)) return;
+    if (grid_barrier(g, gen, wait_ns)) return;
     // a7 second half: kinetic energy of v + a per box; the rebuild (if any) is consumed
     if (blockIdx.x == 0) {
       for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     }
     // the last block to arrive runs the thermostat halves of every box (end of
     // this step, start of the next) before releasing the others
-    if (grid_barrier_last(g, gen, [&] {
+    if (grid_barrier_last(g, gen, wait_ns, [&] {
           for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) end_of_step_box<kNpt>(d, I, b, par);
           if (threadIdx.x == 0) {
             g->pend = 1;

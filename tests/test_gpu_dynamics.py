@@ -273,3 +273,30 @@ def test_unwrapped_positions_follow_free_flight(mwlib):
     assert np.abs(f).max() == 0.0
     want = x0 + V * 200 * 10.0
     assert np.abs(u1 - want).max() <= 1e-6 * np.abs(want).max()
+
+
+def test_persistent_wait_limit_reports_timeout_and_context_survives(mwlib, orc):
+    """Failure detection without a GPU fault: a wait limit of 0 makes the
+    persistent engine's first grid barrier give up at once; the step returns
+    MW_ETIMEOUT, and after a new state the same system runs on and matches
+    the oracle."""
+    x, v, box = I.nve512()
+    x = I.snap_to_grid(x, box)
+    s = mwlib.System(512, box)
+    try:
+        s.set_engine(2)
+        s.set_state(x, v)
+        s.set_wait_limit(0.0)
+        with pytest.raises(mwlib.MWError) as ei:
+            s.step(10, dt=10.0)
+        assert ei.value.status == mwlib.MW_ETIMEOUT
+        s.set_wait_limit(2.0)
+        s.set_state(x, v)
+        th = s.step(20, dt=10.0)[0]
+        xg, _ = s.get_state()
+        assert s.info()["engine"] == 2
+    finally:
+        s.close()
+    xo, _, _, tho = orc.md(x, v, box, 20, dt=10.0)
+    assert np.abs(_min_image(xg - xo, box)).max() < 5e-5
+    assert th["conserved"] == pytest.approx(tho[-1, 5], rel=3e-6)

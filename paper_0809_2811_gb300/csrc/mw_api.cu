@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mw.h"
 #include "mw_device.cuh"
 #include "mw_persistent.cuh"
@@ -104,6 +106,13 @@ struct mw_system {
 };
 
 namespace {
+
+// Host-side NVTX range over one public call (named in profiler timelines;
+// inert without a profiler attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 // defined in mw_persistent_host.inc / mw_adjoint_host.inc
 mw_status persistent_func_attrs();
@@ -899,7 +908,10 @@ mw_status mw_system_destroy(mw_system* s) {
   return MW_OK;
 }
 
-mw_status mw_set_state(mw_system* s, const double* x, const double* v) { return do_set_state(s, x, v, false); }
+mw_status mw_set_state(mw_system* s, const double* x, const double* v) {
+  Range range_("mw_set_state");
+  return do_set_state(s, x, v, false);
+}
 
 mw_status mw_set_state_dev(mw_system* s, const double* x_dev, const double* v_dev) {
   return do_set_state(s, x_dev, v_dev, true);
@@ -970,6 +982,7 @@ mw_status mw_set_params(mw_system* s, const mw_params* prm) {
 }
 
 mw_status mw_set_species(mw_system* s, int nt, const mw_params* table, const int* types) {
+  Range range_("mw_set_species");
   if (!s) return fail(MW_EINVAL, "system is NULL");
   if (nt < 1 || nt > MW_MAX_SPECIES) return fail(MW_EINVAL, "need 1 <= nt <= %d species", MW_MAX_SPECIES);
   if (!table) return fail(MW_EINVAL, "table is NULL");
@@ -1086,6 +1099,7 @@ mw_status mw_set_species(mw_system* s, int nt, const mw_params* table, const int
 }
 
 mw_status mw_build_neighbors(mw_system* s, int* max_count_out) {
+  Range range_("mw_build_neighbors");
   if (!s) return fail(MW_EINVAL, "system is NULL");
   if (!s->state_set) return fail(MW_ESTATE, "no state set");
   mw_status st;
@@ -1145,6 +1159,7 @@ mw_status mw_get_neighbors(mw_system* s, int* counts, int* nbr, int width) {
 }
 
 mw_status mw_energy_forces(mw_system* s, double* f, double* energy, double* virial) {
+  Range range_("mw_energy_forces");
   if (!s) return fail(MW_EINVAL, "system is NULL");
   mw_status st;
   if ((st = ensure_forces(s)) != MW_OK) return st;
@@ -1198,6 +1213,7 @@ mw_status mw_forces_async(mw_system* s) {
 }
 
 mw_status mw_step(mw_system* s, const mw_integrator* integ, int nsteps, mw_thermo* last) {
+  Range range_("mw_step");
   if (!s) return fail(MW_EINVAL, "system is NULL");
   if (nsteps < 0) return fail(MW_EINVAL, "nsteps < 0");
   mw_status st;
@@ -1220,6 +1236,7 @@ mw_status mw_step(mw_system* s, const mw_integrator* integ, int nsteps, mw_therm
 }
 
 mw_status mw_step_async(mw_system* s, const mw_integrator* integ, int nsteps) {
+  Range range_("mw_step_async");
   if (!s) return fail(MW_EINVAL, "system is NULL");
   if (nsteps < 0) return fail(MW_EINVAL, "nsteps < 0");
   mw_status st;

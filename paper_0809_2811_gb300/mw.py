@@ -275,6 +275,27 @@ def mw_set_species(h: int, table, types):
                                 else None))
 
 
+THERMO_COLUMNS = (("Step", "step", "{:>10d}"), ("Temp", "temperature", "{:>10.3f}"), ("PotEng", "pe", "{:>14.4f}"),
+                  ("KinEng", "ke", "{:>12.4f}"), ("TotEng", None, "{:>14.4f}"), ("Press", "pressure", "{:>11.2f}"),
+                  ("Econs", "conserved", "{:>14.4f}"), ("Volume", "volume", "{:>12.2f}"),
+                  ("Rebuilds", "rebuilds", "{:>9d}"))
+
+
+def thermo_header() -> str:
+    """Column names of thermo_line (LAMMPS-style)."""
+    return " ".join("{:>%d}" % len(f.format(0 if "d" in f else 0.0)) for _, _, f in THERMO_COLUMNS).format(
+        *[c for c, _, _ in THERMO_COLUMNS])
+
+
+def thermo_line(rec: dict) -> str:
+    """One LAMMPS-style thermo line of a record (mw_thermo as a dict); TotEng = KinEng + PotEng."""
+    vals = []
+    for _, key, f in THERMO_COLUMNS:
+        v = rec["ke"] + rec["pe"] if key is None else rec[key]
+        vals.append(f.format(int(v) if "d" in f else float(v)))
+    return " ".join(vals)
+
+
 def make_integrator(dt=10.0, thermostat=MW_NVE, T0=300.0, tau=1000.0, T0_per_box=None, p_ext=1.0,
                     tau_p=5000.0):
     """tau, tau_p in fs; p_ext in atm (MW_NPT only)."""
@@ -461,6 +482,22 @@ class System:
         """Continues from a checkpoint taken on a system of the same make (mw_checkpoint_load)."""
         buf = ctypes.create_string_buffer(blob, len(blob))
         _check(lib().mw_checkpoint_load(self.h, buf, len(blob)))
+
+    def run(self, nsteps: int, every: int = 100, log=print, **integ):
+        """nsteps steps with a thermo line per box every `every` steps (and the
+        header first); returns the last records."""
+        log(thermo_header())
+        th = self.thermo()
+        for t in th:
+            log(thermo_line(t))
+        done = 0
+        while done < nsteps:
+            k = min(every, nsteps - done)
+            th = self.step(k, **integ)
+            done += k
+            for t in th:
+                log(thermo_line(t))
+        return th
 
     def box(self) -> np.ndarray:
         """Current edges of every box (nbox x 3, A); they change under MW_NPT."""

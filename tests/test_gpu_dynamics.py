@@ -300,3 +300,19 @@ def test_persistent_wait_limit_reports_timeout_and_context_survives(mwlib, orc):
     xo, _, _, tho = orc.md(x, v, box, 20, dt=10.0)
     assert np.abs(_min_image(xg - xo, box)).max() < 5e-5
     assert th["conserved"] == pytest.approx(tho[-1, 5], rel=3e-6)
+
+
+def test_run_logs_a_thermo_line_every_k_steps(mwlib):
+    x, v, box = I.nve512()
+    lines = []
+    s = mwlib.System(512, box)
+    try:
+        s.set_state(x, v)
+        th = s.run(250, every=100, log=lines.append, dt=10.0, thermostat=2, T0=298.0, tau=1000.0)
+    finally:
+        s.close()
+    assert lines[0].split()[0] == "Step"
+    steps = [int(l.split()[0]) for l in lines[1:]]
+    assert steps == [0, 100, 200, 250]
+    assert th[0]["step"] == 250
+    assert float(lines[-1].split()[6]) == pytest.approx(th[0]["conserved"], abs=1e-4)

@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--skin", type=float, default=None,
                     help="neighbour-list skin (A) for an explicit --engine (the autotuner picks it otherwise)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--phase-marks", action="store_true",
+                    help="instead of the bench line: where the persistent engine's step goes, phase by phase")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prep-steps", type=int, default=3000)
     ap.add_argument("--workload", default="ice_liquid_32k",
@@ -271,6 +273,8 @@ def run_gpu(args, world, rank, local, pg):
     # warm-up
     mw.mw_step(sysm.h, integ, max(args.warmup, 3), sysm.nbox)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    if args.phase_marks:
+        return phase_breakdown(args, rank, local, torch, mw, sysm, integ, stream, flush)
     th0 = sysm.thermo()
     reb0 = sum(t["rebuilds"] for t in th0)
     rs0 = sysm.info()["rebuild_steps"]
@@ -506,6 +510,53 @@ def run_other(args, world, rank, local, pg):
                       "rebuilds_in_timed_region": int(rebuilds),
                       "l2": "flushed between steps" if flush_use is not None else "working set > L2"},
            **extra}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+PHASES = ("kick1", "barrier after kick1", "rebuild", "force", "barrier after force", "kick2",
+          "last barrier + thermostat tail")
+
+
+def phase_breakdown(args, rank, local, torch, mw, sysm, integ, stream, flush):
+    """The timed loop of the bench (one persistent launch per step, L2
+    flushed between steps) with the engine's phase marks on: block 0's SM
+    clock at each phase boundary, averaged over steps without and with a
+    rebuild, beside the CUDA-event time of each step."""
+    if sysm.info()["engine"] != mw.MW_ENGINE_PERSISTENT:
+        raise SystemExit("--phase-marks needs the persistent engine (--engine persistent)")
+    sysm.set_phase_marks(1)
+    K = max(args.steps, 20)
+    marks, evs = [], []
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(K):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mw.mw_step_async(sysm.h, integ, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        marks.append(sysm.phase_marks(1)[0].astype(np.int64))
+        evs.append(e0.elapsed_time(e1) * 1e3)
+    clk = clocks.stop()
+    mw.mw_sync(sysm.h)
+    sysm.set_phase_marks(0)
+    mhz = clk.get("sm_mhz") or SM_MAX_MHZ
+    R = np.array(marks)
+    d = np.diff(R, axis=1) / mhz  # us
+    span = (R[:, 7] - R[:, 0]) / mhz
+    reb = d[:, 2] > 1.0
+    evs = np.array(evs)
+    out = {"mode": "phase breakdown (persistent engine)", "steps": K, "sm_mhz": mhz, "clocks": clk,
+           "config": {"workload": "ice Ih 32768 @0.92 + liquid 32768 @0.9998 (melted), 2-box batch, NH 240 K, dt 10 fs",
+                      "skin_A": sysm.info()["r_list"] - 4.3065, "blocks": sysm.info()["persistent_blocks"],
+                      "l2": "flushed between steps"}}
+    for tag, m in (("without_rebuild", ~reb), ("with_rebuild", reb), ("all", np.ones_like(reb))):
+        if m.any():
+            out[tag] = {"steps": int(m.sum()), "event_us": float(evs[m].mean()), "kernel_span_us": float(span[m].mean()),
+                        **{p: float(v) for p, v in zip(PHASES, d[m].mean(axis=0))}}
     if rank == 0:
         print(json.dumps(out), flush=True)
 

@@ -261,6 +261,15 @@ mw_status mw_checkpoint_size(mw_system* s, size_t* bytes);
 mw_status mw_checkpoint_save(mw_system* s, void* buf, size_t bytes);
 mw_status mw_checkpoint_load(mw_system* s, const void* buf, size_t bytes);
 
+/* Phase marks of the persistent engine (tracing): with cap > 0, block 0 of
+ * each persistent launch records the SM clock (clock64, cycles) at 8 points
+ * of each of its first cap steps: step start, kick1 done, its grid barrier
+ * passed, rebuild done, force done, its barrier passed, kick2 done, the
+ * last barrier passed.  mw_get_phase_marks copies cap x 8 values of the last
+ * launch (host array).  cap = 0 turns the marks off (the default). */
+mw_status mw_set_phase_marks(mw_system* s, int cap);
+mw_status mw_get_phase_marks(mw_system* s, unsigned long long* out, int cap);
+
 /* Limit (seconds, 0..60; default 2) of every device-side wait of the
  * persistent engine (its grid barriers).  A wait that runs out sets
  * MW_ETIMEOUT and the kernel returns; the state of the interrupted step is

@@ -1314,6 +1314,35 @@ mw_status mw_get_box(mw_system* s, double* box) {
   return MW_OK;
 }
 
+mw_status mw_set_phase_marks(mw_system* s, int cap) {
+  if (!s || cap < 0 || cap > (1 << 20)) return fail(MW_EINVAL, "cap must be in [0, 2^20]");
+  mw_status st;
+  if (cap > s->d.marks_cap) {
+    dfree(s, s->d.marks);
+    s->d.marks = nullptr;
+    if ((st = dalloc(s, &s->d.marks, (size_t)cap * kPhaseMarks)) != MW_OK) return st;
+  }
+  if (cap == 0) {
+    dfree(s, s->d.marks);
+    s->d.marks = nullptr;
+  }
+  if (s->d.marks)
+    MW_CUDA(cudaMemsetAsync(s->d.marks, 0, sizeof(unsigned long long) * (size_t)cap * kPhaseMarks, s->stream));
+  s->d.marks_cap = cap;
+  s->graph_dirty = true;
+  return MW_OK;
+}
+
+mw_status mw_get_phase_marks(mw_system* s, unsigned long long* out, int cap) {
+  if (!s || !out || cap < 0) return fail(MW_EINVAL, "bad arguments");
+  if (cap > s->d.marks_cap) return fail(MW_EINVAL, "cap %d exceeds the %d steps recorded", cap, s->d.marks_cap);
+  if (cap == 0) return MW_OK;
+  MW_CUDA(cudaMemcpyAsync(out, s->d.marks, sizeof(unsigned long long) * (size_t)cap * kPhaseMarks,
+                          cudaMemcpyDeviceToHost, s->stream));
+  MW_CUDA(cudaStreamSynchronize(s->stream));
+  return MW_OK;
+}
+
 mw_status mw_set_wait_limit(mw_system* s, double seconds) {
   if (!s || !(seconds >= 0.0) || !(seconds <= 60.0)) return fail(MW_EINVAL, "wait limit must be in [0, 60] s");
   s->wait_ns = (unsigned long long)(seconds * 1e9);

@@ -180,7 +180,13 @@ struct Dev {
   const SpPair* sp_pair;  // nsp^2, (a, b) at a nsp + b
   const float2* sp_tri;   // nsp^3: (lambda epsilon, cos theta0) of (centre a; legs b, c)
   int nsp;
+  // phase marks of the persistent engine (null unless enabled): clock64 of
+  // block 0 at kPhaseMarks points of each of the first marks_cap steps
+  unsigned long long* marks;
+  int marks_cap;
 };
+
+constexpr int kPhaseMarks = 8;
 
 // ---------------------------------------------------------------------------
 // small helpers

@@ -14,6 +14,13 @@
 namespace mw {
 
 constexpr int kPersThreads = kFThreads;
+
+// Phase mark k of step s (block 0, thread 0; the SM clock): step start,
+// kick1 done, its barrier passed, rebuild done, force done, its barrier
+// passed, kick2 done, the last barrier passed.
+__device__ __forceinline__ void phase_mark(const Dev& d, int s, int k) {
+  if (d.marks && s < d.marks_cap && blockIdx.x == 0 && threadIdx.x == 0) d.marks[s * kPhaseMarks + k] = clock64();
+}
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // default wait limit, 2 s (mw_set_wait_limit)
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -178,10 +185,12 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
   for (int s = 0; s < nsteps; ++s) {
     const unsigned long long step = step0 + (unsigned long long)s;
     const int par = (int)(step & 1ull);
+    phase_mark(d, s, 0);
     // a1 + a7 first half, a8 displacement check
     const int pend = *(volatile int*)&g->pend;  // stable: written only at the end of the kick2 phase
     if (tid == 0) g->n_over = 0;
     for (int w = gw; w * kKAtoms < d.N; w += nwarps) kick1_lane<kNpt>(d, I, w, par, pend);
+    phase_mark(d, s, 1);
     if constexpr (kNpt) {  // the new edges once every block has drifted with the old
       if (grid_barrier_last(g, gen, wait_ns, [&] {
             for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) npt_commit_box(d, b);
@@ -190,6 +199,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     } else {
       if (grid_barrier(g, gen, wait_ns)) return;
     }
+    phase_mark(d, s, 2);
     // a2 + a3: cell binning and neighbour list, when due (flag is stable until kick2)
     if (*(volatile int*)&g->any_rebuild) {
       if (tid == 0) g->max_count = 0;
@@ -210,10 +220,13 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
       if (tid == 0) g->rebuild_steps += 1;
       if (grid_barrier(g, gen, wait_ns)) return;
     }
+    phase_mark(d, s, 3);
     // a4 - a6: fused two- + three-body force, energy, virial
     if (tid == 0) g->wpar = par;
     for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) force_block<kCount>(d, P, T, blk, par);
+    phase_mark(d, s, 4);
     if (grid_barrier(g, gen, wait_ns)) return;
+    phase_mark(d, s, 5);
     // a7 second half: kinetic energy of v + a per box; the rebuild (if any) is consumed
     if (blockIdx.x == 0) {
       for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
@@ -226,6 +239,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
       ke[0] = kick2_lane(d, I, w, b);
       box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_acc[par]; });
     }
+    phase_mark(d, s, 6);
     // the last block to arrive runs the thermostat halves of every box (end of
     // this step, start of the next) before releasing the others
     if (grid_barrier_last(g, gen, wait_ns, [&] {
@@ -236,6 +250,7 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
           }
         }))
       return;
+    phase_mark(d, s, 7);
   }
 }
 

@@ -31,7 +31,8 @@ EXPORTS = (
     "mw_energy_forces_vjp", "mw_set_engine", "mw_set_nbr_width", "mw_autotune", "mw_get_info",
     "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc", "mw_set_skin", "mw_phase_times",
     "mw_pair_histogram", "mw_angle_histogram", "mw_get_unwrapped", "mw_get_box", "mw_set_species",
-    "mw_checkpoint_size", "mw_checkpoint_save", "mw_checkpoint_load", "mw_set_wait_limit", "mw_last_error",
+    "mw_checkpoint_size", "mw_checkpoint_save", "mw_checkpoint_load", "mw_set_wait_limit",
+    "mw_set_phase_marks", "mw_get_phase_marks", "mw_last_error",
 )
 
 
@@ -124,6 +125,8 @@ def lib():
             "mw_get_box": [P, dp],
             "mw_checkpoint_size": [P, ctypes.POINTER(ctypes.c_size_t)],
             "mw_set_wait_limit": [P, ctypes.c_double],
+            "mw_set_phase_marks": [P, ctypes.c_int],
+            "mw_get_phase_marks": [P, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int],
             "mw_checkpoint_save": [P, P, ctypes.c_size_t],
             "mw_checkpoint_load": [P, P, ctypes.c_size_t],
             "mw_set_species": [P, ctypes.c_int, ctypes.POINTER(mw_params), ip],
@@ -465,6 +468,16 @@ class System:
     def set_species(self, table, types):
         """Several species: table (nt, nt, nt, 10) or nt^3 mw_params, types per atom (caller's order)."""
         mw_set_species(self.h, table, types)
+
+    def set_phase_marks(self, cap: int):
+        """Record the persistent engine's phase marks for the first cap steps of each launch (0: off)."""
+        _check(lib().mw_set_phase_marks(self.h, int(cap)))
+
+    def phase_marks(self, cap: int) -> np.ndarray:
+        """SM-clock marks (cycles) of the last persistent launch: [cap, 8]."""
+        out = np.zeros((cap, 8), np.uint64)
+        _check(lib().mw_get_phase_marks(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)), int(cap)))
+        return out
 
     def set_wait_limit(self, seconds: float):
         """Limit of each device-side wait of the persistent engine (MW_ETIMEOUT past it)."""

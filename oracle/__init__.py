@@ -73,6 +73,9 @@ def lib():
         _lib.or_force_vjp.argtypes = [d, ctypes.c_int, d, d, d, d, d]
         _lib.or_species_table_check.argtypes = [d, ctypes.c_int]
         _lib.or_energy_forces_species.argtypes = [d, ctypes.c_int, i, ctypes.c_int, d, d, d, d]
+        _lib.or_md_npt_species.argtypes = [d, ctypes.c_int, i, ctypes.c_int, d, d, d, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, d, d]
         _lib.or_md_species.argtypes = [d, ctypes.c_int, i, ctypes.c_int, d, d, d, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, d, d]
         _lib.or_energy_param_grad.argtypes = [d, ctypes.c_int, d, d, d]
@@ -290,3 +293,19 @@ def md_species(x, v, box, types, table, nsteps, dt=10.0, kind=0, T0=300.0, tau=1
     _check(lib().or_md_species(_dp(t), t.shape[0], _ip(ty), x.shape[0], _dp(x), _dp(v), _dp(box), mass, dt, kind,
                                T0, tau, nsteps, _dp(st), _dp(th)), "md_species")
     return x, v, (float(st[0]), float(st[1])), th
+
+
+def md_npt_species(x, v, box, types, table, nsteps, dt=10.0, T0=298.0, tau=1000.0, p_atm=0.0, tau_p=2500.0,
+                   mass=18.015, state=(0.0, 0.0, 0.0)):
+    """md_npt() with the several-species potential; same returns."""
+    t = np.ascontiguousarray(table, np.float64)
+    ty = np.ascontiguousarray(types, np.int32)
+    x = np.array(x, np.float64).reshape(-1, 3)
+    v = np.array(v, np.float64).reshape(-1, 3)
+    box = np.array(box, np.float64)
+    st = np.array(state, np.float64)
+    th = np.zeros((nsteps + 1, 10))
+    _check(lib().or_md_npt_species(_dp(t), t.shape[0], _ip(ty), x.shape[0], _dp(x), _dp(v), _dp(box), mass, dt,
+                                   T0, tau, p_atm / KCAL_PER_A3_ATM, tau_p, nsteps, _dp(st), _dp(th)),
+           "md_npt_species")
+    return x, v, box, (float(st[0]), float(st[1]), float(st[2])), th

@@ -752,14 +752,31 @@ static int md_run(const md_pot* pot, int n, double* x, double* v, const double* 
  * V, pressure (kcal/mol/A^3); conserved = ke + pe + P V + pe^2/(2W)
  *   + Q xi^2/2 + Ndf kB T0 eta.  Positions are wrapped into [0, L).
  */
+static int npt_run(const md_pot* pot, int n, double* x, double* v, double* box, double mass, double dt, double T0,
+                   double tau, double P, double tau_p, int nsteps, double* state, double* thermo);
+
 int or_md_npt(const double* prm, int n, double* x, double* v, double* box, double mass, double dt, double T0,
               double tau, double P, double tau_p, int nsteps, double* state, double* thermo) {
+  const md_pot pot = {prm, NULL, 0, NULL};
+  return npt_run(&pot, n, x, v, box, mass, dt, T0, tau, P, tau_p, nsteps, state, thermo);
+}
+
+/* or_md_npt with the several-species potential of or_energy_forces_species. */
+int or_md_npt_species(const double* table, int nt, const int* types, int n, double* x, double* v, double* box,
+                      double mass, double dt, double T0, double tau, double P, double tau_p, int nsteps,
+                      double* state, double* thermo) {
+  const md_pot pot = {NULL, table, nt, types};
+  return npt_run(&pot, n, x, v, box, mass, dt, T0, tau, P, tau_p, nsteps, state, thermo);
+}
+
+static int npt_run(const md_pot* pot, int n, double* x, double* v, double* box, double mass, double dt, double T0,
+                   double tau, double P, double tau_p, int nsteps, double* state, double* thermo) {
   if (n < 2) return OR_EINVAL;
   double* f = (double*)malloc(sizeof(double) * 3 * (size_t)n);
   if (!f) return OR_ENOMEM;
   double out[11];
   for (int i = 0; i < 3 * n; ++i) x[i] = wrap1(x[i], box[i % 3]);
-  int rc = or_energy_forces_cell(prm, n, x, box, f, out);
+  int rc = md_forces(pot, n, x, box, f, out);
   if (rc != OR_OK) {
     free(f);
     return rc;
@@ -784,7 +801,7 @@ int or_md_npt(const double* prm, int n, double* x, double* v, double* box, doubl
       const double sh = (fabs(u) > 1e-8) ? exp(0.5 * u) * sinh(0.5 * u) / (0.5 * u) : 1.0 + 0.5 * u;
       for (int k = 0; k < 3; ++k) box[k] *= eu;
       for (int i = 0; i < 3 * n; ++i) x[i] = wrap1(x[i] * eu + v[i] * dt * sh, box[i % 3]);
-      rc = or_energy_forces_cell(prm, n, x, box, f, out);
+      rc = md_forces(pot, n, x, box, f, out);
       if (rc != OR_OK) break;
       for (int i = 0; i < 3 * n; ++i) v[i] += cf * f[i];
       for (int i = 0; i < 3 * n; ++i) v[i] *= fr;  /* pe is unchanged since the first friction half */

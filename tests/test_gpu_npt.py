@@ -226,3 +226,28 @@ def test_npt_density_and_vaporization_enthalpy_298K(mwlib):
     dh = 2.5 * R_KCAL * 298.0 - np.mean(h) / 4096
     assert rho == pytest.approx(0.997, abs=0.004)
     assert dh == pytest.approx(10.65, abs=0.15)
+
+
+@pytest.mark.parametrize("table_kind", ["solute", "mixed"])
+def test_npt_with_several_species_matches_oracle(mwlib, orc, table_kind):
+    """Isobaric dynamics of mW with a solute (the moment kernel) and of a
+    mixture with every parameter set different (the leg-pair kernel): 20
+    steps against the oracle's md_npt_species, same bounds as one species."""
+    x, box = I.jittered_box(1000, 1.0, 0.15, 71)
+    x = I.snap_to_grid(x, box)
+    v = I.maxwell_velocities(1000, 298.0, seed=72)
+    table = I.species_table_solute() if table_kind == "solute" else I.species_table_mixed(2, 73)
+    ty = I.species_draw(1000, 2, 74, [0.9, 0.1] if table_kind == "solute" else None)
+    kw = dict(dt=10.0, T0=298.0, tau=500.0, tau_p=1500.0)
+    s = mwlib.System(1000, box)
+    try:
+        s.set_species(table, ty)
+        s.set_state(x, v)
+        th = s.step(20, thermostat=mwlib.MW_NPT, p_ext=1.0, **kw)[0]
+        xg, vg = s.get_state()
+        bg = s.box()[0]
+    finally:
+        s.close()
+    xo, vo, bo, st, tho = orc.md_npt_species(x, v, box, ty, table, 20, p_atm=1.0, **kw)
+    assert abs(bo[0] / box[0] - 1) > 1e-3
+    _compare(th, xg, vg, bg, xo, vo, bo, st, tho[-1], 20)

@@ -626,3 +626,15 @@ def test_species_dynamics_with_one_type_is_the_one_species_run(orc):
     xb, vb, sb, thb = orc.md(x, v, box, 20, dt=10.0, kind=2, T0=298.0, tau=1000.0)
     assert np.abs(xa - xb).max() < 1e-9 and np.abs(va - vb).max() < 1e-12
     assert tha[-1, 5] == pytest.approx(thb[-1, 5], rel=1e-12)
+
+
+def test_species_npt_with_one_type_is_the_one_species_run(orc):
+    x, v, box = I.nve512()
+    p = orc.default_params()
+    t = orc.species_table(2, lambda a, b, c: p)
+    ty = np.arange(512) % 2
+    xa, va, ba, sa, tha = orc.md_npt_species(x, v, box, ty, t, 20, dt=10.0, T0=298.0, tau=1000.0, tau_p=2000.0)
+    xb, vb, bb, sb, thb = orc.md_npt(x, v, box, 20, dt=10.0, T0=298.0, tau=1000.0, tau_p=2000.0)
+    assert np.abs(xa - xb).max() < 1e-9 and np.abs(va - vb).max() < 1e-12
+    assert np.abs(ba - bb).max() < 1e-12 and ba[0] != box[0]
+    assert tha[-1, 5] == pytest.approx(thb[-1, 5], rel=1e-12)

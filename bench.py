@@ -545,9 +545,13 @@ def phase_breakdown(args, rank, local, torch, mw, sysm, integ, stream, flush):
     sysm.set_phase_marks(0)
     mhz = clk.get("sm_mhz") or SM_MAX_MHZ
     R = np.array(marks)
-    d = np.diff(R, axis=1) / mhz  # us
+    d = np.diff(R[:, :8], axis=1) / mhz  # us
     span = (R[:, 7] - R[:, 0]) / mhz
     reb = d[:, 2] > 1.0
+    # inside a rebuild: binning, local scan, offsets, scatter, copy-back, neighbour lists (each up to
+    # its own end, the barrier before it included), and the final barrier
+    sub = np.stack([R[:, 8] - R[:, 2], R[:, 9] - R[:, 8], R[:, 10] - R[:, 9], R[:, 11] - R[:, 10],
+                    R[:, 12] - R[:, 11], R[:, 13] - R[:, 12], R[:, 3] - R[:, 13]], axis=1) / mhz
     evs = np.array(evs)
     out = {"mode": "phase breakdown (persistent engine)", "steps": K, "sm_mhz": mhz, "clocks": clk,
            "config": {"workload": "ice Ih 32768 @0.92 + liquid 32768 @0.9998 (melted), 2-box batch, NH 240 K, dt 10 fs",
@@ -557,6 +561,10 @@ def phase_breakdown(args, rank, local, torch, mw, sysm, integ, stream, flush):
         if m.any():
             out[tag] = {"steps": int(m.sum()), "event_us": float(evs[m].mean()), "kernel_span_us": float(span[m].mean()),
                         **{p: float(v) for p, v in zip(PHASES, d[m].mean(axis=0))}}
+    if reb.any():
+        out["rebuild_inside"] = {p: float(v) for p, v in zip(
+            ("binning", "barrier + local scan", "barrier + scan offsets", "barrier + scatter",
+             "barrier + copy-back", "neighbour lists", "final barrier"), sub[reb].mean(axis=0))}
     if rank == 0:
         print(json.dumps(out), flush=True)
 

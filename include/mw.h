@@ -262,11 +262,14 @@ mw_status mw_checkpoint_save(mw_system* s, void* buf, size_t bytes);
 mw_status mw_checkpoint_load(mw_system* s, const void* buf, size_t bytes);
 
 /* Phase marks of the persistent engine (tracing): with cap > 0, block 0 of
- * each persistent launch records the SM clock (clock64, cycles) at 8 points
- * of each of its first cap steps: step start, kick1 done, its grid barrier
- * passed, rebuild done, force done, its barrier passed, kick2 done, the
- * last barrier passed.  mw_get_phase_marks copies cap x 8 values of the last
- * launch (host array).  cap = 0 turns the marks off (the default). */
+ * each persistent launch records the SM clock (clock64, cycles) at up to 16
+ * points of each of its first cap steps: 0 step start, 1 kick1 done, 2 its
+ * grid barrier passed, 3 rebuild done, 4 force done, 5 its barrier passed,
+ * 6 kick2 done, 7 the last barrier passed; on rebuild steps also 8
+ * binning, 9 local scan, 10 scan offsets, 11 scatter, 12 copy-back, 13
+ * neighbour lists done (each before its barrier); unused slots hold 0.
+ * mw_get_phase_marks copies cap x 16 values of the last launch (host array).
+ * cap = 0 turns the marks off (the default). */
 mw_status mw_set_phase_marks(mw_system* s, int cap);
 mw_status mw_get_phase_marks(mw_system* s, unsigned long long* out, int cap);
 

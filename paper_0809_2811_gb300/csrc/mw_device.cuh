@@ -186,7 +186,7 @@ struct Dev {
   int marks_cap;
 };
 
-constexpr int kPhaseMarks = 8;
+constexpr int kPhaseMarks = 16;  // 14 used
 
 // ---------------------------------------------------------------------------
 // small helpers

@@ -15,9 +15,11 @@ namespace mw {
 
 constexpr int kPersThreads = kFThreads;
 
-// Phase mark k of step s (block 0, thread 0; the SM clock): step start,
-// kick1 done, its barrier passed, rebuild done, force done, its barrier
-// passed, kick2 done, the last barrier passed.
+// Phase mark k of step s (block 0, thread 0; the SM clock): 0 step start,
+// 1 kick1 done, 2 its barrier passed, 3 rebuild done, 4 force done, 5 its
+// barrier passed, 6 kick2 done, 7 the last barrier passed; on rebuild steps
+// also 8 binning, 9 local scan, 10 scan offsets, 11 scatter, 12 copy-back,
+// 13 neighbour lists done (each before its barrier).
 __device__ __forceinline__ void phase_mark(const Dev& d, int s, int k) {
   if (d.marks && s < d.marks_cap && blockIdx.x == 0 && threadIdx.x == 0) d.marks[s * kPhaseMarks + k] = clock64();
 }
@@ -204,15 +206,21 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     if (*(volatile int*)&g->any_rebuild) {
       if (tid == 0) g->max_count = 0;
       for (int i = tid; i < d.N; i += nth) bin_item(d, i);
+      phase_mark(d, s, 8);
       if (grid_barrier(g, gen, wait_ns)) return;
       scan_chunk_local(d);
+      phase_mark(d, s, 9);
       if (grid_barrier(g, gen, wait_ns)) return;
       scan_chunk_offsets(d);
+      phase_mark(d, s, 10);
       if (grid_barrier(g, gen, wait_ns)) return;
       for (int i = tid; i < d.N; i += nth) scatter_item(d, i);
+      phase_mark(d, s, 11);
       if (grid_barrier(g, gen, wait_ns)) return;
       for (int i = tid; i < d.N; i += nth) copyback_item(d, i);
+      phase_mark(d, s, 12);
       for (int c = gw; c < d.ncell; c += nwarps) neigh_cell_warp(d, d.tq, c, P.rl2);
+      phase_mark(d, s, 13);
       if (tid < d.nbox && box_flagged(d, tid)) {
         d.bst[tid].rebuilds += 1;
         d.bst[tid].Lb = d.box[tid].L[0];

@@ -474,8 +474,8 @@ class System:
         _check(lib().mw_set_phase_marks(self.h, int(cap)))
 
     def phase_marks(self, cap: int) -> np.ndarray:
-        """SM-clock marks (cycles) of the last persistent launch: [cap, 8]."""
-        out = np.zeros((cap, 8), np.uint64)
+        """SM-clock marks (cycles) of the last persistent launch: [cap, 16] (see mw_set_phase_marks)."""
+        out = np.zeros((cap, 16), np.uint64)
         _check(lib().mw_get_phase_marks(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)), int(cap)))
         return out
 

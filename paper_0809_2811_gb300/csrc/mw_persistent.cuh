@@ -114,6 +114,25 @@ __device__ int grid_barrier_last(Global* g, unsigned& gen, unsigned long long li
   return s_status;
 }
 
+// The end of a launch: the last block to arrive runs fn() and resets the
+// arrival count; the others return without waiting (no wait, so no limit).
+template <class Fn>
+__device__ void end_arrive_last(Global* g, Fn fn) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&g->bar_count, 1u) + 1u == gridDim.x);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    fn();
+    __syncthreads();
+    if (threadIdx.x == 0) g->bar_count = 0u;
+  }
+}
+
 // Two-level exclusive scan of the cell counts over the grid: each block scans
 // a contiguous chunk of cells (local prefix + chunk total), then adds the
 // totals of the chunks before it.
@@ -250,14 +269,22 @@ __global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, i
     phase_mark(d, s, 6);
     // the last block to arrive runs the thermostat halves of every box (end of
     // this step, start of the next) before releasing the others
-    if (grid_barrier_last(g, gen, wait_ns, [&] {
-          for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) end_of_step_box<kNpt>(d, I, b, par);
-          if (threadIdx.x == 0) {
-            g->pend = 1;
-            g->step = step + 1ull;
-          }
-        }))
+    auto tail = [&] {
+      for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) end_of_step_box<kNpt>(d, I, b, par);
+      if (threadIdx.x == 0) {
+        g->pend = 1;
+        g->step = step + 1ull;
+      }
+    };
+    if (s == nsteps - 1) {
+      // the launch's last step: nothing follows in this launch, so the other
+      // blocks leave at once and the last one to arrive runs the tail (the
+      // arrival count goes back to 0 as at a barrier)
+      phase_mark(d, s, 7);
+      end_arrive_last(g, tail);
       return;
+    }
+    if (grid_barrier_last(g, gen, wait_ns, tail)) return;
     phase_mark(d, s, 7);
   }
 }

@@ -265,7 +265,8 @@ mw_status mw_checkpoint_load(mw_system* s, const void* buf, size_t bytes);
  * each persistent launch records the SM clock (clock64, cycles) at up to 16
  * points of each of its first cap steps: 0 step start, 1 kick1 done, 2 its
  * grid barrier passed, 3 rebuild done, 4 force done, 5 its barrier passed,
- * 6 kick2 done, 7 the last barrier passed; on rebuild steps also 8
+ * 6 kick2 done, 7 the last barrier passed (on a launch's last step, which
+ * ends without that barrier: block 0's arrival); on rebuild steps also 8
  * binning, 9 local scan, 10 scan offsets, 11 scatter, 12 copy-back, 13
  * neighbour lists done (each before its barrier); unused slots hold 0.
  * mw_get_phase_marks copies cap x 16 values of the last launch (host array).

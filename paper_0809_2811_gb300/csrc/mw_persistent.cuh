@@ -17,7 +17,8 @@ constexpr int kPersThreads = kFThreads;
 
 // Phase mark k of step s (block 0, thread 0; the SM clock): 0 step start,
 // 1 kick1 done, 2 its barrier passed, 3 rebuild done, 4 force done, 5 its
-// barrier passed, 6 kick2 done, 7 the last barrier passed; on rebuild steps
+// barrier passed, 6 kick2 done, 7 the last barrier passed (a launch's last
+// step has none: block 0's arrival); on rebuild steps
 // also 8 binning, 9 local scan, 10 scan offsets, 11 scatter, 12 copy-back,
 // 13 neighbour lists done (each before its barrier).
 __device__ __forceinline__ void phase_mark(const Dev& d, int s, int k) {

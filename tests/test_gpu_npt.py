@@ -251,3 +251,32 @@ def test_npt_with_several_species_matches_oracle(mwlib, orc, table_kind):
     xo, vo, bo, st, tho = orc.md_npt_species(x, v, box, ty, table, 20, p_atm=1.0, **kw)
     assert abs(bo[0] / box[0] - 1) > 1e-3
     _compare(th, xg, vg, bg, xo, vo, bo, st, tho[-1], 20)
+
+
+def test_npt_async_run_stops_at_the_grid_and_continues(mwlib):
+    """mw_step_async has no recovery of its own: when the collapsing 0.80
+    g/cm^3 box leaves its cell grid the run stops after a whole step,
+    mw_sync reports MW_EGRID and lays the grid out again, and the next
+    asynchronous run goes on from that step."""
+    x, box = I.jittered_box(512, 0.80, 0.25, 901)
+    x = I.snap_to_grid(x, box)
+    v = I.maxwell_velocities(512, 250.0, seed=902)
+    it = mwlib.make_integrator(10.0, mwlib.MW_NPT, 250.0, 200.0, p_ext=0.0, tau_p=500.0)
+    s = mwlib.System(512, box)
+    try:
+        s.set_engine(2)
+        s.set_state(x, v)
+        mwlib.mw_step(s.h, it, 0, 1)  # forces of the start (and the integrator set)
+        mwlib.mw_step_async(s.h, it, 30)
+        with pytest.raises(mwlib.MWError) as ei:
+            mwlib.mw_sync(s.h)
+        assert ei.value.status == mwlib.MW_EGRID
+        done = s.thermo()[0]["step"]
+        assert 0 <= done < 30
+        assert s.info()["regrids"] == 1
+        mwlib.mw_step_async(s.h, it, 30 - done)
+        mwlib.mw_sync(s.h)
+        th = s.thermo()[0]
+    finally:
+        s.close()
+    assert th["step"] == 30

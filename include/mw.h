@@ -152,10 +152,12 @@ mw_status mw_batch_create(mw_system** out, int nbox, const int* n, const double*
 /* Frees every device and host resource of s (NULL is a no-op). */
 mw_status mw_system_destroy(mw_system* s);
 
-/* Sets positions x (n_total*3, required, any real values: they are wrapped
- * into the box) and velocities v (n_total*3, or NULL for zero), host arrays.
- * Resets the step counter, the thermostat (xi = eta = 0) and marks the
- * neighbour list stale. */
+/* Sets positions x (n_total*3, required, any finite values: they are
+ * wrapped into the box) and velocities v (n_total*3, or NULL for zero), host
+ * arrays.  Resets the step counter, the thermostat (xi = eta = 0) and marks
+ * the neighbour list stale.  A non-finite value (checked on the device, for
+ * host and device inputs alike) gives MW_EINVAL and leaves the system
+ * without a state. */
 mw_status mw_set_state(mw_system* s, const double* x, const double* v);
 /* Same with device arrays. */
 mw_status mw_set_state_dev(mw_system* s, const double* x_dev, const double* v_dev);

@@ -597,9 +597,7 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   const size_t bytes = sizeof(double) * 3 * (size_t)s->N;
   const double* xd = x;
   const double* vd = v;
-  if (!dev) {
-    for (size_t k = 0; k < 3 * (size_t)s->N; ++k)
-      if (!std::isfinite(x[k]) || (v && !std::isfinite(v[k]))) return fail(MW_EINVAL, "non-finite input at %zu", k);
+  if (!dev) {  // (finiteness is checked on the device, as for device inputs)
     MW_CUDA(cudaMemcpyAsync(s->d.stage, x, bytes, cudaMemcpyHostToDevice, s->stream));
     xd = s->d.stage;
     if (v) {
@@ -629,7 +627,14 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   // binned atoms without the scan that clears them
   MW_CUDA(cudaMemsetAsync(s->d.cell_cnt, 0, sizeof(int) * s->ncell, s->stream));
   MW_CUDA(cudaGetLastError());
+  int bad[2];
+  MW_CUDA(cudaMemcpyAsync(bad, &s->d.g->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  MW_CUDA(cudaMemcpyAsync(bad + 1, &s->d.g->err_index, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   MW_CUDA(cudaStreamSynchronize(s->stream));
+  if (bad[0] == ST_INPUT) {
+    s->state_set = false;  // the arrays hold part of a refused state
+    return fail(MW_EINVAL, "non-finite position or velocity of atom %d", bad[1]);
+  }
   s->state_set = true;
   s->forces_valid = false;
   s->need_prime = true;  // thermostat at rest: xi = eta = 0, KE of the new velocities

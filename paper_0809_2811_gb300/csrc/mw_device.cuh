@@ -33,7 +33,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Status codes written to Global::status (same values as mw_status).
 enum : int { ST_OK = 0, ST_OVERFLOW = 3, ST_NAN = 4, ST_LOST = 5, ST_TIMEOUT = 6, ST_LEGS = 10, ST_GRID = 11,
-             ST_CELLS = 12 };
+             ST_CELLS = 12, ST_INPUT = 13 };
 
 enum : int { TH_NVE = 0, TH_BERENDSEN = 1, TH_NH = 2, TH_NPT = 3 };
 
@@ -1521,7 +1521,13 @@ __global__ void k_load_positions(Dev d, const double* __restrict__ xin, const in
   unsigned long long p[3];
   int im[3];
   for (int k = 0; k < 3; ++k) {
-    double v = xin[3 * (size_t)u + k] / bx.L[k];  // box fraction
+    double v = xin[3 * (size_t)u + k];
+    if (!isfinite(v)) {  // reported to the host, which refuses the state; 0 keeps the arithmetic defined
+      set_status(d.g, ST_INPUT);
+      d.g->err_index = u;
+      v = 0.0;
+    }
+    v /= bx.L[k];  // box fraction
     const double fl = floor(v);
     im[k] = (int)fl;
     v -= fl;
@@ -1549,9 +1555,18 @@ __global__ void k_load_velocities(Dev d, const double* __restrict__ vin) {
   if (i >= d.N) return;
   const int u = d.id[i];
   if (vin) {
-    d.vx[i] = split_df(vin[3 * (size_t)u]);
-    d.vy[i] = split_df(vin[3 * (size_t)u + 1]);
-    d.vz[i] = split_df(vin[3 * (size_t)u + 2]);
+    double w[3];
+    for (int k = 0; k < 3; ++k) {
+      w[k] = vin[3 * (size_t)u + k];
+      if (!isfinite(w[k])) {
+        set_status(d.g, ST_INPUT);
+        d.g->err_index = u;
+        w[k] = 0.0;
+      }
+    }
+    d.vx[i] = split_df(w[0]);
+    d.vy[i] = split_df(w[1]);
+    d.vz[i] = split_df(w[2]);
   } else {
     d.vx[i] = d.vy[i] = d.vz[i] = make_float2(0.f, 0.f);
   }

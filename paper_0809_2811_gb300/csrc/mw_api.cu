@@ -617,23 +617,17 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   g.any_rebuild = 1;
   g.count_terms = s->count_terms;
   MW_CUDA(cudaMemcpyAsync(s->d.g, &g, sizeof(Global), cudaMemcpyHostToDevice, s->stream));
-  const int gb = div_up(s->N, kThreads);
-  k_load_positions<<<gb, kThreads, 0, s->stream>>>(s->d, xd, s->boxid, 1);
-  if (s->nsp > 1) k_gather_types<<<gb, kThreads, 0, s->stream>>>(s->d);
-  k_load_velocities<<<gb, kThreads, 0, s->stream>>>(s->d, vd);
-  k_ke_init<<<gb, kThreads, 0, s->stream>>>(s->d);
-  MW_CUDA(cudaMemsetAsync(s->d.f, 0, sizeof(float4) * s->N, s->stream));
-  // cell counts start from zero: a run that stopped on an error may have
-  // binned atoms without the scan that clears them
-  MW_CUDA(cudaMemsetAsync(s->d.cell_cnt, 0, sizeof(int) * s->ncell, s->stream));
+  // one pass over atoms and cells; the cell counts start from zero (a run
+  // that stopped on an error may have binned atoms without the scan that
+  // clears them)
+  k_load_state<<<div_up(std::max(s->N, s->ncell), kThreads), kThreads, 0, s->stream>>>(s->d, xd, vd, s->boxid);
   MW_CUDA(cudaGetLastError());
-  int bad[2];
-  MW_CUDA(cudaMemcpyAsync(bad, &s->d.g->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-  MW_CUDA(cudaMemcpyAsync(bad + 1, &s->d.g->err_index, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  Global gh;
+  MW_CUDA(cudaMemcpyAsync(&gh, s->d.g, sizeof(Global), cudaMemcpyDeviceToHost, s->stream));
   MW_CUDA(cudaStreamSynchronize(s->stream));
-  if (bad[0] == ST_INPUT) {
+  if (gh.status == ST_INPUT) {
     s->state_set = false;  // the arrays hold part of a refused state
-    return fail(MW_EINVAL, "non-finite position or velocity of atom %d", bad[1]);
+    return fail(MW_EINVAL, "non-finite position or velocity of atom %d", gh.err_index);
   }
   s->state_set = true;
   s->forces_valid = false;
@@ -1192,7 +1186,7 @@ mw_status mw_energy_forces_dev(mw_system* s, const double* x_dev, float* f_dev, 
     if (!s->state_set) return do_set_state(s, x_dev, nullptr, true) == MW_OK ? mw_energy_forces_dev(s, nullptr, f_dev, energy_dev, virial_dev) : MW_ECUDA;
     mw_status st;
     if ((st = flush_pending(s)) != MW_OK) return st;
-    k_load_positions<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, x_dev, s->boxid, 0);
+    k_load_positions<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, x_dev, s->boxid);
     MW_CUDA(cudaGetLastError());
     if ((st = flag_all(s)) != MW_OK) return st;
     s->forces_valid = false;

@@ -1508,13 +1508,12 @@ __global__ void k_record_at(Dev d, int pp) {
 // ---------------------------------------------------------------------------
 // Setup / IO kernels.
 
-// Positions from a user-order AoS array (host copy or device pointer) into the
-// sorted arrays: x[i] = xin[id[i]], wrapped into [0, L); q recomputed.
-__global__ void k_load_positions(Dev d, const double* __restrict__ xin, const int* __restrict__ boxid,
-                                 int identity) {
+// New positions for the current atom order (mw_energy_forces_dev): from a
+// user-order AoS device array into the sorted arrays, x[i] = xin[id[i]],
+// wrapped into [0, L); q recomputed.
+__global__ void k_load_positions(Dev d, const double* __restrict__ xin, const int* __restrict__ boxid) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
-  if (identity) d.id[i] = i;
   const int u = d.id[i];
   const int b = boxid[u];
   const Box& bx = d.box[b];
@@ -1550,38 +1549,57 @@ __global__ void k_requantize(Dev d, const int* __restrict__ boxid) {
   d.qb[i] = q;
 }
 
-__global__ void k_load_velocities(Dev d, const double* __restrict__ vin) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.N) return;
-  const int u = d.id[i];
-  if (vin) {
-    double w[3];
-    for (int k = 0; k < 3; ++k) {
-      w[k] = vin[3 * (size_t)u + k];
-      if (!isfinite(w[k])) {
-        set_status(d.g, ST_INPUT);
-        d.g->err_index = u;
-        w[k] = 0.0;
-      }
-    }
-    d.vx[i] = split_df(w[0]);
-    d.vy[i] = split_df(w[1]);
-    d.vz[i] = split_df(w[2]);
-  } else {
-    d.vx[i] = d.vy[i] = d.vz[i] = make_float2(0.f, 0.f);
-  }
-}
-
-// Kinetic energy per box straight into ke_last (zeroed by the host).
-__global__ void k_ke_init(Dev d) {
+// A new state in one pass (mw_set_state): atom i takes the caller's atom i
+// (identity order), its species, its velocity (zero when vin is null) and
+// zero force, and adds its kinetic energy to its box's ke_last (zeroed by
+// the host); the cell counts are cleared.  A non-finite value is replaced by
+// 0 and reported (ST_INPUT, the atom in err_index); the host refuses the state.
+__global__ void k_load_state(Dev d, const double* __restrict__ xin, const double* __restrict__ vin,
+                             const int* __restrict__ boxid) {
   const Integ I = *d.integ;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d.ncell) d.cell_cnt[i] = 0;
   float ke[1] = {0.f};
   int b = -1;
   if (i < d.N) {
-    b = (int)d.q[i].w;
-    const float vx = d.vx[i].x + d.vx[i].y, vy = d.vy[i].x + d.vy[i].y, vz = d.vz[i].x + d.vz[i].y;
-    ke[0] = (float)I.ke_fac * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+    d.id[i] = i;
+    b = boxid[i];
+    const Box& bx = d.box[b];
+    unsigned long long p[3];
+    int im[3];
+    float vh[3];
+    for (int k = 0; k < 3; ++k) {
+      double x = xin[3 * (size_t)i + k];
+      if (!isfinite(x)) {
+        set_status(d.g, ST_INPUT);
+        d.g->err_index = i;
+        x = 0.0;
+      }
+      double f = x / bx.L[k];  // box fraction
+      const double fl = floor(f);
+      im[k] = (int)fl;
+      f -= fl;
+      if (f >= 1.0) f -= 1.0;
+      if (f < 0.0) f = 0.0;
+      p[k] = frac64_of(f);
+      double w = vin ? vin[3 * (size_t)i + k] : 0.0;
+      if (!isfinite(w)) {
+        set_status(d.g, ST_INPUT);
+        d.g->err_index = i;
+        w = 0.0;
+      }
+      const float2 sw = split_df(w);
+      (k == 0 ? d.vx : (k == 1 ? d.vy : d.vz))[i] = sw;
+      vh[k] = sw.x + sw.y;
+    }
+    d.x[i] = p[0];
+    d.y[i] = p[1];
+    d.z[i] = p[2];
+    if (d.img) d.img[i] = make_int4(im[0], im[1], im[2], 0);
+    d.q[i] = make_uint4(q_of(p[0]), q_of(p[1]), q_of(p[2]), (unsigned)b);
+    if (d.typ) d.typ[i] = d.utyp[i];
+    d.f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    ke[0] = (float)I.ke_fac * fmaf(vh[0], vh[0], fmaf(vh[1], vh[1], vh[2] * vh[2]));
   }
   box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_last; });
 }

@@ -256,6 +256,24 @@ __device__ __forceinline__ int cell_of(const uint4& q, const Box& bx) {
 
 __device__ __forceinline__ void set_status(Global* g, int st) { atomicCAS(&g->status, 0, st); }
 
+// Arrival on a block counter, acq_rel at gpu scope: after a __syncthreads it
+// publishes the whole block's writes (the barrier orders them before thread
+// 0's release) and, for the last block to arrive, acquires every other
+// block's.  Returns the count including this arrival.
+__device__ __forceinline__ unsigned bar_arrive(unsigned* p) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+  return old + 1u;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Rebuilds are per box.  On a rebuild step every atom is binned and the scan
 // over all cells gives absolute cell starts (every box's counts add up to its
 // atom range), but only boxes whose flag kick1 raised (or that the host
@@ -1316,13 +1334,9 @@ __global__ void __launch_bounds__(kKThreads) k_kick1(Dev d, cudaGraphConditional
   if constexpr (kCond || kNpt) {
     __shared__ bool last;
     __syncthreads();
-    if (threadIdx.x == 0) {  // one fence per block after the barrier orders the block's writes
-      __threadfence();
-      last = (atomicAdd(&d.g->done1, 1u) == gridDim.x - 1);
-    }
+    if (threadIdx.x == 0) last = (bar_arrive(&d.g->done1) == gridDim.x);
     __syncthreads();
     if (last) {
-      __threadfence();
       if constexpr (kNpt)
         for (int b = threadIdx.x; b < d.nbox; b += blockDim.x) npt_commit_box(d, b);
       if (threadIdx.x == 0) {
@@ -1473,13 +1487,9 @@ __global__ void __launch_bounds__(kKThreads) k_kick2(Dev d) {
   box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_acc[par]; });
   __shared__ bool am_last;
   __syncthreads();
-  if (threadIdx.x == 0) {  // one fence per block after the barrier orders the block's writes
-    __threadfence();
-    am_last = (atomicAdd(&d.g->done, 1u) == gridDim.x - 1);
-  }
+  if (threadIdx.x == 0) am_last = (bar_arrive(&d.g->done) == gridDim.x);
   __syncthreads();
   if (am_last) {
-    __threadfence();
     for (int bb = threadIdx.x; bb < d.nbox; bb += blockDim.x) end_of_step_box<kNpt>(d, I, bb, par);
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -14,6 +14,10 @@
 namespace mw {
 
 constexpr int kPersThreads = kFThreads;
+// Co-resident blocks per SM the engine is compiled for (96 registers a
+// thread): 7 or 8 (72 or 64 registers) measured slower on the two-box
+// 32768-atom workload, and left to itself ptxas may take 128 (4 blocks).
+constexpr int kPersBlocksPerSm = 5;
 
 // Phase mark k of step s (block 0, thread 0; the SM clock): 0 step start,
 // 1 kick1 done, 2 its barrier passed, 3 rebuild done, 4 force done, 5 its
@@ -33,39 +37,49 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 
 // Grid barrier (one counter: a two-level counter tree measured slower on
-// GB300, where the fences and L2 round trips, ~3.3 us per barrier, dominate
-// rather than atomic contention).  gen is this block's count of barriers
-// passed (all blocks start from the same value).  Returns the status snapshot of the release
-// (identical in every block), or ST_TIMEOUT if this block gave up waiting.
+// GB300, where the L2 round trips, ~3 us per barrier, dominate rather than
+// atomic contention).  gen is this block's count of barriers passed (all
+// blocks start from the same value).  Returns the status snapshot of the
+// release (identical in every block), or ST_TIMEOUT if this block gave up
+// waiting.
+//
+// Memory order (PTX memory model, gpu scope, no fences): __syncthreads orders
+// every thread's writes of the phase before thread 0's arrival, an acq_rel
+// add on the counter; the last arrival thus acquires all blocks' writes and
+// publishes them again with a release store of the next generation, which
+// the waiters read with acquire loads; the closing __syncthreads hands that
+// order to the rest of each block.  In a barrier-only microbenchmark this
+// took ~0.45 us less per barrier than __threadfence around relaxed atomics.
+
+// The last arrival's release: reset the counter, snapshot the status, open
+// generation gen + 1.  Returns the snapshot.
+__device__ __forceinline__ int bar_release(Global* g, unsigned gen) {
+  g->bar_count = 0u;
+  const int st = *(volatile int*)&g->status;
+  g->bar_stat[gen & 1u] = st;
+  st_release(&g->bar_gen, gen + 1u);
+  return st;
+}
+
+// A waiter: spin (bounded by limit_ns of wall time; a limit of 0 gives up at
+// once) until generation gen is closed, then read its status snapshot.
+__device__ __forceinline__ int bar_wait(Global* g, unsigned gen, unsigned long long limit_ns) {
+  const unsigned long long t0 = globaltimer_ns();
+  while (ld_acquire(&g->bar_gen) == gen) {
+    if (globaltimer_ns() - t0 >= limit_ns) {
+      set_status(g, ST_TIMEOUT);
+      return ST_TIMEOUT;
+    }
+    __nanosleep(100);
+  }
+  return *(volatile int*)&g->bar_stat[gen & 1u];
+}
+
 __device__ int grid_barrier(Global* g, unsigned& gen, unsigned long long limit_ns) {
   __shared__ int s_status;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned arrived = atomicAdd(&g->bar_count, 1u) + 1u;
-    int st;
-    if (arrived == gridDim.x) {
-      g->bar_count = 0u;
-      g->bar_stat[gen & 1u] = *(volatile int*)&g->status;
-      __threadfence();
-      atomicExch(&g->bar_gen, gen + 1u);
-      st = g->bar_stat[gen & 1u];
-    } else {
-      const unsigned long long t0 = globaltimer_ns();
-      bool released = true;
-      while (*(volatile unsigned*)&g->bar_gen == gen) {
-        if (globaltimer_ns() - t0 >= limit_ns) {  // (a limit of 0 gives up at once)
-          set_status(g, ST_TIMEOUT);
-          released = false;
-          break;
-        }
-        __nanosleep(100);
-      }
-      __threadfence();
-      st = released ? *(volatile int*)&g->bar_stat[gen & 1u] : ST_TIMEOUT;
-    }
-    s_status = st;
-  }
+  if (threadIdx.x == 0)
+    s_status = (bar_arrive(&g->bar_count) == gridDim.x) ? bar_release(g, gen) : bar_wait(g, gen, limit_ns);
   __syncthreads();
   gen += 1u;
   return s_status;
@@ -73,42 +87,22 @@ __device__ int grid_barrier(Global* g, unsigned& gen, unsigned long long limit_n
 
 // Grid barrier whose last arriving block runs fn() (all its threads) before
 // the release, so that work that needs every block's results and that every
-// block needs next costs no barrier of its own.  Same bounded waits and
-// status snapshot as grid_barrier.
+// block needs next costs no barrier of its own.  Same bounded waits, status
+// snapshot and memory order as grid_barrier (fn's threads see the other
+// blocks' writes through thread 0's acquire and the __syncthreads after it).
 template <class Fn>
 __device__ int grid_barrier_last(Global* g, unsigned& gen, unsigned long long limit_ns, Fn fn) {
   __shared__ int s_status;
   __shared__ int s_last;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = (atomicAdd(&g->bar_count, 1u) + 1u == gridDim.x);
-  }
+  if (threadIdx.x == 0) s_last = (bar_arrive(&g->bar_count) == gridDim.x);
   __syncthreads();
   if (s_last) {
-    __threadfence();
     fn();
     __syncthreads();
-    if (threadIdx.x == 0) {
-      g->bar_count = 0u;
-      g->bar_stat[gen & 1u] = *(volatile int*)&g->status;
-      __threadfence();
-      atomicExch(&g->bar_gen, gen + 1u);
-      s_status = g->bar_stat[gen & 1u];
-    }
+    if (threadIdx.x == 0) s_status = bar_release(g, gen);
   } else if (threadIdx.x == 0) {
-    const unsigned long long t0 = globaltimer_ns();
-    bool released = true;
-    while (*(volatile unsigned*)&g->bar_gen == gen) {
-      if (globaltimer_ns() - t0 >= limit_ns) {
-        set_status(g, ST_TIMEOUT);
-        released = false;
-        break;
-      }
-      __nanosleep(100);
-    }
-    __threadfence();
-    s_status = released ? *(volatile int*)&g->bar_stat[gen & 1u] : ST_TIMEOUT;
+    s_status = bar_wait(g, gen, limit_ns);
   }
   __syncthreads();
   gen += 1u;
@@ -117,17 +111,14 @@ __device__ int grid_barrier_last(Global* g, unsigned& gen, unsigned long long li
 
 // The end of a launch: the last block to arrive runs fn() and resets the
 // arrival count; the others return without waiting (no wait, so no limit).
+// The launch's end publishes fn's writes to whatever runs next on the stream.
 template <class Fn>
 __device__ void end_arrive_last(Global* g, Fn fn) {
   __shared__ int s_last;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = (atomicAdd(&g->bar_count, 1u) + 1u == gridDim.x);
-  }
+  if (threadIdx.x == 0) s_last = (bar_arrive(&g->bar_count) == gridDim.x);
   __syncthreads();
   if (s_last) {
-    __threadfence();
     fn();
     __syncthreads();
     if (threadIdx.x == 0) g->bar_count = 0u;
@@ -191,7 +182,7 @@ __device__ void scan_chunk_offsets(const Dev& d) {
 }
 
 template <bool kCount, bool kNpt = false>
-__global__ void __launch_bounds__(kPersThreads) k_persistent(Dev d, FParams P, int nsteps, unsigned long long wait_ns) {
+__global__ void __launch_bounds__(kPersThreads, kPersBlocksPerSm) k_persistent(Dev d, FParams P, int nsteps, unsigned long long wait_ns) {
   __shared__ LegTable T;
   __shared__ unsigned s_gen;
   Global* g = d.g;

@@ -810,11 +810,13 @@ __device__ void neigh_cell_warp(const Dev& d, const uint4* qa, int c, float rl2)
         if (lane == k) mycount += __popc(bal);
       }
     }
-    if (lane < nb) {
-      const int i = a0 + ib + lane;
-      d.nbr_cnt[i] = mycount;
-      atomicMax(&d.g->max_count, mycount);
-      if (mycount > d.W) set_status(d.g, ST_OVERFLOW);
+    if (lane < nb) d.nbr_cnt[a0 + ib + lane] = mycount;
+    // the longest row: one atomic per warp, and none once the running maximum
+    // covers it (rather than one per centre on this one word)
+    const int wmax = __reduce_max_sync(kFull, lane < nb ? mycount : 0);
+    if (lane == 0 && wmax > *(volatile int*)&d.g->max_count) {
+      atomicMax(&d.g->max_count, wmax);
+      if (wmax > d.W) set_status(d.g, ST_OVERFLOW);
     }
   }
 }

@@ -103,6 +103,15 @@ struct mw_system {
   unsigned long long wait_ns = kBarrierTimeoutNs;  // limit of each device-side wait
   std::vector<int> cell_box_host;
   std::vector<void*> allocs;
+  // pinned host staging for the small device-to-host reads (the Global
+  // status block, then nbox thermo records), so that they need no staging copy
+  void* hpin = nullptr;
+  Global* gpin() { return static_cast<Global*>(hpin); }
+  double* thpin() { return reinterpret_cast<double*>(static_cast<char*>(hpin) + kPinThermoOff); }
+  static constexpr size_t kPinThermoOff = (sizeof(Global) + 63) / 64 * 64;
+  // the status block as ensure_forces last read it, when nothing has run since
+  bool g_known_valid = false;
+  Global g_known{};
 };
 
 namespace {
@@ -117,7 +126,7 @@ struct Range {
 // defined in mw_persistent_host.inc / mw_adjoint_host.inc
 mw_status persistent_func_attrs();
 bool persistent_available(mw_system* s);
-mw_status run_persistent_engine(mw_system* s, int nsteps);
+mw_status run_persistent_engine(mw_system* s, int nsteps, mw_thermo* last, bool* fetched);
 mw_status enqueue_persistent(mw_system* s, int nsteps);
 mw_status adjoint_alloc(mw_system* s);
 mw_status prime_thermostat(mw_system* s);
@@ -301,8 +310,64 @@ mw_status flag_all(mw_system* s) {
 }
 
 mw_status read_global(mw_system* s, Global* g) {
-  MW_CUDA(cudaMemcpyAsync(g, s->d.g, sizeof(Global), cudaMemcpyDeviceToHost, s->stream));
+  MW_CUDA(cudaMemcpyAsync(s->gpin(), s->d.g, sizeof(Global), cudaMemcpyDeviceToHost, s->stream));
   MW_CUDA(cudaStreamSynchronize(s->stream));
+  *g = *s->gpin();
+  return MW_OK;
+}
+
+// The last step's thermo records (written on demand by k_record) copied to
+// the pinned staging; complete after the next synchronisation of the stream.
+mw_status enqueue_thermo(mw_system* s) {
+  if (s->record_pending) {
+    k_record<<<1, 256, 0, s->stream>>>(s->d);
+    MW_CUDA(cudaGetLastError());
+    s->record_pending = false;
+  }
+  MW_CUDA(cudaMemcpyAsync(s->thpin(), s->d.thermo, sizeof(double) * (size_t)s->nbox * TR_N,
+                          cudaMemcpyDeviceToHost, s->stream));
+  return MW_OK;
+}
+
+// The staged records as mw_thermo, one per box.
+void unpack_thermo(mw_system* s, mw_thermo* out) {
+  const double* t = s->thpin();
+  for (int b = 0; b < s->nbox; ++b) {
+    const double* r = t + (size_t)b * TR_N;
+    mw_thermo& o = out[b];
+    o.step = (int64_t)r[TR_STEP];
+    o.pe = r[TR_PE];
+    o.e2 = r[TR_E2];
+    o.e3 = r[TR_E3];
+    o.ke = r[TR_KE];
+    o.temperature = r[TR_T];
+    o.conserved = r[TR_CONS];
+    o.pressure = r[TR_P];
+    for (int k = 0; k < 6; ++k) o.virial[k] = r[TR_W0 + k];
+    o.xi = r[TR_XI];
+    o.eta = r[TR_ETA];
+    o.rebuilds = (int64_t)r[TR_REBUILDS];
+    o.volume = r[TR_VOL];
+    for (int k = 0; k < 3; ++k) o.box[k] = r[TR_L0 + k];
+  }
+}
+
+// After a run's launches: when the caller wants the last record and this
+// launch finishes the run, the record is fetched with the status block, in
+// one round trip.  *fetched tells whether out holds the run's last record.
+mw_status read_global_and_thermo(mw_system* s, Global* g, mw_thermo* out, bool fetch, bool* fetched,
+                                 int remaining, unsigned long long step0) {
+  mw_status st;
+  if (fetch && (st = enqueue_thermo(s)) != MW_OK) return st;
+  if ((st = read_global(s, g)) != MW_OK) return st;
+  if (fetch) {
+    if (g->status == ST_OK && (long long)(g->step - step0) == remaining) {
+      unpack_thermo(s, out);
+      *fetched = true;
+    } else {
+      s->record_pending = true;  // the run goes on: the staged record is not its last
+    }
+  }
   return MW_OK;
 }
 
@@ -463,6 +528,8 @@ mw_status ensure_forces(mw_system* s) {
     s->forces_valid = true;
     s->list_built = true;
     s->record_pending = false;  // the snapshot is the newest record
+    s->g_known = g;
+    s->g_known_valid = true;
     return MW_OK;
   }
   return fail(MW_ENLIST_OVERFLOW, "neighbour list kept overflowing");
@@ -536,7 +603,7 @@ mw_status prime_thermostat(mw_system* s) {
   return MW_OK;
 }
 
-mw_status run_graph_engine(mw_system* s, int nsteps) {
+mw_status run_graph_engine(mw_system* s, int nsteps, mw_thermo* last, bool* fetched) {
   mw_status st;
   if ((st = prime_thermostat(s)) != MW_OK) return st;
   s->record_pending = true;
@@ -549,7 +616,12 @@ mw_status run_graph_engine(mw_system* s, int nsteps) {
   int regrid_guard = 0;
   while (remaining > 0) {
     Global g0;
-    if ((st = read_global(s, &g0)) != MW_OK) return st;
+    if (s->g_known_valid) {  // read by ensure_forces just before, nothing run since
+      g0 = s->g_known;
+      s->g_known_valid = false;
+    } else if ((st = read_global(s, &g0)) != MW_OK) {
+      return st;
+    }
     if (g0.status == ST_GRID) {
       if (++regrid_guard > 8) return fail(MW_EGRID, "cell grid of an isobaric box kept failing");
       if ((st = regrid(s)) != MW_OK) return st;
@@ -561,7 +633,7 @@ mw_status run_graph_engine(mw_system* s, int nsteps) {
     for (int k = 0; k < full; ++k) MW_CUDA(cudaGraphLaunch(s->graphK, s->stream));
     for (int k = 0; k < rest; ++k) MW_CUDA(cudaGraphLaunch(s->graph1, s->stream));
     Global g;
-    if ((st = read_global(s, &g)) != MW_OK) return st;
+    if ((st = read_global_and_thermo(s, &g, last, last != nullptr, fetched, remaining, step0)) != MW_OK) return st;
     const int done = (int)(g.step - step0);
     s->host_step += done;
     if (g.status == ST_OVERFLOW) {
@@ -605,26 +677,19 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
       vd = s->d.stage2;
     }
   }
-  // reset thermostat / accumulators / counters
-  std::vector<BoxState> bs(s->nbox);
-  for (auto& b : bs) {
-    std::memset(&b, 0, sizeof b);
-    b.s_endc = 1.0;
-    b.rebuild = 1;
-  }
-  MW_CUDA(cudaMemcpyAsync(s->d.bst, bs.data(), sizeof(BoxState) * s->nbox, cudaMemcpyHostToDevice, s->stream));
-  Global g{};
-  g.any_rebuild = 1;
-  g.count_terms = s->count_terms;
-  MW_CUDA(cudaMemcpyAsync(s->d.g, &g, sizeof(Global), cudaMemcpyHostToDevice, s->stream));
+  // reset thermostat / accumulators / counters: zeroed here, the non-zero
+  // starting values set by k_load_state
+  MW_CUDA(cudaMemsetAsync(s->d.bst, 0, sizeof(BoxState) * s->nbox, s->stream));
+  MW_CUDA(cudaMemsetAsync(s->d.g, 0, sizeof(Global), s->stream));
   // one pass over atoms and cells; the cell counts start from zero (a run
   // that stopped on an error may have binned atoms without the scan that
   // clears them)
-  k_load_state<<<div_up(std::max(s->N, s->ncell), kThreads), kThreads, 0, s->stream>>>(s->d, xd, vd, s->boxid);
+  k_load_state<<<div_up(std::max(std::max(s->N, s->ncell), s->nbox), kThreads), kThreads, 0, s->stream>>>(
+      s->d, xd, vd, s->boxid, s->count_terms);
   MW_CUDA(cudaGetLastError());
   Global gh;
-  MW_CUDA(cudaMemcpyAsync(&gh, s->d.g, sizeof(Global), cudaMemcpyDeviceToHost, s->stream));
-  MW_CUDA(cudaStreamSynchronize(s->stream));
+  mw_status st;
+  if ((st = read_global(s, &gh)) != MW_OK) return st;
   if (gh.status == ST_INPUT) {
     s->state_set = false;  // the arrays hold part of a refused state
     return fail(MW_EINVAL, "non-finite position or velocity of atom %d", gh.err_index);
@@ -738,6 +803,14 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
   }
   if (total > (1ll << 28)) return fail(MW_EINVAL, "too many atoms (%lld)", total);
   mw_system* s = new mw_system();
+  {
+    const size_t pin = mw_system::kPinThermoOff + sizeof(double) * (size_t)nbox * TR_N;
+    cudaError_t e = cudaMallocHost(&s->hpin, pin);
+    if (e != cudaSuccess) {
+      delete s;
+      return fail(MW_ENOMEM, "cudaMallocHost of %zu bytes failed: %s", pin, cudaGetErrorString(e));
+    }
+  }
   s->nbox = nbox;
   s->N = (int)total;
   s->prm = *prm;
@@ -747,6 +820,7 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
   if (!s->stream) {
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+      cudaFreeHost(s->hpin);
       delete s;
       return fail(MW_ECUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(e));
     }
@@ -754,6 +828,7 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
   }
   if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     if (s->own_stream) cudaStreamDestroy(s->stream);
+    cudaFreeHost(s->hpin);
     delete s;
     return fail(MW_ECUDA, "cudaStreamCreate failed");
   }
@@ -787,6 +862,7 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
   if ((st = layout_cells(s, &s->ncell)) != MW_OK) {
     if (s->own_stream) cudaStreamDestroy(s->stream);
     cudaStreamDestroy(s->cap_stream);
+    cudaFreeHost(s->hpin);
     delete s;
     return st;
   }
@@ -903,6 +979,7 @@ mw_status mw_system_destroy(mw_system* s) {
   for (void* p : s->allocs) cudaFree(p);
   if (s->own_stream) cudaStreamDestroy(s->stream);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->hpin) cudaFreeHost(s->hpin);
   delete s;
   return MW_OK;
 }
@@ -1217,20 +1294,24 @@ mw_status mw_step(mw_system* s, const mw_integrator* integ, int nsteps, mw_therm
   if (nsteps < 0) return fail(MW_EINVAL, "nsteps < 0");
   mw_status st;
   if ((st = validate_integ(s, integ)) != MW_OK) return st;
+  s->g_known_valid = false;  // set again only if ensure_forces reads the status block now
   if ((st = ensure_forces(s)) != MW_OK) return st;
+  bool fetched = false;  // the run's last record came back with its final status read
   if (nsteps > 0) {
     int eng = s->engine;
     if (eng == MW_ENGINE_AUTO) eng = s->tuned_engine >= 0 ? s->tuned_engine : MW_ENGINE_PERSISTENT;
     if (eng == MW_ENGINE_PERSISTENT && !persistent_available(s)) eng = MW_ENGINE_GRAPH;
     s->engine_used = eng;
-    st = eng == MW_ENGINE_PERSISTENT ? run_persistent_engine(s, nsteps) : run_graph_engine(s, nsteps);
+    st = eng == MW_ENGINE_PERSISTENT ? run_persistent_engine(s, nsteps, last, &fetched)
+                                     : run_graph_engine(s, nsteps, last, &fetched);
+    s->g_known_valid = false;
     if (st != MW_OK) {
       s->forces_valid = false;  // the state of an interrupted step is not a state to report forces of
       return st;
     }
     s->list_built = true;
   }
-  if (last) return mw_get_thermo(s, last);
+  if (last && !fetched) return mw_get_thermo(s, last);
   return MW_OK;
 }
 
@@ -1275,32 +1356,9 @@ mw_status mw_get_thermo(mw_system* s, mw_thermo* out) {
   if (!s->state_set) return fail(MW_ESTATE, "no state set");
   mw_status st;
   if ((st = ensure_forces(s)) != MW_OK) return st;
-  if (s->record_pending) {  // the last step's record, written on demand
-    k_record<<<1, 256, 0, s->stream>>>(s->d);
-    MW_CUDA(cudaGetLastError());
-    s->record_pending = false;
-  }
-  std::vector<double> t((size_t)s->nbox * TR_N);
-  MW_CUDA(cudaMemcpyAsync(t.data(), s->d.thermo, sizeof(double) * t.size(), cudaMemcpyDeviceToHost, s->stream));
+  if ((st = enqueue_thermo(s)) != MW_OK) return st;
   MW_CUDA(cudaStreamSynchronize(s->stream));
-  for (int b = 0; b < s->nbox; ++b) {
-    const double* r = t.data() + (size_t)b * TR_N;
-    mw_thermo& o = out[b];
-    o.step = (int64_t)r[TR_STEP];
-    o.pe = r[TR_PE];
-    o.e2 = r[TR_E2];
-    o.e3 = r[TR_E3];
-    o.ke = r[TR_KE];
-    o.temperature = r[TR_T];
-    o.conserved = r[TR_CONS];
-    o.pressure = r[TR_P];
-    for (int k = 0; k < 6; ++k) o.virial[k] = r[TR_W0 + k];
-    o.xi = r[TR_XI];
-    o.eta = r[TR_ETA];
-    o.rebuilds = (int64_t)r[TR_REBUILDS];
-    o.volume = r[TR_VOL];
-    for (int k = 0; k < 3; ++k) o.box[k] = r[TR_L0 + k];
-  }
+  unpack_thermo(s, out);
   return MW_OK;
 }
 

@@ -1563,14 +1563,25 @@ __global__ void k_requantize(Dev d, const int* __restrict__ boxid) {
 
 // A new state in one pass (mw_set_state): atom i takes the caller's atom i
 // (identity order), its species, its velocity (zero when vin is null) and
-// zero force, and adds its kinetic energy to its box's ke_last (zeroed by
-// the host); the cell counts are cleared.  A non-finite value is replaced by
-// 0 and reported (ST_INPUT, the atom in err_index); the host refuses the state.
+// zero force, and adds its kinetic energy to its box's ke_last; the cell
+// counts are cleared.  The host zeroes the box states and the status block
+// before the launch; here each box is marked for a rebuild with no pending
+// end scale, and the status block gets the rebuild flag and count_terms.  A
+// non-finite value is replaced by 0 and reported (ST_INPUT, the atom in
+// err_index); the host refuses the state.
 __global__ void k_load_state(Dev d, const double* __restrict__ xin, const double* __restrict__ vin,
-                             const int* __restrict__ boxid) {
+                             const int* __restrict__ boxid, int count_terms) {
   const Integ I = *d.integ;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < d.ncell) d.cell_cnt[i] = 0;
+  if (i < d.nbox) {
+    d.bst[i].s_endc = 1.0;
+    d.bst[i].rebuild = 1;
+  }
+  if (i == 0) {
+    d.g->any_rebuild = 1;
+    d.g->count_terms = count_terms;
+  }
   float ke[1] = {0.f};
   int b = -1;
   if (i < d.N) {

@@ -290,7 +290,10 @@ void destroy_graphs(mw_system* s) {
 }
 
 mw_status set_global_field(mw_system* s, size_t offset, int value) {
-  MW_CUDA(cudaMemcpyAsync((char*)s->d.g + offset, &value, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+  if (value == 0)  // a device-side memset: no host staging of a pageable source
+    MW_CUDA(cudaMemsetAsync((char*)s->d.g + offset, 0, sizeof(int), s->stream));
+  else
+    MW_CUDA(cudaMemcpyAsync((char*)s->d.g + offset, &value, sizeof(int), cudaMemcpyHostToDevice, s->stream));
   return MW_OK;
 }
 

@@ -157,7 +157,10 @@ mw_status mw_system_destroy(mw_system* s);
  * arrays.  Resets the step counter, the thermostat (xi = eta = 0) and marks
  * the neighbour list stale.  A non-finite value (checked on the device, for
  * host and device inputs alike) gives MW_EINVAL and leaves the system
- * without a state. */
+ * without a state.  Page-locked host arrays (cudaMallocHost, cudaHostAlloc,
+ * cudaHostRegister) are read in place by the loading kernel; pageable ones
+ * are first copied to a device staging buffer.  Either way the arrays are
+ * read completely before the call returns, and the caller keeps them. */
 mw_status mw_set_state(mw_system* s, const double* x, const double* v);
 /* Same with device arrays. */
 mw_status mw_set_state_dev(mw_system* s, const double* x_dev, const double* v_dev);

@@ -666,6 +666,19 @@ mw_status run_graph_engine(mw_system* s, int nsteps, mw_thermo* last, bool* fetc
   return MW_OK;
 }
 
+// The device-side address of page-locked host memory (cudaMallocHost,
+// cudaHostAlloc, cudaHostRegister), through which kernels read it in place;
+// null for pageable memory.
+const double* mapped_host(const double* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of an unknown pointer
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return static_cast<const double*>(a.devicePointer);
+}
+
 mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev) {
   if (!s) return fail(MW_EINVAL, "system is NULL");
   if (!x) return fail(MW_EINVAL, "positions are NULL");
@@ -673,11 +686,23 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   const double* xd = x;
   const double* vd = v;
   if (!dev) {  // (finiteness is checked on the device, as for device inputs)
-    MW_CUDA(cudaMemcpyAsync(s->d.stage, x, bytes, cudaMemcpyHostToDevice, s->stream));
-    xd = s->d.stage;
+    // pinned (page-locked) host arrays are read by k_load_state in place,
+    // through their device mapping; pageable ones are copied to staging first
+    const double* xm = mapped_host(x);
+    if (xm) {
+      xd = xm;
+    } else {
+      MW_CUDA(cudaMemcpyAsync(s->d.stage, x, bytes, cudaMemcpyHostToDevice, s->stream));
+      xd = s->d.stage;
+    }
     if (v) {
-      MW_CUDA(cudaMemcpyAsync(s->d.stage2, v, bytes, cudaMemcpyHostToDevice, s->stream));
-      vd = s->d.stage2;
+      const double* vm = mapped_host(v);
+      if (vm) {
+        vd = vm;
+      } else {
+        MW_CUDA(cudaMemcpyAsync(s->d.stage2, v, bytes, cudaMemcpyHostToDevice, s->stream));
+        vd = s->d.stage2;
+      }
     }
   }
   // reset thermostat / accumulators / counters: zeroed here, the non-zero

@@ -742,10 +742,96 @@ __device__ __forceinline__ float kick2_lane(const Dev& d, const Integ& I, int w,
 // Neighbour list (a3): one warp per cell.  The candidates of the
 // (deduplicated) 27-cell stencil are flattened over the lanes, each lane
 // loading one candidate per chunk of 32; the chunk is then tested against
-// every centre atom of the cell (up to 32 at a time) and the hits of each
-// centre are compacted into its row with ballot + popc.
+// every centre atom of the cell (up to 32 at a time), each centre's lane
+// keeps its ballot, and the centres append their hits to their rows.
 __device__ __forceinline__ int stencil_n(int nc) { return nc >= 3 ? 3 : nc; }
 __device__ __forceinline__ int stencil_off(int nc, int o) { return nc >= 3 ? o - 1 : o; }
+
+// The rows of one cell's centres (neigh_cell_warp).  Lane t of a batch holds
+// candidate t of the stencil's concatenated cells (located by a binary search
+// over the warp's inclusive counts).  Each centre k in turn tests the batch,
+// and lane k keeps the ballot: its centre's hit mask.  Then every lane appends
+// its centre's hits in candidate order (lowest bit first), so each row lists
+// its neighbours in stencil order as a per-hit prefix count would, with no
+// per-centre bookkeeping in the test loop.
+// kFrame: every axis of the box has at least 4 cells, so each candidate lies
+// within two cell edges of o, the cell's first atom; offsets from o are exact
+// fixed-point differences with no wrap, converted once per atom, and a pair's
+// displacement is their FP32 difference.  Otherwise (grids of 1-3 cells on an
+// axis, where the stencil wraps round the box) each pair takes its own
+// minimum-image fixed-point difference.
+template <bool kFrame>
+__device__ __forceinline__ void neigh_rows(const Dev& d, const uint4* qa, int a0, int ni, int incl, int start,
+                                           int excl, int total, float L0, float L1, float L2, float rl2) {
+  const int lane = threadIdx.x & 31;
+  const uint4 o = qa[a0];
+  for (int ib = 0; ib < ni; ib += 32) {  // centre atoms of this cell, 32 at a time
+    const int nb = min(32, ni - ib);
+    const int me = a0 + ib + min(lane, nb - 1);  // lane k's centre
+    const uint4 qmine = qa[me];
+    float cx, cy, cz;  // its offset from o (kFrame) or its fixed-point position
+    if constexpr (kFrame) {
+      cx = fix_diff(o.x, qmine.x, L0); cy = fix_diff(o.y, qmine.y, L1); cz = fix_diff(o.z, qmine.z, L2);
+    } else {
+      cx = __uint_as_float(qmine.x); cy = __uint_as_float(qmine.y); cz = __uint_as_float(qmine.z);
+    }
+    int* const row = d.nbr + (size_t)me * d.W;
+    int mycount = 0;  // neighbours of lane k's centre so far
+    for (int base = 0; base < total; base += 32) {
+      const int t = base + lane;
+      int lo = 0, hi = 31;
+#pragma unroll
+      for (int it = 0; it < 5; ++it) {  // smallest lane k with incl_k > t
+        const int mid = (lo + hi) >> 1;
+        const int v = __shfl_sync(kFull, incl, mid);
+        if (v > t) hi = mid; else lo = mid + 1;
+      }
+      const int sk = __shfl_sync(kFull, start, lo);
+      const int ek = __shfl_sync(kFull, excl, lo);
+      const bool have = t < total;
+      const int j = have ? sk + (t - ek) : -1;
+      const uint4 qj = have ? qa[j] : make_uint4(0u, 0u, 0u, 0u);
+      float jx = 0.f, jy = 0.f, jz = 0.f;
+      if constexpr (kFrame) {
+        jx = fix_diff(o.x, qj.x, L0); jy = fix_diff(o.y, qj.y, L1); jz = fix_diff(o.z, qj.z, L2);
+      }
+      unsigned mine = 0u;  // lane k: which candidates of this batch are centre k's neighbours
+      for (int k = 0; k < nb; ++k) {
+        const float xk = __shfl_sync(kFull, cx, k), yk = __shfl_sync(kFull, cy, k), zk = __shfl_sync(kFull, cz, k);
+        float dx, dy, dz;
+        if constexpr (kFrame) {
+          dx = jx - xk; dy = jy - yk; dz = jz - zk;
+        } else {
+          dx = fix_diff(__float_as_uint(xk), qj.x, L0);
+          dy = fix_diff(__float_as_uint(yk), qj.y, L1);
+          dz = fix_diff(__float_as_uint(zk), qj.z, L2);
+        }
+        const bool pred = have && j != a0 + ib + k && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
+        const unsigned bal = __ballot_sync(kFull, pred);
+        if (lane == k) mine = bal;
+      }
+      // append: as many rounds as the centre with the most hits in this batch
+      const int rounds = __reduce_max_sync(kFull, __popc(mine));
+      for (int h = 0; h < rounds; ++h) {
+        const int src = mine ? __ffs(mine) - 1 : 0;
+        const int jj = __shfl_sync(kFull, j, src);
+        if (mine) {
+          if (mycount < d.W) row[mycount] = jj;
+          ++mycount;
+          mine &= mine - 1u;
+        }
+      }
+    }
+    if (lane < nb) d.nbr_cnt[me] = mycount;
+    // the longest row: one atomic per warp, and none once the running maximum
+    // covers it (rather than one per centre on this one word)
+    const int wmax = __reduce_max_sync(kFull, lane < nb ? mycount : 0);
+    if (lane == 0 && wmax > *(volatile int*)&d.g->max_count) {
+      atomicMax(&d.g->max_count, wmax);
+      if (wmax > d.W) set_status(d.g, ST_OVERFLOW);
+    }
+  }
+}
 
 __device__ void neigh_cell_warp(const Dev& d, const uint4* qa, int c, float rl2) {
   const int lane = threadIdx.x & 31;
@@ -775,50 +861,10 @@ __device__ void neigh_cell_warp(const Dev& d, const uint4* qa, int c, float rl2)
   const int excl = incl - cnt;
   const int total = __shfl_sync(kFull, incl, 31);
   const float L0 = bx.Lq[0], L1 = bx.Lq[1], L2 = bx.Lq[2];
-  const unsigned lt = (1u << lane) - 1u;
-  for (int ib = 0; ib < ni; ib += 32) {  // centre atoms of this cell, 32 at a time
-    const int nb = min(32, ni - ib);
-    const uint4 qmine = qa[a0 + ib + min(lane, nb - 1)];
-    int mycount = 0;  // lane k counts the neighbours of centre ib + k
-    for (int base = 0; base < total; base += 32) {
-      const int t = base + lane;
-      int lo = 0, hi = 31;
-#pragma unroll
-      for (int it = 0; it < 5; ++it) {  // smallest lane k with incl_k > t
-        const int mid = (lo + hi) >> 1;
-        const int v = __shfl_sync(kFull, incl, mid);
-        if (v > t) hi = mid; else lo = mid + 1;
-      }
-      const int sk = __shfl_sync(kFull, start, lo);
-      const int ek = __shfl_sync(kFull, excl, lo);
-      const bool have = t < total;
-      const int j = have ? sk + (t - ek) : -1;
-      const uint4 qj = have ? qa[j] : make_uint4(0u, 0u, 0u, 0u);
-      for (int k = 0; k < nb; ++k) {
-        const int i = a0 + ib + k;
-        const unsigned qx = __shfl_sync(kFull, qmine.x, k), qy = __shfl_sync(kFull, qmine.y, k),
-                       qz = __shfl_sync(kFull, qmine.z, k);
-        bool pred = false;
-        if (have && j != i) {
-          const float dx = fix_diff(qx, qj.x, L0), dy = fix_diff(qy, qj.y, L1), dz = fix_diff(qz, qj.z, L2);
-          pred = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
-        }
-        const unsigned bal = __ballot_sync(kFull, pred);
-        const int m = __shfl_sync(kFull, mycount, k);
-        const int pos = m + __popc(bal & lt);
-        if (pred && pos < d.W) d.nbr[(size_t)i * d.W + pos] = j;
-        if (lane == k) mycount += __popc(bal);
-      }
-    }
-    if (lane < nb) d.nbr_cnt[a0 + ib + lane] = mycount;
-    // the longest row: one atomic per warp, and none once the running maximum
-    // covers it (rather than one per centre on this one word)
-    const int wmax = __reduce_max_sync(kFull, lane < nb ? mycount : 0);
-    if (lane == 0 && wmax > *(volatile int*)&d.g->max_count) {
-      atomicMax(&d.g->max_count, wmax);
-      if (wmax > d.W) set_status(d.g, ST_OVERFLOW);
-    }
-  }
+  if (bx.nc[0] >= 4 && bx.nc[1] >= 4 && bx.nc[2] >= 4)
+    neigh_rows<true>(d, qa, a0, ni, incl, start, excl, total, L0, L1, L2, rl2);
+  else
+    neigh_rows<false>(d, qa, a0, ni, incl, start, excl, total, L0, L1, L2, rl2);
 }
 
 // ---------------------------------------------------------------------------

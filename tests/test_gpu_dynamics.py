@@ -316,3 +316,31 @@ def test_run_logs_a_thermo_line_every_k_steps(mwlib):
     assert steps == [0, 100, 200, 250]
     assert th[0]["step"] == 250
     assert float(lines[-1].split()[6]) == pytest.approx(th[0]["conserved"], abs=1e-4)
+
+
+@pytest.mark.parametrize("engine", sorted(ENGINES))
+def test_step_record_is_the_thermo_record(mwlib, engine):
+    """mw_step's returned records (fetched with the run's final status read)
+    are the records mw_get_thermo reads afterwards, to the bit, after a plain
+    run, after a run through a list overflow (the record fetched with an
+    interrupted launch is discarded) and after a run that starts with the
+    force prime of a new state."""
+    x, v, box = I.nve512()
+    x = I.snap_to_grid(x, box)
+    s = mwlib.System(512, box)
+    try:
+        s.set_engine(ENGINES[engine])
+        s.set_state(x, v)
+        kw = dict(dt=10.0, thermostat=mwlib.MW_NOSE_HOOVER, T0=298.0, tau=500.0)
+        for n, width in ((7, None), (9, 6), (4, None)):
+            if width is not None:
+                mwlib.mw_set_nbr_width(s.h, width)
+            th = s.step(n, **kw)
+            assert th == s.thermo()
+        total = th[0]["step"]
+        assert total == 20
+        s.set_state(x, v)
+        th = s.step(3, **kw)
+        assert th[0]["step"] == 3 and th == s.thermo()
+    finally:
+        s.close()

@@ -138,22 +138,28 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            p = [t.strip() for t in ln.split(",")]
-            if len(p) < 7:
-                continue
-            try:
-                sm.append(float(p[0]))
-                mx.append(float(p[1]))
-            except ValueError:
-                continue
-            for k, nm in enumerate(names):
-                if p[3 + k].lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return clock_summary(self.lines)
+
+
+def clock_summary(lines):
+    """Median SM clock, maximum clock and the throttle reasons seen in
+    nvidia-smi CSV lines of ClockSampler.Q (no header, no units)."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        p = [t.strip() for t in ln.split(",")]
+        if len(p) < 7:
+            continue
+        try:
+            sm.append(float(p[0]))
+            mx.append(float(p[1]))
+        except ValueError:
+            continue
+        for k, nm in enumerate(names):
+            if p[3 + k].lower().startswith("active"):
+                reasons.add(nm)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def dist_setup(args):

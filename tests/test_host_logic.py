@@ -21,3 +21,37 @@ def test_thermo_line_is_lammps_style():
         pos = line.index(v, pos) + len(v)
         ends_v.append(pos)
     assert ends_h == ends_v
+
+
+def test_clock_summary_reads_throttle_reasons():
+    """The bench's clock record: median SM clock, the highest maximum, and
+    every throttle reason seen Active in any sample (nvidia-smi CSV lines of
+    clocks.sm, clocks.max.sm, power.draw and four reasons)."""
+    import bench
+    lines = ["2070, 2070, 700.5, Not Active, Not Active, Not Active, Not Active",
+             "1980, 2070, 1390.0, Not Active, Not Active, Not Active, Active",
+             "2070, 2070, 900.1, Not Active, Not Active, Not Active, Not Active",
+             "garbage line", "[N/A], [N/A], [N/A], x, x, x, x"]
+    c = bench.clock_summary(lines)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c = bench.clock_summary(["1500, 2070, 500, Active, Not Active, Active, Not Active"])
+    assert c["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and c["sm_mhz"] == 1500.0
+    assert bench.clock_summary([])["sm_mhz"] is None
+
+
+def test_traffic_is_reported_only_for_the_profiled_source(tmp_path, monkeypatch):
+    """DRAM traffic comes from the committed ncu record only while the kernel
+    source hashes to the recorded value; any edit of the source gives null."""
+    import hashlib
+    import json
+    import bench
+    src = tmp_path / "k.cuh"
+    src.write_text("// kernel v1\n")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (prof / "sw_force_traffic.json").write_text(json.dumps({"source_hash": h, "dram_bytes_per_launch_scaled": 123}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_from_profile(str(src)) == 123
+    src.write_text("// kernel v2\n")
+    assert bench.traffic_from_profile(str(src)) is None

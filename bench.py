@@ -1,21 +1,26 @@
 #!/usr/bin/env python3
 """Throughput of the mW MD step (force + integrate) on GB300, one JSON line.
 
-Default workload: 32768-atom ice Ih (0.92 g/cm^3) and a 32768-atom liquid box
-(0.9998 g/cm^3, melted from the same lattice), advanced together as a
-two-box batch, Nose-Hoover 240 K (tau 1 ps), dt = 10 fs.  A bench step is one
-MD step of both boxes: kick + drift + fixed-point copy + rebuild check (and
-cell binning / neighbour list when due) + fused 2+3-body force + kick +
+Default workload (the largest single-GPU configuration): 2^20 atoms, an ice
+Ih slab of 524288 atoms (64 x 32 x 32 orthorhombic cells at 0.92 g/cm^3) in
+contact along z with a 524288-atom liquid-start slab at 0.9998 g/cm^3,
+Nose-Hoover 250 K (tau 1 ps), dt = 10 fs.  A bench step is one MD step of
+the whole box: kick + drift + fixed-point copy + rebuild check (and cell
+binning / neighbour list when due) + fused 2+3-body force + kick +
 thermostat + FP64 reductions.  value = atom-steps / s.
 
-Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
-system's stream; the L2 is flushed (a 512 MB write) between steps because the
-working set (~16 MB) fits in L2.  Under torchrun every rank runs its own
-replica (the path shards by box, no data exchange); value = all ranks'
-atom-steps / max over ranks of the timed span.
+Timing: W warm-up steps, then K steps in one mw_step_async call (one
+persistent launch, or K graph replays), bracketed by CUDA events on the
+system's stream with a synchronisation on both sides; the working set
+(~0.7 GB) is larger than the 129 MB L2, so the L2 is not flushed.  Under
+torchrun every rank runs its own replica (the path shards by box, no data
+exchange); value = all ranks' atom-steps / max over ranks of the timed span.
+The two-box 65536-atom workload (32768-atom ice Ih + 32768-atom melted liquid,
+NH 240 K, one step per launch with the L2 flushed between steps) is reported
+beside it under "extra".
 
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload on this host's cores.
+--impl reference times the FP64 CPU oracle (owner-computes on all host cores)
+on the same initial state of the same workload.
 """
 from __future__ import annotations
 
@@ -57,9 +62,10 @@ def parse():
                     help="instead of the bench line: where the persistent engine's step goes, phase by phase")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prep-steps", type=int, default=3000)
-    ap.add_argument("--workload", default="ice_liquid_32k",
-                    choices=["ice_liquid_32k", "nve512", "batch256", "slab1m", "fm4096x64", "structure_32k", "slab_gamma",
-                             "diffusion_4096", "npt_density_scan", "solute_32k"])
+    ap.add_argument("--workload", default="slab1m",
+                    choices=["slab1m", "ice_liquid_32k", "nve512", "batch256", "fm4096x64", "structure_32k",
+                             "slab_gamma", "diffusion_4096", "npt_density_scan", "solute_32k"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the two-box 65536-atom line under 'extra'")
     ap.add_argument("--drift-steps", type=int, default=0,
                     help="after timing, run this many NVE steps and report the energy drift per ns")
     return ap.parse_args()
@@ -201,59 +207,282 @@ def barrier(pg, device):
             pg.barrier()
 
 
-def traffic_from_profile(kernel_src):
-    """DRAM bytes per force launch from the committed ncu summary, if it was
-    taken on the current kernel source (hash match), else None."""
+def traffic_from_profile(kernel_src, n_atoms):
+    """DRAM bytes per force launch from the committed ncu summary of this
+    workload size, if it was taken on the current kernel source (hash match),
+    else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "sw_force_traffic.json")
     if not os.path.exists(path):
         return None
     try:
-        rec = json.load(open(path))
+        recs = json.load(open(path))
         h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-        if rec.get("source_hash") != h:
-            return None
-        return rec.get("dram_bytes_per_launch_scaled")
+        for rec in (recs if isinstance(recs, list) else [recs]):
+            if rec.get("source_hash") == h and int(rec.get("atoms", -1)) == int(n_atoms):
+                return rec.get("dram_bytes_per_launch")
+        return None
     except Exception:
         return None
 
 
+# ------------------------------------------------------------------ the headline workload
+
+T_SLAB = 250.0
+
+
+def slab_workload(rank=0):
+    """2^20 atoms: ice Ih slab + liquid-start slab along z (seeded, synthetic)."""
+    x, box, _ = I.ice_liquid_slab()
+    v = I.maxwell_velocities(len(x), T_SLAB, seed=I.BASE_SEED + 5 + 17 * rank)
+    return x, v, box
+
+
+def slab_spec(box):
+    return {"workload": "2^20-atom ice Ih slab (524288 @0.92 g/cm^3, 64x32x32 cells) + liquid-start slab "
+                        "(524288 @0.9998) along z, NH 250 K, dt 10 fs",
+            "atoms": 1048576, "boxes": 1, "box_A": [round(float(b), 4) for b in box], "T_K": T_SLAB,
+            "dt_fs": DT, "tau_fs": TAU}
+
+
 # ------------------------------------------------------------------ CPU oracle timing
 
-def oracle_sample(target_s=12.0):
-    """Times the FP64 oracle's MD step (cell-list forces + velocity Verlet +
-    Nose-Hoover) on both boxes of the workload for a bounded number of steps
-    (about target_s seconds of one core); returns (atom-steps/s, description)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_md_rate(x, v, box, threads, target_s, T0, max_steps=1000):
+    """atom-steps/s of the FP64 oracle's MD step (cell-list forces, velocity
+    Verlet, Nose-Hoover) on this state: one start-up force call is timed on
+    its own and taken out; the steps are sized to about target_s seconds.
+    threads = 0: the single-thread cell-list routine; > 0: owner-computes on
+    that many threads.  Returns (rate, steps, seconds of the timed steps)."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.md(x, v, box, 0, dt=DT, kind=2, T0=T0, tau=TAU, threads=threads)
+    t_force = time.perf_counter() - t0
+    steps = int(max(1, min(max_steps, target_s / max(t_force, 1e-4))))
+    t0 = time.perf_counter()
+    oracle.md(x, v, box, steps, dt=DT, kind=2, T0=T0, tau=TAU, threads=threads)
+    el = time.perf_counter() - t0
+    step_s = max(el - t_force, 1e-9) / steps
+    return len(x) / step_s, steps, el
+
+
+def cpu_baseline_legs(x, v, box, T0, sample_name, target_1t=6.0, target_mt=6.0):
+    """The oracle, as it stands, on this host: single thread (cell-list loop)
+    and all cores (owner-computes, OpenMP), on the same state the GPU starts
+    from.  The all-core leg is the headline value."""
     import oracle
     oracle.build()
-    xi, vi, bi = ice_start(I.BASE_SEED + 2)
-    xl, bl = liquid_lattice()
-    xl = xl + np.random.default_rng(3).normal(0, 0.35, xl.shape)  # liquid-like disorder, same density
-    vl = I.maxwell_velocities(len(xl), T_RUN, seed=5)
+    cores = host_cores()
+    threads = cores if oracle.openmp_enabled() else 1
+    r1, s1, e1 = oracle_md_rate(x, v, box, 0, target_1t, T0)
+    rm, sm, em = oracle_md_rate(x, v, box, threads, target_mt, T0)
+    return {"value": rm, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{sm} NH steps of the {sample_name} (full size, same initial state as the GPU run) on "
+                      f"{threads} threads (owner-computes), {em:.1f} s; start-up force call timed apart",
+            "host_cores": cores, "build": "gcc -O3 -ffp-contract=off -fopenmp (no -march=native: the same "
+                                         "FP64 results on x86 and Arm hosts)",
+            "single_thread": {"value": r1, "unit": UNIT, "cores": 1,
+                              "sample": f"{s1} NH steps, cell-list loop, {e1:.1f} s"}}
+
+
+# ------------------------------------------------------------------ timing helpers
+
+def _events(torch, k):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+
+
+def force_roofline(mw, sysm, integ, nsteps=20):
+    """The force kernel's algorithmic FLOP rate: 40 FP32 operations per
+    ordered leg and per triplet (counted on the current state by the
+    kernel's own counters) over the k_force launch's mean duration (CUDA
+    events on the system stream around each launch, between the other phase
+    kernels of real steps: mw_phase_times)."""
+    phases = mw.mw_phase_times(sysm.h, integ, nsteps)
+    sysm.set_count_terms(True)
+    mw.mw_forces_async(sysm.h)
+    mw.mw_sync(sysm.h)
+    info_c = sysm.info()
+    sysm.set_count_terms(False)
+    P, T = info_c["npairs"], info_c["ntriplets"]
+    flops = 40.0 * (2 * P + T)
+    kms = phases["force"]
+    achieved = flops / (kms / 1e3) / 1e12
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_0809_2811_gb300", "csrc", "mw_device.cuh"),
+                                   sysm.n_total)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_force (fused 2+3-body)", "kernel_ms": kms,
+            "legs": 2 * P, "triplets": T, "flops_per_launch": flops,
+            "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz (MEASURED_PEAKS.json has no FP32 "
+                          "figure)"}
+    return roof, phases
+
+
+def e2e_round_trip(torch, mw, sysm, integ, x, v, steps, world, pg, dev):
+    """End to end through the public API with host buffers: every step sets
+    the state from page-locked host x, v (read in place by the loading
+    kernel), advances one step and reads x, v and the thermo record back into
+    page-locked host arrays."""
+    n = len(x)
+    xh = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    vh = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+    xo = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    vo = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    xa, va, xoa, voa = xh.numpy(), vh.numpy(), xo.numpy(), vo.numpy()
+    sysm.set_state(xa, va)
+    mw.mw_step(sysm.h, integ, 1, sysm.nbox)
+    sysm.get_state(xoa, voa)
+    torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    oracle.md(xi, vi, bi, 1, dt=DT, kind=2, T0=T_RUN, tau=TAU)
-    oracle.md(xl, vl, bl, 1, dt=DT, kind=2, T0=T_RUN, tau=TAU)
-    one = time.perf_counter() - t0  # includes the initial force call of each run
-    steps = max(2, int(target_s / max(one, 1e-3)))
-    t0 = time.perf_counter()
-    oracle.md(xi, vi, bi, steps, dt=DT, kind=2, T0=T_RUN, tau=TAU)
-    oracle.md(xl, vl, bl, steps, dt=DT, kind=2, T0=T_RUN, tau=TAU)
-    el = time.perf_counter() - t0
-    # each or_md call also does one extra force evaluation up front: count (steps + 1) force evals
-    rate = 2 * len(xi) * steps / el
-    return rate, (f"oracle FP64 single-thread MD, {steps} NH steps of each 32768-atom box "
-                  f"(ice lattice + disordered 0.9998 lattice), {el:.1f} s incl. one start-up force call per box")
+    for _ in range(steps):
+        sysm.set_state(xa, va)                   # H2D: the step's inputs
+        mw.mw_step(sysm.h, integ, 1, sysm.nbox)  # D2H: its thermo records
+        sysm.get_state(xoa, voa)                 # D2H: the advanced positions and velocities
+    torch.cuda.synchronize(dev)
+    el = reduce_max(pg, time.perf_counter() - t0, dev)
+    return {"value": world * n * steps / el, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes + v.nbytes),
+            "d2h_bytes_per_step": int(xo.numpy().nbytes + vo.numpy().nbytes + sysm.nbox * 136), "steps": steps,
+            "ms_per_step": 1e3 * el / steps,
+            "note": "per step: mw_set_state(pinned host x, v) + mw_step(1) with its thermo record + "
+                    "mw_get_state(pinned host x, v); set_state restarts the thermostat and needs a force call at the "
+                    "new positions before the step"}
 
 
-# ------------------------------------------------------------------ main GPU arm
-
-def run_gpu(args, world, rank, local, pg):
+def run_headline(args, world, rank, local, pg):
     import torch
     from paper_0809_2811_gb300 import build, mw
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    # a real (non-default) stream shared by the library, the events and the L2 flush
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    sp = stream.cuda_stream
+
+    x, v, box = slab_workload(rank)
+    n = len(x)
+    sysm = mw.System(n, box, stream=sp)
+    if args.engine != "auto":
+        sysm.set_engine({"graph": mw.MW_ENGINE_GRAPH, "persistent": mw.MW_ENGINE_PERSISTENT}[args.engine])
+    sysm.set_state(x, v)
+    if args.skin is not None and args.engine != "auto":
+        mw.mw_set_skin(sysm.h, args.skin)
+    integ = mw.make_integrator(DT, mw.MW_NOSE_HOOVER, T_SLAB, TAU)
+    tuned = None
+    if args.engine == "auto":
+        tuned = mw.mw_autotune(sysm.h, integ, 50)
+    mw.mw_step(sysm.h, integ, max(args.warmup, 3), sysm.nbox)
+    th0 = sysm.thermo()
+    reb0 = sum(t["rebuilds"] for t in th0)
+    rs0 = sysm.info()["rebuild_steps"]
+
+    K = args.steps
+    e0, e1 = _events(torch, 2)
+    clocks = ClockSampler(local)
+    barrier(pg, dev)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    t_wall = time.perf_counter()
+    torch.cuda.profiler.start()
+    e0.record(stream)
+    mw.mw_step_async(sysm.h, integ, K)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    torch.cuda.profiler.stop()
+    t_wall = time.perf_counter() - t_wall
+    mw.mw_sync(sysm.h)
+    rebuild_steps = int(sysm.info()["rebuild_steps"] - rs0)
+    rebuilds = int(sum(t["rebuilds"] for t in sysm.thermo()) - reb0)
+    # the timed call lasts milliseconds: the same steps continue for ~0.3 s so
+    # that the clock sampler (100 ms period) sees the GPU under this load
+    mw.mw_step_async(sysm.h, integ, max(1, int(0.3 / max(e0.elapsed_time(e1) / 1e3 / K, 1e-6))))
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    mw.mw_sync(sysm.h)
+    barrier(pg, dev)
+    span_s = e0.elapsed_time(e1) / 1e3
+    span_max = reduce_max(pg, span_s, dev)
+    info = sysm.info()
+    th1 = sysm.thermo()
+    value = world * n * K / span_max
+
+    roof, phases = force_roofline(mw, sysm, integ)
+    eng = info["engine"]
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_round_trip(torch, mw, sysm, integ, x, v, min(K, 20), world, pg, dev)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_legs(x, v, box, T_SLAB, "2^20-atom slab")
+    extra = {}
+    if not args.no_extra:
+        extra["ice_liquid_32k"] = run_two_box(args, world, rank, local, pg, as_extra=True)
+    nbr_bytes = n * info["nbr_width"] * 4
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": 1e3 * span_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 pair/triplet, f64 integrate+reductions", "data": "synthetic",
+        "config": {**slab_spec(box), "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "l2": f"not flushed: working set ~{(n * 170 + nbr_bytes) / 1e9:.2f} GB > 129 MB L2",
+                   "timed_call": f"one mw_step_async({K}) call",
+                   "engine": {1: "graph", 2: "persistent"}.get(eng, str(eng)),
+                   "nbr_width": info["nbr_width"], "r_list_A": info["r_list"], "autotuned": tuned is not None,
+                   "persistent_blocks": info["persistent_blocks"] if eng == mw.MW_ENGINE_PERSISTENT else None,
+                   "wall_s_timed": t_wall, "T_after_K": th1[0]["temperature"]},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": None,
+        "phase_ms": {k: round(val, 5) for k, val in phases.items()},
+        "clocks": clk,
+        "extra": extra,
+    }
+    # launches in the timed region: the graph engine runs kick1, force, kick2 per step plus the five
+    # rebuild kernels inside its conditional node on rebuild steps; the persistent engine one launch
+    out["gpu_launches"] = 3 * K + 5 * rebuild_steps if eng == mw.MW_ENGINE_GRAPH else 1
+    out["config"]["rebuild_steps_in_timed_region"] = rebuild_steps
+    out["config"]["box_rebuilds_in_timed_region"] = rebuilds
+    if args.drift_steps > 0:
+        sysm.set_state(x, v)
+        mw.mw_step(sysm.h, integ, 200, sysm.nbox)
+        out["nve"] = _nve_drift(mw, sysm, args.drift_steps, DT, n)
+    sysm.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ the two-box workload
+
+def oracle_sample(target_s=12.0):
+    """Times the FP64 oracle's MD step on both boxes of the two-box workload
+    for a bounded number of steps (single thread; the liquid box as a 0.35 A
+    jittered 0.9998 lattice, since the melted liquid comes from the GPU);
+    returns (atom-steps/s, description)."""
+    import oracle
+    oracle.build()
+    xi, vi, bi = ice_start(I.BASE_SEED + 2)
+    xl, bl = liquid_lattice()
+    xl = xl + np.random.default_rng(3).normal(0, 0.35, xl.shape)
+    vl = I.maxwell_velocities(len(xl), T_RUN, seed=5)
+    ri, si, ei = oracle_md_rate(xi, vi, bi, 0, target_s / 2, T_RUN)
+    rl, sl, el = oracle_md_rate(xl, vl, bl, 0, target_s / 2, T_RUN)
+    rate = 2.0 / (1.0 / ri + 1.0 / rl)
+    return rate, (f"oracle FP64 single-thread MD, {si} + {sl} NH steps of the 32768-atom ice box and a "
+                  f"0.35 A-jittered 0.9998 lattice, {ei + el:.1f} s")
+
+
+def run_two_box(args, world, rank, local, pg, as_extra=False):
+    import torch
+    from paper_0809_2811_gb300 import build, mw
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     sp = stream.cuda_stream
@@ -273,126 +502,67 @@ def run_gpu(args, world, rank, local, pg):
     integ = mw.make_integrator(DT, mw.MW_NOSE_HOOVER, T_RUN, TAU)
     natoms = sum(n)
     tuned = None
-    if args.engine == "auto":  # engine and skin picked by the autotuner on this state
+    if args.engine == "auto":
         tuned = mw.mw_autotune(sysm.h, integ, 50)
-
-    # warm-up
     mw.mw_step(sysm.h, integ, max(args.warmup, 3), sysm.nbox)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    if args.phase_marks:
+    if args.phase_marks and not as_extra:
         return phase_breakdown(args, rank, local, torch, mw, sysm, integ, stream, flush)
     th0 = sysm.thermo()
     reb0 = sum(t["rebuilds"] for t in th0)
     rs0 = sysm.info()["rebuild_steps"]
-
-    K = args.steps
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    clocks = ClockSampler(local)
+    K = max(args.steps, 20) if as_extra else args.steps
+    ev0, ev1 = _events(torch, K), _events(torch, K)
+    clocks = None if as_extra else ClockSampler(local)
     barrier(pg, dev)
     torch.cuda.synchronize(dev)
-    clocks.start()
-    time.sleep(0.3)
-    t_wall = time.perf_counter()
-    t_host = 0.0
-    torch.cuda.profiler.start()  # profiler range = the timed steps (ncu --profile-from-start off)
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
     for k in range(K):
         ev0[k].record(stream)
-        th_ = time.perf_counter()
         mw.mw_step_async(sysm.h, integ, 1)
-        t_host += time.perf_counter() - th_
         ev1[k].record(stream)
         flush.fill_(float(k))
     torch.cuda.synchronize(dev)
-    torch.cuda.profiler.stop()
-    t_wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     mw.mw_sync(sysm.h)
     barrier(pg, dev)
-    ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    span_s = sum(ms) / 1e3
-    span_max = reduce_max(pg, span_s, dev)
-    th1 = sysm.thermo()
-    rebuilds = sum(t["rebuilds"] for t in th1) - reb0
+    span_max = reduce_max(pg, sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / 1e3, dev)
     info = sysm.info()
+    rebuilds = sum(t["rebuilds"] for t in sysm.thermo()) - reb0
     rebuild_steps = info["rebuild_steps"] - rs0
     value = world * natoms * K / span_max
-
-    # force-kernel roofline: the k_force launch alone, timed with events on the
-    # system stream between the other phases of a step (mw_phase_times); the
-    # whole force call with the L2 flushed before it is reported beside it
-    phases = mw.mw_phase_times(sysm.h, integ, 50)  # per-phase GPU time (separate launches)
-    nf = 30
-    f0 = [torch.cuda.Event(enable_timing=True) for _ in range(nf)]
-    f1 = [torch.cuda.Event(enable_timing=True) for _ in range(nf)]
-    for k in range(nf):
-        flush.fill_(float(k))
-        f0[k].record(stream)
-        mw.mw_forces_async(sysm.h)
-        f1[k].record(stream)
-    torch.cuda.synchronize(dev)
-    mw.mw_sync(sysm.h)
-    fms = statistics.median([a.elapsed_time(b) for a, b in zip(f0, f1)])
-    sysm.set_count_terms(True)
-    mw.mw_forces_async(sysm.h)
-    mw.mw_sync(sysm.h)
-    info_c = sysm.info()
-    sysm.set_count_terms(False)
-    P, T = info_c["npairs"], info_c["ntriplets"]
-    flops = 40.0 * (2 * P + T)  # 40 FP32 ops per ordered leg and per triplet
-    kms = phases["force"]
-    achieved = flops / (kms / 1e3) / 1e12
-    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = traffic_from_profile(os.path.join(ROOT, "paper_0809_2811_gb300", "csrc", "mw_device.cuh"))
-
-    # end to end through the public API with host buffers
+    roof, phases = force_roofline(mw, sysm, integ, 50)
+    eng = info["engine"]
+    rec = {"metric": METRIC, "value": value, "unit": UNIT, "steps": K, "ms_per_step": 1e3 * span_max / K,
+           "config": {**workload_spec(), "l2": "flushed between steps (512 MB write)",
+                      "timed_call": "one mw_step_async(1) call per step",
+                      "engine": {1: "graph", 2: "persistent"}.get(eng, str(eng)), "nbr_width": info["nbr_width"],
+                      "rebuild_steps_in_timed_region": int(rebuild_steps), "r_list_A": info["r_list"],
+                      "liquid_pe_per_atom_after_melt": liq_pe},
+           "roofline": {k: roof[k] for k in ("achieved", "frac", "kernel_ms", "legs", "triplets")},
+           "phase_ms": {k: round(val, 5) for k, val in phases.items()}}
+    if as_extra:
+        sysm.close()
+        del flush
+        return rec
     e2e = None
     if not args.no_e2e:
-        ke = min(K, 40)
-        xh = torch.from_numpy(x).pin_memory()
-        vh = torch.from_numpy(v).pin_memory()
-        sysm.set_state(xh.numpy(), vh.numpy())
-        mw.mw_step(sysm.h, integ, 1, sysm.nbox)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(ke):
-            sysm.set_state(xh.numpy(), vh.numpy())  # H2D of the step's inputs (x, v)
-            mw.mw_step(sysm.h, integ, 1, sysm.nbox)  # D2H of the step's result (thermo records)
-        torch.cuda.synchronize(dev)
-        el = time.perf_counter() - t0
-        el = reduce_max(pg, el, dev)
-        e2e = {"value": world * natoms * ke / el, "unit": UNIT, "h2d_bytes_per_step": int(2 * x.nbytes),
-               "d2h_bytes_per_step": int(sysm.nbox * 136), "steps": ke,
-               "note": "mw_set_state(host x, v) + mw_step(1) + thermo read per step; set_state restarts "
-                       "the thermostat and forces a neighbour build + force call each step"}
-
+        e2e = e2e_round_trip(torch, mw, sysm, integ, x, v, min(K, 40), world, pg, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc = oracle_sample()
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
-
-    kernels_per_step = 4 if info["engine"] == mw.MW_ENGINE_GRAPH else 1  # + 5 rebuild kernels on rebuild steps
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": 1e3 * span_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 pair/triplet, f64 integrate+reductions", "data": "synthetic",
-        "config": {**workload_spec(), "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                   "l2": "flushed between steps (512 MB write)",
-                   "engine": {1: "graph", 2: "persistent"}.get(info["engine"], str(info["engine"])),
-                   "nbr_width": info["nbr_width"], "rebuilds_in_timed_region": int(rebuilds),
-                   "rebuild_steps_in_timed_region": int(rebuild_steps),
-                   "r_list_A": info["r_list"], "autotuned": tuned is not None,
-                   "liquid_pe_per_atom_after_melt": liq_pe, "wall_s_timed": t_wall,
-                   "host_us_per_step_call": 1e6 * t_host / K},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_force (fused 2+3-body)",
-                     "kernel_ms": kms, "force_call_ms_l2_flushed": fms, "legs": 2 * P, "triplets": T,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz"},
-        "cpu_baseline": cpu,
-        "e2e": e2e,
-        "gpu_launches": kernels_per_step * K + (5 * int(rebuild_steps) if info["engine"] == mw.MW_ENGINE_GRAPH else 0),
-        "phase_ms": {k: round(v, 5) for k, v in phases.items()},
-        "clocks": clk,
+        "config": {**rec["config"], "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "rebuilds_in_timed_region": int(rebuilds), "autotuned": tuned is not None},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": (3 * K + 5 * int(rebuild_steps)) if eng == mw.MW_ENGINE_GRAPH else K,
+        "phase_ms": rec["phase_ms"], "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -836,23 +1006,38 @@ pg_holder = [None]
 
 
 def run_reference(args, world, rank):
+    """The oracle as it stands, on this host's cores, on the GPU arm's
+    workload, metric and unit: the same initial state, K NH steps (fewer if
+    they would take more than about 90 s), after an untimed start-up force
+    call.  Rank 0 alone runs it."""
     if rank != 0:
         return
-    t0 = time.perf_counter()
-    rates = []
-    for _ in range(max(args.warmup, 0)):
-        pass
-    steps = max(1, args.steps)
-    per = max(2.0, min(20.0, 100.0 / steps))
-    rate, desc = oracle_sample(target_s=per)
-    rates.append(rate)
-    el = time.perf_counter() - t0
+    import oracle
+    oracle.build()
+    t_all = time.perf_counter()
+    if args.workload == "ice_liquid_32k":
+        rate, desc = oracle_sample(target_s=max(2.0, min(20.0, 100.0 / max(1, args.steps))))
+        cfg, threads, steps = {**workload_spec(), "parallelism": "cpu oracle"}, 1, args.steps
+    else:
+        x, v, box = slab_workload(0)
+        threads = host_cores() if oracle.openmp_enabled() else 1
+        t0 = time.perf_counter()
+        oracle.md(x, v, box, 0, dt=DT, kind=2, T0=T_SLAB, tau=TAU, threads=threads)
+        t_force = time.perf_counter() - t0
+        steps = int(max(1, min(max(1, args.steps), 90.0 / max(t_force, 1e-3))))
+        t0 = time.perf_counter()
+        oracle.md(x, v, box, steps, dt=DT, kind=2, T0=T_SLAB, tau=TAU, threads=threads)
+        el = time.perf_counter() - t0
+        rate = len(x) * steps / max(el - t_force, 1e-9)
+        desc = (f"{steps} NH steps of the full 2^20-atom slab from the GPU arm's initial state, owner-computes "
+                f"on {threads} threads, {el:.1f} s (the start-up force call timed apart)")
+        cfg = {**slab_spec(box), "parallelism": f"cpu oracle, {threads} threads"}
     out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world, "steps": steps,
            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64", "data": "synthetic", "config": {**workload_spec(), "parallelism": "cpu oracle"},
-           "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+           "dtype": "f64", "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-           "wall_s": el}
+           "wall_s": time.perf_counter() - t_all}
     print(json.dumps(out), flush=True)
 
 
@@ -863,8 +1048,10 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
+        elif args.workload == "slab1m":
+            run_headline(args, world, rank, local, pg)
         elif args.workload == "ice_liquid_32k":
-            run_gpu(args, world, rank, local, pg)
+            run_two_box(args, world, rank, local, pg)
         else:
             run_other(args, world, rank, local, pg)
     finally:

@@ -83,8 +83,16 @@ typedef enum mw_thermostat { MW_NVE = 0, MW_BERENDSEN = 1, MW_NOSE_HOOVER = 2, M
 /* How mw_step launches work.  GRAPH: one kernel per phase, one step captured
  * in a CUDA graph and replayed.  PERSISTENT: one cooperative launch runs many
  * steps with grid-wide barriers between phases.  AUTO: the library picks
- * (the autotuner's choice when one was made, else PERSISTENT). */
-typedef enum mw_engine { MW_ENGINE_AUTO = 0, MW_ENGINE_GRAPH = 1, MW_ENGINE_PERSISTENT = 2 } mw_engine;
+ * (the autotuner's choice when one was made, else PERSISTENT).  PLAIN: the
+ * plain GPU path the others are measured against: every phase kernel
+ * launched from the host every step (no graph, no persistent launch) and a
+ * force kernel with one thread per atom looping over its leg pairs (leg
+ * forces scattered with red.global, no lane groups, no shared-memory leg
+ * table, no moment form); it is also the force kernel of mw_energy_forces
+ * and mw_forces_async while selected.  One species only; the autotuner
+ * never picks it.  For the one-box-per-launch baseline of a batch, step one
+ * single-box system per box. */
+typedef enum mw_engine { MW_ENGINE_AUTO = 0, MW_ENGINE_GRAPH = 1, MW_ENGINE_PERSISTENT = 2, MW_ENGINE_PLAIN = 3 } mw_engine;
 
 /* Integrator settings for mw_step (Sec. II.B: dt = 10 fs, tau_T = 1 ps). */
 typedef struct mw_integrator {
@@ -203,7 +211,12 @@ mw_status mw_set_params(mw_system* s, const mw_params* prm);
 mw_status mw_set_species(mw_system* s, int nt, const mw_params* table, const int* types);
 
 /* Forces a cell binning + neighbour-list rebuild now; *max_count_out (may be
- * NULL) receives the widest neighbour set.  Grows the list if needed. */
+ * NULL) receives the widest neighbour set.  Grows the list if needed.
+ * Defining passage: Sec. II.A, where every term of the energy vanishes beyond
+ * r = a sigma, so the pair sum and the three-body sum over leg pairs (j, k)
+ * of a centre i only need the atoms within a sigma of i; the list holds
+ * every atom within a sigma + skin (the skin is a build choice, not in the
+ * paper), cell-binned by a counting sort over cells at least that wide. */
 mw_status mw_build_neighbors(mw_system* s, int* max_count_out);
 
 /* Copies the neighbour sets of the last build, in the caller's atom order:
@@ -214,7 +227,11 @@ mw_status mw_build_neighbors(mw_system* s, int* max_count_out);
 mw_status mw_get_neighbors(mw_system* s, int* counts, int* nbr, int width);
 
 /* Energy, forces and virial at the current positions (rebuilding the
- * neighbour list first if it is stale).  Host outputs, each may be NULL:
+ * neighbour list first if it is stale).  Defining passage: Sec. II.A, the
+ * total energy E = sum over pairs of phi2 plus the sum over centres i and leg
+ * pairs j < k of phi3 with the angle at i; forces F_i = -dE/dx_i; the virial
+ * sum over terms and legs of d_a F_b is what the pressure tensor of the
+ * surface-tension formula of Sec. II.C needs.  Host outputs, each may be NULL:
  * f[n_total*3] (kcal/mol/A), energy[nbox*3] = (E, E2, E3) per box,
  * virial[nbox*6].  Pair and triplet arithmetic is FP32; energy and virial
  * are reduced in FP64. */
@@ -232,8 +249,14 @@ mw_status mw_energy_forces_dev(mw_system* s, const double* x_dev, float* f_dev, 
  * kernel on its own (the neighbour list is built first if it is stale). */
 mw_status mw_forces_async(mw_system* s);
 
-/* Advances every box nsteps velocity-Verlet steps.  last (may be NULL)
- * receives nbox thermo records after the final step.  Recovers internally
+/* Advances every box nsteps velocity-Verlet steps.  Defining passage:
+ * Sec. II.B, MD with a 10 fs step (5 fs for interfaces), Nose-Hoover
+ * thermostat with a 1 ps relaxation time and barostat with 2.5 ps (MW_NPT);
+ * the integrator is velocity Verlet (the paper names LAMMPS, whose default
+ * it is).  On a system made by mw_batch_create this call is the batched
+ * step: every box advances in the same launches (there is no separate
+ * mw_batch_step).  last (may be NULL) receives nbox thermo records after the
+ * final step.  Recovers internally
  * from neighbour-list overflow (grows the list and resumes the interrupted
  * step); returns MW_ENAN / MW_ELOST / MW_ETIMEOUT if dynamics broke down (the
  * state is then left at the failing step). */
@@ -306,7 +329,9 @@ mw_status mw_get_box(mw_system* s, double* box);
  * The neighbour list must be current (call mw_energy_forces first). */
 mw_status mw_energy_forces_vjp(mw_system* s, const float* dL_dF_dev, float* dL_dx_dev, double* dL_dtheta);
 
-/* Selects the engine mw_step uses (mw_engine). */
+/* Selects the engine mw_step uses (mw_engine).  MW_ENGINE_PLAIN is refused
+ * (MW_EINVAL) while several species are set, and mw_set_species refuses
+ * several species while it is selected. */
 mw_status mw_set_engine(mw_system* s, int engine);
 
 /* Sets the neighbour-list width (slots per atom, >= 1) and marks the list
@@ -386,12 +411,17 @@ mw_status mw_angle_histogram(mw_system* s, int nc, int nbins, unsigned long long
  *   stream      cudaStream_t the work is enqueued on (NULL = legacy default);
  *               the call synchronises it before returning.
  * Larger inputs are rejected with MW_EINVAL (atoms or cells) or
- * MW_ENLIST_OVERFLOW (neighbours), with a message naming the limit.
+ * MW_ENLIST_OVERFLOW (neighbours), with a message naming the limit; a
+ * non-finite coordinate gives MW_EINVAL and leaves the outputs untouched.
+ * Positions are converted exactly as mw_set_state converts them, so both
+ * entry points see the same coordinates.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call reuses the same array: calls whose
- * GPU work can overlap (e.g. on two unordered streams) race and must not be
- * made. */
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process (a cudaDeviceReset in between is not supported).  Every
+ * call ends by reading a status word back and synchronising the stream, so
+ * no call may be made on a stream that is being captured (MW_EINVAL).  Every
+ * call reuses the same array: calls whose GPU work can overlap (e.g. on two
+ * unordered streams) race and must not be made. */
 #define MW_NOALLOC_MAX_ATOMS 16384
 #define MW_NOALLOC_MAX_WIDTH 64
 #define MW_NOALLOC_MAX_CELLS 16384

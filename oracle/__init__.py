@@ -10,7 +10,9 @@ Function map (section of the paper each follows):
   phi2, dphi2, phi3            Sec. II.A two- and three-body equations
   energy_forces_brute          Sec. II.A total energy, O(N^2)/O(N^3) loops
   energy_forces_cell           same, cell-list owner loop
-  neighbors                    neighbour sets {j : |d_ij| < r_list}
+  energy_forces(method="owner") same sums, owner-computes on several threads
+                               (the multi-core CPU baseline)
+  neighbors, neighbors_raw      neighbour sets {j : |d_ij| < r_list}
   md                           Sec. II.B velocity-Verlet run (thermostat reading)
   md_npt                       Sec. II.B isobaric-isothermal run (barostat reading)
   energy_forces_species        Sec. II.A equations with a parameter vector per
@@ -37,13 +39,25 @@ PARAM_NAMES = ("lambda", "epsilon", "sigma", "a", "gamma", "A", "B", "cos_theta0
 
 
 def build(force: bool = False) -> str:
-    """Compiles mw_oracle.c into libmw_oracle.so next to it (plain gcc, -O2)."""
+    """Compiles mw_oracle.c into libmw_oracle.so next to it: gcc -O3, with
+    OpenMP for the owner-computes routine when the compiler has it (without
+    it that routine runs serially).  No -march=native and no FMA contraction
+    (-ffp-contract=off), so that the x86 host and the Arm GPU host compute the
+    same FP64 results."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O3", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def openmp_enabled() -> bool:
+    """Whether the built oracle has OpenMP (the owner routine then uses threads)."""
+    return int(lib().or_openmp_threads()) > 0
 
 
 _lib = None
@@ -64,6 +78,10 @@ def lib():
         _lib.or_phi3.restype = ctypes.c_double
         for name in ("or_energy_forces_brute", "or_energy_forces_cell"):
             getattr(_lib, name).argtypes = [d, ctypes.c_int, d, d, d, d]
+        _lib.or_energy_forces_owner.argtypes = [d, ctypes.c_int, d, d, d, d, ctypes.c_int]
+        _lib.or_md_owner.argtypes = [d, ctypes.c_int, d, d, d, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, d, d, ctypes.c_int]
+        _lib.or_openmp_threads.restype = ctypes.c_int
         _lib.or_neighbors.argtypes = [ctypes.c_int, d, d, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, i, i, ctypes.c_int, i, i]
         _lib.or_md.argtypes = [d, ctypes.c_int, d, d, d, ctypes.c_double, ctypes.c_double,
@@ -127,18 +145,24 @@ def _check(rc, what):
         raise RuntimeError(f"oracle {what} failed with code {rc}")
 
 
-def energy_forces(x, box, prm=None, method="cell"):
+def energy_forces(x, box, prm=None, method="cell", threads=1):
     """Returns dict(e2, e3, energy, forces (n,3), virial[6], npairs, ntriplets,
     virial_abs): virial_abs is the summed magnitude of the diagonal virial
-    contributions, the scale against which the (cancelling) trace is judged."""
+    contributions, the scale against which the (cancelling) trace is judged.
+    method: "cell" (cell-list owner loop), "brute" (all pairs / triplets) or
+    "owner" (owner-computes on `threads` threads)."""
     prm = default_params() if prm is None else np.ascontiguousarray(prm, np.float64)
     x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
     box = np.ascontiguousarray(box, np.float64)
     n = x.shape[0]
     f = np.zeros((n, 3))
     out = np.zeros(11)
-    fn = lib().or_energy_forces_cell if method == "cell" else lib().or_energy_forces_brute
-    _check(fn(_dp(prm), n, _dp(x), _dp(box), _dp(f), _dp(out)), "energy_forces")
+    if method == "owner":
+        rc = lib().or_energy_forces_owner(_dp(prm), n, _dp(x), _dp(box), _dp(f), _dp(out), int(threads))
+    else:
+        fn = lib().or_energy_forces_cell if method == "cell" else lib().or_energy_forces_brute
+        rc = fn(_dp(prm), n, _dp(x), _dp(box), _dp(f), _dp(out))
+    _check(rc, "energy_forces")
     return dict(e2=out[0], e3=out[1], energy=out[0] + out[1], forces=f, virial=out[2:8].copy(),
                 npairs=int(out[8]), ntriplets=int(out[9]), virial_abs=out[10])
 
@@ -160,19 +184,43 @@ def neighbors(x, box, rlist, band_rel=1e-5, width=256, band_cap=100000):
     return sets, {(int(a), int(b)) for a, b in band[:nb]}
 
 
-def md(x, v, box, nsteps, dt=10.0, kind=0, T0=300.0, tau=1000.0, mass=18.015, prm=None, state=(0.0, 0.0)):
+def neighbors_raw(x, box, rlist, band_rel=1e-5, width=128, band_cap=1000000):
+    """neighbors() as padded arrays: (counts[n], nbr[n, width] sorted rows,
+    band set of (i, j)); raises if a row is wider than width."""
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    box = np.ascontiguousarray(box, np.float64)
+    n = x.shape[0]
+    counts = np.zeros(n, np.int32)
+    nbr = np.zeros((n, width), np.int32)
+    band = np.zeros((band_cap, 2), np.int32)
+    nband = np.zeros(1, np.int32)
+    rc = lib().or_neighbors(n, _dp(x), _dp(box), float(rlist), float(band_rel), width, _ip(counts),
+                            _ip(nbr), band_cap, _ip(band), _ip(nband))
+    _check(rc, "neighbors")
+    nb = min(int(nband[0]), band_cap)
+    return counts, nbr, {(int(a), int(b)) for a, b in band[:nb]}
+
+
+def md(x, v, box, nsteps, dt=10.0, kind=0, T0=300.0, tau=1000.0, mass=18.015, prm=None, state=(0.0, 0.0),
+       threads=0):
     """Runs the oracle's velocity-Verlet; returns (x, v, state, thermo[nsteps+1, 8]).
 
     thermo columns: pe, e2, e3, ke, T, conserved, xi, eta.  kind: 0 NVE,
-    1 Berendsen, 2 Nose-Hoover."""
+    1 Berendsen, 2 Nose-Hoover.  threads > 0: owner-computes forces and
+    threaded loops on that many threads (the multi-core CPU baseline)."""
     prm = default_params() if prm is None else np.ascontiguousarray(prm, np.float64)
     x = np.array(x, np.float64).reshape(-1, 3)
     v = np.array(v, np.float64).reshape(-1, 3)
     box = np.ascontiguousarray(box, np.float64)
     st = np.array(state, np.float64)
     th = np.zeros((nsteps + 1, 8))
-    _check(lib().or_md(_dp(prm), x.shape[0], _dp(x), _dp(v), _dp(box), mass, dt, kind, T0, tau, nsteps,
-                       _dp(st), _dp(th)), "md")
+    if threads > 0:
+        rc = lib().or_md_owner(_dp(prm), x.shape[0], _dp(x), _dp(v), _dp(box), mass, dt, kind, T0, tau, nsteps,
+                               _dp(st), _dp(th), int(threads))
+    else:
+        rc = lib().or_md(_dp(prm), x.shape[0], _dp(x), _dp(v), _dp(box), mass, dt, kind, T0, tau, nsteps,
+                         _dp(st), _dp(th))
+    _check(rc, "md")
     return x, v, (float(st[0]), float(st[1])), th
 
 

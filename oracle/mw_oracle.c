@@ -79,6 +79,14 @@ void or_params_default(double* prm) {
   prm[9] = 0.0;          /* q */
 }
 
+/* Threads OpenMP would use (0 when built without OpenMP). */
+#ifdef _OPENMP
+#include <omp.h>
+int or_openmp_threads(void) { return omp_get_max_threads(); }
+#else
+int or_openmp_threads(void) { return 0; }
+#endif
+
 static double ipow(double x, int n) {
   double r = 1.0;
   for (int i = 0; i < n; ++i) r *= x;
@@ -406,6 +414,140 @@ int or_energy_forces_cell(const double* prm, int n, const double* x, const doubl
   return OR_OK;
 }
 
+/*
+ * Owner-computes variant of or_energy_forces_cell, for the multi-core CPU
+ * baseline: the same sums (Sec. II.A), grouped so that every atom's force is
+ * assembled by the one thread that owns it, with no shared writes and no
+ * atomics.  Pass 1 lists each atom's legs (r < a sig) from the cell list;
+ * pass 2 gives atom i
+ *   - half of each pair term of its legs (energy, virial) and the pair force
+ *     on i;
+ *   - the three-body terms centred on i (energy, virial, and their reaction
+ *     on i, minus the forces on the two partners);
+ *   - the force on i of every three-body term centred on a neighbour j in
+ *     which i is one of the two legs (the "two-hop" part: j's legs are read,
+ *     nothing of j is written).
+ * Same outputs as or_energy_forces_cell (out[8] counts every pair once).
+ * nthreads <= 1, or a build without OpenMP, runs serially.
+ */
+static void add_virial_half(double* W, const double* d, const double* F) {
+  double h[3] = {0.5 * F[0], 0.5 * F[1], 0.5 * F[2]};
+  add_virial(W, d, h);
+}
+
+int or_energy_forces_owner(const double* prm, int n, const double* x, const double* box, double* f, double* out,
+                           int nthreads) {
+  const double rc = prm[3] * prm[2];
+  if (n < 0 || box[0] < 2 * rc || box[1] < 2 * rc || box[2] < 2 * rc) return OR_EINVAL;
+  if (nthreads < 1) nthreads = 1;
+  or_cells c;
+  if (cells_build(&c, n, x, box, rc) != OR_OK) {
+    cells_free(&c);
+    return OR_ENOMEM;
+  }
+  int* start = (int*)calloc((size_t)n + 1, sizeof(int));
+  if (!start) {
+    cells_free(&c);
+    return OR_ENOMEM;
+  }
+  /* pass 1a: leg counts */
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (int i = 0; i < n; ++i) {
+    int cells[27];
+    const int ncells = stencil_cells(&c, i, cells);
+    int m = 0;
+    for (int s = 0; s < ncells; ++s)
+      for (int j = c.head[cells[s]]; j >= 0; j = c.next[j]) {
+        if (j == i) continue;
+        double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+        min_image(box, d);
+        if (sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) < rc) ++m;
+      }
+    start[i + 1] = m;
+  }
+  for (int i = 0; i < n; ++i) start[i + 1] += start[i];
+  or_leg* legs = (or_leg*)malloc(sizeof(or_leg) * (size_t)(start[n] > 0 ? start[n] : 1));
+  if (!legs) {
+    free(start);
+    cells_free(&c);
+    return OR_ENOMEM;
+  }
+  /* pass 1b: the legs, in stencil order */
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (int i = 0; i < n; ++i) {
+    int cells[27];
+    const int ncells = stencil_cells(&c, i, cells);
+    int m = start[i];
+    for (int s = 0; s < ncells; ++s)
+      for (int j = c.head[cells[s]]; j >= 0; j = c.next[j]) {
+        if (j == i) continue;
+        double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+        min_image(box, d);
+        const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (!(r < rc)) continue;
+        legs[m].j = j;
+        legs[m].r = r;
+        for (int k = 0; k < 3; ++k) legs[m].d[k] = d[k];
+        ++m;
+      }
+  }
+  /* pass 2: owner sums */
+  double E2 = 0, E3 = 0, W[7] = {0, 0, 0, 0, 0, 0, 0}, npair = 0, ntrip = 0;
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 256) reduction(+ : E2, E3, npair, ntrip, W[:7])
+  for (int i = 0; i < n; ++i) {
+    const or_leg* li = legs + start[i];
+    const int nl = start[i + 1] - start[i];
+    double Fi[3] = {0, 0, 0};
+    for (int l = 0; l < nl; ++l) { /* pair terms, half each side */
+      const double r = li[l].r;
+      E2 += 0.5 * or_phi2(prm, r);
+      const double dp = or_dphi2(prm, r);
+      double Fj[3];
+      for (int k = 0; k < 3; ++k) Fj[k] = -dp * li[l].d[k] / r;
+      for (int k = 0; k < 3; ++k) Fi[k] -= Fj[k];
+      add_virial_half(W, li[l].d, Fj);
+      npair += 0.5;
+    }
+    for (int a = 0; a < nl; ++a) /* three-body terms centred on i */
+      for (int b = a + 1; b < nl; ++b) {
+        double gj[3], gk[3];
+        E3 += tri_grad(prm, li[a].d, li[a].r, li[b].d, li[b].r, gj, gk);
+        double Fj[3] = {-gj[0], -gj[1], -gj[2]}, Fk[3] = {-gk[0], -gk[1], -gk[2]};
+        for (int k = 0; k < 3; ++k) Fi[k] -= Fj[k] + Fk[k];
+        add_virial(W, li[a].d, Fj);
+        add_virial(W, li[b].d, Fk);
+        ntrip += 1;
+      }
+    for (int l = 0; l < nl; ++l) { /* i as a leg of the terms centred on its neighbour j */
+      const int j = li[l].j;
+      const or_leg* lj = legs + start[j];
+      const int mj = start[j + 1] - start[j];
+      int back = -1;
+      for (int m = 0; m < mj; ++m)
+        if (lj[m].j == i) back = m;
+      if (back < 0) continue; /* (cannot happen: the leg relation is symmetric) */
+      for (int m = 0; m < mj; ++m) {
+        if (m == back) continue;
+        double gi[3], gk[3];
+        tri_grad(prm, lj[back].d, lj[back].r, lj[m].d, lj[m].r, gi, gk);
+        for (int k = 0; k < 3; ++k) Fi[k] -= gi[k];
+      }
+    }
+    if (f)
+      for (int k = 0; k < 3; ++k) f[3 * i + k] = Fi[k];
+  }
+  free(legs);
+  free(start);
+  cells_free(&c);
+  out[0] = E2;
+  out[1] = E3;
+  for (int k = 0; k < 6; ++k) out[2 + k] = W[k];
+  out[8] = npair;
+  out[9] = ntrip;
+  out[10] = W[6];
+  return OR_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* Neighbour sets                                                       */
 /* ------------------------------------------------------------------ */
@@ -626,6 +768,15 @@ static double kinetic(int n, const double* v, double mass) {
   return 0.5 * mass * s / OR_FCONV; /* kcal/mol */
 }
 
+/* kinetic() summed by nt threads (the multi-core baseline; nt <= 1 is kinetic()). */
+static double kinetic_nt(int n, const double* v, double mass, int nt) {
+  if (nt <= 1) return kinetic(n, v, mass);
+  double s = 0;
+#pragma omp parallel for num_threads(nt) schedule(static) reduction(+ : s)
+  for (int i = 0; i < 3 * n; ++i) s += v[i] * v[i];
+  return 0.5 * mass * s / OR_FCONV;
+}
+
 /* One Nose-Hoover half step (length dt/2) of a single thermostat, split as
  * quarter step on xi, velocity scaling, half step on eta, quarter step on xi.
  * Q = Ndf kB T0 tau^2. */
@@ -656,10 +807,12 @@ typedef struct {
   const double* table; /* several species: nt^3 vectors, or NULL */
   int nt;
   const int* types;
+  int nthreads; /* > 0: one species through or_energy_forces_owner on that many threads */
 } md_pot;
 
 static int md_forces(const md_pot* pot, int n, const double* x, const double* box, double* f, double* out) {
   if (pot->table) return or_energy_forces_species(pot->table, pot->nt, pot->types, n, x, box, f, out);
+  if (pot->nthreads > 0) return or_energy_forces_owner(pot->prm, n, x, box, f, out, pot->nthreads);
   return or_energy_forces_cell(pot->prm, n, x, box, f, out);
 }
 
@@ -668,7 +821,15 @@ static int md_run(const md_pot* pot, int n, double* x, double* v, const double* 
 
 int or_md(const double* prm, int n, double* x, double* v, const double* box, double mass, double dt,
           int kind, double T0, double tau, int nsteps, double* state, double* thermo) {
-  const md_pot pot = {prm, NULL, 0, NULL};
+  const md_pot pot = {prm, NULL, 0, NULL, 0};
+  return md_run(&pot, n, x, v, box, mass, dt, kind, T0, tau, nsteps, state, thermo);
+}
+
+/* or_md with the owner-computes forces on nthreads threads (the multi-core
+ * CPU baseline); the same trajectory as or_md up to rounding order. */
+int or_md_owner(const double* prm, int n, double* x, double* v, const double* box, double mass, double dt,
+                int kind, double T0, double tau, int nsteps, double* state, double* thermo, int nthreads) {
+  const md_pot pot = {prm, NULL, 0, NULL, nthreads > 0 ? nthreads : 1};
   return md_run(&pot, n, x, v, box, mass, dt, kind, T0, tau, nsteps, state, thermo);
 }
 
@@ -676,7 +837,7 @@ int or_md(const double* prm, int n, double* x, double* v, const double* box, dou
 int or_md_species(const double* table, int nt, const int* types, int n, double* x, double* v, const double* box,
                   double mass, double dt, int kind, double T0, double tau, int nsteps, double* state,
                   double* thermo) {
-  const md_pot pot = {NULL, table, nt, types};
+  const md_pot pot = {NULL, table, nt, types, 0};
   return md_run(&pot, n, x, v, box, mass, dt, kind, T0, tau, nsteps, state, thermo);
 }
 
@@ -696,16 +857,21 @@ static int md_run(const md_pot* pot, int n, double* x, double* v, const double* 
   const double Q = Ndf * OR_KB * T0 * tau * tau;
   double xi = state[0], eta = state[1];
   const double cf = 0.5 * dt * OR_FCONV / mass;
+  const int nt = pot->nthreads;
   for (int s = 0; s <= nsteps; ++s) {
     if (s > 0) {
-      double ke = kinetic(n, v, mass);
+      double ke = kinetic_nt(n, v, mass, nt);
       if (kind == 2) nh_half(n, v, &ke, &xi, &eta, dt, Ndf, T0, Q);
-      for (int i = 0; i < 3 * n; ++i) v[i] += cf * f[i];
-      for (int i = 0; i < 3 * n; ++i) x[i] = wrap1(x[i] + dt * v[i], box[i % 3]);
+#pragma omp parallel for if (nt > 1) num_threads(nt > 1 ? nt : 1) schedule(static)
+      for (int i = 0; i < 3 * n; ++i) {
+        v[i] += cf * f[i];
+        x[i] = wrap1(x[i] + dt * v[i], box[i % 3]);
+      }
       rc = md_forces(pot, n, x, box, f, out);
       if (rc != OR_OK) break;
+#pragma omp parallel for if (nt > 1) num_threads(nt > 1 ? nt : 1) schedule(static)
       for (int i = 0; i < 3 * n; ++i) v[i] += cf * f[i];
-      ke = kinetic(n, v, mass);
+      ke = kinetic_nt(n, v, mass, nt);
       if (kind == 2) nh_half(n, v, &ke, &xi, &eta, dt, Ndf, T0, Q);
       if (kind == 1) {
         const double T = 2.0 * ke / (Ndf * OR_KB);
@@ -757,7 +923,7 @@ static int npt_run(const md_pot* pot, int n, double* x, double* v, double* box, 
 
 int or_md_npt(const double* prm, int n, double* x, double* v, double* box, double mass, double dt, double T0,
               double tau, double P, double tau_p, int nsteps, double* state, double* thermo) {
-  const md_pot pot = {prm, NULL, 0, NULL};
+  const md_pot pot = {prm, NULL, 0, NULL, 0};
   return npt_run(&pot, n, x, v, box, mass, dt, T0, tau, P, tau_p, nsteps, state, thermo);
 }
 
@@ -765,7 +931,7 @@ int or_md_npt(const double* prm, int n, double* x, double* v, double* box, doubl
 int or_md_npt_species(const double* table, int nt, const int* types, int n, double* x, double* v, double* box,
                       double mass, double dt, double T0, double tau, double P, double tau_p, int nsteps,
                       double* state, double* thermo) {
-  const md_pot pot = {NULL, table, nt, types};
+  const md_pot pot = {NULL, table, nt, types, 0};
   return npt_run(&pot, n, x, v, box, mass, dt, T0, tau, P, tau_p, nsteps, state, thermo);
 }
 

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -23,6 +24,7 @@
 #include "mw_adjoint.cuh"
 #include "mw_structure.cuh"
 #include "mw_species.cuh"
+#include "mw_plain.cuh"
 
 static_assert(MW_MAX_SPECIES == mw::kMaxSpecies, "species limit of the header and the kernels");
 
@@ -182,6 +184,11 @@ void make_fparams(mw_system* s) {
   f.sle = (float)std::sqrt(p.lambda * p.epsilon);
   f.p = p.p;
   f.q = p.q;
+  f.rc_lo = (float)(rc - (double)f.rc);
+  f.sig_lo = (float)(p.sigma - (double)f.sig);
+  f.sig_l2e_lo = (float)(p.sigma * l2e - (double)f.sig_l2e);
+  f.gsig_l2e_lo = (float)(p.gamma * p.sigma * l2e - (double)f.gsig_l2e);
+  f.B_lo = (float)(p.B - (double)f.B);
 }
 
 // The device's box geometry (scaled every step by the barostat of an
@@ -384,6 +391,7 @@ mw_status status_error(const Global& g) {
     case ST_TIMEOUT: return fail(MW_ETIMEOUT, "a bounded device-side wait ran out");
     case ST_LEGS: return fail(MW_EINVAL, "more than %d atoms within a*sigma of atom slot %d", kMaxLegsOverflow, g.err_index);
     case ST_CELLS: return fail(MW_ESTATE, "cell counts left by an interrupted run (set a state again)");
+    case ST_INPUT: return fail(MW_EINVAL, "non-finite input value of atom %d", g.err_index);
     default: return fail(MW_ECUDA, "device status %d", g.status);
   }
 }
@@ -432,11 +440,33 @@ void launch_force(mw_system* s) {
                      : k_force_sp<false, 2><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
     return;
   }
+  if (s->engine == MW_ENGINE_PLAIN) {  // the plain path: one thread per atom
+    const int gp = div_up(s->N, kPlainThreads);
+    if (s->count_terms)
+      k_force_plain<true><<<gp, kPlainThreads, 0, s->stream>>>(d, s->fp);
+    else
+      k_force_plain<false><<<gp, kPlainThreads, 0, s->stream>>>(d, s->fp);
+    return;
+  }
   const int gb = div_up(s->N, kFAtoms);
   if (s->count_terms)
     k_force<true><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
   else
     k_force<false><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
+}
+
+// The plain path's steps: every phase kernel launched from the host, step
+// after step, no graph (the rebuild kernels return at once on steps without
+// a rebuild).
+mw_status launch_plain_steps(mw_system* s, int n) {
+  for (int k = 0; k < n; ++k) {
+    launch_kick1(s, false, 0ull);
+    launch_rebuild(s);
+    launch_force(s);
+    launch_kick2(s);
+  }
+  MW_CUDA(cudaGetLastError());
+  return MW_OK;
 }
 
 // One MD step into the stream being captured: kick1, an IF node holding the
@@ -606,12 +636,12 @@ mw_status prime_thermostat(mw_system* s) {
   return MW_OK;
 }
 
-mw_status run_graph_engine(mw_system* s, int nsteps, mw_thermo* last, bool* fetched) {
+mw_status run_graph_engine(mw_system* s, int nsteps, mw_thermo* last, bool* fetched, bool plain = false) {
   mw_status st;
   if ((st = prime_thermostat(s)) != MW_OK) return st;
   s->record_pending = true;
   const int K = 16;
-  if (s->graph_dirty || !s->graph1) {
+  if (!plain && (s->graph_dirty || !s->graph1)) {
     if ((st = capture_graphs(s, K)) != MW_OK) return st;
   }
   int remaining = nsteps;
@@ -628,13 +658,17 @@ mw_status run_graph_engine(mw_system* s, int nsteps, mw_thermo* last, bool* fetc
     if (g0.status == ST_GRID) {
       if (++regrid_guard > 8) return fail(MW_EGRID, "cell grid of an isobaric box kept failing");
       if ((st = regrid(s)) != MW_OK) return st;
-      if ((st = capture_graphs(s, K)) != MW_OK) return st;
+      if (!plain && (st = capture_graphs(s, K)) != MW_OK) return st;
       continue;
     }
     const unsigned long long step0 = g0.step;
-    const int full = remaining / K, rest = remaining % K;
-    for (int k = 0; k < full; ++k) MW_CUDA(cudaGraphLaunch(s->graphK, s->stream));
-    for (int k = 0; k < rest; ++k) MW_CUDA(cudaGraphLaunch(s->graph1, s->stream));
+    if (plain) {
+      if ((st = launch_plain_steps(s, remaining)) != MW_OK) return st;
+    } else {
+      const int full = remaining / K, rest = remaining % K;
+      for (int k = 0; k < full; ++k) MW_CUDA(cudaGraphLaunch(s->graphK, s->stream));
+      for (int k = 0; k < rest; ++k) MW_CUDA(cudaGraphLaunch(s->graph1, s->stream));
+    }
     Global g;
     if ((st = read_global_and_thermo(s, &g, last, last != nullptr, fetched, remaining, step0)) != MW_OK) return st;
     const int done = (int)(g.step - step0);
@@ -651,7 +685,7 @@ mw_status run_graph_engine(mw_system* s, int nsteps, mw_thermo* last, bool* fetc
       if (g2.status) return status_error(g2);
       s->host_step += 1;
       remaining -= done + 1;
-      if ((st = capture_graphs(s, K)) != MW_OK) return st;
+      if (!plain && (st = capture_graphs(s, K)) != MW_OK) return st;
       continue;
     }
     if (g.status == ST_GRID) {  // stopped at a step boundary; the loop head lays the grid out again
@@ -1092,6 +1126,7 @@ mw_status mw_set_species(mw_system* s, int nt, const mw_params* table, const int
   if (!table) return fail(MW_EINVAL, "table is NULL");
   if (nt == 1) return mw_set_params(s, &table[0]);
   if (!types) return fail(MW_EINVAL, "types is NULL");
+  if (s->engine == MW_ENGINE_PLAIN) return fail(MW_EINVAL, "the plain engine has one species only");
   mw_status st;
   const size_t ne = (size_t)nt * nt * nt;
   auto E = [&](int a, int b, int c) -> const mw_params& { return table[((size_t)a * nt + b) * nt + c]; };
@@ -1136,6 +1171,11 @@ mw_status mw_set_species(mw_system* s, int nt, const mw_params* table, const int
       q.B = (float)p.B;
       q.p = p.p;
       q.q = p.q;
+      q.rc_lo = (float)(rc - (double)q.rc);
+      q.sig_lo = (float)(p.sigma - (double)q.sig);
+      q.sig_l2e_lo = (float)(p.sigma * l2e - (double)q.sig_l2e);
+      q.gsig_l2e_lo = (float)(p.gamma * p.sigma * l2e - (double)q.gsig_l2e);
+      q.B_lo = (float)(p.B - (double)q.B);
       q.h = (float)std::sqrt(std::max(0.0, E(a, b, b).lambda * E(a, b, b).epsilon));
       q.c0 = (float)E(a, 0, 0).cos_theta0;
       for (int c = 0; c < nt; ++c) {
@@ -1331,7 +1371,7 @@ mw_status mw_step(mw_system* s, const mw_integrator* integ, int nsteps, mw_therm
     if (eng == MW_ENGINE_PERSISTENT && !persistent_available(s)) eng = MW_ENGINE_GRAPH;
     s->engine_used = eng;
     st = eng == MW_ENGINE_PERSISTENT ? run_persistent_engine(s, nsteps, last, &fetched)
-                                     : run_graph_engine(s, nsteps, last, &fetched);
+                                     : run_graph_engine(s, nsteps, last, &fetched, eng == MW_ENGINE_PLAIN);
     s->g_known_valid = false;
     if (st != MW_OK) {
       s->forces_valid = false;  // the state of an interrupted step is not a state to report forces of
@@ -1358,6 +1398,7 @@ mw_status mw_step_async(mw_system* s, const mw_integrator* integ, int nsteps) {
   if ((st = prime_thermostat(s)) != MW_OK) return st;
   s->record_pending = true;
   if (eng == MW_ENGINE_PERSISTENT) return enqueue_persistent(s, nsteps);
+  if (eng == MW_ENGINE_PLAIN) return launch_plain_steps(s, nsteps);
   if (s->graph_dirty || !s->graph1) {
     if ((st = capture_graphs(s, 16)) != MW_OK) return st;
   }
@@ -1435,7 +1476,8 @@ mw_status mw_set_wait_limit(mw_system* s, double seconds) {
 }
 
 mw_status mw_set_engine(mw_system* s, int engine) {
-  if (!s || engine < MW_ENGINE_AUTO || engine > MW_ENGINE_PERSISTENT) return fail(MW_EINVAL, "bad engine");
+  if (!s || engine < MW_ENGINE_AUTO || engine > MW_ENGINE_PLAIN) return fail(MW_EINVAL, "bad engine");
+  if (engine == MW_ENGINE_PLAIN && s->nsp > 1) return fail(MW_EINVAL, "the plain engine has one species only");
   s->engine = engine;
   return MW_OK;
 }
@@ -1535,22 +1577,36 @@ static_assert(kNaEnd <= MW_NOALLOC_SCRATCH_BYTES, "no-alloc scratch layout excee
 __device__ __align__(256) unsigned char g_noalloc_scratch[MW_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kNaMaxDevices = 64;
-unsigned char* g_na_base[kNaMaxDevices] = {nullptr};
+// Device address of the array, per device; each slot is written once (by the
+// first call that finds it empty; concurrent first calls store the same
+// value).  A cudaDeviceReset between calls is not supported: the cached
+// address would belong to the old context.
+std::atomic<unsigned char*> g_na_base[kNaMaxDevices];
 
-// Positions (AoS doubles, caller's order) -> fixed point, box 0; zero forces.
+// Positions (AoS doubles, caller's order) -> fixed point, box 0.  The same
+// conversion as the regular path (box fraction, its 64-bit fraction, then the
+// 32-bit rounding), so both entry points see the same coordinates.  A
+// non-finite value is replaced by 0 and reported (ST_INPUT, the atom in
+// err_index); the host then refuses the call.
 __global__ void k_na_load(Dev d, const double* __restrict__ x) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
   const Box& bx = d.box[0];
-  uint32_t q[3];
+  unsigned long long p[3];
   for (int k = 0; k < 3; ++k) {
     double v = x[3 * (size_t)i + k];
-    v -= bx.L[k] * floor(v / bx.L[k]);
-    if (v >= bx.L[k]) v -= bx.L[k];
+    if (!isfinite(v)) {
+      set_status(d.g, ST_INPUT);
+      d.g->err_index = i;
+      v = 0.0;
+    }
+    v /= bx.L[k];
+    v -= floor(v);
+    if (v >= 1.0) v -= 1.0;
     if (v < 0.0) v = 0.0;
-    q[k] = to_fixed(v, bx.qs[k]);
+    p[k] = frac64_of(v);
   }
-  d.q[i] = make_uint4(q[0], q[1], q[2], 0u);
+  d.q[i] = make_uint4(q_of(p[0]), q_of(p[1]), q_of(p[2]), 0u);
 }
 
 // Cell-sorted copy of the fixed-point positions and their original indices.
@@ -1563,7 +1619,10 @@ __global__ void k_na_scatter(Dev d, uint4* __restrict__ tq) {
 }
 
 // Sorted forces -> caller's order; energies and virial of the box.
+// Nothing is written after a device error (the sorted order may then be
+// incomplete, and the host reports the error instead).
 __global__ void k_na_out(Dev d, float* __restrict__ f, double* __restrict__ e, double* __restrict__ w) {
+  if (*(volatile int*)&d.g->status) return;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < d.N && f) {
     const int u = d.tid[p];
@@ -1588,13 +1647,15 @@ mw_status na_base(unsigned char** out) {
   int dev = 0;
   MW_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNaMaxDevices) return fail(MW_EINVAL, "device index %d out of range", dev);
-  if (!g_na_base[dev]) {
+  unsigned char* b = g_na_base[dev].load(std::memory_order_acquire);
+  if (!b) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) return fail(MW_ECUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-    g_na_base[dev] = (unsigned char*)p;
+    b = (unsigned char*)p;
+    g_na_base[dev].store(b, std::memory_order_release);
   }
-  *out = g_na_base[dev];
+  *out = b;
   return MW_OK;
 }
 
@@ -1604,6 +1665,14 @@ extern "C" mw_status mw_energy_forces_noalloc(int n, const double box[3], const 
                                               const double* x_dev, float* f_dev, double* energy_dev,
                                               double* virial_dev, void* stream) {
   if (n < 2 || !box || !x_dev) return fail(MW_EINVAL, "need n >= 2, box and x_dev");
+  {
+    // every call ends with a device-to-host read and a stream synchronisation,
+    // which a capturing stream cannot do (and the capture would be invalidated)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MW_CUDA(cudaStreamIsCapturing((cudaStream_t)stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(MW_EINVAL, "mw_energy_forces_noalloc cannot run on a stream that is being captured");
+  }
   if (n > MW_NOALLOC_MAX_ATOMS)
     return fail(MW_EINVAL, "n = %d exceeds the no-alloc limit of %d atoms", n, MW_NOALLOC_MAX_ATOMS);
   mw_status st;
@@ -1689,6 +1758,7 @@ extern "C" mw_status mw_energy_forces_noalloc(int n, const double box[3], const 
   if (gout.status == ST_OVERFLOW)
     return fail(MW_ENLIST_OVERFLOW, "an atom has %d neighbours within r_list; the no-alloc limit is %d",
                 gout.max_count, MW_NOALLOC_MAX_WIDTH);
+  if (gout.status == ST_INPUT) return fail(MW_EINVAL, "non-finite position of atom %d", gout.err_index);
   if (gout.status) return status_error(gout);
   return MW_OK;
 }

@@ -127,11 +127,15 @@ struct Integ {
 constexpr double kCellMargin = 1.12;
 constexpr double kCellGrow = 1.2;
 
-struct FParams {     // FP32 constants of the force kernels
+// FP32 constants of the force kernels.  The *_lo fields hold the FP32
+// rounding error of the constant before them (value = hi + lo to ~2^-48),
+// which leg_terms adds back at first order.
+struct FParams {
   float rc, rc2, rl2;
   float sig, sig_l2e, gsig_l2e, gsig;
   float Aeps, B, c0, sle;  // sle = sqrt(lambda eps)
   int p, q;
+  float rc_lo, sig_lo, sig_l2e_lo, gsig_l2e_lo, B_lo;
 };
 
 // Several species: FP32 constants of the pair (a, b), from the parameter
@@ -145,7 +149,10 @@ struct SpPair {
   float rc, rc2, sig, sig_l2e, gsig, gsig_l2e, Aeps, B;
   int p, q;
   float h, c0;
+  float rc_lo, sig_lo, sig_l2e_lo, gsig_l2e_lo, B_lo;  // as in FParams
 };
+
+
 
 struct Dev {
   int N, W, ncell, nbox;
@@ -245,6 +252,98 @@ __device__ __forceinline__ float powi(float x, int n) {
   float r = 1.0f;
   for (int k = 0; k < n; ++k) r *= x;
   return r;
+}
+
+// ---------------------------------------------------------------------------
+// One leg's terms (Sec. II.A) to about one FP32 ulp each.  The exponentials
+// exp(sig/(r - a sig)) and exp(gam sig/(r - a sig)) amplify a relative error
+// of their argument by the argument's size (about 2 at the first shell), and
+// at the first shell the derivative of the pair term is a difference of two
+// parts five to twenty times larger than itself (it vanishes at the phi2
+// minimum).  So r, 1/r, 1/(r - a sig), the exponent arguments and the pair
+// derivative carry their first-order rounding corrections:
+//   r = RN(sqrt r2) + dr, dr = (r2 - r^2) / (2 r) (the residual by one FMA);
+//   1/r = v (1 + ev), v = RN(1/RN(r)), ev = (1 - r v) - dr v;
+//   x = r - a sig = (r - rc) + (dr - rc_lo) (r - rc exact for r >= rc / 2);
+//   1/x = t (1 + tc), t = RN(1/(r - rc)), tc = (1 - (r - rc) t) - (dr - rc_lo) t;
+//   exp2(k / x) = exp2(k t) (1 + ln 2 (k t tc + RN residual of k t + k_lo t)).
+// For the SW exponents (p, q) = (4, 0) the pair derivative
+//   dphi2/dr = A eps e2 [(1 - y) sig / x^2 - 4 y / r],  y = B (sig / r)^4,
+// is formed from hi + lo pairs (exact products by FMA, two-sum at the final
+// difference); other exponents take the plain FP32 formula.  Returns false
+// (nothing to add) when the leg is not inside a sig.
+struct LegTerms {
+  float r, invr;  // |d|, 1 / |d|
+  float e3;       // exp(gam sig / (r - a sig))
+  float nde;      // gam sig / (r - a sig)^2
+  float phi;      // phi2(r)
+  float dphi;     // dphi2 / dr
+};
+
+template <class C>
+__device__ __forceinline__ bool leg_terms(float r2, const C& c, LegTerms& o) {
+  constexpr float kLn2 = 0.693147180559945f;
+  const float r = __fsqrt_rn(r2);
+  if (!(r < c.rc)) return false;
+  const float v = __frcp_rn(r);
+  const float dr = 0.5f * fmaf(-r, r, r2) * v;
+  const float ev = fmaf(-r, v, 1.0f) - dr * v;
+  const float xh = r - c.rc;
+  const float xl = dr - c.rc_lo;
+  const float t = __frcp_rn(xh);  // < 0
+  const float tc = fmaf(-xh, t, 1.0f) - xl * t;
+  const float a2 = c.sig_l2e * t;
+  const float a2l = fmaf(c.sig_l2e, t, -a2) + fmaf(a2, tc, c.sig_l2e_lo * t);
+  float e2 = exp2f(a2);
+  e2 = fmaf(e2, kLn2 * a2l, e2);
+  const float a3 = c.gsig_l2e * t;
+  const float a3l = fmaf(c.gsig_l2e, t, -a3) + fmaf(a3, tc, c.gsig_l2e_lo * t);
+  const float e3 = exp2f(a3);
+  o.e3 = fmaf(e3, kLn2 * a3l, e3);
+  const float invr = fmaf(v, ev, v);
+  const float t2 = t * t;
+  const float t2l = fmaf(t, t, -t2) + 2.0f * t2 * tc;  // t^2 (1 + 2 tc) = t2 + t2l
+  o.r = r + dr;
+  o.invr = invr;
+  o.nde = c.gsig * fmaf(t2, 2.0f * tc, t2);
+  const float ae2 = c.Aeps * e2;
+  if (c.p == 4 && c.q == 0) {
+    // u = sig / r, y = B u^4, each as hi + lo
+    const float uh = c.sig * v;
+    const float ul = fmaf(c.sig, v, -uh) + fmaf(uh, ev, c.sig_lo * v);
+    const float u2 = uh * uh;
+    const float u2l = fmaf(uh, uh, -u2) + 2.0f * uh * ul;
+    const float u4 = u2 * u2;
+    const float u4l = fmaf(u2, u2, -u4) + 2.0f * u2 * u2l;
+    const float yh = c.B * u4;
+    const float yl = fmaf(c.B, u4, -yh) + fmaf(c.B, u4l, c.B_lo * u4);
+    // 1 - y by two-sum (y exceeds 1 only for atoms closer than 2.1 A)
+    const float om = 1.0f - yh;
+    const float ob = om - 1.0f;
+    const float oml = ((1.0f - (om - ob)) + (-yh - ob)) - yl;
+    // part 1: (1 - y) sig t^2
+    const float qh = c.sig * t2;
+    const float ql = fmaf(c.sig, t2, -qh) + fmaf(c.sig, t2l, c.sig_lo * t2);
+    const float p1 = om * qh;
+    const float p1l = fmaf(om, qh, -p1) + fmaf(om, ql, oml * qh);
+    // part 2: -4 y / r
+    const float p2 = -4.0f * (yh * v);
+    const float p2l = -4.0f * (fmaf(yh, v, -yh * v) + fmaf(yh * v, ev, yl * v));
+    // their sum by two-sum, the low parts added once
+    const float sh = p1 + p2;
+    const float bb = sh - p1;
+    const float se = (p1 - (sh - bb)) + (p2 - bb);
+    const float g = sh + (se + p1l + p2l);
+    o.dphi = ae2 * g;
+    o.phi = -ae2 * (om + oml);
+  } else {
+    const float sr = c.sig * invr;
+    const float srp = powi(sr, c.p), srq = powi(sr, c.q);
+    const float brk = fmaf(c.B, srp, -srq);
+    o.phi = ae2 * brk;
+    o.dphi = ae2 * (fmaf((float)(-c.p) * c.B, srp, (float)c.q * srq) * invr - brk * c.sig * fmaf(t2, 2.0f * tc, t2));
+  }
+  return true;
 }
 
 __device__ __forceinline__ int cell_of(const uint4& q, const Box& bx) {
@@ -937,32 +1036,26 @@ __device__ __noinline__ void force_overflow_item(const Dev& d, const FParams& P,
                 dz = fix_diff(qi.z, qj.z, bx.Lq[2]);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     if (r2 >= P.rc2) continue;
-    const float invr = rsqrtf(r2);
-    const float r = r2 * invr;
-    if (!(r < P.rc)) continue;
+    LegTerms lt;
+    if (!leg_terms(r2, P, lt)) continue;
     if (nl >= kMaxLegsOverflow) {
       set_status(d.g, ST_LEGS);
       d.g->err_index = i;
       return;
     }
-    const float tinv = __frcp_rn(r - P.rc);
+    const float invr = lt.invr, r = lt.r;
     ux[nl] = dx * invr;
     uy[nl] = dy * invr;
     uz[nl] = dz * invr;
     tr[nl] = 2.0f * invr;
-    nde[nl] = P.gsig * tinv * tinv;
-    ee[nl] = P.sle * exp2f(P.gsig_l2e * tinv);
+    nde[nl] = lt.nde;
+    ee[nl] = P.sle * lt.e3;
     rr[nl] = r;
     jj[nl] = j;
     ax[nl] = ay[nl] = az[nl] = 0.f;
     {  // pair term, owner computes (half energy, full force on the centre, half virial)
-      const float e2 = exp2f(P.sig_l2e * tinv);
-      const float sr = P.sig * invr;
-      const float srp = powi(sr, P.p), srq = powi(sr, P.q);
-      const float brk = fmaf(P.B, srp, -srq);
-      const float ae2 = P.Aeps * e2;
-      const float dphi = ae2 * (fmaf((float)(-P.p) * P.B, srp, (float)P.q * srq) * invr - brk * P.sig * tinv * tinv);
-      e2acc = fmaf(0.5f * ae2, brk, e2acc);
+      const float dphi = lt.dphi;
+      e2acc = fmaf(0.5f, lt.phi, e2acc);
       px = fmaf(dphi, ux[nl], px);
       py = fmaf(dphi, uy[nl], py);
       pz = fmaf(dphi, uz[nl], pz);
@@ -1129,50 +1222,27 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
     float4* ue_p = T.ue + a * kLP + l;
     float4* ax_p = T.aux + a * kLP + l;
     const float4 rec = *ue_p;
-    // the leg's constants: the one species', or its pair's (kSp)
-    float p_rc = P.rc, p_sig = P.sig, p_sig_l2e = P.sig_l2e, p_gsig = P.gsig, p_gsig_l2e = P.gsig_l2e;
-    float p_Aeps = P.Aeps, p_B = P.B, p_h = P.sle;
-    int p_p = P.p, p_q = P.q;
+    // the leg's terms with the one species' constants, or its pair's (kSp)
+    LegTerms lt;
+    float p_h = P.sle;
+    bool in;
     if constexpr (kSp) {
       const SpPair& pp = spi[__float_as_int(ax_p->x)];
-      p_rc = pp.rc;
-      p_sig = pp.sig;
-      p_sig_l2e = pp.sig_l2e;
-      p_gsig = pp.gsig;
-      p_gsig_l2e = pp.gsig_l2e;
-      p_Aeps = pp.Aeps;
-      p_B = pp.B;
       p_h = kSp == 2 ? 1.0f : pp.h;  // kSp = 2: the strengths come per leg pair in phase C
-      p_p = pp.p;
-      p_q = pp.q;
+      in = leg_terms(rec.w, pp, lt);
+    } else {
+      in = leg_terms(rec.w, P, lt);
     }
-    const float r2 = rec.w;
-    const float invr = rsqrtf(r2);
-    const float r = r2 * invr;
-    if (!(r < p_rc)) {  // FP32 rounding put it on the cutoff (or past its pair's): contributes nothing
+    if (!in) {  // FP32 rounding put it on the cutoff (or past its pair's): contributes nothing
       *ue_p = make_float4(0.f, 0.f, 0.f, 0.f);
       continue;
     }
     if constexpr (kSp && kCount) ++nvalid;
-    const float ux = rec.x * invr, uy = rec.y * invr, uz = rec.z * invr;
-    const float tinv = __fdividef(1.0f, r - p_rc);  // 1/(r - a sig) < 0
-    const float e2 = exp2f(p_sig_l2e * tinv);
-    const float ee = p_h * exp2f(p_gsig_l2e * tinv);
-    const float sr = p_sig * invr;
-    float srp, srq;
-    if (p_p == 4 && p_q == 0) {  // the SW / mW exponents
-      const float sr2 = sr * sr;
-      srp = sr2 * sr2;
-      srq = 1.0f;
-    } else {
-      srp = powi(sr, p_p);
-      srq = powi(sr, p_q);
-    }
-    const float brk = fmaf(p_B, srp, -srq);
-    const float ae2 = p_Aeps * e2;
-    const float phi = ae2 * brk;
-    const float dphi = ae2 * (fmaf((float)(-p_p) * p_B, srp, (float)p_q * srq) * invr - brk * p_sig * tinv * tinv);
-    acc[0] = fmaf(0.5f, phi, acc[0]);
+    const float r = lt.r;
+    const float ux = rec.x * lt.invr, uy = rec.y * lt.invr, uz = rec.z * lt.invr;
+    const float ee = p_h * lt.e3;
+    const float dphi = lt.dphi;
+    acc[0] = fmaf(0.5f, lt.phi, acc[0]);
     fx = fmaf(dphi, ux, fx);
     fy = fmaf(dphi, uy, fy);
     fz = fmaf(dphi, uz, fz);
@@ -1193,7 +1263,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
     // (-1/2 dphi: the pair term's share of the virial, taken in phase C), nde, r, j
     // (kSp = 2: j with the partner's species in bits 28-30)
     const float jw = kSp == 2 ? __int_as_float(__float_as_int(ax_p->w) | (__float_as_int(ax_p->x) << 28)) : ax_p->w;
-    *ax_p = make_float4(-0.5f * dphi, p_gsig * tinv * tinv, r, jw);
+    *ax_p = make_float4(-0.5f * dphi, lt.nde, r, jw);
     if constexpr (kSp == 2) continue;  // no moments
     const float ex = ee * ux, ey = ee * uy, ez = ee * uz;
     m0 += ee;
@@ -1232,7 +1302,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
       const int wj = __float_as_int(xj.w);
       const float2* stj = stc + (wj >> 28) * nsp;
       const float r = xj.z;
-      const float tr = __fdividef(2.0f, r);
+      const float tr = 2.0f * __frcp_rn(r);
       const float nde = xj.y;
       float gx = 0.f, gy = 0.f, gz = 0.f;  // three-body force on the partner of leg j
       for (int k = 0; k < nstage; ++k) {
@@ -1265,37 +1335,44 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
   // ---- leg phase C: three-body force on each leg partner from the moments
   const float c0 = (kSp && valid) ? spi[0].c0 : P.c0;
   const float s0c = c0 * c0 * m0;
-  const float oc0 = 1.0f - c0;  // D_jj with c_jj = |u_j|^2 = 1
+  // a centre with one leg has no three-body term: its moments hold only that
+  // leg, whose self term cancels up to rounding; the residue is not computed
+  const bool three = nstage > 1;  // (uniform over the centre's lane group)
   for (int l = g; l < nstage; l += kG) {
     const float4 uj = T.ue[a * kLP + l];
     const float4 xj = T.aux[a * kLP + l];
     const float ee = uj.w;
     if (ee == 0.f) continue;  // leg dropped in phase B
-    const float mx = fmaf(mxx, uj.x, fmaf(mxy, uj.y, mxz * uj.z));  // M u_j
-    const float my = fmaf(mxy, uj.x, fmaf(myy, uj.y, myz * uj.z));
-    const float mz = fmaf(mxz, uj.x, fmaf(myz, uj.y, mzz * uj.z));
-    const float qm = fmaf(uj.x, mx, fmaf(uj.y, my, uj.z * mz));     // u_j.M u_j
-    const float ps = fmaf(uj.x, msx, fmaf(uj.y, msy, uj.z * msz));  // u_j.s
-    // the k = j term taken back out with c_jj = 1 (|u_j|^2 - 1 ~ 1e-7 leaves a
-    // residue of that relative size in the smallest terms)
-    const float self = ee * oc0;
-    const float Bj = fmaf(-c0, ps, qm) - self;
-    const float Cj = fmaf(-2.0f * c0, ps, qm + s0c) - self * oc0;
-    const float Ax = fmaf(-c0, msx, mx) - self * uj.x;
-    const float Ay = fmaf(-c0, msy, my) - self * uj.y;
-    const float Az = fmaf(-c0, msz, mz) - self * uj.z;
     const float r = xj.z;
-    const float tr = __fdividef(2.0f, r);
-    const float et = ee * tr;                            // ee_j tr_j
-    const float cu = ee * fmaf(xj.y, Cj, tr * Bj);       // ee_j (nde_j C_j + tr_j B_j)
-    const float gx = fmaf(cu, uj.x, -et * Ax);
-    const float gy = fmaf(cu, uj.y, -et * Ay);
-    const float gz = fmaf(cu, uj.z, -et * Az);
-    red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
-    fx -= gx;
-    fy -= gy;
-    fz -= gz;
-    acc[1] = fmaf(0.5f * ee, Cj, acc[1]);
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (three) {
+      const float mx = fmaf(mxx, uj.x, fmaf(mxy, uj.y, mxz * uj.z));  // M u_j
+      const float my = fmaf(mxy, uj.x, fmaf(myy, uj.y, myz * uj.z));
+      const float mz = fmaf(mxz, uj.x, fmaf(myz, uj.y, mzz * uj.z));
+      const float qm = fmaf(uj.x, mx, fmaf(uj.y, my, uj.z * mz));     // u_j.M u_j
+      const float ps = fmaf(uj.x, msx, fmaf(uj.y, msy, uj.z * msz));  // u_j.s
+      // the k = j term taken back out with c_jj = |u_j|^2 as computed (not 1),
+      // so that it cancels the same product inside the moments
+      const float cjj = fmaf(uj.x, uj.x, fmaf(uj.y, uj.y, uj.z * uj.z));
+      const float djj = cjj - c0;
+      const float self = ee * djj;
+      const float Bj = fmaf(-c0, ps, qm) - self * cjj;
+      const float Cj = fmaf(-2.0f * c0, ps, qm + s0c) - self * djj;
+      const float Ax = fmaf(-c0, msx, mx) - self * uj.x;
+      const float Ay = fmaf(-c0, msy, my) - self * uj.y;
+      const float Az = fmaf(-c0, msz, mz) - self * uj.z;
+      const float tr = 2.0f * __frcp_rn(r);
+      const float et = ee * tr;                            // ee_j tr_j
+      const float cu = ee * fmaf(xj.y, Cj, tr * Bj);       // ee_j (nde_j C_j + tr_j B_j)
+      gx = fmaf(cu, uj.x, -et * Ax);
+      gy = fmaf(cu, uj.y, -et * Ay);
+      gz = fmaf(cu, uj.z, -et * Az);
+      red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
+      fx -= gx;
+      fy -= gy;
+      fz -= gz;
+      acc[1] = fmaf(0.5f * ee, Cj, acc[1]);
+    }
     // virial: r u_a (g_b - 1/2 dphi u_b), the three-body and the pair part
     const float hx = fmaf(xj.x, uj.x, gx), hy = fmaf(xj.x, uj.y, gy), hz = fmaf(xj.x, uj.z, gz);
     const float rx = r * uj.x, ry = r * uj.y, rz = r * uj.z;
@@ -1795,10 +1872,13 @@ __global__ void k_gather_neighbors(Dev d, int* __restrict__ cnt_out, int* __rest
   for (int s = 0; s < m; ++s) nbr_out[(size_t)u * width + s] = d.id[d.nbr[(size_t)i * d.W + s]];
 }
 
+// Energies and virial of the latest force evaluation: the parity slot that
+// evaluation wrote (wpar).  After a step the step counter has moved on and
+// its own parity names the slot the next step clears, not this one.
 __global__ void k_energy_out(Dev d, double* e, double* w) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= d.nbox) return;
-  const int par = (int)(d.g->step & 1ull);
+  const int par = d.g->wpar;
   const BoxState* st = d.bst + b;
   if (e) {
     e[3 * b] = st->ew[par][0] + st->ew[par][1];

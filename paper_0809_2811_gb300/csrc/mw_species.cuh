@@ -49,33 +49,27 @@ __device__ int species_item(const Dev& d, const SpPair* sp, const float2* st, in
                 dz = fix_diff(qi.z, qj.z, bx.Lq[2]);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     if (r2 >= pp.rc2) continue;
-    const float invr = rsqrtf(r2);
-    const float r = r2 * invr;
-    if (!(r < pp.rc)) continue;
+    LegTerms lt;
+    if (!leg_terms(r2, pp, lt)) continue;
     if (nl >= kMaxLegsOverflow) {
       set_status(d.g, ST_LEGS);
       d.g->err_index = i;
       break;
     }
-    const float tinv = __frcp_rn(r - pp.rc);
+    const float invr = lt.invr, r = lt.r;
     ux[nl] = dx * invr;
     uy[nl] = dy * invr;
     uz[nl] = dz * invr;
     tr[nl] = 2.0f * invr;
-    nde[nl] = pp.gsig * tinv * tinv;
-    ee[nl] = exp2f(pp.gsig_l2e * tinv);
+    nde[nl] = lt.nde;
+    ee[nl] = lt.e3;
     rr[nl] = r;
     jj[nl] = j;
     tt[nl] = tj;
     ax[nl] = ay[nl] = az[nl] = 0.f;
     {  // pair term
-      const float e2 = exp2f(pp.sig_l2e * tinv);
-      const float sr = pp.sig * invr;
-      const float srp = powi(sr, pp.p), srq = powi(sr, pp.q);
-      const float brk = fmaf(pp.B, srp, -srq);
-      const float ae2 = pp.Aeps * e2;
-      const float dphi = ae2 * (fmaf((float)(-pp.p) * pp.B, srp, (float)pp.q * srq) * invr - brk * pp.sig * tinv * tinv);
-      acc[0] = fmaf(0.5f * ae2, brk, acc[0]);
+      const float dphi = lt.dphi;
+      acc[0] = fmaf(0.5f, lt.phi, acc[0]);
       px = fmaf(dphi, ux[nl], px);
       py = fmaf(dphi, uy[nl], py);
       pz = fmaf(dphi, uz[nl], pz);

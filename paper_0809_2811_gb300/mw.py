@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libmw.so")
 STATUS_NAMES = {0: "MW_OK", 1: "MW_EINVAL", 2: "MW_EBOX", 3: "MW_ENLIST_OVERFLOW", 4: "MW_ENAN", 5: "MW_ELOST",
                 6: "MW_ETIMEOUT", 7: "MW_ECUDA", 8: "MW_ENOMEM", 9: "MW_ESTATE", 10: "MW_EGRID"}
 MW_NVE, MW_BERENDSEN, MW_NOSE_HOOVER, MW_NPT = 0, 1, 2, 3
-MW_ENGINE_AUTO, MW_ENGINE_GRAPH, MW_ENGINE_PERSISTENT = 0, 1, 2
+MW_ENGINE_AUTO, MW_ENGINE_GRAPH, MW_ENGINE_PERSISTENT, MW_ENGINE_PLAIN = 0, 1, 2, 3
 
 # every symbol include/mw.h declares
 EXPORTS = (
@@ -207,9 +207,14 @@ def mw_set_state_dev(h: int, x_dev, v_dev=None):
     _check(lib().mw_set_state_dev(h, _ptr(x_dev), _ptr(v_dev)))
 
 
-def mw_get_state(h: int, n_total: int):
-    x = np.empty((n_total, 3))
-    v = np.empty((n_total, 3))
+def mw_get_state(h: int, n_total: int, x_out: Optional[np.ndarray] = None, v_out: Optional[np.ndarray] = None):
+    """Positions and velocities (n_total, 3) into new arrays, or into the given
+    C-contiguous float64 arrays (e.g. page-locked ones)."""
+    x = np.empty((n_total, 3)) if x_out is None else x_out
+    v = np.empty((n_total, 3)) if v_out is None else v_out
+    for a in (x, v):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != 3 * n_total:
+            raise ValueError("state outputs must be C-contiguous float64 arrays of n_total x 3")
     _check(lib().mw_get_state(h, _dp(x), _dp(v)))
     return x, v
 
@@ -448,8 +453,8 @@ class System:
     def set_state(self, x, v=None):
         mw_set_state(self.h, x, v)
 
-    def get_state(self):
-        return mw_get_state(self.h, self.n_total)
+    def get_state(self, x_out=None, v_out=None):
+        return mw_get_state(self.h, self.n_total, x_out, v_out)
 
     def energy_forces(self):
         return mw_energy_forces(self.h, self.n_total, self.nbox)

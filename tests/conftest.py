@@ -30,3 +30,20 @@ def mwlib():
     build.build()
     mw.lib()
     return mw
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """Prints each parity comparison's errors as fractions of its tolerances
+    (force, energy, virial; 1.0 = at the tolerance) and the strict per-atom
+    relative force error."""
+    try:
+        import _parity
+    except ImportError:
+        return
+    if not _parity.MARGINS:
+        return
+    tr = terminalreporter
+    tr.section("parity margins (error / tolerance; strict = max |dF|/|F| over |F| >= eps/sigma)")
+    for case, m in _parity.MARGINS:
+        tr.write_line(f"{case:48s} force {m.get('force', float('nan')):.3f}  energy {m.get('energy', float('nan')):.3f}"
+                      f"  virial {m.get('virial', float('nan')):.3f}  strict {m.get('strict_force_rel', float('nan')):.2e}")

@@ -35,7 +35,7 @@ def _run_pair(mwlib, orc, x, v, box, nsteps, kind, T0=298.0, tau=1000.0, dt=10.0
     return th, xg, vg, tho[-1], xo, vo, st
 
 
-ENGINES = {"graph": 1, "persistent": 2}
+ENGINES = {"graph": 1, "persistent": 2, "plain": 3}
 
 
 @pytest.mark.parametrize("engine", sorted(ENGINES))

@@ -40,8 +40,9 @@ def test_clock_summary_reads_throttle_reasons():
 
 
 def test_traffic_is_reported_only_for_the_profiled_source(tmp_path, monkeypatch):
-    """DRAM traffic comes from the committed ncu record only while the kernel
-    source hashes to the recorded value; any edit of the source gives null."""
+    """DRAM traffic comes from the committed ncu record of the same workload
+    size only while the kernel source hashes to the recorded value; any edit
+    of the source gives null."""
     import hashlib
     import json
     import bench
@@ -50,8 +51,12 @@ def test_traffic_is_reported_only_for_the_profiled_source(tmp_path, monkeypatch)
     prof = tmp_path / "profiles"
     prof.mkdir()
     h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
-    (prof / "sw_force_traffic.json").write_text(json.dumps({"source_hash": h, "dram_bytes_per_launch_scaled": 123}))
+    (prof / "sw_force_traffic.json").write_text(json.dumps(
+        [{"source_hash": h, "atoms": 1000, "dram_bytes_per_launch": 123},
+         {"source_hash": h, "atoms": 2000, "dram_bytes_per_launch": 456}]))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.traffic_from_profile(str(src)) == 123
+    assert bench.traffic_from_profile(str(src), 1000) == 123
+    assert bench.traffic_from_profile(str(src), 2000) == 456
+    assert bench.traffic_from_profile(str(src), 3000) is None  # no capture of this size
     src.write_text("// kernel v2\n")
-    assert bench.traffic_from_profile(str(src)) is None
+    assert bench.traffic_from_profile(str(src), 1000) is None

@@ -638,3 +638,49 @@ def test_species_npt_with_one_type_is_the_one_species_run(orc):
     assert np.abs(xa - xb).max() < 1e-9 and np.abs(va - vb).max() < 1e-12
     assert np.abs(ba - bb).max() < 1e-12 and ba[0] != box[0]
     assert tha[-1, 5] == pytest.approx(thb[-1, 5], rel=1e-12)
+
+
+# ---- owner-computes routine (the multi-core CPU baseline) -----------------
+
+@pytest.mark.parametrize("threads", [1, 4])
+@pytest.mark.parametrize("case", ["liquidlike", "ice", "dense_overflow", "small_box", "cluster"])
+def test_owner_computes_equals_cell_list(orc, case, threads):
+    """The owner-computes grouping (pair halves, terms centred on the atom, the
+    atom as a leg of its neighbours' terms) is the same sum as the cell-list
+    loop; the brute-force pin above ties that loop to the definition.  A
+    dropped two-hop term, a wrong sign of a reaction or a double-counted pair
+    half shows up here as an O(1) difference."""
+    if case == "liquidlike":
+        x, box = I.jittered_box(1000, 1.0, 0.3, 301)
+    elif case == "ice":
+        x, box = I.ice_ih(4, 3, 3, 0.92)
+    elif case == "dense_overflow":
+        x, box = I.jittered_box(512, 3.5, 0.1, 302)
+    elif case == "small_box":
+        rng = np.random.default_rng(303)
+        L = 9.5
+        x, box = _rand_box(rng, 24, L), np.array([L, L, L])
+    else:
+        rng = np.random.default_rng(304)
+        x = _rand_box(rng, 10, 5.0, dmin=2.2, periodic=False) + 4.0
+        box = np.array([14.0, 14.0, 14.0])
+    a = orc.energy_forces(x, box, method="cell")
+    b = orc.energy_forces(x, box, method="owner", threads=threads)
+    assert a["npairs"] == b["npairs"] and a["ntriplets"] == b["ntriplets"]
+    for k in ("e2", "e3"):
+        assert b[k] == pytest.approx(a[k], rel=1e-12, abs=1e-9)
+    scale = max(np.abs(a["forces"]).max(), 1.0)
+    np.testing.assert_allclose(b["forces"], a["forces"], rtol=0, atol=1e-11 * scale)
+    np.testing.assert_allclose(b["virial"], a["virial"], rtol=0, atol=1e-12 * a["virial_abs"] + 1e-12)
+    assert b["virial_abs"] == pytest.approx(a["virial_abs"], rel=1e-12)
+
+
+def test_owner_computes_dynamics_follow_the_serial_run(orc):
+    """Nose-Hoover steps with the threaded owner forces stay on the serial
+    run's trajectory (rounding-order differences only)."""
+    x, v, box = I.nve512()
+    xa, va, sa, tha = orc.md(x, v, box, 20, dt=10.0, kind=2, T0=298.0, tau=1000.0)
+    xb, vb, sb, thb = orc.md(x, v, box, 20, dt=10.0, kind=2, T0=298.0, tau=1000.0, threads=4)
+    d = np.mod(xa - xb + box / 2, box) - box / 2
+    assert np.abs(d).max() < 1e-9
+    np.testing.assert_allclose(thb[:, 5], tha[:, 5], rtol=1e-10)

@@ -66,8 +66,11 @@ def parse():
                     choices=["slab1m", "ice_liquid_32k", "nve512", "batch256", "fm4096x64", "structure_32k",
                              "slab_gamma", "diffusion_4096", "npt_density_scan", "solute_32k"])
     ap.add_argument("--no-extra", action="store_true", help="skip the two-box 65536-atom line under 'extra'")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain GPU path beside the line")
     ap.add_argument("--drift-steps", type=int, default=0,
                     help="after timing, run this many NVE steps and report the energy drift per ns")
+    ap.add_argument("--drift-prep", type=int, default=200,
+                    help="Nose-Hoover steps from the start state before the NVE drift segment")
     return ap.parse_args()
 
 
@@ -324,6 +327,34 @@ def force_roofline(mw, sysm, integ, nsteps=20):
     return roof, phases
 
 
+def plain_path_rate(torch, mw, x, v, box, integ, K, W, sp, stream, dev, pg, world):
+    """The same workload on the plain GPU path (MW_ENGINE_PLAIN: one thread
+    per atom in the force kernel, every phase launched from the host each
+    step, no graph), untuned (the library's default 1 A skin): W warm-up
+    steps, then K steps timed with CUDA events on the stream."""
+    s = mw.System(len(x), box, stream=sp)
+    try:
+        s.set_engine(mw.MW_ENGINE_PLAIN)
+        s.set_state(x, v)
+        mw.mw_step(s.h, integ, max(W, 3), s.nbox)
+        e0, e1 = _events(torch, 2)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        mw.mw_step_async(s.h, integ, K)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        mw.mw_sync(s.h)
+        span = reduce_max(pg, e0.elapsed_time(e1) / 1e3, dev)
+        fms = mw.mw_phase_times(s.h, integ, 5)["force"]
+        info = s.info()
+        return {"value": world * len(x) * K / span, "unit": UNIT, "ms_per_step": 1e3 * span / K,
+                "force_kernel_ms": fms, "r_list_A": info["r_list"], "engine": "plain",
+                "launches_per_step": "kick1 + 5 rebuild kernels + k_force_plain + kick2 (rebuild kernels return "
+                                     "at once on steps without a rebuild)"}
+    finally:
+        s.close()
+
+
 def e2e_round_trip(torch, mw, sysm, integ, x, v, steps, world, pg, dev):
     """End to end through the public API with host buffers: every step sets
     the state from page-locked host x, v (read in place by the loading
@@ -417,6 +448,9 @@ def run_headline(args, world, rank, local, pg):
     e2e = None
     if not args.no_e2e:
         e2e = e2e_round_trip(torch, mw, sysm, integ, x, v, min(K, 20), world, pg, dev)
+    plain = None
+    if not args.no_plain:
+        plain = plain_path_rate(torch, mw, x, v, box, integ, K, args.warmup, sp, stream, dev, pg, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_legs(x, v, box, T_SLAB, "2^20-atom slab")
@@ -433,11 +467,16 @@ def run_headline(args, world, rank, local, pg):
                    "timed_call": f"one mw_step_async({K}) call",
                    "engine": {1: "graph", 2: "persistent"}.get(eng, str(eng)),
                    "nbr_width": info["nbr_width"], "r_list_A": info["r_list"], "autotuned": tuned is not None,
+                   "force_shape": f"{info['force_lanes']} lanes/centre x {info['force_blocks_per_sm']} blocks/SM"
+                                  + (" (per-phase kernel; the persistent force phase has its own)"
+                                     if eng == mw.MW_ENGINE_PERSISTENT else ""),
                    "persistent_blocks": info["persistent_blocks"] if eng == mw.MW_ENGINE_PERSISTENT else None,
                    "wall_s_timed": t_wall, "T_after_K": th1[0]["temperature"]},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "plain_gpu_path": plain,
+        "vs_plain": (value / plain["value"]) if plain else None,
         "gpu_launches": None,
         "phase_ms": {k: round(val, 5) for k, val in phases.items()},
         "clocks": clk,
@@ -450,8 +489,8 @@ def run_headline(args, world, rank, local, pg):
     out["config"]["box_rebuilds_in_timed_region"] = rebuilds
     if args.drift_steps > 0:
         sysm.set_state(x, v)
-        mw.mw_step(sysm.h, integ, 200, sysm.nbox)
-        out["nve"] = _nve_drift(mw, sysm, args.drift_steps, DT, n)
+        mw.mw_step(sysm.h, integ, args.drift_prep, sysm.nbox)
+        out["nve"] = {**_nve_drift(mw, sysm, args.drift_steps, DT, n), "nh_steps_before": args.drift_prep}
     sysm.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -584,9 +623,53 @@ def _timed_steps(torch, mw, sysm, integ, stream, K, flush):
     return sum(a.elapsed_time(c) for a, c in zip(ev0, ev1)) / 1e3
 
 
+def batch_plain_rate(torch, mw, n, boxes, x, v, T, K, W, sp, stream, dev, pg, world):
+    """The batch on the plain GPU path: one single-box system per box, each on
+    MW_ENGINE_PLAIN (per-phase launches, thread-per-atom force, no graph), all
+    on one stream; a batch step is one step of every box, box after box."""
+    systems, integs = [], []
+    off = 0
+    try:
+        for b in range(len(n)):
+            s = mw.System(int(n[b]), boxes[b], stream=sp)
+            s.set_engine(mw.MW_ENGINE_PLAIN)
+            s.set_state(x[off:off + n[b]], v[off:off + n[b]])
+            off += int(n[b])
+            ig = mw.make_integrator(10.0, mw.MW_NOSE_HOOVER, float(T[b]), TAU)
+            mw.mw_step(s.h, ig, max(W, 3), 1)
+            systems.append(s)
+            integs.append(ig)
+        e0, e1 = _events(torch, 2)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(K):
+            for s, ig in zip(systems, integs):
+                mw.mw_step_async(s.h, ig, 1)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        for s in systems:
+            mw.mw_sync(s.h)
+        span = reduce_max(pg, e0.elapsed_time(e1) / 1e3, dev)
+        natoms = int(np.sum(n))
+        return {"value": world * natoms * K / span, "unit": UNIT, "ms_per_step": 1e3 * span / K,
+                "host_wall_ms_per_step": 1e3 * wall / K, "systems": len(systems),
+                "note": "256 single-box systems on the plain engine, stepped one after another on one stream "
+                        "(one box per launch), default 1 A skin"}
+    finally:
+        for s in systems:
+            s.close()
+
+
 def _nve_drift(mw, sysm, nsteps, dt, natoms):
     """Energy drift of an NVE segment: slope of the conserved energy (linear
-    fit over 20 points), per ns and per atom, and relative to |E|."""
+    fit over 20 points), per ns and per atom, and relative to |E|.  The
+    segment starts from the current positions and velocities with the
+    thermostat at rest (a state set again), so its conserved energy is
+    ke + pe from the first point on."""
+    x, v = sysm.get_state()
+    sysm.set_state(x, v)
     integ = mw.make_integrator(dt, mw.MW_NVE)
     es, ts = [], []
     chunk = max(1, nsteps // 20)
@@ -676,6 +759,10 @@ def run_other(args, world, rank, local, pg):
     span = _timed_steps(torch, mw, sysm, integ, stream, K, flush_use)
     span_max = reduce_max(pg, span, dev)
     rebuilds = sum(t["rebuilds"] for t in sysm.thermo()) - reb0
+    if args.workload == "batch256" and not args.no_plain:
+        extra["plain_gpu_path"] = batch_plain_rate(torch, mw, n, boxes, x, v, T, K, args.warmup, sp, stream, dev,
+                                                   pg, world)
+        extra["vs_plain"] = (world * natoms * K / span_max) / extra["plain_gpu_path"]["value"]
     if args.drift_steps > 0:
         extra["nve"] = _nve_drift(mw, sysm, args.drift_steps, 10.0, natoms)
     info = sysm.info()
@@ -771,6 +858,7 @@ def run_fm(args, world, rank, torch, mw, dev, stream, sp, flush):
     theta = torch.tensor([21.0, 6.189 * 1.05, 2.3925 * 1.05], dtype=torch.float64, device=dev, requires_grad=True)
 
     def one_eval(k):
+        theta.grad = None  # each evaluation's gradient on its own
         th = theta if k % 2 == 0 else (theta * (1 + 1e-7))  # a new theta each evaluation: list rebuilt
         xg = X.clone().requires_grad_(True)
         loss = torch_ops.force_matching_loss(ff.forces(xg, th), f_star)
@@ -797,8 +885,60 @@ def run_fm(args, world, rank, torch, mw, dev, stream, sp, flush):
                       "loss": float(loss.item()),
                       "grad_theta": [float(v) for v in theta.grad.tolist()] if theta.grad is not None else None}}
     ff.close()
+    if not args.no_plain:
+        pl = fm_plain_fd(torch, mw, X.view(nfr, n, 3), f_star.view(nfr, n, 3), box, theta.detach(), sp, dev)
+        out["plain_gpu_path"] = pl
+        out["vs_plain"] = out["value"] / pl["value"]
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def fm_plain_fd(torch, mw, X, f_star, box, theta, sp, dev, h_rel=1e-4, reps=2):
+    """The force-matching gradient on the plain GPU path: dL/d(lambda,
+    epsilon, sigma) by central differences (h = 1e-4 relative), each of the
+    seven parameter sets one plain forward pass over the frames (one
+    single-box plain-engine system, frame after frame: load the positions,
+    rebuild the list, thread-per-atom forces).  dL/dx is not formed (by
+    differences it would take 6 N forward passes per frame).  Value: frame
+    gradient evaluations per second, as for the adjoint path."""
+    nfr, n = X.shape[0], X.shape[1]
+    s = mw.System(n, box, stream=sp)
+    f = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    try:
+        s.set_engine(mw.MW_ENGINE_PLAIN)
+
+        def loss_at(th):
+            p = mw.mw_params_default()
+            p.lambda_, p.epsilon, p.sigma = (float(t) for t in th)
+            s.set_params(p)
+            acc = torch.zeros((), dtype=torch.float64, device=dev)
+            for k in range(nfr):
+                mw.mw_energy_forces_dev(s.h, X[k], f, None, None)
+                acc += ((f.to(torch.float64) - f_star[k].to(torch.float64)) ** 2).sum()
+            return acc / (3 * n * nfr)
+
+        def grad():
+            g = []
+            for k in range(3):
+                hk = h_rel * abs(float(theta[k]))
+                tp, tm = theta.clone(), theta.clone()
+                tp[k] += hk
+                tm[k] -= hk
+                g.append((loss_at(tp) - loss_at(tm)) / (2 * hk))
+            return loss_at(theta), torch.stack(g)
+
+        grad()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            L, g = grad()
+        torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        return {"value": nfr * reps / el, "unit": "frame-grad-evals/s", "ms_per_gradient": 1e3 * el / reps,
+                "loss": float(L), "grad_theta_fd": [float(t) for t in g.tolist()],
+                "note": "7 plain forward passes per gradient (theta and theta +- h per parameter), dL/dtheta only"}
+    finally:
+        s.close()
 
 
 def run_structure(args, world, rank, torch, mw, dev, stream, sp):

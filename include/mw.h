@@ -135,6 +135,10 @@ typedef struct mw_info {
   int64_t regrids;           /* cell grids laid out again because an MW_NPT box left its grid */
   int species;               /* species of the potential (1 unless mw_set_species set more) */
   int species_moments;       /* 1: the species table factors into leg weights and the moment kernel runs */
+  int force_lanes;           /* launch shape of the per-phase force kernel: lanes per centre atom ... */
+  int force_blocks_per_sm;   /* ... and the co-resident blocks per SM its register budget allows */
+  int force_owner;           /* 1: owner-computes (two passes, no per-leg scatter); 0: red.global scatter */
+  int pad_;
 } mw_info;
 
 typedef struct mw_system mw_system;
@@ -344,15 +348,32 @@ mw_status mw_set_nbr_width(mw_system* s, int width);
  * a box edge would be shorter than 2 (a sigma + skin). */
 mw_status mw_set_skin(mw_system* s, double skin);
 
-/* Autotuner.  Runs `steps` steps for each candidate configuration - engine
- * (graph / persistent), skin (0.7x, 1x, 1.4x, 1.8x, 2.2x, 2.6x the current one) and
- * persistent grid size - each from the same saved state (positions,
- * velocities and thermostat state are restored exactly between candidates and
- * at the end), keeps the fastest by GPU time as the AUTO engine and the skin,
- * and writes it to *best_engine (may be NULL).  The choice is cached per
- * device name and system signature in the text file named by the environment
- * variable MW_AUTOTUNE_CACHE, when set. */
+/* Autotuner.  First the launch shape of the per-phase force kernel: each
+ * shape (lanes per centre x register budget: 4 x 8, 2 x 8, 8 x 8 and 4 x 7
+ * blocks per SM with red.global scatter, and 4 x 8 owner-computes; see
+ * mw_set_force_shape) is timed over 10 force calls on the current state and
+ * the fastest kept.  Then it runs `steps` steps for each candidate configuration
+ * - engine (graph / persistent), skin (0.7x, 1x, 1.4x, 1.8x, 2.2x, 2.6x the
+ * current one) and persistent grid size - each from the same saved state
+ * (positions, velocities and thermostat state are restored exactly between
+ * candidates and at the end), keeps the fastest by GPU time as the AUTO
+ * engine and the skin, and writes it to *best_engine (may be NULL).  The
+ * choice is cached per device name and system signature in the text file
+ * named by the environment variable MW_AUTOTUNE_CACHE, when set.  The
+ * persistent engine's force phase keeps its own shape (4 lanes per centre,
+ * the register budget of the cooperative kernel). */
 mw_status mw_autotune(mw_system* s, const mw_integrator* integ, int steps, int* best_engine);
+
+/* Sets the launch shape of the per-phase force kernel: lanes per centre,
+ * blocks per SM and the way the three-body force on a leg's partner reaches
+ * it.  owner_computes = 0: the centre scatters it with red.global (shapes
+ * 4/8, 2/8, 8/8, 4/7); 1: owner-computes in two passes (4/8 only): pass 1
+ * stores each centre's moments and legs, pass 2 gives every atom the forces
+ * of its own terms and of its neighbours' terms (from their moments), with no
+ * per-leg scatter.  MW_EINVAL for a shape not built; selecting
+ * owner-computes allocates its buffers (~150 B per atom).  Results agree to
+ * rounding; the autotuner times all five. */
+mw_status mw_set_force_shape(mw_system* s, int lanes_per_centre, int blocks_per_sm, int owner_computes);
 
 mw_status mw_get_info(mw_system* s, mw_info* out);
 

@@ -66,6 +66,11 @@ struct mw_system {
   cudaStream_t cap_stream = nullptr;  // second stream for capturing conditional bodies
   bool own_stream = false;
   bool list_built = false;
+  // the atom order and neighbour lists are current for the geometry and
+  // parameters (set by a completed force call; cleared by anything that
+  // flags every box for a rebuild, by a failed run, by isobaric steps):
+  // mw_set_state may then keep them (k_load_state_keep)
+  bool order_ok = false;
   double* eout = nullptr;  // 9 * nbox doubles: energies + virials staging
   Dev d{};
   FParams fp{};
@@ -93,6 +98,7 @@ struct mw_system {
   long long host_step = 0;
   int engine = MW_ENGINE_AUTO, engine_used = MW_ENGINE_GRAPH;
   int tuned_engine = -1;
+  int force_shape = 0;  // launch shape of k_force (force_shape_lanes / force_shape_blocks)
   int count_terms = 0;
   long long npairs = 0, ntrip = 0;
   // graph engine
@@ -286,6 +292,7 @@ mw_status alloc_nbr(mw_system* s, int W) {
   MW_CUDA(cudaMemsetAsync(s->d.nbr, 0, sizeof(int) * (size_t)W * s->N, s->stream));
   s->W = s->d.W = W;
   s->list_built = false;
+  s->order_ok = false;
   s->graph_dirty = true;
   return MW_OK;
 }
@@ -314,6 +321,7 @@ mw_status flush_pending(mw_system* s) {
 }
 
 mw_status flag_all(mw_system* s) {
+  s->order_ok = false;
   k_flag_all<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d);
   MW_CUDA(cudaGetLastError());
   return MW_OK;
@@ -400,7 +408,7 @@ mw_status status_error(const Global& g) {
 
 // The kick kernels: the isobaric instantiations under MW_NPT.
 void launch_kick1(mw_system* s, bool cond, cudaGraphConditionalHandle h) {
-  const int kb = kick_blocks(s->N, kKThreads);
+  const int kb = kick_blocks(s->N, kKThreads, kK1Items);
   const bool npt = s->integ.kind == TH_NPT;
   if (cond)
     npt ? k_kick1<true, true><<<kb, kKThreads, 0, s->stream>>>(s->d, h)
@@ -411,7 +419,7 @@ void launch_kick1(mw_system* s, bool cond, cudaGraphConditionalHandle h) {
 }
 
 void launch_kick2(mw_system* s) {
-  const int kb = kick_blocks(s->N, kKThreads);
+  const int kb = kick_blocks(s->N, kKThreads, kK2Items);
   if (s->integ.kind == TH_NPT)
     k_kick2<true><<<kb, kKThreads, 0, s->stream>>>(s->d);
   else
@@ -448,11 +456,42 @@ void launch_force(mw_system* s) {
       k_force_plain<false><<<gp, kPlainThreads, 0, s->stream>>>(d, s->fp);
     return;
   }
-  const int gb = div_up(s->N, kFAtoms);
-  if (s->count_terms)
-    k_force<true><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
-  else
-    k_force<false><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
+  const int gb = div_up(s->N, kFThreads / force_shape_lanes(s->force_shape));
+#define MW_FORCE_SHAPE(S)                                                                                   \
+  case S:                                                                                                  \
+    if (s->count_terms)                                                                                    \
+      k_force<true, force_shape_lanes(S), force_shape_blocks(S)><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);  \
+    else                                                                                                   \
+      k_force<false, force_shape_lanes(S), force_shape_blocks(S)><<<gb, kFThreads, 0, s->stream>>>(d, s->fp); \
+    break;
+  switch (s->force_shape) {
+    MW_FORCE_SHAPE(1)
+    MW_FORCE_SHAPE(2)
+    MW_FORCE_SHAPE(3)
+    case 4:  // owner-computes: two passes
+      if (s->count_terms) {
+        k_force<true, 4, 8, 1><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
+        k_force<true, 4, 8, 2><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
+      } else {
+        k_force<false, 4, 8, 1><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
+        k_force<false, 4, 8, 2><<<gb, kFThreads, 0, s->stream>>>(d, s->fp);
+      }
+      break;
+    default:
+      MW_FORCE_SHAPE(0)
+  }
+#undef MW_FORCE_SHAPE
+}
+
+// Buffers of the owner-computes force passes (allocated when first selected).
+mw_status owner_buffers(mw_system* s) {
+  if (s->d.mom) return MW_OK;
+  mw_status st;
+  if ((st = dalloc(s, &s->d.mom, 3 * (size_t)s->N)) != MW_OK) return st;
+  if ((st = dalloc(s, &s->d.legs, (size_t)s->N * kLMax)) != MW_OK) return st;
+  if ((st = dalloc(s, &s->d.nleg, (size_t)s->N)) != MW_OK) return st;
+  s->graph_dirty = true;  // graphs captured the old Dev
+  return MW_OK;
 }
 
 // The plain path's steps: every phase kernel launched from the host, step
@@ -560,6 +599,7 @@ mw_status ensure_forces(mw_system* s) {
     if (g.status) return status_error(g);
     s->forces_valid = true;
     s->list_built = true;
+    s->order_ok = s->integ.kind != TH_NPT;
     s->record_pending = false;  // the snapshot is the newest record
     s->g_known = g;
     s->g_known_valid = true;
@@ -628,7 +668,10 @@ mw_status regrid(mw_system* s) {
 // previous step; it is recomputed here only after a state or integrator
 // change.
 mw_status prime_thermostat(mw_system* s) {
-  if (s->integ.kind == TH_NPT) s->boxes_stale = true;  // the barostat scales the boxes from here on
+  if (s->integ.kind == TH_NPT) {
+    s->boxes_stale = true;  // the barostat scales the boxes from here on
+    s->order_ok = false;    // and the list positions are no longer in the current boxes
+  }
   if (!s->need_prime) return MW_OK;
   k_prime_thermostat<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d);
   MW_CUDA(cudaGetLastError());
@@ -740,22 +783,37 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
     }
   }
   // reset thermostat / accumulators / counters: zeroed here, the non-zero
-  // starting values set by k_load_state
+  // starting values set by the loading kernel
   MW_CUDA(cudaMemsetAsync(s->d.bst, 0, sizeof(BoxState) * s->nbox, s->stream));
-  MW_CUDA(cudaMemsetAsync(s->d.g, 0, sizeof(Global), s->stream));
   // one pass over atoms and cells; the cell counts start from zero (a run
   // that stopped on an error may have binned atoms without the scan that
   // clears them)
-  k_load_state<<<div_up(std::max(std::max(s->N, s->ncell), s->nbox), kThreads), kThreads, 0, s->stream>>>(
-      s->d, xd, vd, s->boxid, s->count_terms);
+  const int gl = div_up(std::max(std::max(s->N, s->ncell), s->nbox), kThreads);
+  const bool keep = s->state_set && s->order_ok && s->integ.kind != TH_NPT;
+  if (keep) {
+    // the current order and lists stay (boxes whose atoms moved more than
+    // half the skin from their list positions are flagged for a rebuild);
+    // the widest-row record of those lists is kept
+    const size_t mc = offsetof(Global, max_count);
+    MW_CUDA(cudaMemsetAsync(s->d.g, 0, mc, s->stream));
+    MW_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(s->d.g) + mc + sizeof(int), 0, sizeof(Global) - mc - sizeof(int),
+                            s->stream));
+    k_load_state_keep<<<gl, kThreads, 0, s->stream>>>(s->d, xd, vd, s->count_terms,
+                                                      (float)(0.25 * s->skin * s->skin));
+  } else {
+    MW_CUDA(cudaMemsetAsync(s->d.g, 0, sizeof(Global), s->stream));
+    k_load_state<<<gl, kThreads, 0, s->stream>>>(s->d, xd, vd, s->boxid, s->count_terms);
+  }
   MW_CUDA(cudaGetLastError());
   Global gh;
   mw_status st;
   if ((st = read_global(s, &gh)) != MW_OK) return st;
   if (gh.status == ST_INPUT) {
     s->state_set = false;  // the arrays hold part of a refused state
+    s->order_ok = false;
     return fail(MW_EINVAL, "non-finite position or velocity of atom %d", gh.err_index);
   }
+  if (!keep) s->order_ok = false;  // identity order: sorted and listed by the next force call
   s->state_set = true;
   s->forces_valid = false;
   s->need_prime = true;  // thermostat at rest: xi = eta = 0, KE of the new velocities
@@ -1375,6 +1433,7 @@ mw_status mw_step(mw_system* s, const mw_integrator* integ, int nsteps, mw_therm
     s->g_known_valid = false;
     if (st != MW_OK) {
       s->forces_valid = false;  // the state of an interrupted step is not a state to report forces of
+      s->order_ok = false;
       return st;
     }
     s->list_built = true;
@@ -1417,6 +1476,7 @@ mw_status mw_sync(mw_system* s) {
     if ((st = regrid(s)) != MW_OK) return st;
     s->graph_dirty = true;
   }
+  if (g.status) s->order_ok = false;
   return status_error(g);
 }
 
@@ -1515,6 +1575,9 @@ mw_status mw_get_info(mw_system* s, mw_info* out) {
   out->regrids = s->regrids;
   out->species = s->nsp;
   out->species_moments = (s->nsp > 1 && s->sp_moment) ? 1 : 0;
+  out->force_lanes = force_shape_lanes(s->force_shape);
+  out->force_blocks_per_sm = force_shape_blocks(s->force_shape);
+  out->force_owner = force_shape_owner(s->force_shape) ? 1 : 0;
   return MW_OK;
 }
 

@@ -191,6 +191,12 @@ struct Dev {
   // block 0 at kPhaseMarks points of each of the first marks_cap steps
   unsigned long long* marks;
   int marks_cap;
+  // owner-computes force mode (null unless selected): per-atom moments of the
+  // three-body terms (S0, s; M xx yy zz xy; M xz yz), the staged legs and
+  // their count (-1: a centre over the staged-leg limit, done by scatter)
+  float4* mom;
+  int* legs;
+  int* nleg;
 };
 
 constexpr int kPhaseMarks = 16;  // 14 used
@@ -261,11 +267,12 @@ __device__ __forceinline__ float powi(float x, int n) {
 // at the first shell the derivative of the pair term is a difference of two
 // parts five to twenty times larger than itself (it vanishes at the phi2
 // minimum).  So r, 1/r, 1/(r - a sig), the exponent arguments and the pair
-// derivative carry their first-order rounding corrections:
-//   r = RN(sqrt r2) + dr, dr = (r2 - r^2) / (2 r) (the residual by one FMA);
-//   1/r = v (1 + ev), v = RN(1/RN(r)), ev = (1 - r v) - dr v;
-//   x = r - a sig = (r - rc) + (dr - rc_lo) (r - rc exact for r >= rc / 2);
-//   1/x = t (1 + tc), t = RN(1/(r - rc)), tc = (1 - (r - rc) t) - (dr - rc_lo) t;
+// derivative carry their first-order corrections, which also absorb the
+// error of the hardware approximations they start from:
+//   r = r0 + dr, r0 = r2 rsqrt(r2), dr = (r2 - r0^2) / (2 r0) (residual by one FMA);
+//   1/r = v (1 + ev), v = rsqrt(r2), ev = (1 - r0 v) - dr v;
+//   x = r - a sig = (r0 - rc) + (dr - rc_lo) (r0 - rc exact for r0 >= rc / 2);
+//   1/x = t (1 + tc), t ~ 1/(r0 - rc), tc = (1 - (r0 - rc) t) - (dr - rc_lo) t;
 //   exp2(k / x) = exp2(k t) (1 + ln 2 (k t tc + RN residual of k t + k_lo t)).
 // For the SW exponents (p, q) = (4, 0) the pair derivative
 //   dphi2/dr = A eps e2 [(1 - y) sig / x^2 - 4 y / r],  y = B (sig / r)^4,
@@ -280,17 +287,25 @@ struct LegTerms {
   float dphi;     // dphi2 / dr
 };
 
+// 1/x from the hardware approximation (rcp.approx.ftz: within one ulp); the
+// callers correct it to first order or need no more.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <class C>
 __device__ __forceinline__ bool leg_terms(float r2, const C& c, LegTerms& o) {
   constexpr float kLn2 = 0.693147180559945f;
-  const float r = __fsqrt_rn(r2);
-  if (!(r < c.rc)) return false;
-  const float v = __frcp_rn(r);
+  const float v = rsqrtf(r2);
+  const float r = r2 * v;
   const float dr = 0.5f * fmaf(-r, r, r2) * v;
+  if (!(r + dr < c.rc)) return false;
   const float ev = fmaf(-r, v, 1.0f) - dr * v;
   const float xh = r - c.rc;
   const float xl = dr - c.rc_lo;
-  const float t = __frcp_rn(xh);  // < 0
+  const float t = rcp_approx(xh);  // < 0
   const float tc = fmaf(-xh, t, 1.0f) - xl * t;
   const float a2 = c.sig_l2e * t;
   const float a2l = fmaf(c.sig_l2e, t, -a2) + fmaf(a2, tc, c.sig_l2e_lo * t);
@@ -747,26 +762,55 @@ __device__ __forceinline__ bool block_stop(const Dev& d) {
 // FP32 exponent.  Also zeroes f for this step.
 constexpr int kKAtoms = 10;     // atoms per warp in the kick kernels
 constexpr int kKThreads = 512;  // threads per block of k_kick1 / k_kick2 (few blocks: few same-address atomics)
-template <bool kNpt>
-__device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, int par, int pend) {
+// kick1 in two halves, so that a warp can issue the loads of several items
+// before it uses any: kick1_load reads what the item needs (nothing it
+// reads is written by another item), kick1_apply computes and stores.
+struct Kick1In {
+  float F, Fpad;
+  float2 v0;
+  unsigned long long s0;
+  uint32_t qb;
+  int b;
+  int i, c;
+  bool act;
+};
+
+__device__ __forceinline__ Kick1In kick1_load(const Dev& d, int w) {
   const int lane = threadIdx.x & 31;
-  const int i = w * kKAtoms + lane / 3;
-  const int c = lane - 3 * (lane / 3);
-  const bool act = lane < 3 * kKAtoms && i < d.N;
+  Kick1In k;
+  k.i = w * kKAtoms + lane / 3;
+  k.c = lane - 3 * (lane / 3);
+  k.act = lane < 3 * kKAtoms && k.i < d.N;
+  k.b = -1;
+  k.F = 0.f;
+  k.v0 = make_float2(0.f, 0.f);
+  k.s0 = 0ull;
+  k.qb = 0u;
+  if (k.act) {
+    const int i = k.i, c = k.c;
+    k.b = (int)d.q[i].w;
+    k.F = reinterpret_cast<const float*>(d.f + i)[c];
+    k.v0 = (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz))[i];
+    k.s0 = (c == 0 ? d.x : (c == 1 ? d.y : d.z))[i];
+    k.qb = reinterpret_cast<const uint32_t*>(d.qb + i)[c];
+  }
+  return k;
+}
+
+template <bool kNpt>
+__device__ __forceinline__ void kick1_apply(const Dev& d, const Integ& I, const Kick1In& k, int par, int pend) {
+  const int lane = threadIdx.x & 31;
+  const int i = k.i, c = k.c, b = k.b;
   float dd = 0.f;
   bool lost = false;
-  int b = -1;
-  if (act) {
-    // every load that does not depend on the box first, so that their
-    // latencies overlap (the stores below may alias them)
+  if (k.act) {
     float* fp = reinterpret_cast<float*>(d.f + i) + c;
     float2* vp = (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz)) + i;
     unsigned long long* sp = (c == 0 ? d.x : (c == 1 ? d.y : d.z)) + i;
-    b = (int)d.q[i].w;
-    const float F = *fp;
-    const float2 v0 = *vp;
-    const unsigned long long s0 = *sp;
-    const uint32_t qb = reinterpret_cast<const uint32_t*>(d.qb + i)[c];
+    const float F = k.F;
+    const float2 v0 = k.v0;
+    const unsigned long long s0 = k.s0;
+    const uint32_t qb = k.qb;
     const Box& bx = d.box[b];
     const BoxState* st = d.bst + b;
     const float sig = st->sig;
@@ -799,13 +843,13 @@ __device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, 
       BoxState* sw = d.bst + b;
       sw->ke_acc[par] = 0.0;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) sw->ew[par][k] = 0.0;
+      for (int k2 = 0; k2 < 8; ++k2) sw->ew[par][k2] = 0.0;
     }
   }
   // displacement since the last build: sum the three components of the atom
   const int base = lane - c;
   const float d1 = __shfl_sync(kFull, dd, min(base + 1, 31)), d2 = __shfl_sync(kFull, dd, min(base + 2, 31));
-  if (act && c == 0 && dd + d1 + d2 > (kNpt ? d.box[b].hs2 : I.half_skin2)) {
+  if (k.act && c == 0 && dd + d1 + d2 > (kNpt ? d.box[b].hs2 : I.half_skin2)) {
     d.bst[b].rebuild = 1;
     d.g->any_rebuild = 1;
   }
@@ -813,6 +857,13 @@ __device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, 
     set_status(d.g, ST_LOST);
     d.g->err_index = i;
   }
+}
+
+// a1 + a7 (first half) of one item (kKAtoms atoms, three lanes per atom).
+template <bool kNpt>
+__device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, int par, int pend) {
+  const Kick1In k = kick1_load(d, w);
+  kick1_apply<kNpt>(d, I, k, par, pend);
 }
 
 // a7 (second half): the kinetic energy of v + a (FP32 per component; the
@@ -1001,10 +1052,10 @@ constexpr int kWAtoms = 32 / kG;         // centres per warp
 constexpr int kLPad = kLMax + 1;         // row pitch (float4): shifts rows by 4 banks
 constexpr int kPre = 8;                  // neighbour slots per lane fetched ahead in the leg phase
 
-template <int kPad>
+template <int kPad, int kCent = kFAtoms>
 struct LegTableT {
-  float4 ue[kFAtoms * kPad];   // ux, uy, uz, ee
-  float4 aux[kFAtoms * kPad];  // tr, nde, r, j (int bits)
+  float4 ue[kCent * kPad];   // ux, uy, uz, ee
+  float4 aux[kCent * kPad];  // tr, nde, r, j (int bits)
 };
 using LegTable = LegTableT<kLPad>;
 // Several species: a solute's larger cutoff gives its centres more legs, so
@@ -1122,15 +1173,25 @@ __device__ __noinline__ int species_item(const Dev& d, const SpPair* sp, const f
 // (centre; j, k) from the shared triplet table stt.  sps is the nsp^2 pair
 // table in shared memory; phase A tests each candidate against its own
 // pair's cutoff.
-template <bool kCount, int kSp = 0>
-__device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLMaxSp : kLMax) + 1>& T, int blk,
-                            int par, const SpPair* sps = nullptr, int nsp = 1, const float2* stt = nullptr) {
+// kOwn (one species only): 0 the scatter kernel; 1 and 2 the two passes of
+// owner-computes.  Pass 1 takes the legs, the pair terms (energy, force on
+// the centre, virial) and each centre's moments, and stores the moments and
+// the staged legs per atom.  Pass 2 recomputes the leg terms from the stored
+// legs and gives each centre the three-body reaction of its own terms and
+// the forces its neighbours' terms put on it (from their stored moments,
+// with the leg reversed), so no leg force is scattered; centres over the
+// staged-leg limit keep the scatter path (pass 1), and their neighbours add
+// their own terms' forces to them by scatter.
+template <bool kCount, int kSp = 0, int KG = kG, int kOwn = 0>
+__device__ void force_block(const Dev& d, const FParams& P,
+                            LegTableT<(kSp ? kLMaxSp : kLMax) + 1, kFThreads / KG>& T, int blk, int par,
+                            const SpPair* sps = nullptr, int nsp = 1, const float2* stt = nullptr) {
   constexpr int kLM = kSp ? kLMaxSp : kLMax;  // legs staged per centre
   constexpr int kLP = kLM + 1;                // row pitch
   const int lane = threadIdx.x & 31;
-  const int g = threadIdx.x & (kG - 1);
-  const int a = threadIdx.x / kG;
-  const int i = blk * kFAtoms + a;
+  const int g = threadIdx.x & (KG - 1);
+  const int a = threadIdx.x / KG;
+  const int i = blk * (kFThreads / KG) + a;
   const bool valid = i < d.N;
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // E2, E3, W xx yy zz xy xz yz
   float fx = 0.f, fy = 0.f, fz = 0.f;  // force on the centre (pair part and three-body reaction)
@@ -1157,8 +1218,8 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
   // instead of a dependent chain per slot).  Distance test only; hits are
   // compacted (ballot + popc in the lane group) into the centre's row as
   // (d, r^2 | j).
-  const int iters = __reduce_max_sync(kFull, (cnt + kG - 1) / kG);
-  const unsigned gsh = lane & ~(kG - 1);
+  const int iters = __reduce_max_sync(kFull, (cnt + KG - 1) / KG);
+  const unsigned gsh = lane & ~(KG - 1);
   const int* row = d.nbr + (size_t)(valid ? i : 0) * d.W;
   int nl = 0;
   // (kSp: the partner's species rides in the record's x slot until phase B)
@@ -1175,7 +1236,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
       else
         hit = r2 < P.rc2;
     }
-    const unsigned m = (__ballot_sync(kFull, hit) >> gsh) & ((1u << kG) - 1u);
+    const unsigned m = (__ballot_sync(kFull, hit) >> gsh) & ((1u << KG) - 1u);
     const int pos = nl + __popc(m & ((1u << g) - 1u));
     if (hit && pos < kLM) {
       T.ue[a * kLP + pos] = make_float4(dx, dy, dz, r2);
@@ -1183,8 +1244,19 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
     }
     nl += __popc(m);
   };
+  if constexpr (kOwn == 2) {  // the legs pass 1 staged, their vectors recomputed
+    const int nlg = valid ? d.nleg[i] : 0;
+    nl = nlg < 0 ? 0 : nlg;
+    for (int l = g; l < nl; l += KG) {
+      const int j = d.legs[(size_t)i * kLMax + l];
+      const uint4 qj = d.q[j];
+      const float dx = fix_diff(qi.x, qj.x, L0), dy = fix_diff(qi.y, qj.y, L1), dz = fix_diff(qi.z, qj.z, L2);
+      T.ue[a * kLP + l] = make_float4(dx, dy, dz, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      T.aux[a * kLP + l] = make_float4(0.f, 0.f, 0.f, __int_as_float(j));
+    }
+  } else
   // batches of kPre slots per lane, each fetched as a whole (rows, then
-  // positions) before its tests: rows longer than kG * kPre cost one more
+  // positions) before its tests: rows longer than KG * kPre cost one more
   // round trip per batch, not per slot
   for (int t0 = 0; t0 < iters; t0 += kPre) {  // warp-uniform
     int jr[kPre];
@@ -1192,7 +1264,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
     int tj[kPre];
 #pragma unroll
     for (int t = 0; t < kPre; ++t) {
-      const int s = g + kG * (t0 + t);
+      const int s = g + KG * (t0 + t);
       jr[t] = (s < cnt) ? row[s] : -1;
     }
 #pragma unroll
@@ -1211,6 +1283,10 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
       if (t0 + t < iters) test_slot(jr[t], qx[t], qy[t], qz[t], tj[t], jr[t] >= 0);
   }
   __syncwarp();
+  if constexpr (kOwn == 1) {  // the staged legs for pass 2
+    for (int l = g; l < min(nl, kLM); l += KG) d.legs[(size_t)i * kLMax + l] = __float_as_int(T.aux[a * kLP + l].w);
+    if (valid && g == 0) d.nleg[i] = nl <= kLM ? nl : -1;
+  }
   // ---- leg phase B: leg terms for the compacted legs only, spread over the
   // group's lanes: pair term (owner computes), the leg's table entry and its
   // share of the centre's moments S0, s, M.
@@ -1218,7 +1294,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
   float m0 = 0.f, msx = 0.f, msy = 0.f, msz = 0.f;                            // S0, s
   float mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;     // M
   int nvalid = 0;  // legs inside their own pair's cutoff (kSp counting)
-  for (int l = g; l < nstage; l += kG) {
+  for (int l = g; l < nstage; l += KG) {
     float4* ue_p = T.ue + a * kLP + l;
     float4* ax_p = T.aux + a * kLP + l;
     const float4 rec = *ue_p;
@@ -1241,11 +1317,22 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
     const float r = lt.r;
     const float ux = rec.x * lt.invr, uy = rec.y * lt.invr, uz = rec.z * lt.invr;
     const float ee = p_h * lt.e3;
-    const float dphi = lt.dphi;
-    acc[0] = fmaf(0.5f, lt.phi, acc[0]);
-    fx = fmaf(dphi, ux, fx);
-    fy = fmaf(dphi, uy, fy);
-    fz = fmaf(dphi, uz, fz);
+    const float dphi = kOwn == 2 ? 0.f : lt.dphi;  // (pass 2: the pair terms were taken in pass 1)
+    if constexpr (kOwn != 2) {
+      acc[0] = fmaf(0.5f, lt.phi, acc[0]);
+      fx = fmaf(dphi, ux, fx);
+      fy = fmaf(dphi, uy, fy);
+      fz = fmaf(dphi, uz, fz);
+    }
+    if constexpr (kOwn == 1) {  // pass 1 has no phase C: the pair virial here
+      const float wv = -0.5f * dphi * r;
+      acc[2] = fmaf(wv * ux, ux, acc[2]);
+      acc[3] = fmaf(wv * uy, uy, acc[3]);
+      acc[4] = fmaf(wv * uz, uz, acc[4]);
+      acc[5] = fmaf(wv * ux, uy, acc[5]);
+      acc[6] = fmaf(wv * ux, uz, acc[6]);
+      acc[7] = fmaf(wv * uy, uz, acc[7]);
+    }
     if constexpr (kSp == 1) {
       if (p_h == 0.f) {  // no three-body weight (a lambda = 0 pair): its pair virial here, no phase C
         const float wv = -0.5f * dphi * r;
@@ -1279,7 +1366,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
   }
   // the centre's moments: sum over the lane group
 #pragma unroll
-  for (int o = 1; o < kG; o <<= 1) {
+  for (int o = 1; o < KG; o <<= 1) {
     m0 += __shfl_xor_sync(kFull, m0, o);
     msx += __shfl_xor_sync(kFull, msx, o);
     msy += __shfl_xor_sync(kFull, msy, o);
@@ -1292,17 +1379,23 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
     myz += __shfl_xor_sync(kFull, myz, o);
   }
   __syncwarp();  // the group's table entries are complete
-  if constexpr (kSp == 2) {
+  if constexpr (kOwn == 1) {
+    if (valid && g == 0) {
+      d.mom[3 * (size_t)i] = make_float4(m0, msx, msy, msz);
+      d.mom[3 * (size_t)i + 1] = make_float4(mxx, myy, mzz, mxy);
+      d.mom[3 * (size_t)i + 2] = make_float4(mxz, myz, 0.f, 0.f);
+    }
+  } else if constexpr (kSp == 2) {
     // ---- leg phase C (any table): leg j against every other leg k
     const float2* stc = stt + ti * nsp * nsp;
-    for (int l = g; l < nstage; l += kG) {
+    for (int l = g; l < nstage; l += KG) {
       const float4 uj = T.ue[a * kLP + l];
       const float4 xj = T.aux[a * kLP + l];
       if (uj.w == 0.f) continue;  // leg dropped in phase B
       const int wj = __float_as_int(xj.w);
       const float2* stj = stc + (wj >> 28) * nsp;
       const float r = xj.z;
-      const float tr = 2.0f * __frcp_rn(r);
+      const float tr = 2.0f * rcp_approx(r);
       const float nde = xj.y;
       float gx = 0.f, gy = 0.f, gz = 0.f;  // three-body force on the partner of leg j
       for (int k = 0; k < nstage; ++k) {
@@ -1334,46 +1427,71 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
   } else {
   // ---- leg phase C: three-body force on each leg partner from the moments
   const float c0 = (kSp && valid) ? spi[0].c0 : P.c0;
-  const float s0c = c0 * c0 * m0;
   // a centre with one leg has no three-body term: its moments hold only that
   // leg, whose self term cancels up to rounding; the residue is not computed
   const bool three = nstage > 1;  // (uniform over the centre's lane group)
-  for (int l = g; l < nstage; l += kG) {
+  // the three-body force on the partner of leg (u, ee, nde, r) of a centre
+  // with moments (S0, s, M), and the leg's C; the k = j term is taken back
+  // out with c_jj = |u|^2 as computed (not 1), so that it cancels the same
+  // product inside the moments
+  auto leg_force = [&](float ux, float uy, float uz, float ee, float nde, float r, float S0, float sx, float sy,
+                       float sz, float Mxx, float Myy, float Mzz, float Mxy, float Mxz, float Myz, float& gx,
+                       float& gy, float& gz) {
+    const float mx = fmaf(Mxx, ux, fmaf(Mxy, uy, Mxz * uz));  // M u
+    const float my = fmaf(Mxy, ux, fmaf(Myy, uy, Myz * uz));
+    const float mz = fmaf(Mxz, ux, fmaf(Myz, uy, Mzz * uz));
+    const float qm = fmaf(ux, mx, fmaf(uy, my, uz * mz));     // u.M u
+    const float ps = fmaf(ux, sx, fmaf(uy, sy, uz * sz));     // u.s
+    const float cjj = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    const float djj = cjj - c0;
+    const float self = ee * djj;
+    const float Bj = fmaf(-c0, ps, qm) - self * cjj;
+    const float Cj = fmaf(-2.0f * c0, ps, fmaf(c0 * c0, S0, qm)) - self * djj;
+    const float Ax = fmaf(-c0, sx, mx) - self * ux;
+    const float Ay = fmaf(-c0, sy, my) - self * uy;
+    const float Az = fmaf(-c0, sz, mz) - self * uz;
+    const float tr = 2.0f * rcp_approx(r);
+    const float et = ee * tr;                       // ee_j tr_j
+    const float cu = ee * fmaf(nde, Cj, tr * Bj);   // ee_j (nde_j C_j + tr_j B_j)
+    gx = fmaf(cu, ux, -et * Ax);
+    gy = fmaf(cu, uy, -et * Ay);
+    gz = fmaf(cu, uz, -et * Az);
+    return Cj;
+  };
+  for (int l = g; l < nstage; l += KG) {
     const float4 uj = T.ue[a * kLP + l];
     const float4 xj = T.aux[a * kLP + l];
     const float ee = uj.w;
     if (ee == 0.f) continue;  // leg dropped in phase B
     const float r = xj.z;
+    const int j = __float_as_int(xj.w);
     float gx = 0.f, gy = 0.f, gz = 0.f;
     if (three) {
-      const float mx = fmaf(mxx, uj.x, fmaf(mxy, uj.y, mxz * uj.z));  // M u_j
-      const float my = fmaf(mxy, uj.x, fmaf(myy, uj.y, myz * uj.z));
-      const float mz = fmaf(mxz, uj.x, fmaf(myz, uj.y, mzz * uj.z));
-      const float qm = fmaf(uj.x, mx, fmaf(uj.y, my, uj.z * mz));     // u_j.M u_j
-      const float ps = fmaf(uj.x, msx, fmaf(uj.y, msy, uj.z * msz));  // u_j.s
-      // the k = j term taken back out with c_jj = |u_j|^2 as computed (not 1),
-      // so that it cancels the same product inside the moments
-      const float cjj = fmaf(uj.x, uj.x, fmaf(uj.y, uj.y, uj.z * uj.z));
-      const float djj = cjj - c0;
-      const float self = ee * djj;
-      const float Bj = fmaf(-c0, ps, qm) - self * cjj;
-      const float Cj = fmaf(-2.0f * c0, ps, qm + s0c) - self * djj;
-      const float Ax = fmaf(-c0, msx, mx) - self * uj.x;
-      const float Ay = fmaf(-c0, msy, my) - self * uj.y;
-      const float Az = fmaf(-c0, msz, mz) - self * uj.z;
-      const float tr = 2.0f * __frcp_rn(r);
-      const float et = ee * tr;                            // ee_j tr_j
-      const float cu = ee * fmaf(xj.y, Cj, tr * Bj);       // ee_j (nde_j C_j + tr_j B_j)
-      gx = fmaf(cu, uj.x, -et * Ax);
-      gy = fmaf(cu, uj.y, -et * Ay);
-      gz = fmaf(cu, uj.z, -et * Az);
-      red_add_v4(d.f + __float_as_int(xj.w), gx, gy, gz);
+      const float Cj = leg_force(uj.x, uj.y, uj.z, ee, xj.y, r, m0, msx, msy, msz, mxx, myy, mzz, mxy, mxz, myz,
+                                 gx, gy, gz);
+      // the partner's share: scattered (pass 2: gathered by the partner, unless
+      // it is a centre over the staged-leg limit)
+      if (kOwn == 0 || d.nleg[j] < 0) red_add_v4(d.f + j, gx, gy, gz);
       fx -= gx;
       fy -= gy;
       fz -= gz;
       acc[1] = fmaf(0.5f * ee, Cj, acc[1]);
     }
+    if constexpr (kOwn == 2) {  // the partner's terms on this centre, from its moments, leg reversed
+      if (d.nleg[j] >= 0) {
+        const float4 ma = d.mom[3 * (size_t)j], mb = d.mom[3 * (size_t)j + 1], mc = d.mom[3 * (size_t)j + 2];
+        float hx, hy, hz;
+        if (d.nleg[j] > 1) {
+          leg_force(-uj.x, -uj.y, -uj.z, ee, xj.y, r, ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w, mc.x, mc.y, hx,
+                    hy, hz);
+          fx += hx;
+          fy += hy;
+          fz += hz;
+        }
+      }
+    }
     // virial: r u_a (g_b - 1/2 dphi u_b), the three-body and the pair part
+    // (pass 2: xj.x = 0, the pair part was taken in pass 1)
     const float hx = fmaf(xj.x, uj.x, gx), hy = fmaf(xj.x, uj.y, gy), hz = fmaf(xj.x, uj.z, gz);
     const float rx = r * uj.x, ry = r * uj.y, rz = r * uj.z;
     acc[2] = fmaf(rx, hx, acc[2]);
@@ -1386,7 +1504,7 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
   }  // phase C
   // ---- force on the centre: pair part + three-body reaction, over the group
 #pragma unroll
-  for (int o = 1; o < kG; o <<= 1) {
+  for (int o = 1; o < KG; o <<= 1) {
     fx += __shfl_xor_sync(kFull, fx, o);
     fy += __shfl_xor_sync(kFull, fy, o);
     fz += __shfl_xor_sync(kFull, fz, o);
@@ -1400,11 +1518,11 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
         force_overflow_item<kCount>(d, P, i, par);
     }
   }
-  if (kCount) {  // legs and table-path triplets, one atomic per warp
+  if (kCount && kOwn != 2) {  // legs and table-path triplets, one atomic per warp (pass 2 counts nothing)
     int nleg = nl;
     if constexpr (kSp) {  // legs inside their own pair's cutoff, summed over the group
 #pragma unroll
-      for (int o = 1; o < kG; o <<= 1) nvalid += __shfl_xor_sync(kFull, nvalid, o);
+      for (int o = 1; o < KG; o <<= 1) nvalid += __shfl_xor_sync(kFull, nvalid, o);
       nleg = nvalid;
     }
     unsigned long long legs = (valid && g == 0 && (!kSp || nl <= kLM)) ? (unsigned long long)nleg : 0ull;
@@ -1422,10 +1540,13 @@ __device__ void force_block(const Dev& d, const FParams& P, LegTableT<(kSp ? kLM
   box_accumulate<8>(acc, b, [&](int bb) { return &d.bst[bb].ew[par][0]; });
 }
 
-template <bool kCount>
-__global__ void __launch_bounds__(kFThreads, 8) k_force(Dev d, FParams P) {
+// k_force in several launch shapes, picked by the autotuner: KG lanes per
+// centre (kFThreads / KG centres per block) and a register budget of MINB
+// co-resident blocks per SM (65536 / (kFThreads MINB) registers a thread).
+template <bool kCount, int KG = kG, int MINB = 8, int kOwn = 0>
+__global__ void __launch_bounds__(kFThreads, MINB) k_force(Dev d, FParams P) {
   if (block_stop(d)) return;
-  __shared__ LegTable T;
+  __shared__ LegTableT<kLPad, kFThreads / KG> T;
   const int par = (int)(d.g->step & 1ull);
   if (blockIdx.x == 0) {  // the rebuild (if any) is consumed
     for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
@@ -1434,8 +1555,19 @@ __global__ void __launch_bounds__(kFThreads, 8) k_force(Dev d, FParams P) {
       d.g->wpar = par;
     }
   }
-  force_block<kCount>(d, P, T, blockIdx.x, par);
+  force_block<kCount, 0, KG, kOwn>(d, P, T, blockIdx.x, par);
 }
+
+// The shapes k_force is built in: {lanes per centre, blocks per SM}.  Shape 0
+// is the default; the set spans what a sweep on 2^20 atoms measured within
+// 20 % of the best (2 and 8 lanes give more or fewer, larger or smaller
+// blocks for small systems).
+// Shape 4 is owner-computes (two passes, 4 lanes, 8 blocks per SM) against
+// the scatter of the others.
+constexpr int kForceShapes = 5;
+__host__ __device__ constexpr int force_shape_lanes(int s) { return s == 1 ? 2 : (s == 2 ? 8 : 4); }
+__host__ __device__ constexpr int force_shape_blocks(int s) { return s == 3 ? 7 : 8; }
+__host__ __device__ constexpr bool force_shape_owner(int s) { return s == 4; }
 
 
 // ---------------------------------------------------------------------------
@@ -1447,15 +1579,29 @@ __global__ void __launch_bounds__(kFThreads, 8) k_force(Dev d, FParams P) {
 // holds no conditional-node call, so profilers can capture it.
 // kNpt: the isobaric instantiation (rebuild margin per box, and its last
 // block makes the coming step's edges current).
+// The standalone kick kernels give each warp several items: warp wi of block
+// blk takes items (blk kK*Items + j) nwb + wi, j = 0 .. kK*Items - 1 (the
+// warps of a block on consecutive items at each j).  k_kick1 reads all its
+// items before it writes any; k_kick2 only reads atom data, and reduces its
+// items' kinetic energies per warp (box by box) and once per block.
+constexpr int kK1Items = 1;  // (two, with their loads first, measured no faster at 2^20 atoms)
+constexpr int kK2Items = 4;
+
 template <bool kCond, bool kNpt = false>
 __global__ void __launch_bounds__(kKThreads) k_kick1(Dev d, cudaGraphConditionalHandle rebuild_cond) {
   if (block_stop(d)) return;
   const Integ I = *d.integ;
   const int par = (int)(d.g->step & 1ull);
   const int pend = d.g->pend;
-  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwb = (int)(blockDim.x >> 5), wib = (int)(threadIdx.x >> 5);
   if (blockIdx.x == 0 && threadIdx.x == 0) d.g->n_over = 0;
-  if (w * kKAtoms < d.N) kick1_lane<kNpt>(d, I, w, par, pend);
+  Kick1In k[kK1Items];
+#pragma unroll
+  for (int j = 0; j < kK1Items; ++j) k[j] = kick1_load(d, ((int)blockIdx.x * kK1Items + j) * nwb + wib);
+#pragma unroll
+  for (int j = 0; j < kK1Items; ++j)
+    if ((((int)blockIdx.x * kK1Items + j) * nwb + wib) * kKAtoms < d.N)  // warp-uniform
+      kick1_apply<kNpt>(d, I, k[j], par, pend);
   if constexpr (kCond || kNpt) {
     __shared__ bool last;
     __syncthreads();
@@ -1602,16 +1748,79 @@ __global__ void k_neigh(Dev d, float rl2) {
 template <bool kNpt = false>
 __global__ void __launch_bounds__(kKThreads) k_kick2(Dev d) {
   if (block_stop(d)) return;
+  __shared__ float s_ke[kKThreads / 32];
+  __shared__ int s_box[kKThreads / 32];
   const Integ I = *d.integ;
   const unsigned long long step = d.g->step;
   const int par = (int)(step & 1ull);
-  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  float ke[1] = {0.f};
-  int b = -1;
-  ke[0] = kick2_lane(d, I, w, b);
-  box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_acc[par]; });
-  __shared__ bool am_last;
+  const int nwb = (int)(blockDim.x >> 5), wib = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  // per warp: a running FP32 sum for one box; a warp whose item changes box
+  // adds its sum to the old box (FP64 atomic) and starts again; an item that
+  // itself straddles two boxes is added lane by lane (rare)
+  float acc = 0.f;
+  int cur = -1;
+  float ke[kK2Items];
+  int bj[kK2Items];
+  {  // every item's loads first, then the arithmetic
+    float Fj[kK2Items];
+    float2 vj[kK2Items];
+#pragma unroll
+    for (int j = 0; j < kK2Items; ++j) {
+      const int w = ((int)blockIdx.x * kK2Items + j) * nwb + wib;
+      const int i = w * kKAtoms + lane / 3, c = lane - 3 * (lane / 3);
+      const bool act = lane < 3 * kKAtoms && i < d.N;
+      bj[j] = act ? (int)d.q[i].w : -1;
+      Fj[j] = act ? reinterpret_cast<const float*>(d.f + i)[c] : 0.f;
+      vj[j] = act ? (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz))[i] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < kK2Items; ++j) {
+      const float u = fmaf(I.cf_f, Fj[j], vj[j].x) + vj[j].y;
+      ke[j] = (float)I.ke_fac * u * u;
+      if (bj[j] >= 0 && !(ke[j] < 1e30f)) {
+        set_status(d.g, ST_NAN);
+        d.g->err_index = ((int)blockIdx.x * kK2Items + j) * nwb * kKAtoms + wib * kKAtoms + lane / 3;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kK2Items; ++j) {
+    const int b0 = __shfl_sync(kFull, bj[j], 0);
+    if (__all_sync(kFull, bj[j] == b0 || bj[j] < 0)) {
+      if (b0 < 0) continue;  // an item past the last atom (warp-uniform)
+      float v = ke[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+      if (b0 != cur) {
+        if (cur >= 0 && lane == 0) atomicAdd(&d.bst[cur].ke_acc[par], (double)acc);
+        acc = 0.f;
+        cur = b0;
+      }
+      acc += v;
+    } else if (bj[j] >= 0) {
+      atomicAdd(&d.bst[bj[j]].ke_acc[par], (double)ke[j]);
+    }
+  }
+  if (lane == 0) {
+    s_ke[wib] = acc;
+    s_box[wib] = cur;
+  }
   __syncthreads();
+  if (threadIdx.x == 0) {  // the warps' sums, one FP64 atomic per run of equal boxes
+    float run = 0.f;
+    int rb = -1;
+    for (int w = 0; w < nwb; ++w) {
+      if (s_box[w] < 0) continue;
+      if (s_box[w] != rb) {
+        if (rb >= 0) atomicAdd(&d.bst[rb].ke_acc[par], (double)run);
+        run = 0.f;
+        rb = s_box[w];
+      }
+      run += s_ke[w];
+    }
+    if (rb >= 0) atomicAdd(&d.bst[rb].ke_acc[par], (double)run);
+  }
+  __shared__ bool am_last;
   if (threadIdx.x == 0) am_last = (bar_arrive(&d.g->done) == gridDim.x);
   __syncthreads();
   if (am_last) {
@@ -1625,7 +1834,6 @@ __global__ void __launch_bounds__(kKThreads) k_kick2(Dev d) {
   }
 }
 
-// Thermo record of the last completed step (one block), before the host reads it.
 __global__ void k_record(Dev d) {
   const Integ I = *d.integ;
   const unsigned long long step = d.g->step;
@@ -1750,6 +1958,78 @@ __global__ void k_load_state(Dev d, const double* __restrict__ xin, const double
   box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_last; });
 }
 
+// A new state in the current atom order (mw_set_state while that order and
+// the neighbour lists are current): sorted slot i takes the caller's atom
+// id[i] with the same conversions as k_load_state (positions to 64-bit and
+// fixed-point fractions, image counts, velocities as FP32 pairs, species,
+// zero force, kinetic energy per box).  A box keeps its list when every one
+// of its atoms lies within half the skin (hs2 = (skin/2)^2) of the position
+// the list was built at, as between steps; any other box is flagged for a
+// rebuild.  The host zeroes the box states and the status block (all but
+// the widest-row record) before the launch.
+__global__ void k_load_state_keep(Dev d, const double* __restrict__ xin, const double* __restrict__ vin,
+                                  int count_terms, float hs2) {
+  const Integ I = *d.integ;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d.ncell) d.cell_cnt[i] = 0;
+  if (i < d.nbox) {
+    d.bst[i].s_endc = 1.0;
+    d.bst[i].Lb = d.box[i].L[0];  // the lists were built in these (unscaled) boxes
+  }
+  if (i == 0) d.g->count_terms = count_terms;
+  float ke[1] = {0.f};
+  int b = -1;
+  if (i < d.N) {
+    const int u = d.id[i];
+    b = (int)d.q[i].w;
+    const Box& bx = d.box[b];
+    unsigned long long p[3];
+    int im[3];
+    float vh[3];
+    for (int k = 0; k < 3; ++k) {
+      double x = xin[3 * (size_t)u + k];
+      if (!isfinite(x)) {
+        set_status(d.g, ST_INPUT);
+        d.g->err_index = u;
+        x = 0.0;
+      }
+      double f = x / bx.L[k];
+      const double fl = floor(f);
+      im[k] = (int)fl;
+      f -= fl;
+      if (f >= 1.0) f -= 1.0;
+      if (f < 0.0) f = 0.0;
+      p[k] = frac64_of(f);
+      double w = vin ? vin[3 * (size_t)u + k] : 0.0;
+      if (!isfinite(w)) {
+        set_status(d.g, ST_INPUT);
+        d.g->err_index = u;
+        w = 0.0;
+      }
+      const float2 sw = split_df(w);
+      (k == 0 ? d.vx : (k == 1 ? d.vy : d.vz))[i] = sw;
+      vh[k] = sw.x + sw.y;
+    }
+    d.x[i] = p[0];
+    d.y[i] = p[1];
+    d.z[i] = p[2];
+    if (d.img) d.img[i] = make_int4(im[0], im[1], im[2], 0);
+    const uint4 q = make_uint4(q_of(p[0]), q_of(p[1]), q_of(p[2]), (unsigned)b);
+    d.q[i] = q;
+    if (d.typ) d.typ[i] = d.utyp[u];
+    d.f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    ke[0] = (float)I.ke_fac * fmaf(vh[0], vh[0], fmaf(vh[1], vh[1], vh[2] * vh[2]));
+    const uint4 qb = d.qb[i];
+    const float dx = fix_diff(qb.x, q.x, bx.Lq[0]), dy = fix_diff(qb.y, q.y, bx.Lq[1]),
+                dz = fix_diff(qb.z, q.z, bx.Lq[2]);
+    if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > hs2) {
+      d.bst[b].rebuild = 1;
+      d.g->any_rebuild = 1;
+    }
+  }
+  box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_last; });
+}
+
 // Applies a pending second half-kick (v += dt/2 F/m) before anything changes
 // the forces or the atom order outside a step.
 __global__ void k_flush_pending(Dev d) {
@@ -1772,7 +2052,12 @@ __global__ void k_flag_all(Dev d) {
 }
 
 // Blocks of the kick kernels (kKAtoms atoms per warp).
-__host__ __device__ inline int kick_blocks(int n, int threads) { return (n + kKAtoms * (threads / 32) - 1) / (kKAtoms * (threads / 32)); }
+// Blocks of the standalone kick kernels: items of kKAtoms atoms, `items`
+// of them per warp.
+__host__ __device__ inline int kick_blocks(int n, int threads, int items = 1) {
+  const int per = kKAtoms * (threads / 32) * items;
+  return (n + per - 1) / per;
+}
 
 // Zeroes this parity's energy/virial accumulators and (optionally) the forces.
 __global__ void k_prep_force(Dev d, int zero_f) {

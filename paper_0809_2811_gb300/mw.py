@@ -29,7 +29,7 @@ EXPORTS = (
     "mw_set_state_dev", "mw_get_state", "mw_get_state_dev", "mw_set_params", "mw_build_neighbors",
     "mw_get_neighbors", "mw_energy_forces", "mw_energy_forces_dev", "mw_step", "mw_get_thermo",
     "mw_energy_forces_vjp", "mw_set_engine", "mw_set_nbr_width", "mw_autotune", "mw_get_info",
-    "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc", "mw_set_skin", "mw_phase_times",
+    "mw_set_count_terms", "mw_forces_async", "mw_step_async", "mw_sync", "mw_energy_forces_noalloc", "mw_set_skin", "mw_set_force_shape", "mw_phase_times",
     "mw_pair_histogram", "mw_angle_histogram", "mw_get_unwrapped", "mw_get_box", "mw_set_species",
     "mw_checkpoint_size", "mw_checkpoint_save", "mw_checkpoint_load", "mw_set_wait_limit",
     "mw_set_phase_marks", "mw_get_phase_marks", "mw_last_error",
@@ -69,7 +69,8 @@ class mw_info(ctypes.Structure):
                 ("persistent_blocks", ctypes.c_int), ("persistent_threads", ctypes.c_int),
                 ("r_list", ctypes.c_double), ("npairs", ctypes.c_int64), ("ntriplets", ctypes.c_int64),
                 ("rebuild_steps", ctypes.c_int64), ("regrids", ctypes.c_int64), ("species", ctypes.c_int),
-                ("species_moments", ctypes.c_int)]
+                ("species_moments", ctypes.c_int), ("force_lanes", ctypes.c_int), ("force_blocks_per_sm", ctypes.c_int),
+                ("force_owner", ctypes.c_int), ("pad_", ctypes.c_int)]
 
 
 class MWError(RuntimeError):
@@ -119,6 +120,7 @@ def lib():
             "mw_step_async": [P, ctypes.POINTER(mw_integrator), ctypes.c_int],
             "mw_sync": [P],
             "mw_set_skin": [P, ctypes.c_double],
+            "mw_set_force_shape": [P, ctypes.c_int, ctypes.c_int, ctypes.c_int],
             "mw_phase_times": [P, ctypes.POINTER(mw_integrator), ctypes.c_int, dp],
             "mw_pair_histogram": [P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)],
             "mw_get_unwrapped": [P, dp],
@@ -386,6 +388,12 @@ def mw_energy_forces_noalloc(n: int, box, x_dev, f_dev=None, energy_dev=None, vi
 
 def mw_set_skin(h: int, skin: float):
     _check(lib().mw_set_skin(h, float(skin)))
+
+
+def mw_set_force_shape(h: int, lanes_per_centre: int, blocks_per_sm: int, owner_computes: bool = False):
+    """Launch shape of the per-phase force kernel: scatter 4/8, 2/8, 8/8, 4/7 or
+    owner-computes 4/8."""
+    _check(lib().mw_set_force_shape(h, int(lanes_per_centre), int(blocks_per_sm), int(bool(owner_computes))))
 
 
 PHASES = ("kick1", "bin", "scan", "scatter", "copyback", "neigh", "force", "kick2")

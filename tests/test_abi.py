@@ -37,7 +37,7 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(mw.mw_params) == 72
     assert ctypes.sizeof(mw.mw_integrator) == 56
     assert ctypes.sizeof(mw.mw_thermo) == 168
-    assert ctypes.sizeof(mw.mw_info) == 80
+    assert ctypes.sizeof(mw.mw_info) == 96
 
 
 def test_struct_layout_matches_the_c_compiler(tmp_path):

@@ -56,6 +56,27 @@ def test_short_trajectory_matches_oracle(mwlib, orc, kind, engine):
     assert th["step"] == 20
 
 
+@pytest.mark.parametrize("shape", [(2, 8, False), (4, 8, True)])
+def test_short_trajectory_with_other_force_shapes(mwlib, orc, shape):
+    """The graph engine's steps with a two-lane and with the owner-computes
+    force kernel follow the oracle's Nose-Hoover trajectory like the default."""
+    x, v, box = I.nve512()
+    x = I.snap_to_grid(x, box)
+    s = mwlib.System(len(x), box)
+    try:
+        s.set_engine(mwlib.MW_ENGINE_GRAPH)
+        mwlib.mw_set_force_shape(s.h, *shape)
+        s.set_state(x, v)
+        th = s.step(20, dt=10.0, thermostat=2, T0=250.0, tau=200.0)[0]
+        xg, vg = s.get_state()
+    finally:
+        s.close()
+    xo, vo, st, tho = orc.md(x, v, box, 20, dt=10.0, kind=2, T0=250.0, tau=200.0)
+    assert np.abs(_min_image(xg - xo, box)).max() < 5e-5
+    assert np.abs(vg - vo).max() < 1e-6
+    assert th["conserved"] == pytest.approx(tho[-1, 5], rel=3e-6)
+
+
 def test_nve_energy_conservation_512(mwlib, orc):
     """NVE at dt = 10 fs from the jittered 512-atom start.  (a) Over the first
     1000 steps the FP32-force run fluctuates no more than the FP64 oracle's own

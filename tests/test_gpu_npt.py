@@ -40,14 +40,17 @@ def _gpu_npt(mwlib, x, v, box, nsteps, engine=None, **kw):
     return th, xg, vg, bg, info
 
 
-def _compare(th, xg, vg, bg, xo, vo, bo, st, tho, nsteps, pos_tol=5e-5, vel_tol=5e-7):
+def _compare(th, xg, vg, bg, xo, vo, bo, st, tho, nsteps, pos_tol=5e-5, vel_tol=5e-7, edge_tol=5e-8):
     """Bounds about ten times the differences measured on GB300 (20-30 steps:
     edges 3e-9, positions 2e-6 A (1.4e-5 A through a regrid), velocities
-    4e-8 A/fs, energies 1e-7, thermostat 5e-7, pressure 0.02 atm)."""
+    4e-8 A/fs, energies 1e-7, thermostat 5e-7, pressure 0.02 atm).  The
+    collapsing box of the regrid test integrates a pressure 1e4 atm off
+    target for 80 fs: its edges differ by up to 5.4e-8 (measured), so it is
+    checked at edge_tol = 2e-7."""
     # edges: one factor per step from the FP64 barostat momentum and an FP32 exp
-    assert np.allclose(bg, bo, rtol=5e-8, atol=0)
+    assert np.allclose(bg, bo, rtol=edge_tol, atol=0)
     assert th["box"] == pytest.approx(list(bg), rel=1e-15)
-    assert th["volume"] == pytest.approx(tho[8], rel=1.5e-7)
+    assert th["volume"] == pytest.approx(tho[8], rel=3 * edge_tol)
     assert np.abs(_min_image(xg - xo, bo)).max() < pos_tol
     assert np.abs(vg - vo).max() < vel_tol
     assert th["pe"] == pytest.approx(tho[0], rel=1e-6)
@@ -87,7 +90,7 @@ def test_npt_box_leaves_its_cell_grid_and_the_run_continues(mwlib, orc, engine):
     xo, vo, bo, st, tho = orc.md_npt(x, v, box, 30, dt=10.0, T0=250.0, tau=200.0, p_atm=0.0, tau_p=500.0)
     assert info["regrids"] >= 1
     assert info["ncell_total"] == 4 ** 3
-    _compare(th, xg, vg, bg, xo, vo, bo, st, tho[-1], 30, pos_tol=1.5e-4, vel_tol=2e-6)
+    _compare(th, xg, vg, bg, xo, vo, bo, st, tho[-1], 30, pos_tol=1.5e-4, vel_tol=2e-6, edge_tol=2e-7)
 
 
 @pytest.mark.parametrize("engine", sorted(ENGINES))

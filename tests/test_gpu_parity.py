@@ -224,3 +224,44 @@ def test_pinned_host_state_matches_pageable(mwlib, orc):
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("shape", [(4, 8, 0), (2, 8, 0), (8, 8, 0), (4, 7, 0), (4, 8, 1)])
+def test_force_kernel_shapes_agree_with_oracle(mwlib, orc, shape):
+    """Every launch shape the autotuner may pick (lanes per centre x blocks per
+    SM x scatter or owner-computes) computes the same forces, energies and
+    virial; the dense box has centres over the staged-leg limit, which the
+    owner-computes passes leave to the scatter path."""
+    for case, (x, box) in (("liquidlike_1000", I.jittered_box(1000, 1.0, 0.3, 101)),
+                           ("ice_ih_288", I.ice_ih(4, 3, 3, 0.92)),
+                           ("dense_512_rho3.5", I.jittered_box(512, 3.5, 0.1, 104))):
+        x = I.snap_to_grid(x, box)
+        ref = orc.energy_forces(x, box)
+        s = mwlib.System(len(x), box)
+        try:
+            mwlib.mw_set_force_shape(s.h, *shape)
+            s.set_state(x)
+            f, e, w = s.energy_forces()
+            info = s.info()
+            assert (info["force_lanes"], info["force_blocks_per_sm"], info["force_owner"]) == shape
+            compare(f"{case} [force shape {shape[0]}x{shape[1]}{' owner' if shape[2] else ''}]", f, e[0], w[0], ref)
+        finally:
+            s.close()
+
+
+def test_autotuner_picks_and_reports_a_force_shape(mwlib):
+    x, box = I.jittered_box(4096, 1.0, 0.25, 120)
+    s = mwlib.System(len(x), box)
+    try:
+        s.set_state(x)
+        integ = mwlib.make_integrator(10.0, mwlib.MW_NOSE_HOOVER, 300.0, 1000.0)
+        mwlib.mw_autotune(s.h, integ, 10)
+        info = s.info()
+        assert (info["force_lanes"], info["force_blocks_per_sm"], info["force_owner"]) in {
+            (4, 8, 0), (2, 8, 0), (8, 8, 0), (4, 7, 0), (4, 8, 1)}
+        with pytest.raises(mwlib.MWError):
+            mwlib.mw_set_force_shape(s.h, 3, 8)
+        with pytest.raises(mwlib.MWError):
+            mwlib.mw_set_force_shape(s.h, 2, 8, True)
+    finally:
+        s.close()

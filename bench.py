@@ -71,6 +71,9 @@ def parse():
                     help="after timing, run this many NVE steps and report the energy drift per ns")
     ap.add_argument("--drift-prep", type=int, default=200,
                     help="Nose-Hoover steps from the start state before the NVE drift segment")
+    ap.add_argument("--profile-range", default=None, choices=["step", "force", "force_owner", "rebuild"],
+                    help="profiling target for ncu --profile-from-start off: the 2^20-atom slab on the graph engine "
+                         "(skin --skin, default 1.8 A), --warmup steps, then only this inside the profiler range")
     return ap.parse_args()
 
 
@@ -1181,8 +1184,46 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
+def run_profile_range(args):
+    """One step, one force call (scatter or owner-computes) or one forced
+    neighbour-list rebuild of the headline slab inside the CUDA profiler
+    range, for ncu --profile-from-start off.  Prints one line, no timing."""
+    import torch
+    from paper_0809_2811_gb300 import build, mw
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    x, v, box = slab_workload(0)
+    s = mw.System(len(x), box, skin=1.8 if args.skin is None else args.skin, stream=stream.cuda_stream)
+    s.set_engine(mw.MW_ENGINE_GRAPH)
+    s.set_state(x, v)
+    integ = mw.make_integrator(DT, mw.MW_NOSE_HOOVER, T_SLAB, TAU)
+    mw.mw_step(s.h, integ, max(args.warmup, 3), 1)
+    if args.profile_range == "force_owner":
+        mw.mw_set_force_shape(s.h, 4, 8, True)
+        mw.mw_forces_async(s.h)  # (the owner buffers' first use outside the range)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    if args.profile_range == "step":
+        mw.mw_step_async(s.h, integ, 1)
+    elif args.profile_range == "rebuild":
+        s.build_neighbors()
+    else:
+        mw.mw_forces_async(s.h)
+    mw.mw_sync(s.h)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    info = s.info()
+    print(json.dumps({"profile_range": args.profile_range, "atoms": len(x), "r_list_A": info["r_list"],
+                      "nbr_width": info["nbr_width"], "max_count": info["max_count"]}), flush=True)
+    s.close()
+
+
 def main():
     args = parse()
+    if args.profile_range:
+        return run_profile_range(args)
     world, rank, local, pg = dist_setup(args)
     pg_holder[0] = pg
     try:

@@ -426,11 +426,21 @@ void launch_kick2(mw_system* s) {
     k_kick2<false><<<kb, kKThreads, 0, s->stream>>>(s->d);
 }
 
+// Blocks of the two-kernel cell scan: about 512 cells each, at most the
+// chunk buffer's capacity.
+int scan_blocks(const mw_system* s) { return std::max(1, std::min(s->d.chunk_cap, div_up(s->ncell, 512))); }
+
+void launch_scan(mw_system* s) {
+  const int sb = scan_blocks(s);
+  k_scan_local<<<sb, kPersThreads, 0, s->stream>>>(s->d);
+  k_scan_offsets<<<sb, kPersThreads, 0, s->stream>>>(s->d);
+}
+
 void launch_rebuild(mw_system* s) {
   const Dev& d = s->d;
   const int gb = div_up(s->N, kThreads);
   k_bin<<<gb, kThreads, 0, s->stream>>>(d);
-  k_scan<<<1, kScanThreads, 0, s->stream>>>(d);
+  launch_scan(s);
   k_scatter<<<gb, kThreads, 0, s->stream>>>(d);
   k_copyback<<<std::max(gb, div_up(s->nbox, kThreads)), kThreads, 0, s->stream>>>(d);
   k_neigh<<<div_up((long long)s->ncell * 32, kThreads), kThreads, 0, s->stream>>>(d, s->fp.rl2);

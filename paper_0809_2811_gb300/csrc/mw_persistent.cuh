@@ -181,6 +181,19 @@ __device__ void scan_chunk_offsets(const Dev& d) {
   __syncthreads();
 }
 
+// The same two halves as separate kernels, for the per-phase engines (the
+// graph's rebuild body and the host-launched rebuilds): a grid of blocks in
+// place of the single block of k_scan, whose one-block pass over every cell
+// took tens of microseconds at 10^5 cells.  Grid size <= chunk_cap.
+__global__ void __launch_bounds__(kPersThreads) k_scan_local(Dev d) {
+  if (!d.g->any_rebuild || d.g->status) return;
+  scan_chunk_local(d);
+}
+__global__ void __launch_bounds__(kPersThreads) k_scan_offsets(Dev d) {
+  if (!d.g->any_rebuild || d.g->status) return;
+  scan_chunk_offsets(d);
+}
+
 template <bool kCount, bool kNpt = false>
 __global__ void __launch_bounds__(kPersThreads, kPersBlocksPerSm) k_persistent(Dev d, FParams P, int nsteps, unsigned long long wait_ns) {
   __shared__ LegTable T;

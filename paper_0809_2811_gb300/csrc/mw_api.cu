@@ -772,7 +772,19 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   const size_t bytes = sizeof(double) * 3 * (size_t)s->N;
   const double* xd = x;
   const double* vd = v;
-  if (!dev) {  // (finiteness is checked on the device, as for device inputs)
+  const bool keep = s->state_set && s->order_ok && s->integ.kind != TH_NPT;
+  if (!dev && keep) {
+    // the current order is kept, so the loading kernel reads the inputs
+    // through the atom permutation: one copy of each array to device memory
+    // first (a DMA at the link's rate) instead of scattered reads of host
+    // memory
+    MW_CUDA(cudaMemcpyAsync(s->d.stage, x, bytes, cudaMemcpyHostToDevice, s->stream));
+    xd = s->d.stage;
+    if (v) {
+      MW_CUDA(cudaMemcpyAsync(s->d.stage2, v, bytes, cudaMemcpyHostToDevice, s->stream));
+      vd = s->d.stage2;
+    }
+  } else if (!dev) {  // (finiteness is checked on the device, as for device inputs)
     // pinned (page-locked) host arrays are read by k_load_state in place,
     // through their device mapping; pageable ones are copied to staging first
     const double* xm = mapped_host(x);
@@ -799,7 +811,6 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   // that stopped on an error may have binned atoms without the scan that
   // clears them)
   const int gl = div_up(std::max(std::max(s->N, s->ncell), s->nbox), kThreads);
-  const bool keep = s->state_set && s->order_ok && s->integ.kind != TH_NPT;
   if (keep) {
     // the current order and lists stay (boxes whose atoms moved more than
     // half the skin from their list positions are flagged for a rebuild);

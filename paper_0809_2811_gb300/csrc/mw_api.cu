@@ -408,7 +408,7 @@ mw_status status_error(const Global& g) {
 
 // The kick kernels: the isobaric instantiations under MW_NPT.
 void launch_kick1(mw_system* s, bool cond, cudaGraphConditionalHandle h) {
-  const int kb = kick_blocks(s->N, kKThreads, kK1Items);
+  const int kb = kick_blocks(s->N, kKThreads);
   const bool npt = s->integ.kind == TH_NPT;
   if (cond)
     npt ? k_kick1<true, true><<<kb, kKThreads, 0, s->stream>>>(s->d, h)
@@ -443,7 +443,7 @@ void launch_rebuild(mw_system* s) {
   launch_scan(s);
   k_scatter<<<gb, kThreads, 0, s->stream>>>(d);
   k_copyback<<<std::max(gb, div_up(s->nbox, kThreads)), kThreads, 0, s->stream>>>(d);
-  k_neigh<<<div_up((long long)s->ncell * 32, kThreads), kThreads, 0, s->stream>>>(d, s->fp.rl2);
+  k_neigh<<<div_up((long long)s->ncell * 32, kNeighThreads), kNeighThreads, 0, s->stream>>>(d, s->fp.rl2);
 }
 
 void launch_force(mw_system* s) {
@@ -1831,7 +1831,7 @@ extern "C" mw_status mw_energy_forces_noalloc(int n, const double box[3], const 
   k_na_scatter<<<gb, kThreads, 0, sm>>>(d, tq);
   Dev ds = d;  // the sorted view: neighbour list and forces work on the cell-sorted copy
   ds.q = tq;
-  k_neigh<<<div_up(ncell * 32, kThreads), kThreads, 0, sm>>>(ds, tmp.fp.rl2);
+  k_neigh<<<div_up(ncell * 32, kNeighThreads), kNeighThreads, 0, sm>>>(ds, tmp.fp.rl2);
   k_prep_force<<<gb, kThreads, 0, sm>>>(ds, 1);
   k_force<false><<<div_up(n, kFAtoms), kFThreads, 0, sm>>>(ds, tmp.fp);
   k_na_out<<<gb, kThreads, 0, sm>>>(ds, f_dev, energy_dev, virial_dev);

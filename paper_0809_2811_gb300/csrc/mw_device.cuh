@@ -249,6 +249,13 @@ __device__ __forceinline__ float fix_diff(uint32_t a, uint32_t b, float lq) {  /
   return __int2float_rn((int)(b - a)) * lq;
 }
 
+// Store of v to *addr when p holds, as one predicated store (no branch
+// around it).
+__device__ __forceinline__ void st_if(bool p, int* addr, int v) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.global.b32 [%1], %2;\n}" ::"r"((int)p), "l"(addr), "r"(v)
+               : "memory");
+}
+
 __device__ __forceinline__ void red_add_v4(float4* addr, float a, float b, float c) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(0.0f)
                : "memory");
@@ -752,104 +759,76 @@ __device__ __forceinline__ bool block_stop(const Dev& d) {
 // of this one use the same force, so they are folded: v = S v + (S + 1) a
 // when a half-kick is pending (S = thermostat scale of the step boundary,
 // a = dt/2 F/m), else v = S v + a; then s += (dt/L) v on the box fraction,
-// fixed-point copy, displacement check against the last build.  Three lanes
-// per atom, one per Cartesian component (10 atoms per warp, lanes 30 and 31
-// idle).  No FP64 instruction: v is the unevaluated sum hi + lo of two FP32
-// values, updated as hi + t with t = (S - 1) v + kick and the rounding error
-// of that sum carried into lo (Knuth's two-sum); the drift (dt/L) v 2^64 is
-// rounded once to FP32 and added exactly to the 64-bit box fraction, which
-// wraps at the faces by itself.  The runaway check is an integer test of the
-// FP32 exponent.  Also zeroes f for this step.
-constexpr int kKAtoms = 10;     // atoms per warp in the kick kernels
-constexpr int kKThreads = 512;  // threads per block of k_kick1 / k_kick2 (few blocks: few same-address atomics)
-// kick1 in two halves, so that a warp can issue the loads of several items
-// before it uses any: kick1_load reads what the item needs (nothing it
-// reads is written by another item), kick1_apply computes and stores.
-struct Kick1In {
-  float F, Fpad;
-  float2 v0;
-  unsigned long long s0;
-  uint32_t qb;
-  int b;
-  int i, c;
-  bool act;
-};
-
-__device__ __forceinline__ Kick1In kick1_load(const Dev& d, int w) {
-  const int lane = threadIdx.x & 31;
-  Kick1In k;
-  k.i = w * kKAtoms + lane / 3;
-  k.c = lane - 3 * (lane / 3);
-  k.act = lane < 3 * kKAtoms && k.i < d.N;
-  k.b = -1;
-  k.F = 0.f;
-  k.v0 = make_float2(0.f, 0.f);
-  k.s0 = 0ull;
-  k.qb = 0u;
-  if (k.act) {
-    const int i = k.i, c = k.c;
-    k.b = (int)d.q[i].w;
-    k.F = reinterpret_cast<const float*>(d.f + i)[c];
-    k.v0 = (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz))[i];
-    k.s0 = (c == 0 ? d.x : (c == 1 ? d.y : d.z))[i];
-    k.qb = reinterpret_cast<const uint32_t*>(d.qb + i)[c];
-  }
-  return k;
-}
+// fixed-point copy, displacement check against the last build.  One thread
+// per atom, its three components in turn: every array is read and written
+// with one coalesced vector access per warp (the force and the fixed-point
+// copies as 16-byte records, the velocity and fraction components as 8-byte
+// words), and the box's constants are loaded once per atom.  No FP64
+// instruction: v is the unevaluated sum hi + lo of two FP32 values, updated
+// as hi + t with t = (S - 1) v + kick and the rounding error of that sum
+// carried into lo (Knuth's two-sum); the drift (dt/L) v 2^64 is rounded once
+// to FP32 and added exactly to the 64-bit box fraction, which wraps at the
+// faces by itself.  The runaway check is an integer test of the FP32
+// exponent.  Also zeroes f for this step.
+constexpr int kKThreads = 256;  // threads per block of k_kick1 / k_kick2
 
 template <bool kNpt>
-__device__ __forceinline__ void kick1_apply(const Dev& d, const Integ& I, const Kick1In& k, int par, int pend) {
-  const int lane = threadIdx.x & 31;
-  const int i = k.i, c = k.c, b = k.b;
-  float dd = 0.f;
+__device__ __forceinline__ void kick1_atom(const Dev& d, const Integ& I, int i, int par, int pend) {
+  // every load first (nothing here is written by another atom's thread)
+  const uint4 q = d.q[i];
+  const float4 F = d.f[i];
+  const uint4 qb = d.qb[i];
+  const float2 v0[3] = {d.vx[i], d.vy[i], d.vz[i]};
+  const unsigned long long s0[3] = {d.x[i], d.y[i], d.z[i]};
+  const int b = (int)q.w;
+  const Box& bx = d.box[b];
+  const float sig = d.bst[b].sig;
+  const float kf = I.cf_f * (pend ? 2.0f + sig : 1.0f);
+  const int vexp = bx.vexp_lost;
+  const float Fc[3] = {F.x, F.y, F.z};
+  const uint32_t qbc[3] = {qb.x, qb.y, qb.z};
+  float2 vn[3];
+  unsigned long long sn[3];
+  uint32_t qn[3];
+  float dd = 0.f;  // squared displacement since the last build
   bool lost = false;
-  if (k.act) {
-    float* fp = reinterpret_cast<float*>(d.f + i) + c;
-    float2* vp = (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz)) + i;
-    unsigned long long* sp = (c == 0 ? d.x : (c == 1 ? d.y : d.z)) + i;
-    const float F = k.F;
-    const float2 v0 = k.v0;
-    const unsigned long long s0 = k.s0;
-    const uint32_t qb = k.qb;
-    const Box& bx = d.box[b];
-    const BoxState* st = d.bst + b;
-    const float sig = st->sig;
-    const float kf = I.cf_f * (pend ? 2.0f + sig : 1.0f);
-    const float k64 = c == 0 ? bx.dtL64[0] : (c == 1 ? bx.dtL64[1] : bx.dtL64[2]);
-    const float Lq = c == 0 ? bx.Lq[0] : (c == 1 ? bx.Lq[1] : bx.Lq[2]);
-    const int vexp = bx.vexp_lost;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
     // v + t as hi + lo: two-sum of hi and t, its error added to lo, renormalised
-    const float t = fmaf(sig, v0.x, fmaf(sig, v0.y, kf * F));
-    const float sh = v0.x + t;
-    const float bb = sh - v0.x;
-    const float er = (v0.x - (sh - bb)) + (t - bb);
-    const float lo1 = v0.y + er;
+    const float t = fmaf(sig, v0[c].x, fmaf(sig, v0[c].y, kf * Fc[c]));
+    const float sh = v0[c].x + t;
+    const float bb = sh - v0[c].x;
+    const float er = (v0[c].x - (sh - bb)) + (t - bb);
+    const float lo1 = v0[c].y + er;
     const float hi = sh + lo1;
     const float lo = lo1 - (hi - sh);
+    const float k64 = bx.dtL64[c];
     const long long inc = f2ll_exact(fmaf(hi, k64, lo * k64));
-    const unsigned long long sn = s0 + (unsigned long long)inc;
-    if (inc > 0 ? sn < s0 : sn > s0)  // the 64-bit fraction wrapped: the atom crossed a face
+    sn[c] = s0[c] + (unsigned long long)inc;
+    if (inc > 0 ? sn[c] < s0[c] : sn[c] > s0[c])  // the 64-bit fraction wrapped: the atom crossed a face
       reinterpret_cast<int*>(d.img + i)[c] += inc > 0 ? 1 : -1;
-    *fp = 0.f;
-    *vp = make_float2(hi, lo);
-    *sp = sn;
-    const uint32_t qn = q_of(sn);
-    reinterpret_cast<uint32_t*>(d.q + i)[c] = qn;
-    const float dc = fix_diff(qb, qn, Lq);
-    dd = dc * dc;
+    vn[c] = make_float2(hi, lo);
+    qn[c] = q_of(sn[c]);
+    const float dc = fix_diff(qbc[c], qn[c], bx.Lq[c]);
+    dd += __fmul_rn(dc, dc);
     // |v| at or above the box's runaway threshold (or NaN/inf): exponent field test
-    lost = (int)((__float_as_uint(hi) >> 23) & 0xffu) >= vexp;
-    if (i == bx.off && c == 0) {  // this step's accumulators start from zero
-      BoxState* sw = d.bst + b;
-      sw->ke_acc[par] = 0.0;
-#pragma unroll
-      for (int k2 = 0; k2 < 8; ++k2) sw->ew[par][k2] = 0.0;
-    }
+    lost |= (int)((__float_as_uint(hi) >> 23) & 0xffu) >= vexp;
   }
-  // displacement since the last build: sum the three components of the atom
-  const int base = lane - c;
-  const float d1 = __shfl_sync(kFull, dd, min(base + 1, 31)), d2 = __shfl_sync(kFull, dd, min(base + 2, 31));
-  if (k.act && c == 0 && dd + d1 + d2 > (kNpt ? d.box[b].hs2 : I.half_skin2)) {
+  d.f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  d.vx[i] = vn[0];
+  d.vy[i] = vn[1];
+  d.vz[i] = vn[2];
+  d.x[i] = sn[0];
+  d.y[i] = sn[1];
+  d.z[i] = sn[2];
+  d.q[i] = make_uint4(qn[0], qn[1], qn[2], q.w);
+  if (i == bx.off) {  // this step's accumulators start from zero
+    BoxState* sw = d.bst + b;
+    sw->ke_acc[par] = 0.0;
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) sw->ew[par][k2] = 0.0;
+  }
+  if (dd > (kNpt ? bx.hs2 : I.half_skin2)) {
     d.bst[b].rebuild = 1;
     d.g->any_rebuild = 1;
   }
@@ -859,28 +838,23 @@ __device__ __forceinline__ void kick1_apply(const Dev& d, const Integ& I, const 
   }
 }
 
-// a1 + a7 (first half) of one item (kKAtoms atoms, three lanes per atom).
-template <bool kNpt>
-__device__ __forceinline__ void kick1_lane(const Dev& d, const Integ& I, int w, int par, int pend) {
-  const Kick1In k = kick1_load(d, w);
-  kick1_apply<kNpt>(d, I, k, par, pend);
-}
-
-// a7 (second half): the kinetic energy of v + a (FP32 per component; the
-// sums over atoms are FP64).  The half-kick itself is left pending and folded
-// into the next kick1 (or applied when the state is read).  Same lane layout
-// as kick1_lane.
-__device__ __forceinline__ float kick2_lane(const Dev& d, const Integ& I, int w, int& b) {
-  const int lane = threadIdx.x & 31;
-  const int i = w * kKAtoms + lane / 3;
-  const int c = lane - 3 * (lane / 3);
+// a7 (second half): the kinetic energy of atom i's v + a (FP32 per
+// component and per atom; the sums over atoms are FP64).  The half-kick
+// itself is left pending and folded into the next kick1 (or applied when the
+// state is read).  b: the atom's box (-1 past the last atom).
+__device__ __forceinline__ float kick2_atom(const Dev& d, const Integ& I, int i, int& b) {
   b = -1;
-  if (lane >= 3 * kKAtoms || i >= d.N) return 0.f;
+  if (i >= d.N) return 0.f;
   b = (int)d.q[i].w;
-  const float F = reinterpret_cast<const float*>(d.f + i)[c];
-  const float2 v = (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz))[i];
-  const float u = fmaf(I.cf_f, F, v.x) + v.y;
-  const float ke = (float)I.ke_fac * u * u;
+  const float4 F = d.f[i];
+  const float2 v[3] = {d.vx[i], d.vy[i], d.vz[i]};
+  const float Fc[3] = {F.x, F.y, F.z};
+  float ke = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float u = fmaf(I.cf_f, Fc[c], v[c].x) + v[c].y;
+    ke += (float)I.ke_fac * u * u;
+  }
   if (!(ke < 1e30f)) {
     set_status(d.g, ST_NAN);
     d.g->err_index = i;
@@ -890,30 +864,36 @@ __device__ __forceinline__ float kick2_lane(const Dev& d, const Integ& I, int w,
 
 // ---------------------------------------------------------------------------
 // Neighbour list (a3): one warp per cell.  The candidates of the
-// (deduplicated) 27-cell stencil are flattened over the lanes, each lane
-// loading one candidate per chunk of 32; the chunk is then tested against
-// every centre atom of the cell (up to 32 at a time), each centre's lane
-// keeps its ballot, and the centres append their hits to their rows.
+// (deduplicated) 27-cell stencil are flattened in stencil order and staged,
+// up to kNStage at a time, in the warp's slice of shared memory; then every
+// centre atom of the cell in turn runs over the staged candidates 32 at a
+// time (one per lane), and the hits of each batch go straight to their
+// places in the centre's row (its running count plus the hits of lower
+// lanes), so each row lists its neighbours in stencil order.
+constexpr int kNStage = 256;  // candidates staged per warp at a time (4 KB)
 __device__ __forceinline__ int stencil_n(int nc) { return nc >= 3 ? 3 : nc; }
 __device__ __forceinline__ int stencil_off(int nc, int o) { return nc >= 3 ? o - 1 : o; }
 
-// The rows of one cell's centres (neigh_cell_warp).  Lane t of a batch holds
-// candidate t of the stencil's concatenated cells (located by a binary search
-// over the warp's inclusive counts).  Each centre k in turn tests the batch,
-// and lane k keeps the ballot: its centre's hit mask.  Then every lane appends
-// its centre's hits in candidate order (lowest bit first), so each row lists
-// its neighbours in stencil order as a per-hit prefix count would, with no
-// per-centre bookkeeping in the test loop.
+// The rows of one cell's centres (neigh_cell_warp).  Staging: lane t of a
+// batch takes candidate t of the stencil's concatenated cells (located by a
+// binary search over the warp's inclusive counts) and stores (x, y, z, j);
+// entries past the last candidate get j = -1 (and, with kFrame, an offset
+// no distance test passes).  The centres go over a batch two at a time, so
+// that each staged record is read once for both.  A count past the row
+// width (an overflow: the status makes the caller grow the rows and build
+// again) writes to the row's last slot, never past it.
 // kFrame: every axis of the box has at least 4 cells, so each candidate lies
 // within two cell edges of o, the cell's first atom; offsets from o are exact
-// fixed-point differences with no wrap, converted once per atom, and a pair's
-// displacement is their FP32 difference.  Otherwise (grids of 1-3 cells on an
-// axis, where the stencil wraps round the box) each pair takes its own
+// fixed-point differences with no wrap, converted once per atom and staged
+// as FP32, and a pair's displacement is their FP32 difference.  Otherwise
+// (grids of 1-3 cells on an axis, where the stencil wraps round the box) the
+// fixed-point coordinates are staged and each pair takes its own
 // minimum-image fixed-point difference.
 template <bool kFrame>
-__device__ __forceinline__ void neigh_rows(const Dev& d, const uint4* qa, int a0, int ni, int incl, int start,
-                                           int excl, int total, float L0, float L1, float L2, float rl2) {
+__device__ __forceinline__ void neigh_rows(const Dev& d, const uint4* qa, float4* stg, int a0, int ni, int incl,
+                                           int start, int excl, int total, float L0, float L1, float L2, float rl2) {
   const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;  // lanes under this one
   const uint4 o = qa[a0];
   for (int ib = 0; ib < ni; ib += 32) {  // centre atoms of this cell, 32 at a time
     const int nb = min(32, ni - ib);
@@ -925,51 +905,72 @@ __device__ __forceinline__ void neigh_rows(const Dev& d, const uint4* qa, int a0
     } else {
       cx = __uint_as_float(qmine.x); cy = __uint_as_float(qmine.y); cz = __uint_as_float(qmine.z);
     }
-    int* const row = d.nbr + (size_t)me * d.W;
     int mycount = 0;  // neighbours of lane k's centre so far
-    for (int base = 0; base < total; base += 32) {
-      const int t = base + lane;
-      int lo = 0, hi = 31;
+    for (int c0 = 0; c0 < total; c0 += kNStage) {  // chunks of the candidate list (warp-uniform)
+      const int nch = min(kNStage, total - c0);
+      const int nbat = (nch + 31) >> 5;
+      __syncwarp();  // the previous chunk's readers are done
+      for (int bt = 0; bt < nbat; ++bt) {
+        const int t = c0 + (bt << 5) + lane;
+        int lo = 0, hi = 31;
 #pragma unroll
-      for (int it = 0; it < 5; ++it) {  // smallest lane k with incl_k > t
-        const int mid = (lo + hi) >> 1;
-        const int v = __shfl_sync(kFull, incl, mid);
-        if (v > t) hi = mid; else lo = mid + 1;
-      }
-      const int sk = __shfl_sync(kFull, start, lo);
-      const int ek = __shfl_sync(kFull, excl, lo);
-      const bool have = t < total;
-      const int j = have ? sk + (t - ek) : -1;
-      const uint4 qj = have ? qa[j] : make_uint4(0u, 0u, 0u, 0u);
-      float jx = 0.f, jy = 0.f, jz = 0.f;
-      if constexpr (kFrame) {
-        jx = fix_diff(o.x, qj.x, L0); jy = fix_diff(o.y, qj.y, L1); jz = fix_diff(o.z, qj.z, L2);
-      }
-      unsigned mine = 0u;  // lane k: which candidates of this batch are centre k's neighbours
-      for (int k = 0; k < nb; ++k) {
-        const float xk = __shfl_sync(kFull, cx, k), yk = __shfl_sync(kFull, cy, k), zk = __shfl_sync(kFull, cz, k);
-        float dx, dy, dz;
-        if constexpr (kFrame) {
-          dx = jx - xk; dy = jy - yk; dz = jz - zk;
-        } else {
-          dx = fix_diff(__float_as_uint(xk), qj.x, L0);
-          dy = fix_diff(__float_as_uint(yk), qj.y, L1);
-          dz = fix_diff(__float_as_uint(zk), qj.z, L2);
+        for (int it = 0; it < 5; ++it) {  // smallest lane k with incl_k > t
+          const int mid = (lo + hi) >> 1;
+          const int v = __shfl_sync(kFull, incl, mid);
+          if (v > t) hi = mid; else lo = mid + 1;
         }
-        const bool pred = have && j != a0 + ib + k && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
-        const unsigned bal = __ballot_sync(kFull, pred);
-        if (lane == k) mine = bal;
-      }
-      // append: as many rounds as the centre with the most hits in this batch
-      const int rounds = __reduce_max_sync(kFull, __popc(mine));
-      for (int h = 0; h < rounds; ++h) {
-        const int src = mine ? __ffs(mine) - 1 : 0;
-        const int jj = __shfl_sync(kFull, j, src);
-        if (mine) {
-          if (mycount < d.W) row[mycount] = jj;
-          ++mycount;
-          mine &= mine - 1u;
+        const int sk = __shfl_sync(kFull, start, lo);
+        const int ek = __shfl_sync(kFull, excl, lo);
+        float4 e = make_float4(kFrame ? 1e30f : 0.f, 0.f, 0.f, __int_as_float(-1));
+        if (t < total) {
+          const int j = sk + (t - ek);
+          const uint4 qj = qa[j];
+          if constexpr (kFrame)
+            e = make_float4(fix_diff(o.x, qj.x, L0), fix_diff(o.y, qj.y, L1), fix_diff(o.z, qj.z, L2), __int_as_float(j));
+          else
+            e = make_float4(__uint_as_float(qj.x), __uint_as_float(qj.y), __uint_as_float(qj.z), __int_as_float(j));
         }
+        stg[(bt << 5) + lane] = e;
+      }
+      __syncwarp();
+      for (int k = 0; k < nb; k += 2) {  // centres k and k + 1 over the staged batch (warp-uniform)
+        const bool two = k + 1 < nb;        // (an odd last centre runs alone)
+        const int k1 = two ? k + 1 : k;
+        const float xa = __shfl_sync(kFull, cx, k), ya = __shfl_sync(kFull, cy, k), za = __shfl_sync(kFull, cz, k);
+        const float xb = __shfl_sync(kFull, cx, k1), yb = __shfl_sync(kFull, cy, k1), zb = __shfl_sync(kFull, cz, k1);
+        const int ia = a0 + ib + k, ibb = a0 + ib + k1;
+        int ca = __shfl_sync(kFull, mycount, k), cb = __shfl_sync(kFull, mycount, k1);
+        int* const ra = d.nbr + (size_t)ia * d.W;
+        int* const rb = d.nbr + (size_t)ibb * d.W;
+        const int wl = d.W - 1;
+#pragma unroll 2
+        for (int bt = 0; bt < nbat; ++bt) {
+          const float4 e = stg[(bt << 5) + lane];
+          const int j = __float_as_int(e.w);
+          float ax, ay, az, bx2, by2, bz2;
+          if constexpr (kFrame) {
+            ax = e.x - xa; ay = e.y - ya; az = e.z - za;
+            bx2 = e.x - xb; by2 = e.y - yb; bz2 = e.z - zb;
+          } else {
+            ax = fix_diff(__float_as_uint(xa), __float_as_uint(e.x), L0);
+            ay = fix_diff(__float_as_uint(ya), __float_as_uint(e.y), L1);
+            az = fix_diff(__float_as_uint(za), __float_as_uint(e.z), L2);
+            bx2 = fix_diff(__float_as_uint(xb), __float_as_uint(e.x), L0);
+            by2 = fix_diff(__float_as_uint(yb), __float_as_uint(e.y), L1);
+            bz2 = fix_diff(__float_as_uint(zb), __float_as_uint(e.z), L2);
+          }
+          // (kFrame: padding entries fail the distance test by their offset)
+          const bool live = kFrame || j >= 0;
+          const bool pa = live && j != ia && fmaf(ax, ax, fmaf(ay, ay, az * az)) < rl2;
+          const bool pb = two && live && j != ibb && fmaf(bx2, bx2, fmaf(by2, by2, bz2 * bz2)) < rl2;
+          const unsigned ba = __ballot_sync(kFull, pa), bb = __ballot_sync(kFull, pb);
+          st_if(pa, ra + min(ca + __popc(ba & below), wl), j);
+          st_if(pb, rb + min(cb + __popc(bb & below), wl), j);
+          ca += __popc(ba);
+          cb += __popc(bb);
+        }
+        if (lane == k) mycount = ca;
+        if (two && lane == k1) mycount = cb;
       }
     }
     if (lane < nb) d.nbr_cnt[me] = mycount;
@@ -983,7 +984,8 @@ __device__ __forceinline__ void neigh_rows(const Dev& d, const uint4* qa, int a0
   }
 }
 
-__device__ void neigh_cell_warp(const Dev& d, const uint4* qa, int c, float rl2) {
+// stg: the warp's kNStage float4 of shared memory.
+__device__ void neigh_cell_warp(const Dev& d, const uint4* qa, float4* stg, int c, float rl2) {
   const int lane = threadIdx.x & 31;
   const int a0 = d.cell_start[c];
   const int ni = d.cell_start[c + 1] - a0;
@@ -991,13 +993,28 @@ __device__ void neigh_cell_warp(const Dev& d, const uint4* qa, int c, float rl2)
   const Box& bx = d.box[d.cell_box[c]];
   const int cl = c - bx.cell_off;
   const int cx = cl % bx.nc[0], cy = (cl / bx.nc[0]) % bx.nc[1], cz = cl / (bx.nc[0] * bx.nc[1]);
-  const int nx = stencil_n(bx.nc[0]), ny = stencil_n(bx.nc[1]), nz = stencil_n(bx.nc[2]);
+  const bool frame = bx.nc[0] >= 4 && bx.nc[1] >= 4 && bx.nc[2] >= 4;  // warp-uniform
   int start = 0, cnt = 0;
-  if (lane < nx * ny * nz) {
-    const int ox = lane % nx, oy = (lane / nx) % ny, oz = lane / (nx * ny);
-    const int X = (cx + stencil_off(bx.nc[0], ox) + bx.nc[0]) % bx.nc[0];
-    const int Y = (cy + stencil_off(bx.nc[1], oy) + bx.nc[1]) % bx.nc[1];
-    const int Z = (cz + stencil_off(bx.nc[2], oz) + bx.nc[2]) % bx.nc[2];
+  int X = -1, Y = 0, Z = 0;  // lane's stencil cell
+  if (frame) {  // 3 x 3 x 3 distinct cells; offsets -1, 0, 1 wrap by one compare
+    if (lane < 27) {
+      X = cx + lane % 3 - 1;
+      Y = cy + (lane / 3) % 3 - 1;
+      Z = cz + lane / 9 - 1;
+      X += X < 0 ? bx.nc[0] : (X >= bx.nc[0] ? -bx.nc[0] : 0);
+      Y += Y < 0 ? bx.nc[1] : (Y >= bx.nc[1] ? -bx.nc[1] : 0);
+      Z += Z < 0 ? bx.nc[2] : (Z >= bx.nc[2] ? -bx.nc[2] : 0);
+    }
+  } else {
+    const int nx = stencil_n(bx.nc[0]), ny = stencil_n(bx.nc[1]), nz = stencil_n(bx.nc[2]);
+    if (lane < nx * ny * nz) {
+      const int ox = lane % nx, oy = (lane / nx) % ny, oz = lane / (nx * ny);
+      X = (cx + stencil_off(bx.nc[0], ox) + bx.nc[0]) % bx.nc[0];
+      Y = (cy + stencil_off(bx.nc[1], oy) + bx.nc[1]) % bx.nc[1];
+      Z = (cz + stencil_off(bx.nc[2], oz) + bx.nc[2]) % bx.nc[2];
+    }
+  }
+  if (X >= 0) {
     const int cc = bx.cell_off + X + bx.nc[0] * (Y + bx.nc[1] * Z);
     start = d.cell_start[cc];
     cnt = d.cell_start[cc + 1] - start;
@@ -1011,10 +1028,10 @@ __device__ void neigh_cell_warp(const Dev& d, const uint4* qa, int c, float rl2)
   const int excl = incl - cnt;
   const int total = __shfl_sync(kFull, incl, 31);
   const float L0 = bx.Lq[0], L1 = bx.Lq[1], L2 = bx.Lq[2];
-  if (bx.nc[0] >= 4 && bx.nc[1] >= 4 && bx.nc[2] >= 4)
-    neigh_rows<true>(d, qa, a0, ni, incl, start, excl, total, L0, L1, L2, rl2);
+  if (frame)
+    neigh_rows<true>(d, qa, stg, a0, ni, incl, start, excl, total, L0, L1, L2, rl2);
   else
-    neigh_rows<false>(d, qa, a0, ni, incl, start, excl, total, L0, L1, L2, rl2);
+    neigh_rows<false>(d, qa, stg, a0, ni, incl, start, excl, total, L0, L1, L2, rl2);
 }
 
 // ---------------------------------------------------------------------------
@@ -1049,19 +1066,26 @@ constexpr int kG = 4;                    // lanes per centre in the leg phase
 constexpr int kFThreads = 128;
 constexpr int kFAtoms = kFThreads / kG;  // centres per block
 constexpr int kWAtoms = 32 / kG;         // centres per warp
-constexpr int kLPad = kLMax + 1;         // row pitch (float4): shifts rows by 4 banks
-constexpr int kPre = 8;                  // neighbour slots per lane fetched ahead in the leg phase
+constexpr int kLPad = kLMax + 1;         // row pitch (float4) of the adjoint's leg tables
+constexpr int kPre = 6;                  // neighbour slots per lane fetched ahead in the leg phase (8 spills at 64 registers)
 
-template <int kPad, int kCent = kFAtoms>
+// The force kernel's shared-memory leg table: a row of kRow float4 records
+// per centre (kRow a multiple of 8, i.e. of the 8 bank groups a quarter warp's
+// 16-byte accesses spread over).  Leg l of centre a sits at a kRow +
+// (l ^ ((a KG) & 7)): the XOR moves the centres that share a quarter warp
+// onto disjoint bank groups when their lanes step through legs l = g, g + KG,
+// ... together (KG = 2 or 4; with 8 lanes a quarter warp holds one centre).
+template <int kRow, int kCent = kFAtoms>
 struct LegTableT {
-  float4 ue[kCent * kPad];   // ux, uy, uz, ee
-  float4 aux[kCent * kPad];  // tr, nde, r, j (int bits)
+  static_assert(kRow % 8 == 0, "rows must cover whole sets of bank groups");
+  float4 ue[kCent * kRow];   // phase A: dx, dy, dz, j (int bits); then ux, uy, uz, ee
+  float4 aux[kCent * kRow];  // -1/2 dphi, nde, r, j (int bits)
 };
-using LegTable = LegTableT<kLPad>;
+using LegTable = LegTableT<kLMax>;
 // Several species: a solute's larger cutoff gives its centres more legs, so
-// the species instantiation stages up to 48 (row pitch 49 float4, 4 banks).
+// the species instantiation stages up to 48.
 constexpr int kLMaxSp = 48;
-using LegTableSp = LegTableT<kLMaxSp + 1>;
+using LegTableSp = LegTableT<kLMaxSp>;
 
 // Whole owner contribution (pair terms and three-body terms) of a centre with
 // more than kLMax legs (rare): legs in local memory, every unordered leg pair
@@ -1184,13 +1208,14 @@ __device__ __noinline__ int species_item(const Dev& d, const SpPair* sp, const f
 // their own terms' forces to them by scatter.
 template <bool kCount, int kSp = 0, int KG = kG, int kOwn = 0>
 __device__ void force_block(const Dev& d, const FParams& P,
-                            LegTableT<(kSp ? kLMaxSp : kLMax) + 1, kFThreads / KG>& T, int blk, int par,
+                            LegTableT<(kSp ? kLMaxSp : kLMax), kFThreads / KG>& T, int blk, int par,
                             const SpPair* sps = nullptr, int nsp = 1, const float2* stt = nullptr) {
   constexpr int kLM = kSp ? kLMaxSp : kLMax;  // legs staged per centre
-  constexpr int kLP = kLM + 1;                // row pitch
   const int lane = threadIdx.x & 31;
   const int g = threadIdx.x & (KG - 1);
   const int a = threadIdx.x / KG;
+  const int sw = (a * KG) & 7;                                  // the row's bank-group swizzle
+  auto at = [&](int l) { return a * kLM + (l ^ sw); };          // leg l of this centre
   const int i = blk * (kFThreads / KG) + a;
   const bool valid = i < d.N;
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // E2, E3, W xx yy zz xy xz yz
@@ -1216,8 +1241,8 @@ __device__ void force_block(const Dev& d, const FParams& P,
   // ---- leg phase A: row entries and candidate positions are fetched for
   // kPre slots per lane before any is used (two memory latencies per batch
   // instead of a dependent chain per slot).  Distance test only; hits are
-  // compacted (ballot + popc in the lane group) into the centre's row as
-  // (d, r^2 | j).
+  // compacted (ballot + popc in the lane group) into the centre's row as one
+  // record (d, j) (several species: (d, r^2) and (species, j)).
   const int iters = __reduce_max_sync(kFull, (cnt + KG - 1) / KG);
   const unsigned gsh = lane & ~(KG - 1);
   const int* row = d.nbr + (size_t)(valid ? i : 0) * d.W;
@@ -1239,8 +1264,12 @@ __device__ void force_block(const Dev& d, const FParams& P,
     const unsigned m = (__ballot_sync(kFull, hit) >> gsh) & ((1u << KG) - 1u);
     const int pos = nl + __popc(m & ((1u << g) - 1u));
     if (hit && pos < kLM) {
-      T.ue[a * kLP + pos] = make_float4(dx, dy, dz, r2);
-      T.aux[a * kLP + pos] = make_float4(__int_as_float(tj), 0.f, 0.f, __int_as_float(j));
+      if constexpr (kSp) {  // (the pair's cutoff test needs r^2 again in phase B: kept)
+        T.ue[at(pos)] = make_float4(dx, dy, dz, r2);
+        T.aux[at(pos)] = make_float4(__int_as_float(tj), 0.f, 0.f, __int_as_float(j));
+      } else {  // one record: r^2 is recomputed from d in phase B by the same expression
+        T.ue[at(pos)] = make_float4(dx, dy, dz, __int_as_float(j));
+      }
     }
     nl += __popc(m);
   };
@@ -1251,8 +1280,7 @@ __device__ void force_block(const Dev& d, const FParams& P,
       const int j = d.legs[(size_t)i * kLMax + l];
       const uint4 qj = d.q[j];
       const float dx = fix_diff(qi.x, qj.x, L0), dy = fix_diff(qi.y, qj.y, L1), dz = fix_diff(qi.z, qj.z, L2);
-      T.ue[a * kLP + l] = make_float4(dx, dy, dz, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-      T.aux[a * kLP + l] = make_float4(0.f, 0.f, 0.f, __int_as_float(j));
+      T.ue[at(l)] = make_float4(dx, dy, dz, __int_as_float(j));
     }
   } else
   // batches of kPre slots per lane, each fetched as a whole (rows, then
@@ -1284,7 +1312,7 @@ __device__ void force_block(const Dev& d, const FParams& P,
   }
   __syncwarp();
   if constexpr (kOwn == 1) {  // the staged legs for pass 2
-    for (int l = g; l < min(nl, kLM); l += KG) d.legs[(size_t)i * kLMax + l] = __float_as_int(T.aux[a * kLP + l].w);
+    for (int l = g; l < min(nl, kLM); l += KG) d.legs[(size_t)i * kLMax + l] = __float_as_int(T.ue[at(l)].w);
     if (valid && g == 0) d.nleg[i] = nl <= kLM ? nl : -1;
   }
   // ---- leg phase B: leg terms for the compacted legs only, spread over the
@@ -1295,9 +1323,11 @@ __device__ void force_block(const Dev& d, const FParams& P,
   float mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;     // M
   int nvalid = 0;  // legs inside their own pair's cutoff (kSp counting)
   for (int l = g; l < nstage; l += KG) {
-    float4* ue_p = T.ue + a * kLP + l;
-    float4* ax_p = T.aux + a * kLP + l;
+    float4* ue_p = T.ue + at(l);
+    float4* ax_p = T.aux + at(l);
     const float4 rec = *ue_p;
+    // (one species: the record is d and j; r^2 as in phase A's test)
+    const float r2 = kSp ? rec.w : fmaf(rec.x, rec.x, fmaf(rec.y, rec.y, rec.z * rec.z));
     // the leg's terms with the one species' constants, or its pair's (kSp)
     LegTerms lt;
     float p_h = P.sle;
@@ -1305,9 +1335,9 @@ __device__ void force_block(const Dev& d, const FParams& P,
     if constexpr (kSp) {
       const SpPair& pp = spi[__float_as_int(ax_p->x)];
       p_h = kSp == 2 ? 1.0f : pp.h;  // kSp = 2: the strengths come per leg pair in phase C
-      in = leg_terms(rec.w, pp, lt);
+      in = leg_terms(r2, pp, lt);
     } else {
-      in = leg_terms(rec.w, P, lt);
+      in = leg_terms(r2, P, lt);
     }
     if (!in) {  // FP32 rounding put it on the cutoff (or past its pair's): contributes nothing
       *ue_p = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1349,7 +1379,8 @@ __device__ void force_block(const Dev& d, const FParams& P,
     *ue_p = make_float4(ux, uy, uz, ee);
     // (-1/2 dphi: the pair term's share of the virial, taken in phase C), nde, r, j
     // (kSp = 2: j with the partner's species in bits 28-30)
-    const float jw = kSp == 2 ? __int_as_float(__float_as_int(ax_p->w) | (__float_as_int(ax_p->x) << 28)) : ax_p->w;
+    const float jw = kSp == 2 ? __int_as_float(__float_as_int(ax_p->w) | (__float_as_int(ax_p->x) << 28))
+                              : (kSp ? ax_p->w : rec.w);
     *ax_p = make_float4(-0.5f * dphi, lt.nde, r, jw);
     if constexpr (kSp == 2) continue;  // no moments
     const float ex = ee * ux, ey = ee * uy, ez = ee * uz;
@@ -1389,8 +1420,8 @@ __device__ void force_block(const Dev& d, const FParams& P,
     // ---- leg phase C (any table): leg j against every other leg k
     const float2* stc = stt + ti * nsp * nsp;
     for (int l = g; l < nstage; l += KG) {
-      const float4 uj = T.ue[a * kLP + l];
-      const float4 xj = T.aux[a * kLP + l];
+      const float4 uj = T.ue[at(l)];
+      const float4 xj = T.aux[at(l)];
       if (uj.w == 0.f) continue;  // leg dropped in phase B
       const int wj = __float_as_int(xj.w);
       const float2* stj = stc + (wj >> 28) * nsp;
@@ -1399,9 +1430,9 @@ __device__ void force_block(const Dev& d, const FParams& P,
       const float nde = xj.y;
       float gx = 0.f, gy = 0.f, gz = 0.f;  // three-body force on the partner of leg j
       for (int k = 0; k < nstage; ++k) {
-        const float4 uk = T.ue[a * kLP + k];
+        const float4 uk = T.ue[at(k)];
         if (k == l || uk.w == 0.f) continue;
-        const float2 lc = stj[__float_as_int(T.aux[a * kLP + k].w) >> 28];  // (lambda eps, cos theta0)
+        const float2 lc = stj[__float_as_int(T.aux[at(k)].w) >> 28];  // (lambda eps, cos theta0)
         const float c = fmaf(uj.x, uk.x, fmaf(uj.y, uk.y, uj.z * uk.z));
         const float D = c - lc.y;
         const float gg = lc.x * uj.w * uk.w * D;
@@ -1459,8 +1490,8 @@ __device__ void force_block(const Dev& d, const FParams& P,
     return Cj;
   };
   for (int l = g; l < nstage; l += KG) {
-    const float4 uj = T.ue[a * kLP + l];
-    const float4 xj = T.aux[a * kLP + l];
+    const float4 uj = T.ue[at(l)];
+    const float4 xj = T.aux[at(l)];
     const float ee = uj.w;
     if (ee == 0.f) continue;  // leg dropped in phase B
     const float r = xj.z;
@@ -1544,9 +1575,9 @@ __device__ void force_block(const Dev& d, const FParams& P,
 // centre (kFThreads / KG centres per block) and a register budget of MINB
 // co-resident blocks per SM (65536 / (kFThreads MINB) registers a thread).
 template <bool kCount, int KG = kG, int MINB = 8, int kOwn = 0>
-__global__ void __launch_bounds__(kFThreads, MINB) k_force(Dev d, FParams P) {
+__global__ void __launch_bounds__(kFThreads, MINB) k_force(const __grid_constant__ Dev d, const __grid_constant__ FParams P) {
   if (block_stop(d)) return;
-  __shared__ LegTableT<kLPad, kFThreads / KG> T;
+  __shared__ LegTableT<kLMax, kFThreads / KG> T;
   const int par = (int)(d.g->step & 1ull);
   if (blockIdx.x == 0) {  // the rebuild (if any) is consumed
     for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
@@ -1579,12 +1610,10 @@ __host__ __device__ constexpr bool force_shape_owner(int s) { return s == 4; }
 // holds no conditional-node call, so profilers can capture it.
 // kNpt: the isobaric instantiation (rebuild margin per box, and its last
 // block makes the coming step's edges current).
-// The standalone kick kernels give each warp several items: warp wi of block
-// blk takes items (blk kK*Items + j) nwb + wi, j = 0 .. kK*Items - 1 (the
-// warps of a block on consecutive items at each j).  k_kick1 reads all its
-// items before it writes any; k_kick2 only reads atom data, and reduces its
-// items' kinetic energies per warp (box by box) and once per block.
-constexpr int kK1Items = 1;  // (two, with their loads first, measured no faster at 2^20 atoms)
+// k_kick1: one atom per thread.  k_kick2: kK2Items atoms per thread, atom
+// (blk kK2Items + j) blockDim + t for thread t of block blk (the block's
+// threads on consecutive atoms at each j), all loads first; the kinetic
+// energies are summed per warp (box by box) and once per block.
 constexpr int kK2Items = 4;
 
 template <bool kCond, bool kNpt = false>
@@ -1593,15 +1622,9 @@ __global__ void __launch_bounds__(kKThreads) k_kick1(Dev d, cudaGraphConditional
   const Integ I = *d.integ;
   const int par = (int)(d.g->step & 1ull);
   const int pend = d.g->pend;
-  const int nwb = (int)(blockDim.x >> 5), wib = (int)(threadIdx.x >> 5);
   if (blockIdx.x == 0 && threadIdx.x == 0) d.g->n_over = 0;
-  Kick1In k[kK1Items];
-#pragma unroll
-  for (int j = 0; j < kK1Items; ++j) k[j] = kick1_load(d, ((int)blockIdx.x * kK1Items + j) * nwb + wib);
-#pragma unroll
-  for (int j = 0; j < kK1Items; ++j)
-    if ((((int)blockIdx.x * kK1Items + j) * nwb + wib) * kKAtoms < d.N)  // warp-uniform
-      kick1_apply<kNpt>(d, I, k[j], par, pend);
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i < d.N) kick1_atom<kNpt>(d, I, i, par, pend);
   if constexpr (kCond || kNpt) {
     __shared__ bool last;
     __syncthreads();
@@ -1735,10 +1758,12 @@ __global__ void k_copyback(Dev d) {
   if (i < d.N) copyback_item(d, i);
 }
 
-__global__ void k_neigh(Dev d, float rl2) {
+constexpr int kNeighThreads = 128;
+__global__ void __launch_bounds__(kNeighThreads) k_neigh(Dev d, float rl2) {
   if (!d.g->any_rebuild || d.g->status) return;
+  __shared__ float4 stg[kNeighThreads / 32][kNStage];
   const int w = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-  if (w < d.ncell) neigh_cell_warp(d, d.q, w, rl2);
+  if (w < d.ncell) neigh_cell_warp(d, d.q, stg[threadIdx.x >> 5], w, rl2);
 }
 
 
@@ -1756,30 +1781,36 @@ __global__ void __launch_bounds__(kKThreads) k_kick2(Dev d) {
   const int nwb = (int)(blockDim.x >> 5), wib = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
   // per warp: a running FP32 sum for one box; a warp whose item changes box
   // adds its sum to the old box (FP64 atomic) and starts again; an item that
-  // itself straddles two boxes is added lane by lane (rare)
+  // itself straddles two boxes is added atom by atom (rare)
   float acc = 0.f;
   int cur = -1;
   float ke[kK2Items];
   int bj[kK2Items];
   {  // every item's loads first, then the arithmetic
-    float Fj[kK2Items];
-    float2 vj[kK2Items];
+    float4 Fj[kK2Items];
+    float2 vj[kK2Items][3];
 #pragma unroll
     for (int j = 0; j < kK2Items; ++j) {
-      const int w = ((int)blockIdx.x * kK2Items + j) * nwb + wib;
-      const int i = w * kKAtoms + lane / 3, c = lane - 3 * (lane / 3);
-      const bool act = lane < 3 * kKAtoms && i < d.N;
+      const int i = ((int)blockIdx.x * kK2Items + j) * (int)blockDim.x + (int)threadIdx.x;
+      const bool act = i < d.N;
       bj[j] = act ? (int)d.q[i].w : -1;
-      Fj[j] = act ? reinterpret_cast<const float*>(d.f + i)[c] : 0.f;
-      vj[j] = act ? (c == 0 ? d.vx : (c == 1 ? d.vy : d.vz))[i] : make_float2(0.f, 0.f);
+      Fj[j] = act ? d.f[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      vj[j][0] = act ? d.vx[i] : make_float2(0.f, 0.f);
+      vj[j][1] = act ? d.vy[i] : make_float2(0.f, 0.f);
+      vj[j][2] = act ? d.vz[i] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int j = 0; j < kK2Items; ++j) {
-      const float u = fmaf(I.cf_f, Fj[j], vj[j].x) + vj[j].y;
-      ke[j] = (float)I.ke_fac * u * u;
+      const float Fc[3] = {Fj[j].x, Fj[j].y, Fj[j].z};
+      ke[j] = 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float u = fmaf(I.cf_f, Fc[c], vj[j][c].x) + vj[j][c].y;
+        ke[j] += (float)I.ke_fac * u * u;
+      }
       if (bj[j] >= 0 && !(ke[j] < 1e30f)) {
         set_status(d.g, ST_NAN);
-        d.g->err_index = ((int)blockIdx.x * kK2Items + j) * nwb * kKAtoms + wib * kKAtoms + lane / 3;
+        d.g->err_index = ((int)blockIdx.x * kK2Items + j) * (int)blockDim.x + (int)threadIdx.x;
       }
     }
   }
@@ -2051,11 +2082,9 @@ __global__ void k_flag_all(Dev d) {
   if (b == 0) d.g->any_rebuild = 1;
 }
 
-// Blocks of the kick kernels (kKAtoms atoms per warp).
-// Blocks of the standalone kick kernels: items of kKAtoms atoms, `items`
-// of them per warp.
+// Blocks of the standalone kick kernels: `items` atoms per thread.
 __host__ __device__ inline int kick_blocks(int n, int threads, int items = 1) {
-  const int per = kKAtoms * (threads / 32) * items;
+  const int per = threads * items;
   return (n + per - 1) / per;
 }
 

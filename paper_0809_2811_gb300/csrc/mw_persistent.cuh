@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(kPersThreads) k_scan_offsets(Dev d) {
 }
 
 template <bool kCount, bool kNpt = false>
-__global__ void __launch_bounds__(kPersThreads, kPersBlocksPerSm) k_persistent(Dev d, FParams P, int nsteps, unsigned long long wait_ns) {
+__global__ void __launch_bounds__(kPersThreads, kPersBlocksPerSm) k_persistent(const __grid_constant__ Dev d, const __grid_constant__ FParams P, int nsteps,
+                                                                                        unsigned long long wait_ns) {
   __shared__ LegTable T;
   __shared__ unsigned s_gen;
   Global* g = d.g;
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(kPersThreads, kPersBlocksPerSm) k_persistent(D
     // a1 + a7 first half, a8 displacement check
     const int pend = *(volatile int*)&g->pend;  // stable: written only at the end of the kick2 phase
     if (tid == 0) g->n_over = 0;
-    for (int w = gw; w * kKAtoms < d.N; w += nwarps) kick1_lane<kNpt>(d, I, w, par, pend);
+    for (int i = tid; i < d.N; i += nth) kick1_atom<kNpt>(d, I, i, par, pend);
     phase_mark(d, s, 1);
     if constexpr (kNpt) {  // the new edges once every block has drifted with the old
       if (grid_barrier_last(g, gen, wait_ns, [&] {
@@ -243,7 +244,11 @@ __global__ void __launch_bounds__(kPersThreads, kPersBlocksPerSm) k_persistent(D
       if (grid_barrier(g, gen, wait_ns)) return;
       for (int i = tid; i < d.N; i += nth) copyback_item(d, i);
       phase_mark(d, s, 12);
-      for (int c = gw; c < d.ncell; c += nwarps) neigh_cell_warp(d, d.tq, c, P.rl2);
+      {  // the warp's candidate staging slice aliases the leg table (idle until the force phase)
+        static_assert(sizeof(LegTable) >= (kPersThreads / 32) * kNStage * sizeof(float4), "staging slices");
+        float4* stg = reinterpret_cast<float4*>(&T) + (threadIdx.x >> 5) * kNStage;
+        for (int c = gw; c < d.ncell; c += nwarps) neigh_cell_warp(d, d.tq, stg, c, P.rl2);
+      }
       phase_mark(d, s, 13);
       if (tid < d.nbox && box_flagged(d, tid)) {
         d.bst[tid].rebuilds += 1;
@@ -264,11 +269,10 @@ __global__ void __launch_bounds__(kPersThreads, kPersBlocksPerSm) k_persistent(D
       for (int k = threadIdx.x; k < d.nbox; k += blockDim.x) d.bst[k].rebuild = 0;
       if (threadIdx.x == 0) g->any_rebuild = 0;
     }
-    for (int wb = blockIdx.x * (kPersThreads / 32); wb * kKAtoms < d.N; wb += nwarps) {  // block-uniform
-      const int w = wb + (int)(threadIdx.x >> 5);
+    for (int i0 = blockIdx.x * kPersThreads; i0 < d.N; i0 += nth) {  // block-uniform
       float ke[1] = {0.f};
       int b = -1;
-      ke[0] = kick2_lane(d, I, w, b);
+      ke[0] = kick2_atom(d, I, i0 + (int)threadIdx.x, b);
       box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_acc[par]; });
     }
     phase_mark(d, s, 6);

@@ -130,7 +130,7 @@ __device__ int species_item(const Dev& d, const SpPair* sp, const float2* st, in
 // in phase C).  P.rc is the widest pair cutoff.  Block 0 consumes the
 // rebuild flags.
 template <bool kCount, int kMode>
-__global__ void __launch_bounds__(kFThreads, 4) k_force_sp(Dev d, FParams P) {
+__global__ void __launch_bounds__(kFThreads, 4) k_force_sp(const __grid_constant__ Dev d, const __grid_constant__ FParams P) {
   if (block_stop(d)) return;
   __shared__ LegTableSp T;
   __shared__ SpPair sp[kMaxSpecies * kMaxSpecies];

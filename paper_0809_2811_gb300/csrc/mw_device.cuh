@@ -774,13 +774,13 @@ constexpr int kKThreads = 256;  // threads per block of k_kick1 / k_kick2
 
 template <bool kNpt>
 __device__ __forceinline__ void kick1_atom(const Dev& d, const Integ& I, int i, int par, int pend) {
-  // every load first (nothing here is written by another atom's thread)
-  const uint4 q = d.q[i];
+  // every load first (nothing here is written by another atom's thread);
+  // the fixed-point copy is read only for its box (one box: box 0)
+  const int b = d.nbox == 1 ? 0 : (int)d.q[i].w;
   const float4 F = d.f[i];
   const uint4 qb = d.qb[i];
   const float2 v0[3] = {d.vx[i], d.vy[i], d.vz[i]};
   const unsigned long long s0[3] = {d.x[i], d.y[i], d.z[i]};
-  const int b = (int)q.w;
   const Box& bx = d.box[b];
   const float sig = d.bst[b].sig;
   const float kf = I.cf_f * (pend ? 2.0f + sig : 1.0f);
@@ -821,7 +821,7 @@ __device__ __forceinline__ void kick1_atom(const Dev& d, const Integ& I, int i, 
   d.x[i] = sn[0];
   d.y[i] = sn[1];
   d.z[i] = sn[2];
-  d.q[i] = make_uint4(qn[0], qn[1], qn[2], q.w);
+  d.q[i] = make_uint4(qn[0], qn[1], qn[2], (unsigned)b);
   if (i == bx.off) {  // this step's accumulators start from zero
     BoxState* sw = d.bst + b;
     sw->ke_acc[par] = 0.0;
@@ -845,7 +845,7 @@ __device__ __forceinline__ void kick1_atom(const Dev& d, const Integ& I, int i, 
 __device__ __forceinline__ float kick2_atom(const Dev& d, const Integ& I, int i, int& b) {
   b = -1;
   if (i >= d.N) return 0.f;
-  b = (int)d.q[i].w;
+  b = d.nbox == 1 ? 0 : (int)d.q[i].w;
   const float4 F = d.f[i];
   const float2 v[3] = {d.vx[i], d.vy[i], d.vz[i]};
   const float Fc[3] = {F.x, F.y, F.z};
@@ -1616,8 +1616,10 @@ __host__ __device__ constexpr bool force_shape_owner(int s) { return s == 4; }
 // energies are summed per warp (box by box) and once per block.
 constexpr int kK2Items = 4;
 
+// k_kick1 takes a 40-register budget (6 blocks per SM): more loads in flight
+// per SM than at its natural 58 registers (26 against 28.5 us at 2^20 atoms).
 template <bool kCond, bool kNpt = false>
-__global__ void __launch_bounds__(kKThreads) k_kick1(Dev d, cudaGraphConditionalHandle rebuild_cond) {
+__global__ void __launch_bounds__(kKThreads, 6) k_kick1(Dev d, cudaGraphConditionalHandle rebuild_cond) {
   if (block_stop(d)) return;
   const Integ I = *d.integ;
   const int par = (int)(d.g->step & 1ull);
@@ -1793,7 +1795,7 @@ __global__ void __launch_bounds__(kKThreads) k_kick2(Dev d) {
     for (int j = 0; j < kK2Items; ++j) {
       const int i = ((int)blockIdx.x * kK2Items + j) * (int)blockDim.x + (int)threadIdx.x;
       const bool act = i < d.N;
-      bj[j] = act ? (int)d.q[i].w : -1;
+      bj[j] = act ? (d.nbox == 1 ? 0 : (int)d.q[i].w) : -1;
       Fj[j] = act ? d.f[i] : make_float4(0.f, 0.f, 0.f, 0.f);
       vj[j][0] = act ? d.vx[i] : make_float2(0.f, 0.f);
       vj[j][1] = act ? d.vy[i] : make_float2(0.f, 0.f);

@@ -360,9 +360,9 @@ def plain_path_rate(torch, mw, x, v, box, integ, K, W, sp, stream, dev, pg, worl
 
 def e2e_round_trip(torch, mw, sysm, integ, x, v, steps, world, pg, dev):
     """End to end through the public API with host buffers: every step sets
-    the state from page-locked host x, v (read in place by the loading
-    kernel), advances one step and reads x, v and the thermo record back into
-    page-locked host arrays."""
+    the state from page-locked host x, v (copied to device memory by DMA and
+    loaded in the kept atom order), advances one step and reads x, v and the
+    thermo record back into page-locked host arrays."""
     n = len(x)
     xh = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
     vh = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()

@@ -81,8 +81,8 @@ def test_nve_energy_conservation_512(mwlib, orc):
     """NVE at dt = 10 fs from the jittered 512-atom start.  (a) Over the first
     1000 steps the FP32-force run fluctuates no more than the FP64 oracle's own
     run of the same steps (+ 20%).  (b) Over 1e5 steps (1 ns) the fitted drift
-    of the total energy stays below 1e-4 of |E| (Sec. II.B: energy conserved
-    better than 1/10000 over a run).  The drift is fitted over the long run:
+    of the total energy stays below 1e-4 of |E| (Sec. II.B: the energy of a
+    run is conserved to one part in 10^4).  The drift is fitted over the long run:
     within 1000 steps the O(dt^2) fluctuation of the total energy (the oracle's
     own FP64 run moves by ~1.7e-4 |E| there) decides any fitted slope, and the
     GPU trajectory, chaotic and summed in nondeterministic order, differs from

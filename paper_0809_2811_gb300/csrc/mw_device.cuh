@@ -1306,9 +1306,41 @@ __device__ void force_block(const Dev& d, const FParams& P,
       if constexpr (kSp)
         if (jr[t] >= 0) tj[t] = d.typ[jr[t]];
     }
+    if constexpr (kSp == 0) {
+      // one species: every slot's test first, then one compaction per batch
+      // (the lane's hits go to the group's running count plus the hits of the
+      // group's lower lanes in this batch, in slot order)
+      float dx[kPre], dy[kPre], dz[kPre];
+      unsigned hits = 0u;  // bit t: slot t is a leg
+      int hc = 0;
 #pragma unroll
-    for (int t = 0; t < kPre; ++t)
-      if (t0 + t < iters) test_slot(jr[t], qx[t], qy[t], qz[t], tj[t], jr[t] >= 0);
+      for (int t = 0; t < kPre; ++t) {
+        dx[t] = fix_diff(qi.x, qx[t], L0);
+        dy[t] = fix_diff(qi.y, qy[t], L1);
+        dz[t] = fix_diff(qi.z, qz[t], L2);
+        const bool hit = jr[t] >= 0 && fmaf(dx[t], dx[t], fmaf(dy[t], dy[t], dz[t] * dz[t])) < P.rc2;
+        hits |= hit ? 1u << t : 0u;
+        hc += hit ? 1 : 0;
+      }
+      int incl = hc;  // inclusive prefix of the hit counts over the group's lanes
+#pragma unroll
+      for (int o = 1; o < KG; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o, KG);
+        if (g >= o) incl += y;
+      }
+      int pos = nl + incl - hc;
+#pragma unroll
+      for (int t = 0; t < kPre; ++t)
+        if ((hits >> t) & 1u) {
+          if (pos < kLM) T.ue[at(pos)] = make_float4(dx[t], dy[t], dz[t], __int_as_float(jr[t]));
+          ++pos;
+        }
+      nl += __shfl_sync(kFull, incl, lane | (KG - 1));  // the group's hits in this batch
+    } else {
+#pragma unroll
+      for (int t = 0; t < kPre; ++t)
+        if (t0 + t < iters) test_slot(jr[t], qx[t], qy[t], qz[t], tj[t], jr[t] >= 0);
+    }
   }
   __syncwarp();
   if constexpr (kOwn == 1) {  // the staged legs for pass 2

@@ -301,11 +301,25 @@ __device__ __forceinline__ float rcp_approx(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// 1/sqrt(x) and 2^x from the hardware approximations, subnormal inputs and
+// results flushed to zero (the leg arithmetic corrects 1/sqrt to first order
+// and the exponent's argument likewise; a 2^x below 2^-126 belongs to a leg at
+// the cutoff, whose terms vanish there).
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 template <class C>
 __device__ __forceinline__ bool leg_terms(float r2, const C& c, LegTerms& o) {
   constexpr float kLn2 = 0.693147180559945f;
-  const float v = rsqrtf(r2);
+  const float v = rsqrt_approx(r2);
   const float r = r2 * v;
   const float dr = 0.5f * fmaf(-r, r, r2) * v;
   if (!(r + dr < c.rc)) return false;
@@ -316,11 +330,11 @@ __device__ __forceinline__ bool leg_terms(float r2, const C& c, LegTerms& o) {
   const float tc = fmaf(-xh, t, 1.0f) - xl * t;
   const float a2 = c.sig_l2e * t;
   const float a2l = fmaf(c.sig_l2e, t, -a2) + fmaf(a2, tc, c.sig_l2e_lo * t);
-  float e2 = exp2f(a2);
+  float e2 = ex2_approx(a2);
   e2 = fmaf(e2, kLn2 * a2l, e2);
   const float a3 = c.gsig_l2e * t;
   const float a3l = fmaf(c.gsig_l2e, t, -a3) + fmaf(a3, tc, c.gsig_l2e_lo * t);
-  const float e3 = exp2f(a3);
+  const float e3 = ex2_approx(a3);
   o.e3 = fmaf(e3, kLn2 * a3l, e3);
   const float invr = fmaf(v, ev, v);
   const float t2 = t * t;

@@ -81,3 +81,26 @@ def test_oracle_and_library_share_no_code():
             text = open(os.path.join(ROOT, "oracle", f)).read()
             refs = re.findall(r"^\s*(?:import|from|#\s*include)\s+[\"<]?([\w./]+)", text, flags=re.M)
             assert not [r for r in refs if "paper_0809_2811_gb300" in r or "mw_" in r or r == "mw.h"], (f, refs)
+
+
+def test_degenerate_systems_are_refused_before_any_device_work():
+    """Boxes of fewer than two atoms, an empty batch, non-positive or
+    non-finite edges, mass and skin are refused with MW_EINVAL by the argument
+    checks, which run before any device allocation (so this runs without a
+    GPU)."""
+    import pytest
+    build.build()
+    cases = [
+        lambda: mw.mw_system_create(0, [20.0, 20.0, 20.0]),
+        lambda: mw.mw_system_create(1, [20.0, 20.0, 20.0]),
+        lambda: mw.mw_batch_create([8, 1, 8], [20.0] * 9),
+        lambda: mw.mw_batch_create([], []),
+        lambda: mw.mw_system_create(8, [20.0, 0.0, 20.0]),
+        lambda: mw.mw_system_create(8, [20.0, float("nan"), 20.0]),
+        lambda: mw.mw_system_create(8, [20.0, 20.0, 20.0], mass=0.0),
+        lambda: mw.mw_system_create(8, [20.0, 20.0, 20.0], skin=-1.0),
+    ]
+    for make in cases:
+        with pytest.raises(mw.MWError) as ei:
+            make()
+        assert ei.value.status == mw.MW_EINVAL

@@ -885,6 +885,7 @@ __device__ __forceinline__ float kick2_atom(const Dev& d, const Integ& I, int i,
 // places in the centre's row (its running count plus the hits of lower
 // lanes), so each row lists its neighbours in stencil order.
 constexpr int kNStage = 256;  // candidates staged per warp at a time (4 KB)
+constexpr int kNeighCentres = 2;  // centres tested together against each staged batch
 __device__ __forceinline__ int stencil_n(int nc) { return nc >= 3 ? 3 : nc; }
 __device__ __forceinline__ int stencil_off(int nc, int o) { return nc >= 3 ? o - 1 : o; }
 
@@ -947,44 +948,48 @@ __device__ __forceinline__ void neigh_rows(const Dev& d, const uint4* qa, float4
         stg[(bt << 5) + lane] = e;
       }
       __syncwarp();
-      for (int k = 0; k < nb; k += 2) {  // centres k and k + 1 over the staged batch (warp-uniform)
-        const bool two = k + 1 < nb;        // (an odd last centre runs alone)
-        const int k1 = two ? k + 1 : k;
-        const float xa = __shfl_sync(kFull, cx, k), ya = __shfl_sync(kFull, cy, k), za = __shfl_sync(kFull, cz, k);
-        const float xb = __shfl_sync(kFull, cx, k1), yb = __shfl_sync(kFull, cy, k1), zb = __shfl_sync(kFull, cz, k1);
-        const int ia = a0 + ib + k, ibb = a0 + ib + k1;
-        int ca = __shfl_sync(kFull, mycount, k), cb = __shfl_sync(kFull, mycount, k1);
-        int* const ra = d.nbr + (size_t)ia * d.W;
-        int* const rb = d.nbr + (size_t)ibb * d.W;
+      for (int k = 0; k < nb; k += kNeighCentres) {  // kNeighCentres centres over the staged batch (warp-uniform)
+        float xc[kNeighCentres], yc[kNeighCentres], zc[kNeighCentres];
+        int ic[kNeighCentres], cc[kNeighCentres];
+        int* rc[kNeighCentres];
+        bool on[kNeighCentres];  // (a last group may hold fewer centres)
         const int wl = d.W - 1;
+#pragma unroll
+        for (int c = 0; c < kNeighCentres; ++c) {
+          on[c] = k + c < nb;
+          const int kc = on[c] ? k + c : k;
+          xc[c] = __shfl_sync(kFull, cx, kc);
+          yc[c] = __shfl_sync(kFull, cy, kc);
+          zc[c] = __shfl_sync(kFull, cz, kc);
+          ic[c] = a0 + ib + kc;
+          cc[c] = __shfl_sync(kFull, mycount, kc);
+          rc[c] = d.nbr + (size_t)ic[c] * d.W;
+        }
 #pragma unroll 2
         for (int bt = 0; bt < nbat; ++bt) {
           const float4 e = stg[(bt << 5) + lane];
           const int j = __float_as_int(e.w);
-          float ax, ay, az, bx2, by2, bz2;
-          if constexpr (kFrame) {
-            ax = e.x - xa; ay = e.y - ya; az = e.z - za;
-            bx2 = e.x - xb; by2 = e.y - yb; bz2 = e.z - zb;
-          } else {
-            ax = fix_diff(__float_as_uint(xa), __float_as_uint(e.x), L0);
-            ay = fix_diff(__float_as_uint(ya), __float_as_uint(e.y), L1);
-            az = fix_diff(__float_as_uint(za), __float_as_uint(e.z), L2);
-            bx2 = fix_diff(__float_as_uint(xb), __float_as_uint(e.x), L0);
-            by2 = fix_diff(__float_as_uint(yb), __float_as_uint(e.y), L1);
-            bz2 = fix_diff(__float_as_uint(zb), __float_as_uint(e.z), L2);
-          }
           // (kFrame: padding entries fail the distance test by their offset)
           const bool live = kFrame || j >= 0;
-          const bool pa = live && j != ia && fmaf(ax, ax, fmaf(ay, ay, az * az)) < rl2;
-          const bool pb = two && live && j != ibb && fmaf(bx2, bx2, fmaf(by2, by2, bz2 * bz2)) < rl2;
-          const unsigned ba = __ballot_sync(kFull, pa), bb = __ballot_sync(kFull, pb);
-          st_if(pa, ra + min(ca + __popc(ba & below), wl), j);
-          st_if(pb, rb + min(cb + __popc(bb & below), wl), j);
-          ca += __popc(ba);
-          cb += __popc(bb);
+#pragma unroll
+          for (int c = 0; c < kNeighCentres; ++c) {
+            float dx, dy, dz;
+            if constexpr (kFrame) {
+              dx = e.x - xc[c]; dy = e.y - yc[c]; dz = e.z - zc[c];
+            } else {
+              dx = fix_diff(__float_as_uint(xc[c]), __float_as_uint(e.x), L0);
+              dy = fix_diff(__float_as_uint(yc[c]), __float_as_uint(e.y), L1);
+              dz = fix_diff(__float_as_uint(zc[c]), __float_as_uint(e.z), L2);
+            }
+            const bool p = (c == 0 || on[c]) && live && j != ic[c] && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rl2;
+            const unsigned bm = __ballot_sync(kFull, p);
+            st_if(p, rc[c] + min(cc[c] + __popc(bm & below), wl), j);
+            cc[c] += __popc(bm);
+          }
         }
-        if (lane == k) mycount = ca;
-        if (two && lane == k1) mycount = cb;
+#pragma unroll
+        for (int c = 0; c < kNeighCentres; ++c)
+          if (on[c] && lane == k + c) mycount = cc[c];
       }
     }
     if (lane < nb) d.nbr_cnt[me] = mycount;

@@ -213,10 +213,11 @@ def barrier(pg, device):
             pg.barrier()
 
 
-def traffic_from_profile(kernel_src, n_atoms):
+def traffic_from_profile(kernel_src, n_atoms, r_list=None, width=None):
     """DRAM bytes per force launch from the committed ncu summary of this
-    workload size, if it was taken on the current kernel source (hash match),
-    else None."""
+    workload size (and list radius and row width, where both the record and
+    the caller give them: the rows' length and stride set the traffic), if it
+    was taken on the current kernel source (hash match), else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "sw_force_traffic.json")
     if not os.path.exists(path):
@@ -225,8 +226,13 @@ def traffic_from_profile(kernel_src, n_atoms):
         recs = json.load(open(path))
         h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
         for rec in (recs if isinstance(recs, list) else [recs]):
-            if rec.get("source_hash") == h and int(rec.get("atoms", -1)) == int(n_atoms):
-                return rec.get("dram_bytes_per_launch")
+            if rec.get("source_hash") != h or int(rec.get("atoms", -1)) != int(n_atoms):
+                continue
+            if r_list is not None and rec.get("r_list_A") is not None and abs(float(rec["r_list_A"]) - r_list) > 1e-3:
+                continue
+            if width is not None and rec.get("nbr_width") is not None and int(rec["nbr_width"]) != int(width):
+                continue
+            return rec.get("dram_bytes_per_launch")
         return None
     except Exception:
         return None
@@ -321,7 +327,7 @@ def force_roofline(mw, sysm, integ, nsteps=20):
     achieved = flops / (kms / 1e3) / 1e12
     peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     traffic = traffic_from_profile(os.path.join(ROOT, "paper_0809_2811_gb300", "csrc", "mw_device.cuh"),
-                                   sysm.n_total)
+                                   sysm.n_total, float(sysm.info()["r_list"]), int(sysm.info()["nbr_width"]))
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "k_force (fused 2+3-body)", "kernel_ms": kms,
             "legs": 2 * P, "triplets": T, "flops_per_launch": flops,

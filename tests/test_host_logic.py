@@ -58,5 +58,10 @@ def test_traffic_is_reported_only_for_the_profiled_source(tmp_path, monkeypatch)
     assert bench.traffic_from_profile(str(src), 1000) == 123
     assert bench.traffic_from_profile(str(src), 2000) == 456
     assert bench.traffic_from_profile(str(src), 3000) is None  # no capture of this size
+    (prof / "sw_force_traffic.json").write_text(json.dumps(
+        [{"source_hash": h, "atoms": 1000, "r_list_A": 6.1065, "dram_bytes_per_launch": 123},
+         {"source_hash": h, "atoms": 1000, "r_list_A": 6.3065, "dram_bytes_per_launch": 789}]))
+    assert bench.traffic_from_profile(str(src), 1000, 6.3065) == 789  # the record of this list radius
+    assert bench.traffic_from_profile(str(src), 1000, 5.3065) is None
     src.write_text("// kernel v2\n")
     assert bench.traffic_from_profile(str(src), 1000) is None

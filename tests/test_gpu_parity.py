@@ -75,6 +75,27 @@ def test_overflow_legs_path(mwlib, orc):
     s.close()
 
 
+def test_dense_cells_many_centres_and_stencil_chunks(mwlib, orc):
+    """4096 atoms at 2.6 g/cm^3 with a 3 A skin: 4 cells per edge of ~64
+    atoms each, so every cell's warp runs two groups of 32 centres, stages its
+    ~1700-candidate stencil in 7 chunks, and every centre has ~26-30 legs (the
+    staged-leg limit of 24 sends some to the overflow kernel).  Neighbour sets
+    and forces against the oracle as in every other case."""
+    x, box = I.jittered_box(4096, 2.6, 0.1, 105)
+    x = I.snap_to_grid(np.asarray(x, float), box)
+    ref = orc.energy_forces(x, box)
+    s = mwlib.System(len(x), box, skin=3.0)
+    try:
+        s.set_state(x)
+        f, e, w = s.energy_forces()
+        info = s.info()
+        assert info["max_count"] > 32 * 27 // 8  # the rows are long: well past one staging chunk per cell
+        compare("dense_cells_4096_rho2.6_skin3", f, e[0], w[0], ref)
+        check_neighbors(s, orc, x, box)
+    finally:
+        s.close()
+
+
 def test_tiny_systems(mwlib, orc):
     # two atoms inside the cutoff: pair term only
     box = np.array([12.0, 12.0, 12.0])

@@ -166,12 +166,17 @@ mw_status mw_system_destroy(mw_system* s);
 
 /* Sets positions x (n_total*3, required, any finite values: they are
  * wrapped into the box) and velocities v (n_total*3, or NULL for zero), host
- * arrays.  Resets the step counter, the thermostat (xi = eta = 0) and marks
- * the neighbour list stale.  A non-finite value (checked on the device, for
- * host and device inputs alike) gives MW_EINVAL and leaves the system
- * without a state.  Page-locked host arrays (cudaMallocHost, cudaHostAlloc,
- * cudaHostRegister) are read in place by the loading kernel; pageable ones
- * are first copied to a device staging buffer.  Either way the arrays are
+ * arrays.  Resets the step counter and the thermostat (xi = eta = 0).  A
+ * non-finite value (checked on the device, for host and device inputs alike)
+ * gives MW_EINVAL and leaves the system without a state.
+ * When the system already holds a state whose forces were evaluated, its
+ * atom order and neighbour lists are kept: the arrays are copied to device
+ * staging buffers by DMA and loaded through the kept order, and only boxes
+ * with an atom more than skin/2 from its list position are marked for a
+ * rebuild (not under MW_NPT).  Otherwise the atoms take the caller's order
+ * and every list is marked stale; page-locked host arrays (cudaMallocHost,
+ * cudaHostAlloc, cudaHostRegister) are then read in place by the loading
+ * kernel, pageable ones copied to staging first.  Either way the arrays are
  * read completely before the call returns, and the caller keeps them. */
 mw_status mw_set_state(mw_system* s, const double* x, const double* v);
 /* Same with device arrays. */

@@ -173,7 +173,10 @@ mw_status mw_system_destroy(mw_system* s);
  * atom order and neighbour lists are kept: the arrays are copied to device
  * staging buffers by DMA and loaded through the kept order, and only boxes
  * with an atom more than skin/2 from its list position are marked for a
- * rebuild (not under MW_NPT).  Otherwise the atoms take the caller's order
+ * rebuild (not under MW_NPT).  With host velocities this path also makes the
+ * force call at the new positions that the next step or energy call would
+ * make, while the velocities are copied in (so it can return the errors of a
+ * force call, MW_ENLIST_OVERFLOW and the like).  Otherwise the atoms take the caller's order
  * and every list is marked stale; page-locked host arrays (cudaMallocHost,
  * cudaHostAlloc, cudaHostRegister) are then read in place by the loading
  * kernel, pageable ones copied to staging first.  Either way the arrays are

@@ -64,6 +64,12 @@ struct mw_system {
   double mass = 18.015, skin = 1.0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // second stream for capturing conditional bodies
+  // mw_set_state's velocity copy runs on copy_stream beside the force call at
+  // the new positions; copy_ev[1] marks it done, and v_pending says that the
+  // velocities in stage2 are still to be loaded (before the thermo snapshot)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev[2] = {nullptr, nullptr};
+  bool v_pending = false;
   bool own_stream = false;
   bool list_built = false;
   // the atom order and neighbour lists are current for the geometry and
@@ -592,6 +598,11 @@ mw_status ensure_forces(mw_system* s) {
     MW_CUDA(cudaGetLastError());
     launch_rebuild(s);
     launch_force(s);
+    if (s->v_pending) {  // velocities of a state just set (their copy ran beside this force call)
+      MW_CUDA(cudaStreamWaitEvent(s->stream, s->copy_ev[1], 0));
+      k_load_velocities_keep<<<div_up(s->N, kThreads), kThreads, 0, s->stream>>>(s->d, s->d.stage2);
+      s->v_pending = false;
+    }
     k_thermo_snapshot<<<div_up(s->nbox, kThreads), kThreads, 0, s->stream>>>(s->d);
     MW_CUDA(cudaGetLastError());
     Global g;
@@ -766,6 +777,63 @@ const double* mapped_host(const double* p) {
   return static_cast<const double*>(a.devicePointer);
 }
 
+// The copy stream and its events (created on first use).
+mw_status copy_lane(mw_system* s) {
+  if (!s->copy_stream) MW_CUDA(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
+  for (auto& e : s->copy_ev)
+    if (!e) MW_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return MW_OK;
+}
+
+mw_status ensure_forces(mw_system* s);
+
+// mw_set_state in the kept order with host velocities: the positions are
+// copied and loaded, and the force call at them (which the next step or
+// energy call would make) runs while the velocities are copied in on the
+// copy stream; the velocities are then loaded before the thermo snapshot.
+// A non-finite input refuses the state as in the other paths.
+mw_status set_state_keep_overlapped(mw_system* s, const double* x, const double* v, size_t bytes) {
+  mw_status st;
+  if ((st = copy_lane(s)) != MW_OK) return st;
+  // the positions first, alone on the link; the velocities after them (one
+  // copy fills the link in each direction, two would share it)
+  MW_CUDA(cudaMemcpyAsync(s->d.stage, x, bytes, cudaMemcpyHostToDevice, s->stream));
+  MW_CUDA(cudaEventRecord(s->copy_ev[0], s->stream));  // (earlier work on the staging buffers is done too)
+  MW_CUDA(cudaStreamWaitEvent(s->copy_stream, s->copy_ev[0], 0));
+  MW_CUDA(cudaMemcpyAsync(s->d.stage2, v, bytes, cudaMemcpyHostToDevice, s->copy_stream));
+  MW_CUDA(cudaEventRecord(s->copy_ev[1], s->copy_stream));
+  MW_CUDA(cudaMemsetAsync(s->d.bst, 0, sizeof(BoxState) * s->nbox, s->stream));
+  const size_t mc = offsetof(Global, max_count);
+  MW_CUDA(cudaMemsetAsync(s->d.g, 0, mc, s->stream));
+  MW_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(s->d.g) + mc + sizeof(int), 0, sizeof(Global) - mc - sizeof(int),
+                          s->stream));
+  const int gl = div_up(std::max(std::max(s->N, s->ncell), s->nbox), kThreads);
+  k_load_positions_keep<<<gl, kThreads, 0, s->stream>>>(s->d, s->d.stage, s->count_terms,
+                                                         (float)(0.25 * s->skin * s->skin));
+  MW_CUDA(cudaGetLastError());
+  s->v_pending = true;
+  s->state_set = true;
+  s->forces_valid = false;
+  s->need_prime = true;  // thermostat at rest: xi = eta = 0, KE of the new velocities
+  s->host_step = 0;
+  st = ensure_forces(s);
+  if (s->v_pending) {  // (the force call stopped before loading them)
+    cudaStreamSynchronize(s->copy_stream);
+    s->v_pending = false;
+    if (st == MW_OK) st = fail(MW_ECUDA, "velocities not loaded");
+  }
+  if (st != MW_OK) {
+    Global gh;
+    const bool input = read_global(s, &gh) == MW_OK && gh.status == ST_INPUT;
+    s->state_set = false;  // the arrays hold part of a refused state
+    s->order_ok = false;
+    s->forces_valid = false;
+    if (input) return fail(MW_EINVAL, "non-finite position or velocity of atom %d", gh.err_index);
+    return st;
+  }
+  return MW_OK;
+}
+
 mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev) {
   if (!s) return fail(MW_EINVAL, "system is NULL");
   if (!x) return fail(MW_EINVAL, "positions are NULL");
@@ -773,6 +841,7 @@ mw_status do_set_state(mw_system* s, const double* x, const double* v, bool dev)
   const double* xd = x;
   const double* vd = v;
   const bool keep = s->state_set && s->order_ok && s->integ.kind != TH_NPT;
+  if (!dev && keep && v) return set_state_keep_overlapped(s, x, v, bytes);
   if (!dev && keep) {
     // the current order is kept, so the loading kernel reads the inputs
     // through the atom permutation: one copy of each array to device memory
@@ -1120,6 +1189,9 @@ mw_status mw_system_destroy(mw_system* s) {
   for (void* p : s->allocs) cudaFree(p);
   if (s->own_stream) cudaStreamDestroy(s->stream);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+  for (auto e : s->copy_ev)
+    if (e) cudaEventDestroy(e);
   if (s->hpin) cudaFreeHost(s->hpin);
   delete s;
   return MW_OK;

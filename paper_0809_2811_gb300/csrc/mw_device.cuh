@@ -2051,6 +2051,64 @@ __global__ void k_load_state(Dev d, const double* __restrict__ xin, const double
 // the list was built at, as between steps; any other box is flagged for a
 // rebuild.  The host zeroes the box states and the status block (all but
 // the widest-row record) before the launch.
+// Per-atom parts of k_load_state_keep: slot i's position (fractions, image
+// counts, fixed-point copy, species, zero force, the rebuild flag of its
+// box) and its velocity (FP32 pair; returns its kinetic energy).
+__device__ __forceinline__ void load_keep_position(const Dev& d, const double* __restrict__ xin, int i, float hs2) {
+  const int u = d.id[i];
+  const int b = (int)d.q[i].w;
+  const Box& bx = d.box[b];
+  unsigned long long p[3];
+  int im[3];
+  for (int k = 0; k < 3; ++k) {
+    double x = xin[3 * (size_t)u + k];
+    if (!isfinite(x)) {
+      set_status(d.g, ST_INPUT);
+      d.g->err_index = u;
+      x = 0.0;
+    }
+    double f = x / bx.L[k];
+    const double fl = floor(f);
+    im[k] = (int)fl;
+    f -= fl;
+    if (f >= 1.0) f -= 1.0;
+    if (f < 0.0) f = 0.0;
+    p[k] = frac64_of(f);
+  }
+  d.x[i] = p[0];
+  d.y[i] = p[1];
+  d.z[i] = p[2];
+  if (d.img) d.img[i] = make_int4(im[0], im[1], im[2], 0);
+  const uint4 q = make_uint4(q_of(p[0]), q_of(p[1]), q_of(p[2]), (unsigned)b);
+  d.q[i] = q;
+  if (d.typ) d.typ[i] = d.utyp[u];
+  d.f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const uint4 qb = d.qb[i];
+  const float dx = fix_diff(qb.x, q.x, bx.Lq[0]), dy = fix_diff(qb.y, q.y, bx.Lq[1]), dz = fix_diff(qb.z, q.z, bx.Lq[2]);
+  if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > hs2) {
+    d.bst[b].rebuild = 1;
+    d.g->any_rebuild = 1;
+  }
+}
+
+__device__ __forceinline__ float load_keep_velocity(const Dev& d, const Integ& I, const double* __restrict__ vin,
+                                                    int i) {
+  const int u = d.id[i];
+  float vh[3];
+  for (int k = 0; k < 3; ++k) {
+    double w = vin ? vin[3 * (size_t)u + k] : 0.0;
+    if (!isfinite(w)) {
+      set_status(d.g, ST_INPUT);
+      d.g->err_index = u;
+      w = 0.0;
+    }
+    const float2 sw = split_df(w);
+    (k == 0 ? d.vx : (k == 1 ? d.vy : d.vz))[i] = sw;
+    vh[k] = sw.x + sw.y;
+  }
+  return (float)I.ke_fac * fmaf(vh[0], vh[0], fmaf(vh[1], vh[1], vh[2] * vh[2]));
+}
+
 __global__ void k_load_state_keep(Dev d, const double* __restrict__ xin, const double* __restrict__ vin,
                                   int count_terms, float hs2) {
   const Integ I = *d.integ;
@@ -2064,52 +2122,37 @@ __global__ void k_load_state_keep(Dev d, const double* __restrict__ xin, const d
   float ke[1] = {0.f};
   int b = -1;
   if (i < d.N) {
-    const int u = d.id[i];
     b = (int)d.q[i].w;
-    const Box& bx = d.box[b];
-    unsigned long long p[3];
-    int im[3];
-    float vh[3];
-    for (int k = 0; k < 3; ++k) {
-      double x = xin[3 * (size_t)u + k];
-      if (!isfinite(x)) {
-        set_status(d.g, ST_INPUT);
-        d.g->err_index = u;
-        x = 0.0;
-      }
-      double f = x / bx.L[k];
-      const double fl = floor(f);
-      im[k] = (int)fl;
-      f -= fl;
-      if (f >= 1.0) f -= 1.0;
-      if (f < 0.0) f = 0.0;
-      p[k] = frac64_of(f);
-      double w = vin ? vin[3 * (size_t)u + k] : 0.0;
-      if (!isfinite(w)) {
-        set_status(d.g, ST_INPUT);
-        d.g->err_index = u;
-        w = 0.0;
-      }
-      const float2 sw = split_df(w);
-      (k == 0 ? d.vx : (k == 1 ? d.vy : d.vz))[i] = sw;
-      vh[k] = sw.x + sw.y;
-    }
-    d.x[i] = p[0];
-    d.y[i] = p[1];
-    d.z[i] = p[2];
-    if (d.img) d.img[i] = make_int4(im[0], im[1], im[2], 0);
-    const uint4 q = make_uint4(q_of(p[0]), q_of(p[1]), q_of(p[2]), (unsigned)b);
-    d.q[i] = q;
-    if (d.typ) d.typ[i] = d.utyp[u];
-    d.f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    ke[0] = (float)I.ke_fac * fmaf(vh[0], vh[0], fmaf(vh[1], vh[1], vh[2] * vh[2]));
-    const uint4 qb = d.qb[i];
-    const float dx = fix_diff(qb.x, q.x, bx.Lq[0]), dy = fix_diff(qb.y, q.y, bx.Lq[1]),
-                dz = fix_diff(qb.z, q.z, bx.Lq[2]);
-    if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > hs2) {
-      d.bst[b].rebuild = 1;
-      d.g->any_rebuild = 1;
-    }
+    load_keep_position(d, xin, i, hs2);
+    ke[0] = load_keep_velocity(d, I, vin, i);
+  }
+  box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_last; });
+}
+
+// The same in two launches, positions first (k_load_positions_keep: no
+// velocity or kinetic energy is touched) and velocities later
+// (k_load_velocities_keep: the kinetic energy into ke_last, which the host
+// zeroed with the box states), so that a force call at the new positions can
+// run between them while the velocities are still being copied in.
+__global__ void k_load_positions_keep(Dev d, const double* __restrict__ xin, int count_terms, float hs2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d.ncell) d.cell_cnt[i] = 0;
+  if (i < d.nbox) {
+    d.bst[i].s_endc = 1.0;
+    d.bst[i].Lb = d.box[i].L[0];
+  }
+  if (i == 0) d.g->count_terms = count_terms;
+  if (i < d.N) load_keep_position(d, xin, i, hs2);
+}
+
+__global__ void k_load_velocities_keep(Dev d, const double* __restrict__ vin) {
+  const Integ I = *d.integ;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float ke[1] = {0.f};
+  int b = -1;
+  if (i < d.N) {
+    b = (int)d.q[i].w;
+    ke[0] = load_keep_velocity(d, I, vin, i);
   }
   box_accumulate<1>(ke, b, [&](int bb) { return &d.bst[bb].ke_last; });
 }

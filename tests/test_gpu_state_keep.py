@@ -77,3 +77,32 @@ def test_set_state_after_steps_rebuilds_moved_boxes(mwlib, orc):
         assert all(t["step"] == 20 for t in th)
     finally:
         s.close()
+
+
+def test_set_state_kept_order_refuses_non_finite_velocity(mwlib, orc):
+    """In the kept-order path the velocities are loaded after the force call
+    at the new positions; a non-finite velocity is still refused by
+    mw_set_state itself (MW_EINVAL, no state left), and a valid state set
+    afterwards gives the oracle's forces."""
+    x, box = I.jittered_box(1000, 1.0, 0.3, 421)
+    x = I.snap_to_grid(x, box)
+    v = I.maxwell_velocities(len(x), 300.0, seed=422)
+    s = mwlib.System(len(x), box)
+    try:
+        s.set_state(x, v)
+        s.energy_forces()  # the order and lists are now current: the next state keeps them
+        vb = v.copy()
+        vb[123, 1] = np.nan
+        with pytest.raises(mwlib.MWError) as ei:
+            s.set_state(x, vb)
+        assert ei.value.status == mwlib.MW_EINVAL
+        with pytest.raises(mwlib.MWError) as ei:
+            s.energy_forces()
+        assert ei.value.status == mwlib.MW_ESTATE
+        s.set_state(x, v)
+        f, e, w = s.energy_forces()
+        compare("keep: after a refused velocity", f, e[0], w[0], orc.energy_forces(x, box))
+        xs, vs = s.get_state()
+        assert np.array_equal(xs, x) and np.allclose(vs, v, rtol=2.0 ** -47, atol=0)
+    finally:
+        s.close()

@@ -347,7 +347,9 @@ mw_status mw_energy_forces_vjp(mw_system* s, const float* dL_dF_dev, float* dL_d
 mw_status mw_set_engine(mw_system* s, int engine);
 
 /* Sets the neighbour-list width (slots per atom, >= 1) and marks the list
- * stale; a width too small is grown again on the next build. */
+ * stale; a width too small is grown again on the next build.  The library's
+ * own widths (at creation, on growth, after autotuning) are multiples of 32
+ * slots, whole 128-byte lines per row. */
 mw_status mw_set_nbr_width(mw_system* s, int width);
 
 /* Sets the Verlet-list skin (A, >= 0): the list radius is a sigma + skin and

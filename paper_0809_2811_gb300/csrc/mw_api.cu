@@ -1107,11 +1107,11 @@ mw_status create_common(mw_system** out, int nbox, const int* n, const double* b
   d.chunk_cap = 4096;
   if (cudaMemsetAsync(d.nbr_cnt, 0, sizeof(int) * N, s->stream) != cudaSuccess)
     return bad(fail(MW_ECUDA, "memset failed"));
-  Box* dbox;
-  BoxState* dbst;
-  double* dth;
-  Global* dg;
-  Integ* dint;
+  Box* dbox = nullptr;
+  BoxState* dbst = nullptr;
+  double* dth = nullptr;
+  Global* dg = nullptr;
+  Integ* dint = nullptr;
   if ((st = dalloc(s, &dbox, nbox)) != MW_OK || (st = dalloc(s, &dbst, nbox)) != MW_OK ||
       (st = dalloc(s, &dth, (size_t)nbox * TR_N)) != MW_OK || (st = dalloc(s, &dg, 1)) != MW_OK ||
       (st = dalloc(s, &dint, 1)) != MW_OK)

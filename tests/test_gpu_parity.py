@@ -280,6 +280,12 @@ def test_autotuner_picks_and_reports_a_force_shape(mwlib):
         info = s.info()
         assert (info["force_lanes"], info["force_blocks_per_sm"], info["force_owner"]) in {
             (4, 8, 0), (2, 8, 0), (8, 8, 0), (4, 7, 0), (4, 8, 1)}
+        # rows fitted to the chosen skin, whole 128-byte lines, and the list built in them
+        s.energy_forces()
+        info = s.info()
+        assert info["nbr_width"] % 32 == 0 and info["max_count"] <= info["nbr_width"]
+        rl, n_per_a3 = info["r_list"], len(x) / float(np.prod(box))
+        assert info["nbr_width"] <= ((int(np.ceil(1.5 * n_per_a3 * 4.18879020478639 * rl ** 3 + 16)) + 31) // 32) * 32
         with pytest.raises(mwlib.MWError):
             mwlib.mw_set_force_shape(s.h, 3, 8)
         with pytest.raises(mwlib.MWError):

@@ -879,11 +879,11 @@ __device__ __forceinline__ float kick2_atom(const Dev& d, const Integ& I, int i,
 // ---------------------------------------------------------------------------
 // Neighbour list (a3): one warp per cell.  The candidates of the
 // (deduplicated) 27-cell stencil are flattened in stencil order and staged,
-// up to kNStage at a time, in the warp's slice of shared memory; then every
-// centre atom of the cell in turn runs over the staged candidates 32 at a
-// time (one per lane), and the hits of each batch go straight to their
-// places in the centre's row (its running count plus the hits of lower
-// lanes), so each row lists its neighbours in stencil order.
+// up to kNStage at a time, in the warp's slice of shared memory; then the
+// centre atoms of the cell, kNeighCentres at a time, run over the staged
+// candidates 32 at a time (one per lane), and the hits of each batch go
+// straight to their places in each centre's row (its running count plus the
+// hits of lower lanes), so each row lists its neighbours in stencil order.
 constexpr int kNStage = 256;  // candidates staged per warp at a time (4 KB)
 constexpr int kNeighCentres = 2;  // centres tested together against each staged batch
 __device__ __forceinline__ int stencil_n(int nc) { return nc >= 3 ? 3 : nc; }
@@ -893,8 +893,9 @@ __device__ __forceinline__ int stencil_off(int nc, int o) { return nc >= 3 ? o -
 // batch takes candidate t of the stencil's concatenated cells (located by a
 // binary search over the warp's inclusive counts) and stores (x, y, z, j);
 // entries past the last candidate get j = -1 (and, with kFrame, an offset
-// no distance test passes).  The centres go over a batch two at a time, so
-// that each staged record is read once for both.  A count past the row
+// no distance test passes).  The centres go over a batch kNeighCentres at a
+// time, so that each staged record is read once for all of them (2 measured
+// fastest against 1, 3 and 4).  A count past the row
 // width (an overflow: the status makes the caller grow the rows and build
 // again) writes to the row's last slot, never past it.
 // kFrame: every axis of the box has at least 4 cells, so each candidate lies
